@@ -1,0 +1,335 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle function through a route that does not reuse its
+code: explicit matrices of Sec. 2-3, brute-force definitions, identities the
+theorems state, and the success rates the paper prints (tests/golden/).
+A plausible slip in the oracle (a dropped wrap term, convolution instead of
+correlation, a wrong index or modulus, a transposed operand) fails at least
+one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle.ftm as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_table(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            a, b = line.split()
+            rows.append((float(a), float(b)))
+    return rows
+
+
+def _pm1(seed, n):
+    return W.pm1_signal(W.rng_for(seed), n).astype(np.int64)
+
+
+# ---------------------------------------------------------------- decoding
+
+def test_decode_bits_lsb_first():
+    # byte 0b00000101: bits LSB first = 1,0,1,0,0,0,0,0
+    xs = np.array([0b00000101, 0b10000000], dtype=np.uint8)
+    got = O.decode(xs, "bits", 10)
+    assert got.tolist() == [1, -1, 1, -1, -1, -1, -1, -1, -1, -1]
+
+
+def test_decode_i8_and_pack_roundtrip():
+    x = W.pm1_signal(W.rng_for(3), 1000)
+    assert O.decode(x, "i8", 1000).tolist() == x.astype(np.int64).tolist()
+    assert O.decode(W.pack_bits(x), "bits", 1000).tolist() == x.astype(np.int64).tolist()
+
+
+# ---------------------------------------------------------------- step 2
+
+def test_plan_paper_and_auto():
+    assert O.plan(65536, 1024, "paper") == (1024, 1025)
+    # s(s+1) > N: 256*257 = 65792 > 65536 >= 255*256
+    assert O.least_s(65536) == 256
+    # 4096*4097 = 16781312 > 2^24 = 16777216 >= 4095*4096 = 16773120
+    assert O.least_s(1 << 24) == 4096
+    assert O.plan(1 << 24, 300, "auto") == (4096, 4097)
+    assert O.plan(1 << 24, 5000, "auto") == (5000, 5001)
+    for N in (1, 2, 3, 6, 7, 100, 12345, 999999):
+        s = O.least_s(N)
+        assert s * (s + 1) > N and (s - 1) * s <= N
+
+
+def test_plan_rejects():
+    with pytest.raises(ValueError):
+        O.plan(1 << 22, 256, "paper")          # 256*257 <= 2^22
+    assert O.plan(1 << 22, 256, "paper", allow_ambig=True) == (256, 257)
+    with pytest.raises(ValueError):
+        O.plan(100, 10, "explicit", 12, 14)    # not co-prime
+    with pytest.raises(ValueError):
+        O.plan(100, 10, "explicit", 9, 16)     # M1 < K
+    with pytest.raises(ValueError):
+        O.plan(10, 11, "paper")                # K > N
+
+
+# ---------------------------------------------------------------- step 3
+
+@pytest.mark.parametrize("N,M,K", [(30, 7, 3), (48, 8, 5), (31, 10, 10), (64, 11, 4), (97, 13, 7)])
+def test_fold_equals_phi_times_x(N, M, K):
+    """y = Phi x with Phi = D_{M+K}(circ(r)), r_k = 1 iff k mod M = 0 (Eq. 3)."""
+    x = _pm1(N * 31 + M, N)
+    Phi = O.phi_matrix(N, M, M + K - 1)
+    assert np.array_equal(O.fold(x, M, K), Phi @ x)
+    xr = W.gaussian_signal(W.rng_for(N + M), N).astype(np.float64)
+    np.testing.assert_allclose(O.fold(xr, M, K), Phi @ xr, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,M,K", [(10, 11, 10), (12, 17, 9), (5, 5, 5), (9, 4, 1)])
+def test_fold_bruteforce_any_size(N, M, K):
+    """Eq. (2) term by term with the (x)_i = (x)_{i mod N} convention, also
+    when M > N (a single, wrapping row)."""
+    x = _pm1(N + 1000 * M, N)
+    L = -(-N // M)
+    want = [sum(int(x[(k + i * M) % N]) for i in range(L)) for k in range(M + K - 1)]
+    assert O.fold(x, M, K).tolist() == want
+
+
+# ---------------------------------------------------------------- steps 4-6
+
+@pytest.mark.parametrize("N,M,K", [(60, 7, 5), (97, 11, 7), (128, 16, 16), (50, 13, 2), (33, 40, 30)])
+def test_eq4_fold_correlation_identity(N, M, K):
+    """r_j = sum_{l < ceil(N/M)} (Tx)_{(j + l M) mod N} for j < M (Eq. (4),
+    Thm. 1 with D_{M+K}); (Tx) comes from the brute-force full search."""
+    x = _pm1(7 * N + M, N)
+    t = _pm1(11 * K + N, K)
+    tx = O.full_search_values(x, t)
+    L = -(-N // M)
+    want = [sum(int(tx[(j + l * M) % N]) for l in range(L)) for j in range(M)]
+    r = O.correlate(O.fold(x, M, K), t, M)
+    assert r.tolist() == want
+    # real-valued signal and template
+    xr = W.gaussian_signal(W.rng_for(N), N).astype(np.float64)
+    tr = W.gaussian_signal(W.rng_for(K + 5), K).astype(np.float64)
+    txr = O.full_search_values(xr, tr)
+    wantr = [sum(txr[(j + l * M) % N] for l in range(L)) for j in range(M)]
+    np.testing.assert_allclose(O.correlate(O.fold(xr, M, K), tr, M), wantr, rtol=1e-12, atol=1e-10)
+
+
+@pytest.mark.parametrize("N,M,K", [(40, 9, 4), (64, 16, 8), (90, 12, 12)])
+def test_thm1_exchange_with_explicit_matrices(N, M, K):
+    """Thm. 1: with That = circ([t 0]) (M x M) and Phi = D_M(circ(r)),
+    (That Phi x)_i = (Phi T x)_i for i in [0, M-K]; generically not beyond.
+    With D_{M+K} (Sec. 3.2 strategy 1) the match covers every i < M, and it
+    equals the oracle's fold + correlation."""
+    x = _pm1(N * 3 + K, N)
+    t = _pm1(K * 5 + N, K)
+    T = O.T_matrix(t, N)
+    PhiM = O.phi_matrix(N, M, M)
+    That = O.circ(np.concatenate([t, np.zeros(M - K, dtype=np.int64)]))
+    lhs = That @ (PhiM @ x)
+    rhs = PhiM @ (T @ x)
+    assert np.array_equal(lhs[: M - K + 1], rhs[: M - K + 1])
+    if N % M == 0:
+        # M | N: Phi = [Phi_M ... Phi_M] with Phi_M = I, the Thm. 2 setting,
+        # where the exchange holds on every row.
+        assert np.array_equal(lhs, rhs)
+    elif K > 1:
+        assert not np.array_equal(lhs[M - K + 1:], rhs[M - K + 1:])
+    PhiMK = O.phi_matrix(N, M, M + K)
+    ThatK = O.circ(np.concatenate([t, np.zeros(M, dtype=np.int64)]))
+    lhsK = ThatK @ (PhiMK @ x)
+    rhsK = PhiMK @ (T @ x)
+    assert np.array_equal(lhsK[:M], rhsK[:M])
+    assert O.correlate(O.fold(x, M, K), t, M).tolist() == rhsK[:M].tolist()
+
+
+@pytest.mark.parametrize("M,K", [(7, 3), (64, 17), (1025, 1024), (300, 299)])
+def test_fft_correlation_equals_direct_sum(M, K):
+    """Steps 4-6 (FFT route, with the conjugate) equal the direct sum."""
+    y = _pm1(M * K, M + K - 1) * 3
+    t = _pm1(M + K, K)
+    r_direct = O.correlate(y, t, M)
+    r_fft = O.correlate_fft(y, t, M)
+    assert np.max(np.abs(r_fft - r_direct)) < 1e-6
+    # a pure-Python loop on the smallest case
+    if M * K < 5000:
+        want = [sum(int(t[i]) * int(y[j + i]) for i in range(K)) for j in range(M)]
+        assert r_direct.tolist() == want
+
+
+def test_convolution_reading_fails_on_planted_window():
+    """Reading R3: Algorithm 1 step 6 printed without a conjugate would
+    convolve; with a planted window only the correlating route peaks at the
+    planted position."""
+    N, K = 4096, 256
+    x = _pm1(77, N)
+    k = 1234
+    t = x[(np.arange(K) + k) % N]
+    M = K
+    y = O.fold(x, M, K)
+    r = O.correlate(y, t, M)
+    assert O.argmax_first(r) == k % M
+    P = 1 << (M + K - 2).bit_length()
+    conv = np.fft.ifft(np.fft.fft(t, P) * np.fft.fft(np.pad(y, (0, P - y.size)))).real[:M]
+    assert int(np.argmax(conv)) != k % M
+
+
+# ---------------------------------------------------------------- step 7
+
+def test_argmax_first_ties():
+    assert O.argmax_first(np.array([1, 5, 5, 2])) == 1
+    assert O.argmax_first(np.array([7])) == 0
+    assert O.argmax_first(np.array([-3.0, -1.0, -1.0])) == 1
+
+
+# ---------------------------------------------------------------- steps 8-9
+
+@pytest.mark.parametrize("M1,M2,N", [(4, 5, 19), (5, 6, 30), (7, 8, 50), (6, 7, 20), (9, 10, 85)])
+def test_crt_recovers_every_shift_exhaustive(M1, M2, N):
+    """Thm. 4: a shift m in [0, N) is recovered from its exact residues
+    m mod M1, m mod M2. Intersection members other than m can only be the
+    wrapped candidates (m~_i + (L_i-1) M_i) - N of Alg. 1 step 8 (R5)."""
+    L1, L2 = -(-N // M1), -(-N // M2)
+    for m in range(N):
+        S1 = O.candidate_set(m % M1, M1, N)
+        S2 = O.candidate_set(m % M2, M2, N)
+        I = S1 & S2
+        assert m in I
+        wrapped = {(m % M1) + (L1 - 1) * M1 - N, (m % M2) + (L2 - 1) * M2 - N}
+        assert I - {m} <= wrapped
+    # exhaustive over all residue pairs: every intersection member is
+    # congruent to both residues or is a wrapped candidate
+    for a in range(M1):
+        for b in range(M2):
+            I = O.candidate_set(a, M1, N) & O.candidate_set(b, M2, N)
+            for m in I:
+                assert (m % M1 == a or m == a + (L1 - 1) * M1 - N)
+                assert (m % M2 == b or m == b + (L2 - 1) * M2 - N)
+
+
+def test_candidate_set_size_and_membership():
+    # ceil(95/10) = 10 members; 3 + 9*10 = 93 < 95 needs no wrap
+    assert O.candidate_set(3, 10, 95) == {3 + 10 * i for i in range(10)}
+    # 7 + 9*10 = 97 wraps to 97 - 95 = 2
+    assert O.candidate_set(7, 10, 95) == {7 + 10 * i for i in range(9)} | {2}
+
+
+# ---------------------------------------------------------------- full search & planted shift
+
+def test_noiseless_planted_tx_equals_K_and_full_search():
+    """Sec. 3.5: with t = [x_m .. x_{m+K-1}], (Tx)_m = K; the full search
+    returns m when the maximum is unique."""
+    N, K = 2048, 64
+    for seed in range(5):
+        q = W.planted_query(seed, N, K)
+        x = O.decode(q.x, "i8", N)
+        t = O.template_values(q.t)
+        tx = O.full_search_values(x, t)
+        assert tx[q.k_star] == K
+        assert O.full_search(x, t) == q.k_star
+        assert np.array_equal(O.full_search_fft(x, t), tx)
+
+
+def test_ftm_single_config_recovers_or_fails_consistently():
+    """Config-1 shape: N = 65536, K = 1024, M = 1024/1025. Whenever the step-7
+    residues equal k* mod M_i, the recovered shift is k* (Thm. 4)."""
+    hits = 0
+    for seed in range(6):
+        q = W.single_query(seed)
+        res = O.match_query(q)
+        k = q.k_star
+        if res["m1"] == k % 1024 and res["m2"] == k % 1025:
+            assert res["shift"] == k and res["status"] == O.FOUND
+            hits += 1
+        else:
+            assert res["shift"] != k or res["status"] == O.RESOLVED
+    assert hits >= 1
+
+
+# ---------------------------------------------------------------- Thm. 3
+
+def test_thm3_sufficient_condition_on_barker_inputs():
+    """Thm. 3: if (Tx)_m / (2 ceil(N/M) + 1) > max_{k != m} (Tx)_k then the
+    true position is among the candidates of step 8 (m = m~ mod M). The
+    Barker-13 template has aperiodic sidelobes of magnitude <= 1."""
+    with open(os.path.join(GOLDEN, "barker13.txt")) as f:
+        b = [int(v) for line in f if not line.startswith("#") for v in line.split()]
+    t = np.array(b, dtype=np.int64)
+    K = t.size
+    for M1, N in ((13, 39), (14, 52), (13, 65)):
+        M2 = M1 + 1
+        for m in range(N):
+            x = np.zeros(N, dtype=np.int64)
+            x[(np.arange(K) + m) % N] = t
+            tx = O.full_search_values(x, t)
+            assert O.thm3_condition(tx, m, M1)
+            res = O.ftm(x, t, M1, M2)
+            assert res["m1"] == m % M1
+            if O.thm3_condition(tx, m, M2):
+                assert res["m2"] == m % M2
+
+
+# ---------------------------------------------------------------- Thm. 5 and Tables 1-2
+
+def _fold_fail_rate(N, K, M, n, seed0):
+    fails = 0
+    for s in range(n):
+        q = W.planted_query(seed0 + s, N, K)
+        x = O.decode(q.x, "i8", N)
+        t = O.template_values(q.t)
+        r = O.correlate_fft(O.fold(x, M, K), t, M)
+        if O.argmax_first(np.rint(r)) != q.k_star % M:
+            fails += 1
+    return fails / n
+
+
+def test_thm5_bound_dominates_empirical_failure():
+    """Per-modulus failure probability <= M e^{-K/(8L)} + 4(L-1)/K (Thm. 5)."""
+    N, K = 1 << 16, 2048
+    bound = O.thm5_fold_failure_bound(N, K, K)
+    assert bound < 1
+    assert _fold_fail_rate(N, K, K, 30, 4242) <= bound
+
+
+def _binom_two_sided_p(k, n, p):
+    """Exact two-sided binomial p-value (sum of outcomes no likelier than k)."""
+    pmf = [math.comb(n, i) * p ** i * (1 - p) ** (n - i) for i in range(n + 1)]
+    pk = pmf[k]
+    return min(1.0, sum(v for v in pmf if v <= pk * (1 + 1e-9)))
+
+
+def _success_rate(N, K, n, seed0, snr=None):
+    ok = 0
+    for s in range(n):
+        q = W.planted_query(seed0 + s, N, K) if snr is None else W.snr_query(seed0 + s, N, K, snr)
+        x = O.decode(q.x, q.xdtype, N)
+        t = O.template_values(q.t)
+        res = O.ftm(x, t, K, K + 1, corr="fft")
+        ok += int(res["shift"] == q.k_star)
+    return ok
+
+
+@pytest.mark.parametrize("log2N,n", [(23, 12), (24, 12), (25, 8)])
+def test_table1_success_rates(log2N, n):
+    """Table 1 (Sec. 4), K = N/2^10: the oracle's success count is consistent
+    with the printed probability (exact binomial test, p > 0.001)."""
+    table = dict(_read_table("table1_success.txt"))
+    p = table[log2N]
+    N = 1 << log2N
+    k = _success_rate(N, N >> 10, n, 9000 + log2N * 100)
+    assert _binom_two_sided_p(k, n, p) > 1e-3, (log2N, k, n, p)
+
+
+@pytest.mark.parametrize("snr,n", [(20.0, 3), (-6.0, 3)])
+def test_table2_success_rates(snr, n):
+    """Table 2 (Sec. 4), N = 2^26, K = 2^16, Gaussian noise on x (R8)."""
+    table = dict(_read_table("table2_success.txt"))
+    p = table[snr]
+    k = _success_rate(1 << 26, 1 << 16, n, 77000 + int(snr * 10), snr=snr)
+    pp = min(max(p, 1e-3), 1 - 1e-3)
+    assert _binom_two_sided_p(k, n, pp) > 1e-3, (snr, k, n, p)
