@@ -1,0 +1,207 @@
+/*
+ * tm.h - C ABI of a GB300 (sm_103a) implementation of the fast template
+ * matcher of Hsieh, Lu & Pei, "Fast Template Matching by Subsampled
+ * Circulant Matrix" (arXiv 1509.04863).
+ *
+ * Problem (Sec. 1 Eq. (1), Sec. 3): given a signal x in R^N and a template
+ * t in R^K, find the cyclic shift m maximising the cross-correlation
+ *     (Tx)_k = sum_{i<K} t_i x_{(k+i) mod N},   0 <= k < N.
+ * Method (Algorithm 1): fold x with two co-prime moduli M1, M2 into
+ * y_{M}[k] = sum_{i<ceil(N/M)} x_{(k+iM) mod N}, k < M+K-1 (step 3, Eq. (2)),
+ * correlate each fold with t by FFT (steps 4-6), take the argmax over
+ * j < M (step 7) and intersect the candidate sets {m~ + i M mod N} (steps
+ * 8-9, Thm. 4).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are CUDA device pointers, *_host host pointers.
+ *    The caller owns every buffer it passes; the library never frees them.
+ *  - Streams: tm_stream_t is the same type as cudaStream_t (NULL = the
+ *    legacy default stream). Work is asynchronous; outputs are valid once
+ *    the stream has synchronised.
+ *  - Errors: every call returns a tm_status; nothing aborts or exits.
+ *    tm_last_error() gives a message for the calling thread's last error.
+ *  - Signals must be 16-byte aligned on the device; templates 4-byte.
+ *  - Inputs must be finite. +-1 int8 signals must hold only 0x01 or 0xFF.
+ */
+#ifndef TM_H_
+#define TM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TM_API __attribute__((visibility("default")))
+#else
+#define TM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tm_stream_t;
+
+typedef enum {
+  TM_OK = 0,
+  TM_EINVAL = 1,        /* invalid argument or plan (see tm_last_error) */
+  TM_ENOMEM = 2,        /* device or host allocation failed */
+  TM_ECUDA = 3,         /* a CUDA runtime call failed (no GPU, launch error) */
+  TM_EBUSY = 4,         /* server: no free slot or memory right now */
+  TM_ETIMEDOUT = 5,     /* a bounded wait (host or device) ran out */
+  TM_EAGAIN = 6,        /* server: queue full, retry later */
+  TM_EUNSUPPORTED = 7   /* valid request outside what this build handles */
+} tm_status;
+
+/* Signal storage. TM_BITS_PM1 packs one element per bit, least significant
+ * bit first; bit 1 is +1 and bit 0 is -1. */
+typedef enum { TM_I8_PM1 = 0, TM_BITS_PM1 = 1, TM_F16 = 2, TM_F32 = 3 } tm_dtype;
+
+/* Choice of the co-prime moduli (Algorithm 1 step 2).
+ *  PAPER:    M1 = K, M2 = K+1 (Sec. 3.5 proof of Thm. 5; Sec. 4).
+ *  AUTO:     M1 = max(K, s), M2 = M1+1, s the least integer with s(s+1) > N,
+ *            so that M1*M2 > N as step 2 requires.
+ *  EXPLICIT: the caller's M1, M2 (co-prime, both >= K). */
+typedef enum { TM_MODE_AUTO = 0, TM_MODE_PAPER = 1, TM_MODE_EXPLICIT = 2 } tm_mode;
+
+/* Plan flag: accept M1*M2 <= N. The intersection of step 9 may then hold
+ * several shifts; they are resolved by their exact (Tx)_m. */
+#define TM_ALLOW_AMBIG 0x1u
+
+/* tm_result.status values (low byte) and flag bits. */
+#define TM_FOUND 0      /* |S1 ∩ S2| = 1 */
+#define TM_EMPTY 1      /* |S1 ∩ S2| = 0; shift = -1 */
+#define TM_RESOLVED 2   /* |S1 ∩ S2| > 1; best exact (Tx)_m, ties -> smallest m */
+#define TM_RF_FULL_RESCORE 0x100  /* too many near-maximal r_j: all j rescored */
+#define TM_RF_DEVICE_ERROR 0x200  /* a device-side bounded wait ran out */
+
+typedef struct {
+  int64_t N;       /* signal length, 1 <= N */
+  int32_t K;       /* template length, 1 <= K <= N */
+  int32_t xdtype;  /* tm_dtype */
+  int32_t mode;    /* tm_mode */
+  int32_t M1, M2;  /* only read for TM_MODE_EXPLICIT */
+  uint32_t flags;  /* TM_ALLOW_AMBIG */
+} tm_plan_desc;
+
+typedef struct {
+  int64_t N;
+  int32_t K, xdtype;
+  int32_t M1, M2;  /* moduli of step 2 */
+  int64_t L1, L2;  /* ceil(N/M1), ceil(N/M2): terms per fold entry (Eq. (2)) */
+  int32_t P;       /* FFT length: the least power of two >= max(M1,M2)+K-1 */
+  int32_t max_cand;/* bound on |S1 ∩ S2|: ceil(N/(M1*M2)) + 2 */
+} tm_plan_info;
+
+/* One matching result (48 bytes), written to device memory. */
+typedef struct {
+  int64_t shift;   /* recovered m^ in [0, N), or -1 (TM_EMPTY) */
+  int32_t status;  /* TM_FOUND / TM_EMPTY / TM_RESOLVED | TM_RF_* flags */
+  int32_t n_cand;  /* |S1 ∩ S2| */
+  int32_t m1, m2;  /* step-7 maxima m~1 < M1, m~2 < M2 */
+  double r1, r2;   /* exact r_{M1}[m~1], r_{M2}[m~2] (rescored, see below) */
+  double score;    /* exact (Tx)_shift, 0 when shift = -1 */
+} tm_result;
+
+/* One query of a batch. */
+typedef struct {
+  const void* x;   /* signal storage (device, 16-byte aligned) */
+  const float* t;  /* template, K floats (device) */
+  int64_t N;
+  int32_t K;
+  int32_t xdtype;
+  int32_t mode;
+  int32_t M1, M2;
+  uint32_t flags;
+} tm_query;
+
+/* ------------------------------------------------------------------ misc */
+
+/* Library version string. */
+TM_API const char* tm_version(void);
+/* Message of the calling thread's last failed call ("" if none). */
+TM_API const char* tm_last_error(void);
+
+/* ------------------------------------------------------------------ plan */
+
+typedef struct tm_plan_s* tm_plan_t;
+
+/* Validate a problem and choose M1, M2 (Algorithm 1 step 2) and the FFT
+ * length P >= max(M)+K-1 (steps 4-5 zero-pad t and y to a common length).
+ * Host only; needs no GPU. TM_EINVAL when K < 1, K > N, M_i < K, M_i > 2N,
+ * gcd(M1, M2) != 1, or M1*M2 <= N without TM_ALLOW_AMBIG;
+ * TM_EUNSUPPORTED when P > 16384 or the byte size of x exceeds 2^31-16. */
+TM_API tm_status tm_plan_create(const tm_plan_desc* desc, tm_plan_t* out);
+TM_API tm_status tm_plan_get_info(tm_plan_t plan, tm_plan_info* info);
+/* Frees the plan and its device workspace. Safe on NULL. */
+TM_API tm_status tm_plan_destroy(tm_plan_t plan);
+
+/* One query, Algorithm 1 steps 3-9 on the device: out_dev receives one
+ * tm_result. The plan owns a device workspace (allocated on the first call
+ * on the current device); calls on one plan must not overlap on the GPU. */
+TM_API tm_status tm_match(tm_plan_t plan, const void* x_dev, const float* t_dev,
+                   tm_result* out_dev, tm_stream_t stream);
+
+/* ----------------------------------------------------------------- batch */
+
+typedef struct tm_batch_s* tm_batch_t;
+
+/* Batch flags. */
+#define TM_BATCH_KEEP_CORR 0x1u   /* keep r_{M1}, r_{M2} for tm_batch_corr */
+#define TM_BATCH_HOST_INPUTS 0x2u /* allocate device copies of x and t so that
+                                     tm_batch_run_host can take host buffers */
+
+/* Plan n queries (each as tm_plan_create does) and allocate one device
+ * workspace for them: partial folds, folds, template spectra. The pointers
+ * in q are recorded (TM_BATCH_HOST_INPUTS: ignored). Needs the GPU that
+ * will run the batch to be current. */
+TM_API tm_status tm_batch_create(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* out);
+/* Replace the x / t pointers of every query (same shapes as at creation). */
+TM_API tm_status tm_batch_set_inputs(tm_batch_t b, const tm_query* q, int32_t n);
+/* Step 3 for the whole batch: one launch that streams every signal once and
+ * writes partial column sums of both folds. */
+TM_API tm_status tm_batch_fold(tm_batch_t b, tm_stream_t stream);
+/* Steps 3 (completion: wrap term, extension k >= M), 4-9 for every query:
+ * one CTA per query; writes n tm_results to out_dev. Must follow
+ * tm_batch_fold on the same stream. */
+TM_API tm_status tm_batch_correlate(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
+/* tm_batch_fold + tm_batch_correlate. */
+TM_API tm_status tm_batch_run(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
+/* End to end from host memory (needs TM_BATCH_HOST_INPUTS): copies each
+ * x_host[i] (tm_query N/xdtype bytes) and t_host[i] (K floats) to the
+ * batch's device buffers, runs the batch and copies the n results back to
+ * out_host. Synchronises the stream before returning. Pinned host memory
+ * gives the fastest copies. */
+TM_API tm_status tm_batch_run_host(tm_batch_t b, const void* const* x_host,
+                            const float* const* t_host, tm_result* out_host,
+                            tm_stream_t stream);
+/* Device pointers to query i's folds from the last run: y[0..P) for M1 then
+ * y[P..2P) for M2, entries k < M_j+K-1 valid. int32 for +-1 signals,
+ * float32 for real signals (*is_float set accordingly). */
+TM_API tm_status tm_batch_folds(tm_batch_t b, int32_t i, void** y_dev, int32_t* is_float);
+/* Device pointer to query i's FFT correlations from the last run (needs
+ * TM_BATCH_KEEP_CORR): r[0..M1) then r[P..P+M2), float32. */
+TM_API tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r_dev);
+/* Number of CUDA kernels one tm_batch_run launches, and fold CTAs. */
+TM_API tm_status tm_batch_stats(tm_batch_t b, int32_t* launches_per_run, int32_t* fold_ctas,
+                         int64_t* workspace_bytes);
+/* Device error word of the last run (0 = none; bit 0: a bounded device-side
+ * wait ran out). Synchronises the stream. */
+TM_API tm_status tm_batch_device_error(tm_batch_t b, tm_stream_t stream, int32_t* err);
+TM_API tm_status tm_batch_destroy(tm_batch_t b);
+
+/* One-shot batch: create, run, destroy (synchronises the stream). */
+TM_API tm_status tm_match_batch(const tm_query* q, int32_t n, tm_result* out_dev, tm_stream_t stream);
+
+/* ----------------------------------------------------------- host helper */
+
+/* Steps 8-9 in closed form on the host: the elements of
+ * S1 ∩ S2, S_i = {(m_i + l M_i) mod N : l < ceil(N/M_i)}, in ascending
+ * order (up to cap of them). Returns |S1 ∩ S2|, or -1 on invalid input.
+ * The device uses the same function. */
+TM_API int32_t tm_crt_candidates(int64_t N, int32_t M1, int32_t M2, int32_t m1, int32_t m2,
+                          int64_t* out, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TM_H_ */

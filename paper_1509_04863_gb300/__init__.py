@@ -1,0 +1,300 @@
+"""Python binding of libtm.so, the GB300 (sm_103a) subsampled-circulant
+template matcher (include/tm.h).
+
+Argument marshalling only: every step of the matcher runs in the library's
+CUDA kernels. torch tensors supply device memory and streams; their data
+pointers and the current CUDA stream are handed to the C ABI as they are.
+The library must have been built (`python -m paper_1509_04863_gb300._build`
+or __graft_entry__.build()); importing this package fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+from . import _build
+
+_LIB_PATH = _build.LIB
+
+# ---------------------------------------------------------------- constants (tm.h)
+TM_OK, TM_EINVAL, TM_ENOMEM, TM_ECUDA, TM_EBUSY, TM_ETIMEDOUT, TM_EAGAIN, TM_EUNSUPPORTED = range(8)
+TM_I8_PM1, TM_BITS_PM1, TM_F16, TM_F32 = range(4)
+TM_MODE_AUTO, TM_MODE_PAPER, TM_MODE_EXPLICIT = range(3)
+TM_ALLOW_AMBIG = 0x1
+TM_FOUND, TM_EMPTY, TM_RESOLVED = 0, 1, 2
+TM_RF_FULL_RESCORE = 0x100
+TM_RF_DEVICE_ERROR = 0x200
+TM_BATCH_KEEP_CORR = 0x1
+TM_BATCH_HOST_INPUTS = 0x2
+
+DTYPE_CODES = {"i8": TM_I8_PM1, "bits": TM_BITS_PM1, "f16": TM_F16, "f32": TM_F32}
+MODE_CODES = {"auto": TM_MODE_AUTO, "paper": TM_MODE_PAPER, "explicit": TM_MODE_EXPLICIT}
+
+
+class tm_plan_desc(C.Structure):
+    _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("xdtype", C.c_int32), ("mode", C.c_int32),
+                ("M1", C.c_int32), ("M2", C.c_int32), ("flags", C.c_uint32)]
+
+
+class tm_plan_info(C.Structure):
+    _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("xdtype", C.c_int32), ("M1", C.c_int32),
+                ("M2", C.c_int32), ("L1", C.c_int64), ("L2", C.c_int64), ("P", C.c_int32),
+                ("max_cand", C.c_int32)]
+
+
+class tm_result(C.Structure):
+    _fields_ = [("shift", C.c_int64), ("status", C.c_int32), ("n_cand", C.c_int32), ("m1", C.c_int32),
+                ("m2", C.c_int32), ("r1", C.c_double), ("r2", C.c_double), ("score", C.c_double)]
+
+
+class tm_query(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("t", C.c_void_p), ("N", C.c_int64), ("K", C.c_int32),
+                ("xdtype", C.c_int32), ("mode", C.c_int32), ("M1", C.c_int32), ("M2", C.c_int32),
+                ("flags", C.c_uint32)]
+
+
+RESULT_BYTES = C.sizeof(tm_result)
+assert RESULT_BYTES == 48
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "tm_version": (C.c_char_p, []),
+    "tm_last_error": (C.c_char_p, []),
+    "tm_plan_create": (C.c_int, [C.POINTER(tm_plan_desc), C.POINTER(C.c_void_p)]),
+    "tm_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(tm_plan_info)]),
+    "tm_plan_destroy": (C.c_int, [C.c_void_p]),
+    "tm_match": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tm_batch_create": (C.c_int, [C.POINTER(tm_query), C.c_int32, C.c_uint32, C.POINTER(C.c_void_p)]),
+    "tm_batch_set_inputs": (C.c_int, [C.c_void_p, C.POINTER(tm_query), C.c_int32]),
+    "tm_batch_fold": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tm_batch_correlate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tm_batch_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tm_batch_run_host": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p,
+                                    C.c_void_p]),
+    "tm_batch_folds": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]),
+    "tm_batch_corr": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "tm_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "tm_batch_device_error": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "tm_batch_destroy": (C.c_int, [C.c_void_p]),
+    "tm_match_batch": (C.c_int, [C.POINTER(tm_query), C.c_int32, C.c_void_p, C.c_void_p]),
+    "tm_crt_candidates": (C.c_int32, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                      C.POINTER(C.c_int64), C.c_int32]),
+}
+
+_lib: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libtm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libtm.so not built at {_LIB_PATH}; run __graft_entry__.build()")
+        L = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class TMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().tm_last_error().decode(errors="replace")
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, where: str):
+    if st != TM_OK:
+        raise TMError(st, where)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def tm_version() -> str:
+    return lib().tm_version().decode()
+
+
+def tm_crt_candidates(N: int, M1: int, M2: int, m1: int, m2: int, cap: int = 4096) -> List[int]:
+    """Host closed-form S1 ∩ S2 (Algorithm 1 steps 8-9), ascending."""
+    buf = (C.c_int64 * cap)()
+    n = lib().tm_crt_candidates(N, M1, M2, m1, m2, buf, cap)
+    if n < 0:
+        raise ValueError("invalid CRT arguments")
+    return [buf[i] for i in range(min(n, cap))]
+
+
+class Plan:
+    """tm_plan_create / tm_plan_get_info / tm_match / tm_plan_destroy."""
+
+    def __init__(self, N: int, K: int, xdtype: str = "i8", mode: str = "paper", M1: int = 0, M2: int = 0,
+                 allow_ambig: bool = False):
+        d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2,
+                         TM_ALLOW_AMBIG if allow_ambig else 0)
+        h = C.c_void_p()
+        _check(lib().tm_plan_create(C.byref(d), C.byref(h)), "tm_plan_create")
+        self._h = h
+        info = tm_plan_info()
+        _check(lib().tm_plan_get_info(h, C.byref(info)), "tm_plan_get_info")
+        self.info = {f: getattr(info, f) for f, _ in tm_plan_info._fields_}
+
+    def match(self, x, t, out, stream=None):
+        """x, t, out: CUDA tensors (out: >= 48 bytes, e.g. torch.empty(6, dtype=torch.int64))."""
+        _check(lib().tm_match(self._h, x.data_ptr(), t.data_ptr(), out.data_ptr(), _stream_ptr(stream)), "tm_match")
+
+    def close(self):
+        if self._h:
+            lib().tm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tm_plan_create(N, K, xdtype="i8", mode="paper", M1=0, M2=0, allow_ambig=False) -> Plan:
+    return Plan(N, K, xdtype, mode, M1, M2, allow_ambig)
+
+
+def _query_struct(x_ptr, t_ptr, N, K, xdtype, mode, M1=0, M2=0, allow_ambig=False) -> tm_query:
+    return tm_query(x_ptr, t_ptr, int(N), int(K), DTYPE_CODES[xdtype], MODE_CODES[mode], int(M1), int(M2),
+                    TM_ALLOW_AMBIG if allow_ambig else 0)
+
+
+class Batch:
+    """tm_batch_create / tm_batch_run / tm_batch_fold / tm_batch_correlate / ...
+
+    `specs` is a list of dicts with keys x (CUDA tensor or None for host-input
+    batches), t (CUDA tensor or None), N, K, xdtype, mode, and optionally M1,
+    M2, allow_ambig."""
+
+    def __init__(self, specs: Sequence[dict], keep_corr: bool = False, host_inputs: bool = False):
+        self.n = len(specs)
+        self.specs = list(specs)
+        arr = (tm_query * self.n)()
+        for i, s in enumerate(specs):
+            xp = s["x"].data_ptr() if s.get("x") is not None else None
+            tp = s["t"].data_ptr() if s.get("t") is not None else None
+            arr[i] = _query_struct(xp, tp, s["N"], s["K"], s.get("xdtype", "i8"), s.get("mode", "paper"),
+                                   s.get("M1", 0), s.get("M2", 0), s.get("allow_ambig", False))
+        self._arr = arr
+        flags = (TM_BATCH_KEEP_CORR if keep_corr else 0) | (TM_BATCH_HOST_INPUTS if host_inputs else 0)
+        h = C.c_void_p()
+        _check(lib().tm_batch_create(arr, self.n, flags, C.byref(h)), "tm_batch_create")
+        self._h = h
+        # per-query plan information (host-only planner calls)
+        self.infos = [Plan(s["N"], s["K"], s.get("xdtype", "i8"), s.get("mode", "paper"), s.get("M1", 0),
+                           s.get("M2", 0), s.get("allow_ambig", False)).info for s in specs]
+
+    def set_inputs(self, xs, ts):
+        for i in range(self.n):
+            self._arr[i].x = xs[i].data_ptr()
+            self._arr[i].t = ts[i].data_ptr()
+        _check(lib().tm_batch_set_inputs(self._h, self._arr, self.n), "tm_batch_set_inputs")
+
+    def run(self, out, stream=None):
+        _check(lib().tm_batch_run(self._h, out.data_ptr(), _stream_ptr(stream)), "tm_batch_run")
+
+    def fold(self, stream=None):
+        _check(lib().tm_batch_fold(self._h, _stream_ptr(stream)), "tm_batch_fold")
+
+    def correlate(self, out, stream=None):
+        _check(lib().tm_batch_correlate(self._h, out.data_ptr(), _stream_ptr(stream)), "tm_batch_correlate")
+
+    def run_host(self, x_host: Sequence, t_host: Sequence, out_host, stream=None):
+        """x_host, t_host: CPU tensors (pinned for speed); out_host: CPU tensor of n*48 bytes."""
+        xs = (C.c_void_p * self.n)(*[x.data_ptr() for x in x_host])
+        ts = (C.c_void_p * self.n)(*[t.data_ptr() for t in t_host])
+        _check(lib().tm_batch_run_host(self._h, xs, ts, out_host.data_ptr(), _stream_ptr(stream)),
+               "tm_batch_run_host")
+
+    def folds_ptr(self, i: int):
+        p = C.c_void_p()
+        f = C.c_int32()
+        _check(lib().tm_batch_folds(self._h, i, C.byref(p), C.byref(f)), "tm_batch_folds")
+        return p.value, bool(f.value)
+
+    def folds(self, i: int):
+        """Query i's folds as a device tensor view: [0, P) for M1, [P, 2P) for M2."""
+        ptr, is_float = self.folds_ptr(i)
+        return device_view(ptr, 2 * self.infos[i]["P"], "<f4" if is_float else "<i4")
+
+    def corr(self, i: int):
+        """Query i's FFT correlations (float32 view): r1 at [0, M1), r2 at [P, P+M2)."""
+        return device_view(self.corr_ptr(i), 2 * self.infos[i]["P"], "<f4")
+
+    def corr_ptr(self, i: int):
+        p = C.c_void_p()
+        _check(lib().tm_batch_corr(self._h, i, C.byref(p)), "tm_batch_corr")
+        return p.value
+
+    def stats(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().tm_batch_stats(self._h, C.byref(a), C.byref(b), C.byref(c)), "tm_batch_stats")
+        return {"launches_per_run": a.value, "fold_ctas": b.value, "workspace_bytes": c.value}
+
+    def device_error(self, stream=None) -> int:
+        e = C.c_int32()
+        _check(lib().tm_batch_device_error(self._h, _stream_ptr(stream), C.byref(e)), "tm_batch_device_error")
+        return e.value
+
+    def close(self):
+        if self._h:
+            lib().tm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tm_batch_create(specs, keep_corr=False, host_inputs=False) -> Batch:
+    return Batch(specs, keep_corr, host_inputs)
+
+
+def tm_match_batch(specs, out, stream=None):
+    arr = (tm_query * len(specs))()
+    for i, s in enumerate(specs):
+        arr[i] = _query_struct(s["x"].data_ptr(), s["t"].data_ptr(), s["N"], s["K"], s.get("xdtype", "i8"),
+                               s.get("mode", "paper"), s.get("M1", 0), s.get("M2", 0), s.get("allow_ambig", False))
+    _check(lib().tm_match_batch(arr, len(specs), out.data_ptr(), _stream_ptr(stream)), "tm_match_batch")
+
+
+def decode_results(buf) -> List[dict]:
+    """tm_result records from a CPU tensor / bytes-like of n*48 bytes."""
+    import numpy as np
+    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+    n = len(raw) // RESULT_BYTES
+    out = []
+    for i in range(n):
+        r = tm_result.from_buffer_copy(raw[i * RESULT_BYTES:(i + 1) * RESULT_BYTES])
+        out.append({f: getattr(r, f) for f, _ in tm_result._fields_})
+    return out
+
+
+class _CudaArray:
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2}
+
+
+def device_view(ptr: int, n: int, typestr: str):
+    """Zero-copy torch view of n elements of library-owned device memory."""
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, n, typestr), device="cuda")
+
+
+def result_buffer(n: int, device="cuda"):
+    import torch
+    return torch.zeros(n * RESULT_BYTES // 8, dtype=torch.int64, device=device)

@@ -1,0 +1,544 @@
+// Host runtime and C ABI: planning (Algorithm 1 step 2), batch workspaces,
+// launches and error reporting. See include/tm.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "crt.h"
+#include "tm_internal.h"
+
+namespace {
+
+using namespace ftm;
+
+thread_local std::string g_err;
+
+tm_status fail(tm_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+tm_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(TM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TM_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t pad16(int64_t v) { return (v + 15) & ~int64_t(15); }
+
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) { const int64_t t = a % b; a = b; b = t; }
+  return a;
+}
+
+// Least s with s (s+1) > N.
+int64_t least_s(int64_t N) {
+  int64_t s = std::max<int64_t>(1, int64_t(std::sqrt(double(N))) - 2);
+  while (s * (s + 1) <= N) ++s;
+  while (s > 1 && (s - 1) * s > N) --s;
+  return s;
+}
+
+int64_t signal_bytes(int32_t dtype, int64_t N) {
+  switch (dtype) {
+    case TM_I8_PM1: return N;
+    case TM_BITS_PM1: return ceil_div(N, 8);
+    case TM_F16: return 2 * N;
+    default: return 4 * N;
+  }
+}
+
+struct PlanCore {
+  int64_t N = 0;
+  int32_t K = 0, xdtype = 0;
+  int32_t M[2] = {0, 0};
+  int64_t L[2] = {0, 0};
+  int32_t P = 0, logP = 0;
+  int32_t inv = 0;
+  int32_t R[2] = {1, 1}, Mp[2] = {0, 0};
+  int64_t max_cand = 0;
+};
+
+// Algorithm 1 step 2 and the derived sizes.
+tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t M1, int32_t M2, uint32_t flags,
+                    PlanCore& pc) {
+  if (N < 1 || K < 1 || K > N) return fail(TM_EINVAL, "need 1 <= K <= N");
+  if (xdtype < TM_I8_PM1 || xdtype > TM_F32) return fail(TM_EINVAL, "unknown signal dtype");
+  int64_t m1, m2;
+  if (mode == TM_MODE_PAPER) { m1 = K; m2 = int64_t(K) + 1; }
+  else if (mode == TM_MODE_AUTO) { m1 = std::max<int64_t>(K, least_s(N)); m2 = m1 + 1; }
+  else if (mode == TM_MODE_EXPLICIT) { m1 = M1; m2 = M2; }
+  else return fail(TM_EINVAL, "unknown mode");
+  if (m1 < K || m2 < K) return fail(TM_EINVAL, "step 2 needs M1 >= K and M2 >= K");
+  if (m1 > 2 * N || m2 > 2 * N) return fail(TM_EINVAL, "moduli above 2N are not meaningful");
+  if (gcd64(m1, m2) != 1) return fail(TM_EINVAL, "step 2 needs co-prime M1 and M2");
+  if (m1 * m2 <= N && !(flags & TM_ALLOW_AMBIG))
+    return fail(TM_EINVAL, "step 2 needs M1*M2 > N (set TM_ALLOW_AMBIG to accept several solutions)");
+  const int64_t need = std::max(m1, m2) + K - 1;
+  int32_t logP = 0;
+  while ((int64_t(1) << logP) < need) ++logP;
+  if (logP > kLogPMax) return fail(TM_EUNSUPPORTED, "FFT length above 16384 (max(M1,M2)+K-1 > 16384)");
+  if (signal_bytes(xdtype, N) > kMaxQueryBytes) return fail(TM_EUNSUPPORTED, "signal larger than 2^31-2^16 bytes");
+  pc.N = N; pc.K = K; pc.xdtype = xdtype;
+  pc.M[0] = int32_t(m1); pc.M[1] = int32_t(m2);
+  pc.L[0] = ceil_div(N, m1); pc.L[1] = ceil_div(N, m2);
+  pc.logP = logP; pc.P = 1 << logP;
+  pc.inv = int32_t(mod_inverse(m1, m2));
+  for (int j = 0; j < 2; ++j) {
+    pc.R[j] = int32_t(std::max<int64_t>(1, ceil_div(kFoldMinMp, pc.M[j])));
+    pc.Mp[j] = pc.R[j] * pc.M[j];
+    const int64_t units = ceil_div(pc.Mp[j], 16);
+    if (ceil_div(units, kFoldModThreads) > kFoldJMax)
+      return fail(TM_EUNSUPPORTED, "modulus above 20480 not supported by the fold kernel");
+  }
+  pc.max_cand = ceil_div(N, m1 * m2) + 2;
+  if (xdtype != TM_I8_PM1) return fail(TM_EUNSUPPORTED, "only TM_I8_PM1 signals are folded by this build");
+  return TM_OK;
+}
+
+// ---------------------------------------------------------------- per-device state
+std::mutex g_mu;
+std::vector<float2*> g_twiddles;   // per device
+std::vector<int> g_configured;
+
+tm_status device_setup(int dev, float2** tw) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (int(g_twiddles.size()) <= dev) { g_twiddles.resize(dev + 1, nullptr); g_configured.resize(dev + 1, 0); }
+  if (!g_configured[dev]) {
+    TM_CUDA(fold_configure());
+    TM_CUDA(corr_configure());
+    std::vector<float2> h(kPMax);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int m = 0; m < kPMax; ++m) {
+      const double a = two_pi * double(m) / double(kPMax);
+      h[m] = make_float2(float(std::cos(a)), float(-std::sin(a)));   // W^m = e^{-2 pi i m / PMax}
+    }
+    float2* d = nullptr;
+    TM_CUDA(cudaMalloc(&d, kPMax * sizeof(float2)));
+    TM_CUDA(cudaMemcpy(d, h.data(), kPMax * sizeof(float2), cudaMemcpyHostToDevice));
+    g_twiddles[dev] = d;
+    g_configured[dev] = 1;
+  }
+  *tw = g_twiddles[dev];
+  return TM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- objects
+struct tm_batch_s {
+  int device = 0;
+  uint32_t flags = 0;
+  int32_t n = 0;
+  std::vector<PlanCore> pc;
+  std::vector<tm_query> q;
+  std::vector<FoldQ> fq;
+  std::vector<CorrQ> cq;
+  std::vector<int32_t> order;
+  std::vector<int64_t> xoff, toff;   // device input copies (TM_BATCH_HOST_INPUTS)
+  int32_t nctas = 0;
+  int64_t W = 0;
+  int32_t maxP = 0;
+  int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
+  FoldQ* d_fq = nullptr;
+  CorrQ* d_cq = nullptr;
+  int32_t* d_order = nullptr;
+  int32_t* d_partial = nullptr;
+  void* d_y = nullptr;
+  float2* d_spec = nullptr;
+  float* d_r = nullptr;
+  int32_t* d_err = nullptr;
+  tm_result* d_out = nullptr;
+  uint8_t* d_x = nullptr;
+  float* d_t = nullptr;
+  float2* tw = nullptr;
+  // pinned staging for descriptor uploads, guarded by an event
+  void* h_stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t ev_stage = nullptr;
+  int64_t ws_bytes = 0;
+};
+
+struct tm_plan_s {
+  tm_plan_desc d;
+  PlanCore pc;
+  tm_batch_t b = nullptr;
+};
+
+namespace {
+
+void batch_free(tm_batch_t b) {
+  if (!b) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(b->device);
+  if (b->ev_stage) { cudaEventSynchronize(b->ev_stage); cudaEventDestroy(b->ev_stage); }
+  cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_order); cudaFree(b->d_partial);
+  cudaFree(b->d_y); cudaFree(b->d_spec); cudaFree(b->d_r); cudaFree(b->d_err); cudaFree(b->d_out);
+  cudaFree(b->d_x); cudaFree(b->d_t);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  cudaSetDevice(cur);
+  delete b;
+}
+
+// Fill x/t pointers of the descriptors from b->q (or the batch's own copies).
+void bind_pointers(tm_batch_t b) {
+  for (int i = 0; i < b->n; ++i) {
+    const void* x = (b->flags & TM_BATCH_HOST_INPUTS) ? static_cast<const void*>(b->d_x + b->xoff[i]) : b->q[i].x;
+    const float* t = (b->flags & TM_BATCH_HOST_INPUTS) ? b->d_t + b->toff[i] : b->q[i].t;
+    b->fq[i].x = static_cast<const uint8_t*>(x);
+    b->cq[i].x = x;
+    b->cq[i].t = t;
+  }
+}
+
+// Upload descriptors on `s` through pinned staging (reuse waits for the
+// previous upload to have been consumed by the copy engine).
+tm_status upload_descriptors(tm_batch_t b, cudaStream_t s) {
+  const size_t nf = b->fq.size() * sizeof(FoldQ), nc = b->cq.size() * sizeof(CorrQ);
+  TM_CUDA(cudaEventSynchronize(b->ev_stage));
+  char* h = static_cast<char*>(b->h_stage);
+  std::memcpy(h, b->fq.data(), nf);
+  std::memcpy(h + nf, b->cq.data(), nc);
+  TM_CUDA(cudaMemcpyAsync(b->d_fq, h, nf, cudaMemcpyHostToDevice, s));
+  TM_CUDA(cudaMemcpyAsync(b->d_cq, h + nf, nc, cudaMemcpyHostToDevice, s));
+  TM_CUDA(cudaEventRecord(b->ev_stage, s));
+  return TM_OK;
+}
+
+tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* out) {
+  if (!out) return fail(TM_EINVAL, "null output handle");
+  *out = nullptr;
+  if (n < 1 || !q) return fail(TM_EINVAL, "empty batch");
+  tm_batch_t b = new (std::nothrow) tm_batch_s();
+  if (!b) return fail(TM_ENOMEM, "host allocation");
+  b->flags = flags;
+  b->n = n;
+  b->q.assign(q, q + n);
+  b->pc.resize(n);
+  for (int i = 0; i < n; ++i) {
+    tm_status st = make_plan(q[i].N, q[i].K, q[i].xdtype, q[i].mode, q[i].M1, q[i].M2, q[i].flags, b->pc[i]);
+    if (st != TM_OK) {
+      g_err = "query " + std::to_string(i) + ": " + g_err;
+      delete b;
+      return st;
+    }
+    if (!(flags & TM_BATCH_HOST_INPUTS)) {
+      if (!q[i].x || !q[i].t) { delete b; return fail(TM_EINVAL, "null x or t pointer"); }
+      if (reinterpret_cast<uintptr_t>(q[i].x) & 15) { delete b; return fail(TM_EINVAL, "x must be 16-byte aligned"); }
+      if (reinterpret_cast<uintptr_t>(q[i].t) & 3) { delete b; return fail(TM_EINVAL, "t must be 4-byte aligned"); }
+    }
+  }
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaGetDevice"); }
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+  tm_status st = device_setup(b->device, &b->tw);
+  if (st != TM_OK) { delete b; return st; }
+
+  // ---- fold geometry: flattened byte space, equal shares per CTA
+  b->fq.resize(n);
+  b->cq.resize(n);
+  int64_t W = 0, max_share = INT64_MAX;
+  for (int i = 0; i < n; ++i) {
+    const PlanCore& p = b->pc[i];
+    const int64_t nb = signal_bytes(p.xdtype, p.N) & ~int64_t(15);
+    FoldQ& f = b->fq[i];
+    f.goff = W;
+    f.nbytes = int32_t(nb);
+    for (int j = 0; j < 2; ++j) f.Mp[j] = p.Mp[j];
+    f.moff[0] = 0;
+    f.moff[1] = int32_t(pad16(p.Mp[0]));
+    f.stride = int32_t(pad16(p.Mp[0]) + pad16(p.Mp[1]));
+    W += nb;
+    max_share = std::min<int64_t>(max_share, int64_t(kFoldMaxRowsPerSlot - 2) * std::min(p.Mp[0], p.Mp[1]));
+  }
+  b->W = W;
+  int64_t nctas = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(W, 65536)));
+  if (W > 0) nctas = std::max<int64_t>(nctas, ceil_div(W, max_share));
+  b->nctas = int32_t(nctas);
+  auto cta_of = [&](int64_t pos) {   // CTA whose share holds byte pos
+    int32_t lo = 0, hi = b->nctas - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) / 2;
+      if (fold_cta_begin(W, b->nctas, mid) <= pos) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  int64_t part = 0;
+  for (int i = 0; i < n; ++i) {
+    FoldQ& f = b->fq[i];
+    if (f.nbytes == 0) { f.first_cta = 0; f.nslots = 0; f.part = part; continue; }
+    f.first_cta = cta_of(f.goff);
+    f.nslots = cta_of(f.goff + f.nbytes - 1) - f.first_cta + 1;
+    f.part = part;
+    part += int64_t(f.nslots) * f.stride;
+  }
+  b->part_elems = std::max<int64_t>(part, 16);
+
+  // ---- correlation descriptors and output layout
+  int64_t yo = 0, so = 0, ro = 0;
+  for (int i = 0; i < n; ++i) {
+    const PlanCore& p = b->pc[i];
+    const FoldQ& f = b->fq[i];
+    CorrQ& c = b->cq[i];
+    c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
+    for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
+    c.P = p.P; c.logP = p.logP; c.inv = p.inv;
+    c.nelem16 = int32_t(p.xdtype == TM_I8_PM1 ? f.nbytes : p.xdtype == TM_BITS_PM1 ? std::min<int64_t>(p.N, 8ll * f.nbytes)
+                        : p.xdtype == TM_F16 ? f.nbytes / 2 : f.nbytes / 4);
+    c.nslots = f.nslots; c.stride = f.stride; c.part = f.part;
+    c.y_off = yo; yo += 2ll * p.P;
+    c.spec_off = so; so += p.P;
+    c.r_off = (flags & TM_BATCH_KEEP_CORR) ? ro : -1;
+    if (flags & TM_BATCH_KEEP_CORR) ro += 2ll * p.P;
+    b->maxP = std::max(b->maxP, p.P);
+  }
+  b->y_elems = yo; b->spec_elems = so; b->r_elems = ro;
+  b->order.resize(n);
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return b->pc[a].P > b->pc[c].P; });
+
+  // ---- device allocations
+  auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+    b->ws_bytes += int64_t(bytes);
+    return cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+  };
+  bool ok = alloc((void**)&b->d_fq, n * sizeof(FoldQ)) == cudaSuccess &&
+            alloc((void**)&b->d_cq, n * sizeof(CorrQ)) == cudaSuccess &&
+            alloc((void**)&b->d_order, n * sizeof(int32_t)) == cudaSuccess &&
+            alloc((void**)&b->d_partial, b->part_elems * sizeof(int32_t)) == cudaSuccess &&
+            alloc(&b->d_y, b->y_elems * sizeof(int32_t)) == cudaSuccess &&
+            alloc((void**)&b->d_spec, b->spec_elems * sizeof(float2)) == cudaSuccess &&
+            alloc((void**)&b->d_err, 16) == cudaSuccess &&
+            alloc((void**)&b->d_out, n * sizeof(tm_result)) == cudaSuccess;
+  if (ok && (flags & TM_BATCH_KEEP_CORR)) ok = alloc((void**)&b->d_r, b->r_elems * sizeof(float)) == cudaSuccess;
+  if (ok && (flags & TM_BATCH_HOST_INPUTS)) {
+    int64_t xb = 0, tb = 0;
+    b->xoff.resize(n); b->toff.resize(n);
+    for (int i = 0; i < n; ++i) {
+      b->xoff[i] = xb; xb += pad16(signal_bytes(b->pc[i].xdtype, b->pc[i].N)) + 16;
+      b->toff[i] = tb; tb += pad16(b->pc[i].K);
+    }
+    ok = alloc((void**)&b->d_x, xb) == cudaSuccess && alloc((void**)&b->d_t, tb * sizeof(float)) == cudaSuccess;
+  }
+  b->stage_bytes = n * (sizeof(FoldQ) + sizeof(CorrQ));
+  if (ok) ok = cudaMallocHost(&b->h_stage, b->stage_bytes) == cudaSuccess;
+  if (ok) ok = cudaEventCreateWithFlags(&b->ev_stage, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    batch_free(b);
+    return fail(TM_ENOMEM, "device workspace allocation failed");
+  }
+  cudaMemset(b->d_err, 0, 16);
+  cudaMemcpy(b->d_order, b->order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
+  bind_pointers(b);
+  st = upload_descriptors(b, nullptr);
+  if (st != TM_OK) { batch_free(b); return st; }
+  e = cudaStreamSynchronize(nullptr);
+  if (e != cudaSuccess) { batch_free(b); return cuda_fail(e, "descriptor upload"); }
+  *out = b;
+  return TM_OK;
+}
+
+tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
+  TM_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int32_t), s));
+  if (b->W == 0) return TM_OK;
+  FoldArgs a;
+  a.q = b->d_fq; a.nq = b->n; a.nctas = b->nctas; a.W = b->W;
+  a.partial = b->d_partial; a.err = b->d_err;
+  TM_CUDA(launch_fold_i8(a, s));
+  return TM_OK;
+}
+
+tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s) {
+  CorrArgs a;
+  a.q = b->d_cq; a.order = b->d_order; a.nq = b->n;
+  a.partial = b->d_partial; a.y = b->d_y; a.spec = b->d_spec; a.r = b->d_r; a.tw = b->tw;
+  a.out = out; a.err = b->d_err;
+  TM_CUDA(launch_correlate(a, b->maxP, s));
+  return TM_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* tm_version(void) { return "tm 0.1 (sm_103a)"; }
+const char* tm_last_error(void) { return g_err.c_str(); }
+
+tm_status tm_plan_create(const tm_plan_desc* desc, tm_plan_t* out) {
+  if (!desc || !out) return fail(TM_EINVAL, "null argument");
+  *out = nullptr;
+  tm_plan_t p = new (std::nothrow) tm_plan_s();
+  if (!p) return fail(TM_ENOMEM, "host allocation");
+  p->d = *desc;
+  tm_status st = make_plan(desc->N, desc->K, desc->xdtype, desc->mode, desc->M1, desc->M2, desc->flags, p->pc);
+  if (st != TM_OK) { delete p; return st; }
+  *out = p;
+  return TM_OK;
+}
+
+tm_status tm_plan_get_info(tm_plan_t p, tm_plan_info* info) {
+  if (!p || !info) return fail(TM_EINVAL, "null argument");
+  info->N = p->pc.N; info->K = p->pc.K; info->xdtype = p->pc.xdtype;
+  info->M1 = p->pc.M[0]; info->M2 = p->pc.M[1];
+  info->L1 = p->pc.L[0]; info->L2 = p->pc.L[1];
+  info->P = p->pc.P;
+  info->max_cand = int32_t(std::min<int64_t>(p->pc.max_cand, INT32_MAX));
+  return TM_OK;
+}
+
+tm_status tm_plan_destroy(tm_plan_t p) {
+  if (!p) return TM_OK;
+  batch_free(p->b);
+  delete p;
+  return TM_OK;
+}
+
+tm_status tm_match(tm_plan_t p, const void* x, const float* t, tm_result* out, tm_stream_t stream) {
+  if (!p || !x || !t || !out) return fail(TM_EINVAL, "null argument");
+  tm_query q;
+  q.x = x; q.t = t; q.N = p->d.N; q.K = p->d.K; q.xdtype = p->d.xdtype; q.mode = p->d.mode;
+  q.M1 = p->d.M1; q.M2 = p->d.M2; q.flags = p->d.flags;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!p->b) {
+    tm_status st = batch_build(&q, 1, 0, &p->b);
+    if (st != TM_OK) return st;
+  } else if (p->b->q[0].x != x || p->b->q[0].t != t) {
+    if (reinterpret_cast<uintptr_t>(x) & 15) return fail(TM_EINVAL, "x must be 16-byte aligned");
+    p->b->q[0] = q;
+    bind_pointers(p->b);
+    tm_status st = upload_descriptors(p->b, s);
+    if (st != TM_OK) return st;
+  }
+  tm_status st = batch_fold(p->b, s);
+  if (st != TM_OK) return st;
+  return batch_correlate(p->b, out, s);
+}
+
+tm_status tm_batch_create(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* out) {
+  return batch_build(q, n, flags, out);
+}
+
+tm_status tm_batch_set_inputs(tm_batch_t b, const tm_query* q, int32_t n) {
+  if (!b || !q || n != b->n) return fail(TM_EINVAL, "batch size mismatch");
+  for (int i = 0; i < n; ++i) {
+    if (q[i].N != b->q[i].N || q[i].K != b->q[i].K || q[i].xdtype != b->q[i].xdtype)
+      return fail(TM_EINVAL, "query shapes differ from the batch");
+    if (reinterpret_cast<uintptr_t>(q[i].x) & 15) return fail(TM_EINVAL, "x must be 16-byte aligned");
+  }
+  for (int i = 0; i < n; ++i) { b->q[i].x = q[i].x; b->q[i].t = q[i].t; }
+  bind_pointers(b);
+  return upload_descriptors(b, nullptr);
+}
+
+tm_status tm_batch_fold(tm_batch_t b, tm_stream_t stream) {
+  if (!b) return fail(TM_EINVAL, "null batch");
+  return batch_fold(b, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tm_status tm_batch_correlate(tm_batch_t b, tm_result* out, tm_stream_t stream) {
+  if (!b || !out) return fail(TM_EINVAL, "null argument");
+  return batch_correlate(b, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tm_status tm_batch_run(tm_batch_t b, tm_result* out, tm_stream_t stream) {
+  tm_status st = tm_batch_fold(b, stream);
+  if (st != TM_OK) return st;
+  return tm_batch_correlate(b, out, stream);
+}
+
+tm_status tm_batch_run_host(tm_batch_t b, const void* const* x_host, const float* const* t_host,
+                            tm_result* out_host, tm_stream_t stream) {
+  if (!b || !x_host || !t_host || !out_host) return fail(TM_EINVAL, "null argument");
+  if (!(b->flags & TM_BATCH_HOST_INPUTS)) return fail(TM_EINVAL, "batch was created without TM_BATCH_HOST_INPUTS");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < b->n; ++i) {
+    TM_CUDA(cudaMemcpyAsync(b->d_x + b->xoff[i], x_host[i], signal_bytes(b->pc[i].xdtype, b->pc[i].N),
+                            cudaMemcpyHostToDevice, s));
+    TM_CUDA(cudaMemcpyAsync(b->d_t + b->toff[i], t_host[i], size_t(b->pc[i].K) * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+  }
+  tm_status st = batch_fold(b, s);
+  if (st != TM_OK) return st;
+  st = batch_correlate(b, b->d_out, s);
+  if (st != TM_OK) return st;
+  TM_CUDA(cudaMemcpyAsync(out_host, b->d_out, size_t(b->n) * sizeof(tm_result), cudaMemcpyDeviceToHost, s));
+  TM_CUDA(cudaStreamSynchronize(s));
+  return TM_OK;
+}
+
+tm_status tm_batch_folds(tm_batch_t b, int32_t i, void** y, int32_t* is_float) {
+  if (!b || !y || i < 0 || i >= b->n) return fail(TM_EINVAL, "bad query index");
+  *y = static_cast<char*>(b->d_y) + b->cq[i].y_off * 4;
+  if (is_float) *is_float = (b->pc[i].xdtype == TM_F16 || b->pc[i].xdtype == TM_F32) ? 1 : 0;
+  return TM_OK;
+}
+
+tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r) {
+  if (!b || !r || i < 0 || i >= b->n) return fail(TM_EINVAL, "bad query index");
+  if (!b->d_r) return fail(TM_EINVAL, "batch was created without TM_BATCH_KEEP_CORR");
+  *r = b->d_r + b->cq[i].r_off;
+  return TM_OK;
+}
+
+tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, int64_t* ws) {
+  if (!b) return fail(TM_EINVAL, "null batch");
+  if (launches) *launches = (b->W > 0 ? 1 : 0) + 1;
+  if (fold_ctas) *fold_ctas = b->nctas;
+  if (ws) *ws = b->ws_bytes;
+  return TM_OK;
+}
+
+tm_status tm_batch_device_error(tm_batch_t b, tm_stream_t stream, int32_t* err) {
+  if (!b || !err) return fail(TM_EINVAL, "null argument");
+  TM_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  TM_CUDA(cudaMemcpy(err, b->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return TM_OK;
+}
+
+tm_status tm_batch_destroy(tm_batch_t b) {
+  batch_free(b);
+  return TM_OK;
+}
+
+tm_status tm_match_batch(const tm_query* q, int32_t n, tm_result* out, tm_stream_t stream) {
+  tm_batch_t b = nullptr;
+  tm_status st = batch_build(q, n, 0, &b);
+  if (st != TM_OK) return st;
+  st = tm_batch_run(b, out, stream);
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  batch_free(b);
+  if (st != TM_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "tm_match_batch");
+  return TM_OK;
+}
+
+int32_t tm_crt_candidates(int64_t N, int32_t M1, int32_t M2, int32_t m1, int32_t m2, int64_t* out, int32_t cap) {
+  if (N < 1 || M1 < 1 || M2 < 1 || m1 < 0 || m2 < 0 || m1 >= M1 || m2 >= M2 || gcd64(M1, M2) != 1) return -1;
+  const CrtSet c = crt_intersect(N, M1, M2, mod_inverse(M1, M2), m1, m2);
+  std::vector<int64_t> v;
+  for (int64_t j = 0; j < c.nnat && int64_t(v.size()) < int64_t(cap) + 2; ++j) v.push_back(c.m0 + j * c.step);
+  for (int k = 0; k < c.nw; ++k) v.push_back(c.w[k]);
+  std::sort(v.begin(), v.end());
+  const int64_t total = c.nnat + c.nw;
+  for (int64_t k = 0; k < std::min<int64_t>(cap, int64_t(v.size())); ++k) out[k] = v[k];
+  return int32_t(std::min<int64_t>(total, INT32_MAX));
+}
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// Steps 8-9 of Algorithm 1 in closed form (Thm. 4, Chinese remainder).
+//
+// S_i = {(m_i + l M_i) mod N : 0 <= l < L_i}, L_i = ceil(N / M_i). An
+// element of S_i is either "natural" (m_i + l M_i < N, i.e. any v < N with
+// v = m_i mod M_i) or the single wrapped member w_i = m_i + (L_i-1) M_i - N,
+// present when w_i >= 0. Hence S1 ∩ S2 consists of
+//   - the naturals v < N with v = m1 (mod M1), v = m2 (mod M2): the
+//     progression m0 + j M1 M2, m0 the CRT solution in [0, M1 M2);
+//   - w1 when it lies in S2, and w2 when it lies in S1 (w_i is never
+//     congruent to m_i mod M_i, so it is never a natural of S_i).
+#pragma once
+
+#include <cstdint>
+
+namespace ftm {
+
+struct CrtSet {
+  int64_t m0;      // first natural solution (>= N when there is none)
+  int64_t step;    // M1 * M2
+  int64_t nnat;    // number of natural solutions below N
+  int64_t w[2];    // wrapped members in the intersection
+  int32_t nw;
+};
+
+#if defined(__CUDACC__)
+#define TM_HD __host__ __device__ __forceinline__
+#else
+#define TM_HD inline
+#endif
+
+// Modular inverse of a mod m (gcd(a, m) = 1, m >= 1), by extended Euclid.
+TM_HD int64_t mod_inverse(int64_t a, int64_t m) {
+  if (m == 1) return 0;
+  int64_t r0 = m, r1 = ((a % m) + m) % m, s0 = 0, s1 = 1;
+  while (r1 != 0) {
+    const int64_t qq = r0 / r1;
+    int64_t tmp = r0 - qq * r1; r0 = r1; r1 = tmp;
+    tmp = s0 - qq * s1; s0 = s1; s1 = tmp;
+  }
+  return ((s0 % m) + m) % m;
+}
+
+TM_HD CrtSet crt_intersect(int64_t N, int64_t M1, int64_t M2, int64_t inv, int64_t m1, int64_t m2) {
+  CrtSet c;
+  const int64_t L1 = (N + M1 - 1) / M1, L2 = (N + M2 - 1) / M2;
+  // m0 = m1 + M1 * k with M1 * k = m2 - m1 (mod M2)
+  const int64_t d = ((m2 - m1) % M2 + M2) % M2;
+  const int64_t k = (d * inv) % M2;
+  c.m0 = m1 + M1 * k;
+  c.step = M1 * M2;
+  c.nnat = c.m0 < N ? (N - 1 - c.m0) / c.step + 1 : 0;
+  const int64_t w1 = m1 + (L1 - 1) * M1 - N;
+  const int64_t w2 = m2 + (L2 - 1) * M2 - N;
+  c.nw = 0;
+  if (w1 >= 0 && (w1 % M2 == m2 || w1 == w2)) c.w[c.nw++] = w1;
+  if (w2 >= 0 && w2 != w1 && w2 % M1 == m1) c.w[c.nw++] = w2;
+  return c;
+}
+
+#undef TM_HD
+
+}  // namespace ftm

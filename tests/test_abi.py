@@ -1,0 +1,100 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+- libtm.so loads and exports every function include/tm.h declares;
+- the planner (Algorithm 1 step 2) accepts and rejects what the oracle does
+  and picks the same moduli;
+- the closed-form intersection of steps 8-9 equals the oracle's explicit
+  set intersection, exhaustively on small sizes.
+"""
+import os
+import re
+import subprocess
+
+import pytest
+
+import oracle.ftm as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tm():
+    from paper_1509_04863_gb300 import _build
+    _build.build()
+    import paper_1509_04863_gb300 as tm
+    tm.lib()
+    return tm
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "tm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("tm_plan_create", "tm_match", "tm_match_batch", "tm_batch_create", "tm_batch_run"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(tm):
+    from paper_1509_04863_gb300 import _build
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(tm_\w+)", out))
+    missing = [n for n in _declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in _declared_functions():
+        assert getattr(tm.lib(), n) is not None
+
+
+PLAN_CASES = [
+    # N, K, mode, M1, M2, ambig
+    (65536, 1024, "paper", 0, 0, False),
+    (1 << 24, 4096, "paper", 0, 0, False),
+    (1 << 22, 256, "paper", 0, 0, False),      # rejected: 256*257 <= N
+    (1 << 22, 256, "paper", 0, 0, True),
+    (1 << 24, 300, "auto", 0, 0, False),
+    (20000, 100, "auto", 0, 0, False),
+    (100, 10, "explicit", 12, 14, False),      # not co-prime
+    (100, 10, "explicit", 9, 16, False),       # M1 < K
+    (100, 10, "explicit", 11, 13, False),
+    (10, 11, "paper", 0, 0, False),            # K > N
+    (10, 10, "paper", 0, 0, False),            # M2 = N + 1
+    (1, 1, "auto", 0, 0, False),
+]
+
+
+@pytest.mark.parametrize("N,K,mode,M1,M2,ambig", PLAN_CASES)
+def test_planner_matches_oracle(tm, N, K, mode, M1, M2, ambig):
+    try:
+        want = O.plan(N, K, mode, M1, M2, ambig)
+    except ValueError:
+        want = None
+    if want is None:
+        with pytest.raises(tm.TMError) as e:
+            tm.Plan(N, K, "i8", mode, M1, M2, ambig)
+        assert e.value.status == tm.TM_EINVAL
+        return
+    p = tm.Plan(N, K, "i8", mode, M1, M2, ambig)
+    assert (p.info["M1"], p.info["M2"]) == want
+    assert p.info["L1"] == -(-N // want[0]) and p.info["L2"] == -(-N // want[1])
+    P = p.info["P"]
+    assert P >= max(want) + K - 1 and (P & (P - 1)) == 0 and P // 2 < max(want) + K - 1 or P == 1
+
+
+def test_planner_unsupported_sizes(tm):
+    with pytest.raises(tm.TMError) as e:
+        tm.Plan(1 << 26, 1 << 16, "i8", "paper")       # P = 2^17 > 16384
+    assert e.value.status == tm.TM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("N,M1,M2", [(19, 4, 5), (30, 5, 6), (31, 5, 7), (50, 7, 8), (20, 6, 7), (85, 9, 10),
+                                      (100, 4, 5), (64, 8, 9), (11, 11, 12), (7, 8, 9), (12, 5, 13)])
+def test_crt_closed_form_equals_set_intersection(tm, N, M1, M2):
+    """Steps 8-9: tm_crt_candidates (closed form, used on the device) lists
+    exactly S1 ∩ S2 as the oracle builds it, for every residue pair."""
+    for a in range(M1):
+        for b in range(M2):
+            want = sorted(O.candidate_set(a, M1, N) & O.candidate_set(b, M2, N))
+            assert tm.tm_crt_candidates(N, M1, M2, a, b) == want, (N, M1, M2, a, b)
