@@ -127,6 +127,25 @@ def gen_queries(rank: int):
     return W.batch64(seed=100 + 1000 * rank, n=QUERIES, N=N_SIG, K=K_T, flip_p=FLIP)
 
 
+def run_kernels_only(args):
+    """Small-workload driver for profiler captures: builds one batch of
+    --queries signals of 2^--log2n bytes and runs --steps full steps."""
+    import torch
+    import paper_1509_04863_gb300 as tm
+    qs = W.batch64(seed=100, n=args.queries, N=1 << args.log2n, K=args.K, flip_p=FLIP)
+    specs = [dict(x=torch.from_numpy(q.x).cuda(), t=torch.from_numpy(q.t).cuda(), N=q.N, K=q.K,
+                  xdtype="i8", mode="paper") for q in qs]
+    b = tm.Batch(specs)
+    out = tm.result_buffer(len(qs))
+    for _ in range(args.warmup + args.steps):
+        b.run(out)
+    torch.cuda.synchronize()
+    assert b.device_error() == 0
+    print(json.dumps({"kernels_only": True, "queries": args.queries, "log2n": args.log2n, "K": args.K,
+                      "steps": args.steps, "warmup": args.warmup}))
+    return 0
+
+
 def cpu_oracle_sample(queries, budget_s: float = 15.0, min_q: int = 2):
     from oracle import ftm as O
     t0 = time.perf_counter()
@@ -140,25 +159,33 @@ def cpu_oracle_sample(queries, budget_s: float = 15.0, min_q: int = 2):
     return done, dt
 
 
-def run_reference(args):
+def run_reference(args, budget_s: float = 150.0):
+    """The oracle timed on the host cores, one batch64 query per step. The
+    timed steps stop early once `budget_s` of oracle time has been spent, so
+    the run ends within a few minutes whatever --steps is."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
-    qs = W.batch64(seed=100, n=max(1, args.warmup + args.steps), N=N_SIG, K=K_T, flip_p=FLIP)
     from oracle import ftm as O
-    for q in qs[: args.warmup]:
+    for i in range(args.warmup):
+        O.match_query(W.planted_query(100 + i, N_SIG, K_T, "i8", flip_p=FLIP))
+    dt, done = 0.0, 0
+    for i in range(args.steps):
+        q = W.planted_query(100 + args.warmup + i, N_SIG, K_T, "i8", flip_p=FLIP)   # untimed
+        t0 = time.perf_counter()
         O.match_query(q)
-    t0 = time.perf_counter()
-    for q in qs[args.warmup: args.warmup + args.steps]:
-        O.match_query(q)
-    dt = time.perf_counter() - t0
-    v = args.steps / dt
+        dt += time.perf_counter() - t0
+        done += 1
+        if dt > budget_s:
+            break
+    v = done / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * dt / done,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
             "data": "synthetic", "config": WORKLOAD,
             "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one batch64 query per step ({args.steps} steps), numpy oracle, 1 thread"},
+                             "sample": f"{done} batch64 queries (one per step, of {args.steps} requested), "
+                                       "numpy oracle, 1 thread"},
             "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -311,11 +338,18 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="profiling driver: run the hot path only on a --queries x 2^--log2n batch")
+    ap.add_argument("--queries", type=int, default=64)
+    ap.add_argument("--log2n", type=int, default=22)
+    ap.add_argument("--K", type=int, default=K_T)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernels_only:
+        return run_kernels_only(args)
     return run_native(args)
 
 

@@ -99,8 +99,7 @@ tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t 
   for (int j = 0; j < 2; ++j) {
     pc.R[j] = int32_t(std::max<int64_t>(1, ceil_div(kFoldMinMp, pc.M[j])));
     pc.Mp[j] = pc.R[j] * pc.M[j];
-    const int64_t units = ceil_div(pc.Mp[j], 16);
-    if (ceil_div(units, kFoldModThreads) > kFoldJMax)
+    if (fold_units_per_lane(pc.Mp[j], j == 0 ? kFoldWarps0 : kFoldWarps1) > kFoldJMax)
       return fail(TM_EUNSUPPORTED, "modulus above 20480 not supported by the fold kernel");
   }
   pc.max_cand = ceil_div(N, m1 * m2) + 2;
@@ -151,6 +150,7 @@ struct tm_batch_s {
   int32_t nctas = 0;
   int64_t W = 0;
   int32_t maxP = 0;
+  int32_t jmax = 1;   // most 16-column units per fold consumer
   int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
   FoldQ* d_fq = nullptr;
   CorrQ* d_cq = nullptr;
@@ -265,6 +265,8 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
     f.stride = int32_t(pad16(p.Mp[0]) + pad16(p.Mp[1]));
     W += nb;
     max_share = std::min<int64_t>(max_share, int64_t(kFoldMaxRowsPerSlot - 2) * std::min(p.Mp[0], p.Mp[1]));
+    for (int j = 0; j < 2; ++j)
+      b->jmax = std::max<int32_t>(b->jmax, fold_units_per_lane(p.Mp[j], j == 0 ? kFoldWarps0 : kFoldWarps1));
   }
   b->W = W;
   int64_t nctas = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(W, 65536)));
@@ -360,7 +362,7 @@ tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
   FoldArgs a;
   a.q = b->d_fq; a.nq = b->n; a.nctas = b->nctas; a.W = b->W;
   a.partial = b->d_partial; a.err = b->d_err;
-  TM_CUDA(launch_fold_i8(a, s));
+  TM_CUDA(launch_fold_i8(a, b->jmax, s));
   return TM_OK;
 }
 

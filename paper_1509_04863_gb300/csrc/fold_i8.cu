@@ -5,18 +5,27 @@
 // Design: the signals of a batch are concatenated (16-byte-aligned prefixes)
 // into one byte space that is split into equal contiguous shares, one per
 // CTA. A producer warp streams a CTA's share through a ring of shared-memory
-// stages with bulk asynchronous copies (TMA, cp.async.bulk). Each consumer
-// thread owns fixed 16-column units of one modulus and, for every row of
-// that modulus crossing the stage, adds the unit's 16 bytes into packed
-// byte-lane counters (a byte holding -1 = 0xFF has bit 1 set, +1 = 0x01 has
-// not). Rows of the odd modulus start at every byte offset, so the unit is
-// re-aligned from two aligned 16-byte shared-memory reads with funnel
-// shifts. Byte lanes are widened into 16-bit lanes every few stages and
-// written out as int32 counts of -1 entries per (share, column) at the end
-// of a share. The correlation kernel turns counts into y (Eq. (2)) and adds
+// stages with bulk asynchronous copies (TMA, cp.async.bulk). Consumer lanes
+// own fixed 16-column units of one modulus, dealt out in chunks of 32
+// consecutive units per warp (8 warps for M1, 9 for M2, so that K and K+1
+// columns both come to one chunk per warp when K = 4096). For a stage holding
+// bytes [s, e) of a signal every lane of a warp walks the same rows l of its
+// modulus: rows strictly inside the stage take the fast path (one or two
+// aligned 16-byte shared-memory reads, re-aligned by funnel shifts by the
+// warp-uniform offset (l*Mp - s) mod 16), the first and last row the same
+// read followed by a byte mask for the part inside the stage. Stages carry
+// 16 bytes of slack on both sides so every read stays in bounds.
+//
+// A byte holding -1 (0xFF) has bit 1 set and +1 (0x01) has not, so
+// w & 0x02020202 adds 2 per -1 entry into four packed byte-lane counters.
+// A unit narrower than 16 columns (the last one of a row) still counts all
+// 16 bytes; the lanes past its width see bytes of the next row and are never
+// written out. Byte lanes are widened into 16-bit lanes every few stages and
+// written as int32 counts of -1 entries per (share, column) at the end of a
+// share. The correlation kernel turns the counts into y (Eq. (2)) and adds
 // the wrap-around term and the extension k >= M.
 //
-// To keep every consumer busy the fold runs with an effective modulus
+// To keep every lane busy the fold runs with an effective modulus
 // Mp = R*M >= 4096 (R = ceil(4096/M)); the correlation kernel sums the R
 // columns k + rM of the Mp-fold into column k of the M-fold.
 #include <cuda_runtime.h>
@@ -27,47 +36,56 @@
 namespace ftm {
 namespace {
 
-constexpr int kStageBytes = kFoldTile + 16;   // slack: the re-aligning read may run 15 bytes past
+constexpr int kStageBytes = kFoldTile + 32;   // 16 bytes of slack before and after the data
+constexpr uint32_t kNegBit = 0x02020202u;
 
 __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, uint32_t sh) {
   return __funnelshift_r(lo, hi, sh);
 }
 
-// Bytes [o, o+16) of a stage, o >= 0 and o + 16 <= valid bytes.
-__device__ __forceinline__ void load16(const uint8_t* buf, int o, uint32_t& w0, uint32_t& w1, uint32_t& w2,
-                                       uint32_t& w3) {
+// Bytes [o, o+16) of a stage as 4 words, -16 < o < valid + 16 (the slack
+// keeps both aligned reads inside the stage); r = o & 15 must be the same
+// in every lane of the warp.
+__device__ __forceinline__ void load16(const uint8_t* buf, int o, uint32_t (&w)[4]) {
   const uint4* p = reinterpret_cast<const uint4*>(buf + (o & ~15));
   const uint4 a = p[0];
   const int r = o & 15;
   if (r == 0) {
-    w0 = a.x; w1 = a.y; w2 = a.z; w3 = a.w;
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
     return;
   }
   const uint4 b = p[1];
   const uint32_t sh = uint32_t(r & 3) * 8u;
   switch (r >> 2) {
-    case 0: w0 = fsr(a.x, a.y, sh); w1 = fsr(a.y, a.z, sh); w2 = fsr(a.z, a.w, sh); w3 = fsr(a.w, b.x, sh); break;
-    case 1: w0 = fsr(a.y, a.z, sh); w1 = fsr(a.z, a.w, sh); w2 = fsr(a.w, b.x, sh); w3 = fsr(b.x, b.y, sh); break;
-    case 2: w0 = fsr(a.z, a.w, sh); w1 = fsr(a.w, b.x, sh); w2 = fsr(b.x, b.y, sh); w3 = fsr(b.y, b.z, sh); break;
-    default: w0 = fsr(a.w, b.x, sh); w1 = fsr(b.x, b.y, sh); w2 = fsr(b.y, b.z, sh); w3 = fsr(b.z, b.w, sh); break;
+    case 0: w[0] = fsr(a.x, a.y, sh); w[1] = fsr(a.y, a.z, sh); w[2] = fsr(a.z, a.w, sh); w[3] = fsr(a.w, b.x, sh); break;
+    case 1: w[0] = fsr(a.y, a.z, sh); w[1] = fsr(a.z, a.w, sh); w[2] = fsr(a.w, b.x, sh); w[3] = fsr(b.x, b.y, sh); break;
+    case 2: w[0] = fsr(a.z, a.w, sh); w[1] = fsr(a.w, b.x, sh); w[2] = fsr(b.x, b.y, sh); w[3] = fsr(b.y, b.z, sh); break;
+    default: w[0] = fsr(a.w, b.x, sh); w[1] = fsr(b.x, b.y, sh); w[2] = fsr(b.y, b.z, sh); w[3] = fsr(b.z, b.w, sh); break;
   }
 }
 
-// Bytes i < width of the unit at stage offset o that lie inside [0, len);
-// everything else reads as 0 (counts nothing).
-__device__ __forceinline__ void load_masked(const uint8_t* buf, int o, int len, int width, uint32_t& w0,
-                                            uint32_t& w1, uint32_t& w2, uint32_t& w3) {
-  w0 = w1 = w2 = w3 = 0u;
-  const int i0 = o < 0 ? -o : 0;
-  const int i1 = min(width, len - o);
-  for (int i = i0; i < i1; ++i) {
-    const uint32_t v = uint32_t(buf[o + i]) << (8 * (i & 3));
-    const int k = i >> 2;
-    w0 |= (k == 0) ? v : 0u;
-    w1 |= (k == 1) ? v : 0u;
-    w2 |= (k == 2) ? v : 0u;
-    w3 |= (k == 3) ? v : 0u;
-  }
+// Low n bytes of a word set (n clamped to [0, 4]).
+__device__ __forceinline__ uint32_t low_bytes(int n) {
+  return n <= 0 ? 0u : n >= 4 ? 0xFFFFFFFFu : (1u << (8 * n)) - 1u;
+}
+
+// Counts the bytes of [o, o+16) that lie inside the stage [0, len).
+__device__ __forceinline__ void count_masked(const uint8_t* buf, int o, int len, uint32_t (&c8)[4]) {
+  uint32_t w[4];
+  load16(buf, o, w);
+  const int lo = -o, hi = len - o;   // valid byte positions lo <= i < hi
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c8[k] += w[k] & (kNegBit & low_bytes(hi - 4 * k) & ~low_bytes(lo - 4 * k));
+}
+
+__device__ __forceinline__ void count(uint32_t (&c8)[4], const uint32_t (&w)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c8[i] += w[i] & kNegBit;
+}
+
+__device__ __forceinline__ void count2(uint32_t (&c8)[4], const uint32_t (&w)[4], const uint32_t (&v)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c8[i] += (w[i] & kNegBit) + (v[i] & kNegBit);
 }
 
 // First query whose byte range ends after `pos`.
@@ -80,29 +98,27 @@ __device__ __forceinline__ int first_query(const FoldQ* q, int nq, int64_t pos) 
   return lo;
 }
 
-// One consumer thread's work on one share [lo, hi) (query-local bytes) of a
-// signal, for J units of the effective modulus Mp: units t + 256 j, j < J.
-// Returns false when a bounded wait ran out.
+// One consumer lane's work on one share [lo, hi) (signal-local bytes) for
+// the effective modulus Mp: units lane + 32 (wig + W j), j < J, where wig is
+// the warp's index among the W warps of its modulus. Returns false when a
+// bounded wait ran out.
 template <int J>
 __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* full, uint64_t* empty, int lo, int hi,
-                                              int Mp, int tm, int32_t* dst, uint32_t& it) {
+                                              int Mp, int W, int wig, int32_t* dst, uint32_t& it) {
   const int lane = threadIdx.x & 31;
   const int G = (Mp + 15) >> 4;
   // Stages between widenings: a unit meets at most kFoldTile/Mp + 2 rows
   // per stage and a byte lane holds up to 127 of them (2 per -1 entry).
   const int F = max(1, 127 / (kFoldTile / Mp + 2));
 
-  int pos[J], wid[J];
+  int col[J];
+  bool live[J];
   uint32_t c8[J][4], c16[J][8];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
-    const int g = tm + j * kFoldModThreads;
-    const int col = 16 * g;
-    wid[j] = g < G ? min(16, Mp - col) : 0;
-    // first row whose unit reaches past byte `lo`
-    const int need = lo - col - wid[j] + 1;
-    const int l = need > 0 ? (need + Mp - 1) / Mp : 0;
-    pos[j] = l * Mp + col;
+    const int g = lane + 32 * (wig + W * j);
+    col[j] = 16 * g;
+    live[j] = g < G;
 #pragma unroll
     for (int i = 0; i < 4; ++i) c8[j][i] = 0u;
 #pragma unroll
@@ -115,26 +131,39 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
     // every lane waits; the warp gives up together so no lane is left
     // behind at the __syncwarp below
     if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (it / kFoldStages) & 1u))) return false;
-    const uint8_t* buf = smem + st * kStageBytes;
+    const uint8_t* buf = smem + st * kStageBytes + 16;
     const int len = min(kFoldTile, hi - s);
-    const int e = s + len;
+    const int l0 = s / Mp;               // rows meeting [s, s+len)
+    const int l1 = (s + len - 1) / Mp;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      if (wid[j] == 0) continue;
-      int p = pos[j];
-      while (p < e) {
-        const int o = p - s;
-        uint32_t w0, w1, w2, w3;
-        if (o >= 0 && o + 16 <= len && wid[j] == 16) load16(buf, o, w0, w1, w2, w3);
-        else load_masked(buf, o, len, wid[j], w0, w1, w2, w3);
-        c8[j][0] += w0 & 0x02020202u;
-        c8[j][1] += w1 & 0x02020202u;
-        c8[j][2] += w2 & 0x02020202u;
-        c8[j][3] += w3 & 0x02020202u;
-        if (p + wid[j] > e) break;   // unit continues in the next stage
-        p += Mp;
+      if (!live[j]) continue;
+      // first row: the unit may start before the stage (or end after it)
+      {
+        const int o = l0 * Mp + col[j] - s;
+        if (o > -16 && o < len) count_masked(buf, o, len, c8[j]);
       }
-      pos[j] = p;
+      if (l1 > l0) {
+        // rows strictly inside the stage: all 16 bytes are present (a narrow
+        // last unit reads at most 15 bytes of slack, counted in lanes that
+        // are never written)
+        int l = l0 + 1;
+        for (; l + 1 < l1; l += 2) {
+          uint32_t w[4], v[4];
+          const int o = l * Mp + col[j] - s;
+          load16(buf, o, w);
+          load16(buf, o + Mp, v);
+          count2(c8[j], w, v);
+        }
+        if (l < l1) {
+          uint32_t w[4];
+          load16(buf, l * Mp + col[j] - s, w);
+          count(c8[j], w);
+        }
+        // last row: the unit may run past the stage
+        const int o = l1 * Mp + col[j] - s;
+        if (o < len) count_masked(buf, o, len, c8[j]);
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
@@ -156,7 +185,7 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
   // Widen the remainder and write this share's counts of -1 entries.
 #pragma unroll
   for (int j = 0; j < J; ++j) {
-    if (wid[j] == 0) continue;
+    if (!live[j]) continue;
     int32_t cnt[16];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -167,9 +196,9 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
       cnt[4 * i + 1] = int32_t((e1 & 0xFFFFu) >> 1);
       cnt[4 * i + 3] = int32_t(e1 >> 17);
     }
-    const int col = 16 * (tm + j * kFoldModThreads);
-    if (wid[j] == 16) {
-      int4* d4 = reinterpret_cast<int4*>(dst + col);
+    const int width = min(16, Mp - col[j]);
+    if (width == 16) {
+      int4* d4 = reinterpret_cast<int4*>(dst + col[j]);
       d4[0] = make_int4(cnt[0], cnt[1], cnt[2], cnt[3]);
       d4[1] = make_int4(cnt[4], cnt[5], cnt[6], cnt[7]);
       d4[2] = make_int4(cnt[8], cnt[9], cnt[10], cnt[11]);
@@ -177,12 +206,15 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
     } else {
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        if (i < wid[j]) dst[col + i] = cnt[i];
+        if (i < width) dst[col[j] + i] = cnt[i];
     }
   }
   return true;
 }
 
+// JMAX: the most units any lane of the launch needs (3 covers moduli up to
+// 12288; larger moduli use the 5-unit instantiation).
+template <int JMAX>
 __global__ void __launch_bounds__(kFoldThreads, 1) fold_i8_kernel(const FoldArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kFoldStages * kStageBytes);
@@ -210,11 +242,13 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_i8_kernel(const FoldArgs
       uint32_t it = 0;
       bool ok = true;
       for (int qi = q0; qi < a.nq && ok; ++qi) {
-        const FoldQ Q = a.q[qi];
-        if (Q.goff >= ce) break;
-        if (Q.nbytes == 0) continue;
-        const int64_t lo = max(cb, Q.goff) - Q.goff;
-        const int64_t hi = min(ce, Q.goff + Q.nbytes) - Q.goff;
+        const int64_t goff = a.q[qi].goff;
+        const int32_t nbytes = a.q[qi].nbytes;
+        const uint8_t* x = a.q[qi].x;
+        if (goff >= ce) break;
+        if (nbytes == 0) continue;
+        const int64_t lo = max(cb, goff) - goff;
+        const int64_t hi = min(ce, goff + nbytes) - goff;
         for (int64_t s = lo; s < hi; s += kFoldTile) {
           const uint32_t st = it % kFoldStages;
           if (it >= kFoldStages && !mbar_wait(&empty[st], ((it / kFoldStages) & 1u) ^ 1u)) {
@@ -223,7 +257,7 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_i8_kernel(const FoldArgs
           }
           const uint32_t len = uint32_t(hi - s < kFoldTile ? hi - s : int64_t(kFoldTile));
           mbar_arrive_expect_tx(&full[st], len);
-          bulk_load(smem + st * kStageBytes, Q.x + s, len, &full[st], pol);
+          bulk_load(smem + st * kStageBytes + 16, x + s, len, &full[st], pol);
           ++it;
         }
       }
@@ -236,25 +270,27 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_i8_kernel(const FoldArgs
   }
 
   // ---------------------------------------------------------------- consumers
-  const int m = tid >> 8;           // modulus handled by this thread
-  const int tm = tid & (kFoldModThreads - 1);
+  const int warp = tid >> 5;
+  const int m = warp < kFoldWarps0 ? 0 : 1;         // modulus handled by this warp
+  const int W = m == 0 ? kFoldWarps0 : kFoldWarps1;
+  const int wig = m == 0 ? warp : warp - kFoldWarps0;
   uint32_t it = 0;
   bool ok = true;
   for (int qi = q0; qi < a.nq && ok; ++qi) {
-    const FoldQ& Q = a.q[qi];
-    if (Q.goff >= ce) break;
-    if (Q.nbytes == 0) continue;
-    const int lo = int(max(cb, Q.goff) - Q.goff);
-    const int hi = int(min(ce, Q.goff + Q.nbytes) - Q.goff);
-    const int G = (Q.Mp[m] + 15) >> 4;
-    int32_t* dst = a.partial + Q.part + int64_t(blockIdx.x - Q.first_cta) * Q.stride + Q.moff[m];
-    switch ((G + kFoldModThreads - 1) / kFoldModThreads) {
-      case 1: ok = consume_share<1>(smem, full, empty, lo, hi, Q.Mp[m], tm, dst, it); break;
-      case 2: ok = consume_share<2>(smem, full, empty, lo, hi, Q.Mp[m], tm, dst, it); break;
-      case 3: ok = consume_share<3>(smem, full, empty, lo, hi, Q.Mp[m], tm, dst, it); break;
-      case 4: ok = consume_share<4>(smem, full, empty, lo, hi, Q.Mp[m], tm, dst, it); break;
-      default: ok = consume_share<kFoldJMax>(smem, full, empty, lo, hi, Q.Mp[m], tm, dst, it); break;
-    }
+    const int64_t goff = a.q[qi].goff;
+    const int32_t nbytes = a.q[qi].nbytes;
+    if (goff >= ce) break;
+    if (nbytes == 0) continue;
+    const int lo = int(max(cb, goff) - goff);
+    const int hi = int(min(ce, goff + nbytes) - goff);
+    const int Mp = a.q[qi].Mp[m];
+    int32_t* dst = a.partial + a.q[qi].part + int64_t(blockIdx.x - a.q[qi].first_cta) * a.q[qi].stride +
+                   a.q[qi].moff[m];
+    const int J = fold_units_per_lane(Mp, W);
+    if (J <= 1) ok = consume_share<1>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    else if (J == 2) ok = consume_share<2>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    else if (J == 3 || JMAX == 3) ok = consume_share<3>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    else ok = consume_share<(JMAX > 3 ? JMAX : 3)>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
   }
   if (!ok) atomicOr(a.err, 1);
 }
@@ -263,12 +299,15 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_i8_kernel(const FoldArgs
 
 cudaError_t fold_configure() {
   const int smem = kFoldStages * kStageBytes + 2 * kFoldStages * 8;
-  return cudaFuncSetAttribute(fold_i8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(fold_i8_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fold_i8_kernel<kFoldJMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t launch_fold_i8(const FoldArgs& a, cudaStream_t s) {
+cudaError_t launch_fold_i8(const FoldArgs& a, int jmax, cudaStream_t s) {
   const int smem = kFoldStages * kStageBytes + 2 * kFoldStages * 8;
-  fold_i8_kernel<<<a.nctas, kFoldThreads, smem, s>>>(a);
+  if (jmax <= 3) fold_i8_kernel<3><<<a.nctas, kFoldThreads, smem, s>>>(a);
+  else fold_i8_kernel<kFoldJMax><<<a.nctas, kFoldThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

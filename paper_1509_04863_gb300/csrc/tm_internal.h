@@ -15,19 +15,28 @@ constexpr int64_t kMaxQueryBytes = (int64_t(1) << 31) - (int64_t(1) << 16);
 
 // ---------------------------------------------------------------- fold kernel (step 3)
 // Each CTA streams a contiguous, equal share of the concatenation of all
-// signals' 16-byte-aligned prefixes. Warps 0-7 accumulate the M1 fold,
-// warps 8-15 the M2 fold, warp 16 issues bulk copies into a ring of
+// signals' 16-byte-aligned prefixes. Consumer warps 0-7 accumulate the M1
+// fold, warps 8-16 the M2 fold (the odd modulus K+1 has one more 16-column
+// unit per row than K), warp 17 issues bulk copies into a ring of
 // shared-memory stages.
-constexpr int kFoldModThreads = 256;                 // consumers per modulus
-constexpr int kFoldConsumers = 2 * kFoldModThreads;  // 16 warps
+constexpr int kFoldWarps0 = 8;                       // consumer warps of modulus M1
+constexpr int kFoldWarps1 = 9;                       // consumer warps of modulus M2
+constexpr int kFoldConsumers = 32 * (kFoldWarps0 + kFoldWarps1);
 constexpr int kFoldThreads = kFoldConsumers + 32;    // + producer warp
-constexpr int kFoldStages = 4;
-constexpr int kFoldTile = 32768;                     // bytes per stage
-constexpr int kFoldJMax = 5;                         // 16-column units per consumer
+constexpr int kFoldStages = 3;
+constexpr int kFoldTile = 65536;                     // bytes per stage
+constexpr int kFoldJMax = 5;                         // 16-column units per consumer lane
 constexpr int kFoldMinMp = 4096;                     // effective modulus floor
+constexpr int kFoldMaxMp = 32 * kFoldWarps0 * kFoldJMax * 16;   // 20480
 // A consumer's 16-bit lane counters hold twice the number of -1 entries;
 // the host caps a CTA's share so that no column sees more rows than this.
 constexpr int kFoldMaxRowsPerSlot = 32000;
+
+// 16-column units per lane needed for an effective modulus Mp on `warps` warps.
+__host__ __device__ inline int fold_units_per_lane(int Mp, int warps) {
+  const int chunks = ((Mp + 15) / 16 + 31) / 32;
+  return (chunks + warps - 1) / warps;
+}
 
 struct FoldQ {
   const uint8_t* x;   // signal bytes, 16-byte aligned
@@ -96,7 +105,7 @@ struct CorrArgs {
 };
 
 // ---------------------------------------------------------------- kernels' host launchers
-cudaError_t launch_fold_i8(const FoldArgs& a, cudaStream_t s);
+cudaError_t launch_fold_i8(const FoldArgs& a, int jmax, cudaStream_t s);
 cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s);
 cudaError_t fold_configure();   // one-time kernel attributes
 cudaError_t corr_configure();
