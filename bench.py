@@ -63,18 +63,14 @@ def profile_traffic(kernel_src: str, summary: str):
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
+    import re
     sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()[:16]
-    vals = {}
-    for line in open(path):
-        if ":" in line and line.strip().startswith(("kernel_source_sha", "dram_bytes_per_launch_full")):
-            k, v = line.split(":", 1)
-            vals[k.strip().lstrip("-* ").strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha") != sha:
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha:\s*`?([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_bytes or m_sha.group(1) != sha:
         return None
-    try:
-        return float(vals["dram_bytes_per_launch_full"])
-    except (KeyError, ValueError):
-        return None
+    return float(m_bytes.group(1))
 
 
 class ClockSampler:

@@ -15,14 +15,15 @@
 //  d. Step 7: argmax of r_j over j < M_j. The FFT values carry rounding
 //     error |dr| <= delta (a normwise bound, below); every j with
 //     r_j >= max - 2 delta is rescored exactly from the folds (integers in
-//     int64, reals in fp64), which makes the chosen index exact.
+//     int32/int64, reals in fp64), which makes the chosen index exact.
 //  e. Steps 8-9: closed-form intersection (crt.h); several members are
 //     resolved by their exact (Tx)_m.
 //
 // FFT: Stockham autosort, radix 16 (plus one radix 2/4/8 pass), shared
 // memory resident (P <= 16384 complex entries, padded one entry per 16 to
-// avoid bank conflicts), twiddles from a table W_{16384}^m computed on the
-// host in double precision.
+// avoid bank conflicts). Twiddles W_P^m, m < P/2, are copied once per CTA
+// into shared memory from a table computed on the host in double precision
+// (W_P^{m+P/2} = -W_P^m gives the other half).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -93,11 +94,17 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
   }
 }
 
+// W_P^e for 0 <= e < P from the half table tw[m] = W_P^m, m < P/2.
+__device__ __forceinline__ float2 twiddle(const float2* tw, int e, int halfP) {
+  const float2 w = tw[e & (halfP - 1)];
+  return (e & halfP) ? make_float2(-w.x, -w.y) : w;
+}
+
 // One Stockham pass of radix R over P points whose sub-transforms of length
 // Ns are done: butterfly j takes x[j + r P/R], twiddles by W_{Ns R}^{r (j mod Ns)},
 // and writes to (j - j mod Ns) R + j mod Ns + r Ns.
 template <int R>
-__device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift, const float2* __restrict__ tw) {
+__device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift, const float2* tw) {
   constexpr int NB = (kPMax / R + kCorrThreads - 1) / kCorrThreads;
   const int nbf = P / R;
   float2 v[NB][R];
@@ -110,7 +117,7 @@ __device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift
       for (int r = 0; r < R; ++r) v[b][r] = buf[pad_idx(j + r * nbf)];
       if (Ns > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], __ldg(&tw[(r * k) << twshift]));
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], twiddle(tw, (r * k) << twshift, P >> 1));
       }
       dft<R>(v[b]);
     }
@@ -129,32 +136,34 @@ __device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift
   __syncthreads();
 }
 
-// Forward FFT of length 2^logP in place (padded layout, natural order).
-__device__ void fft(float2* buf, int logP, const float2* __restrict__ tw) {
+// Forward FFT of length 2^logP in place (padded layout, natural order);
+// tw holds W_P^m for m < P/2.
+__device__ void fft(float2* buf, int logP, const float2* tw) {
   const int P = 1 << logP;
   int logNs = 0;
   const int first = logP & 3;
   if (first) {
-    const int twshift = kLogPMax - first;
+    const int twshift = logP - first;
     if (first == 1) fft_pass<2>(buf, P, 1, twshift, tw);
     else if (first == 2) fft_pass<4>(buf, P, 1, twshift, tw);
     else fft_pass<8>(buf, P, 1, twshift, tw);
     logNs = first;
   }
   while (logNs < logP) {
-    fft_pass<16>(buf, P, 1 << logNs, kLogPMax - (logNs + 4), tw);
+    fft_pass<16>(buf, P, 1 << logNs, logP - (logNs + 4), tw);
     logNs += 4;
   }
 }
 
 // ---------------------------------------------------------------- block reductions
-__device__ __forceinline__ double block_sum(double v, double* red) {
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = 0;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) s += red[w];
   return s;
@@ -168,6 +177,17 @@ __device__ __forceinline__ int block_and(int v, int* redi) {
   int s = 1;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) s &= redi[w];
+  return s;
+}
+
+__device__ __forceinline__ int block_max(int v, int* redi) {
+  v = __reduce_max_sync(0xffffffffu, v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) redi[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int s = redi[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) s = max(s, redi[w]);
   return s;
 }
 
@@ -190,15 +210,6 @@ __device__ __forceinline__ void block_argmax(float& v, int& i, float* redv, int*
   for (int w = 1; w < kWarps; ++w) better(v, i, redv[w], redi[w]);
 }
 
-__device__ __forceinline__ void warp_argmaxd(double& v, int64_t& i) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-    const int64_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
-    betterd(v, i, v2, i2);
-  }
-}
-
 // ---------------------------------------------------------------- signal access
 struct Sig {
   const void* x;
@@ -211,23 +222,37 @@ struct Sig {
       default: return static_cast<const float*>(x)[n];
     }
   }
-  __device__ __forceinline__ int ival(int64_t n) const { return int(val(n)); }
+  __device__ __forceinline__ int ival(int64_t n) const {
+    if (dtype == TM_I8_PM1) return (static_cast<const uint8_t*>(x)[n] & 2u) ? -1 : 1;
+    return ((static_cast<const uint8_t*>(x)[n >> 3] >> (n & 7)) & 1u) ? 1 : -1;
+  }
 };
 
 __device__ __forceinline__ bool is_int_dtype(int d) { return d == TM_I8_PM1 || d == TM_BITS_PM1; }
 
-// Exact sum_{i<K} t_i * v(i) over one warp; v integer-valued when `integral`.
+// Exact sum_{i<K} t_i * v(i) over one warp: integer terms in int32 when
+// `small` guarantees no partial sum reaches 2^31, else int64; reals in fp64.
 template <class F>
-__device__ __forceinline__ double warp_dot(const float* __restrict__ t, int K, bool integral, F v) {
+__device__ __forceinline__ double warp_dot(const float* __restrict__ t, int K, bool integral, bool small, F v) {
   const int lane = threadIdx.x & 31;
+  if (integral && small) {
+    int acc = 0;
+#pragma unroll 4
+    for (int i = lane; i < K; i += 32) acc += __float2int_rn(t[i]) * int(v(i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return double(acc);
+  }
   if (integral) {
     long long acc = 0;
+#pragma unroll 4
     for (int i = lane; i < K; i += 32) acc += (long long)__float2int_rn(t[i]) * (long long)v(i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return double(acc);
   }
   double acc = 0.0;
+#pragma unroll 4
   for (int i = lane; i < K; i += 32) acc = fma(double(t[i]), double(v(i)), acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -236,7 +261,9 @@ __device__ __forceinline__ double warp_dot(const float* __restrict__ t, int K, b
 
 __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a) {
   extern __shared__ __align__(16) float2 sbuf[];
-  __shared__ double red[kWarps];
+  __shared__ float redf[kWarps];
+  __shared__ long long redl[kWarps];
+  __shared__ double redd[kWarps];
   __shared__ float redv[kWarps];
   __shared__ int redi[kWarps];
   __shared__ int cand[2][kCandCap];
@@ -248,60 +275,94 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   __shared__ int s_flags;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const CorrQ Q = a.q[a.order[blockIdx.x]];
   const int qi = a.order[blockIdx.x];
+  const CorrQ Q = a.q[qi];
   const int P = Q.P, logP = Q.logP, K = Q.K;
   const int64_t N = Q.N;
   const Sig sig{Q.x, Q.xdtype};
   const bool ints = is_int_dtype(Q.xdtype);
   const float* __restrict__ t = Q.t;
   const int npad = P + (P >> 4);
+  const int halfP = P >> 1;
+  float2* tw = sbuf + npad;   // W_P^m, m < P/2
   if (tid == 0) s_flags = 0;
 
-  // ------------------------------------------------ a. template spectrum
-  double t1 = 0.0, t2 = 0.0;
+  // ------------------------------------------------ twiddles, a. template spectrum
+  {
+    const int stride = kPMax >> logP;
+    for (int m = tid; m < halfP; m += kCorrThreads) tw[m] = __ldg(&a.tw[m * stride]);
+  }
+  float t1 = 0.f, t2 = 0.f;
   int tint = 1;
   for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int k = tid; k < K; k += kCorrThreads) {
     const float v = t[k];
-    sbuf[pad_idx(k)] = make_float2(v, 0.f);
-    t1 += fabs(double(v));
-    t2 += double(v) * double(v);
+    sbuf[pad_idx(k)].x = v;
+    t1 += fabsf(v);
+    t2 = fmaf(v, v, t2);
     tint &= (v == rintf(v) && fabsf(v) <= 1048576.f) ? 1 : 0;
   }
-  __syncthreads();
-  t1 = block_sum(t1, red);
-  t2 = sqrt(block_sum(t2, red));
+  t1 = block_sum(t1, redf);
+  t2 = sqrtf(block_sum(t2, redf));
   const bool t_integral = block_and(tint, redi) != 0;
-  fft(sbuf, logP, a.tw);
-  float2* spec = a.spec + Q.spec_off;
+  fft(sbuf, logP, tw);
+  // the spectrum stays in shared memory when the launch left room for it
+  float2* spec = (npad + halfP + P) * int(sizeof(float2)) <= a.smem_bytes ? tw + halfP : a.spec + Q.spec_off;
   for (int k = tid; k < P; k += kCorrThreads) spec[k] = sbuf[pad_idx(k)];
   __syncthreads();
 
   // ------------------------------------------------ b. folds
   int* ib = reinterpret_cast<int*>(sbuf);     // int view: entry e -> ib[2e] (M1), ib[2e+1] (M2)
   float* fb = reinterpret_cast<float*>(sbuf);
-  for (int k = tid; k < 2 * npad; k += kCorrThreads) ib[k] = 0;
+  for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int j = 0; j < 2; ++j) {
     const int M = Q.M[j], Rr = Q.R[j];
-    const int64_t L = Q.L[j];
-    const int64_t Rw = N - (L - 1) * M;    // length of the last (partial) row
+    const int L = int(Q.L[j]);
+    const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
     const int32_t* part = a.partial + Q.part + Q.moff[j];
-    for (int k = tid; k < M; k += kCorrThreads) {
-      if (ints) {
-        // partial slots hold counts of -1 entries per column of the Mp-fold
-        int neg = 0;
-        for (int s = 0; s < Q.nslots; ++s) {
-          const int32_t* ps = part + int64_t(s) * Q.stride;
-          for (int r = 0; r < Rr; ++r) neg += ps[k + r * M];
+    if (ints) {
+      // Partial slots hold counts of -1 entries per column kp < Mp of the
+      // Mp-fold; column k of the M-fold gathers kp = k + r M, r < R. Four
+      // columns per pass keep enough loads in flight.
+      const int Mp = Rr * M;
+      for (int k0 = 4 * tid; k0 < Mp; k0 += 4 * kCorrThreads) {
+        int4 c = make_int4(0, 0, 0, 0);
+        if (k0 + 4 <= Mp) {
+          for (int s = 0; s < Q.nslots; ++s) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(part + int64_t(s) * Q.stride + k0));
+            c.x += v.x; c.y += v.y; c.z += v.z; c.w += v.w;
+          }
+        } else {
+          for (int s = 0; s < Q.nslots; ++s) {
+            const int32_t* ps = part + int64_t(s) * Q.stride + k0;
+            c.x += ps[0];
+            if (k0 + 1 < Mp) c.y += ps[1];
+            if (k0 + 2 < Mp) c.z += ps[2];
+          }
         }
-        const int64_t nk = (k < N) ? (N - 1 - k) / M + 1 : 0;   // entries n < N, n = k mod M
-        int yk = int(nk) - 2 * neg;
+        const int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int kp = k0 + i;
+          if (kp < Mp && cc[i] != 0) {
+            const int e = 2 * pad_idx(Rr == 1 ? kp : kp % M) + j;
+            if (Rr == 1) ib[e] = cc[i];
+            else atomicAdd(&ib[e], cc[i]);
+          }
+        }
+      }
+      __syncthreads();
+      for (int k = tid; k < M; k += kCorrThreads) {
+        // entries n < N with n = k (mod M): L of them for k < Rw, else L-1
+        const int e = 2 * pad_idx(k) + j;
+        int yk = (L - 1 + (k < Rw ? 1 : 0)) - 2 * ib[e];
         if (k >= Rw) yk += sig.ival(k - Rw);
-        ib[2 * pad_idx(k) + j] = yk;
-      } else {
+        ib[e] = yk;
+      }
+    } else {
+      for (int k = tid; k < M; k += kCorrThreads) {
         // partial slots hold fp32 column sums, added in a fixed order
         const float* pf = reinterpret_cast<const float*>(part);
         float yk = 0.f;
@@ -319,7 +380,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
     for (int64_t n = Q.nelem16; n < N; ++n) {
       for (int j = 0; j < 2; ++j) {
         const int e = 2 * pad_idx(int(n % Q.M[j])) + j;
-        // the count n_k already includes this entry as +1
+        // the count L or L-1 above already includes this entry as +1
         if (ints) ib[e] -= sig.ival(n) < 0 ? 2 : 0;
         else fb[e] += sig.val(n);
       }
@@ -331,43 +392,56 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
     const int64_t LM = Q.L[j] * M;
     for (int i = tid; i < K - 1; i += kCorrThreads) {
       const int e = 2 * pad_idx(M + i) + j, e0 = 2 * pad_idx(i) + j;
-      if (ints) ib[e] = ib[e0] - sig.ival(i) + sig.ival((i + LM) % N);
-      else fb[e] = fb[e0] - sig.val(i) + sig.val((i + LM) % N);
+      int64_t w = i + LM - N;   // LM >= N and i + LM - N < 2M, so one reduction is rare
+      if (w >= N) w %= N;
+      if (ints) ib[e] = ib[e0] - sig.ival(i) + sig.ival(w);
+      else fb[e] = fb[e0] - sig.val(i) + sig.val(w);
     }
   }
   __syncthreads();
-  // export exact folds, convert to float, norms of z
-  double z1 = 0.0, z2 = 0.0;
-  {
+  // export exact folds, convert to float, norms of z (exact integers for +-1
+  // signals; fp32 sums for reals)
+  float z1 = 0.f, z2 = 0.f;
+  int maxy = 0;
+  if (ints) {
+    long long s1 = 0, s2 = 0;
     int32_t* yi = static_cast<int32_t*>(a.y) + Q.y_off;
-    float* yf = static_cast<float*>(a.y) + Q.y_off;
     for (int k = tid; k < P; k += kCorrThreads) {
       const int e = 2 * pad_idx(k);
-      float v0, v1;
-      if (ints) {
-        const int i0 = ib[e], i1 = ib[e + 1];
-        yi[k] = i0; yi[P + k] = i1;
-        v0 = float(i0); v1 = float(i1);
-        sbuf[pad_idx(k)] = make_float2(v0, v1);
-      } else {
-        v0 = fb[e]; v1 = fb[e + 1];
-        yf[k] = v0; yf[P + k] = v1;
-      }
-      z1 += fabs(double(v0)) + fabs(double(v1));
-      z2 += double(v0) * v0 + double(v1) * v1;
+      const int v0 = ib[e], v1 = ib[e + 1];
+      yi[k] = v0;
+      yi[P + k] = v1;
+      sbuf[pad_idx(k)] = make_float2(float(v0), float(v1));
+      s1 += abs(v0) + abs(v1);
+      s2 += (long long)v0 * v0 + (long long)v1 * v1;
+      maxy = max(maxy, max(abs(v0), abs(v1)));
     }
+    s1 = block_sum(s1, redl);
+    s2 = block_sum(s2, redl);
+    z1 = float(s1);
+    z2 = sqrtf(float(s2));
+    maxy = block_max(maxy, redi);
+  } else {
+    float* yf = static_cast<float*>(a.y) + Q.y_off;
+    for (int k = tid; k < P; k += kCorrThreads) {
+      const float2 v = sbuf[pad_idx(k)];
+      yf[k] = v.x;
+      yf[P + k] = v.y;
+      z1 += fabsf(v.x) + fabsf(v.y);
+      z2 = fmaf(v.x, v.x, fmaf(v.y, v.y, z2));
+    }
+    z1 = block_sum(z1, redf);
+    z2 = sqrtf(block_sum(z2, redf));
   }
-  z1 = block_sum(z1, red);
-  z2 = sqrt(block_sum(z2, red));
 
   // ------------------------------------------------ c. correlation by FFT
-  fft(sbuf, logP, a.tw);
+  fft(sbuf, logP, tw);
   for (int k = tid; k < P; k += kCorrThreads) {
     const float2 z = sbuf[pad_idx(k)], T = spec[k];
     sbuf[pad_idx(k)] = make_float2(T.x * z.x + T.y * z.y, T.y * z.x - T.x * z.y);   // T conj(Z)
   }
   __syncthreads();
-  fft(sbuf, logP, a.tw);
+  fft(sbuf, logP, tw);
   const float invP = 1.0f / float(P);   // exact: P is a power of two
 
   if (a.r != nullptr && Q.r_off >= 0) {
@@ -382,10 +456,15 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   // log2(P) (mu + gamma_4 (sqrt 2 + mu)) with a safety factor of two); with
   // |T_k| <= ||t||_1, |Z_k| <= ||z||_1 and the 1/P scaling of the inverse,
   // max_j |dr_j| <= ||dw||_2 <= epsF (||t||_2 ||z||_1 + 2 ||t||_1 ||z||_2) + 3u ||t||_1 ||z||_2.
-  const double u = 5.9604644775390625e-08;
-  const double epsF = 14.0 * u * double(logP > 0 ? logP : 1);
-  const double delta = epsF * (t2 * z1 + 2.0 * t1 * z2) + 3.0 * u * t1 * z2 + 1e-30;
+  // The norms are fp32 sums (relative error below (K + 2P) u < 1e-2); the
+  // factor 1.02 covers them.
+  const float u = 5.9604644775390625e-08f;
+  const float epsF = 14.0f * u * float(logP > 0 ? logP : 1);
+  const float delta = 1.02f * (epsF * (t2 * z1 + 2.0f * t1 * z2) + 3.0f * u * t1 * z2) + 1e-30f;
   const bool exact_int = ints && t_integral;
+  // int32 rescoring is exact when every partial sum stays below 2^31:
+  // |sum| <= ||t||_1 max|y|
+  const bool small = exact_int && double(t1) * double(maxy) < 2.0e9;
   const void* yv = static_cast<const char*>(a.y) + Q.y_off * 4;
 
   for (int j = 0; j < 2; ++j) {
@@ -399,7 +478,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
     block_argmax(bv, bi, redv, redi);
     if (tid == 0) ncand[j] = 0;
     __syncthreads();
-    const float thr = float(double(bv) - 2.0 * delta);
+    const float thr = bv - 2.0f * delta;
     for (int k = tid; k < M; k += kCorrThreads) {
       const float2 w = sbuf[pad_idx(k)];
       const float rv = j == 0 ? w.x * invP : -w.y * invP;
@@ -419,10 +498,10 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
       double v;
       if (ints) {
         const int32_t* y = static_cast<const int32_t*>(yv) + int64_t(j) * P + jj;
-        v = warp_dot(t, K, exact_int, [&](int i) { return y[i]; });
+        v = warp_dot(t, K, exact_int, small, [&](int i) { return y[i]; });
       } else {
         const float* y = static_cast<const float*>(yv) + int64_t(j) * P + jj;
-        v = warp_dot(t, K, false, [&](int i) { return y[i]; });
+        v = warp_dot(t, K, false, false, [&](int i) { return y[i]; });
       }
       betterd(wv, wi, v, jj);
     }
@@ -443,29 +522,52 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   const CrtSet cs = crt_intersect(N, Q.M[0], Q.M[1], Q.inv, s_m[0], s_m[1]);
   const int64_t ncs = cs.nnat + cs.nw;
   auto member = [&](int64_t c) -> int64_t { return c < cs.nnat ? cs.m0 + c * cs.step : cs.w[c - cs.nnat]; };
-  auto tx = [&](int64_t m) -> double {
-    return warp_dot(t, K, exact_int, [&](int i) {
-      int64_t n = m + i;
-      if (n >= N) n -= N;
-      return ints ? double(sig.ival(n)) : double(sig.val(n));
-    });
-  };
-  double wv = -INFINITY;
-  int64_t wi = 0x7fffffffffffffffll;
-  for (int64_t c = warp; c < ncs; c += kWarps) {
-    const int64_t mm = member(c);
-    betterd(wv, wi, tx(mm), mm);
+  double best_v = 0.0;
+  int64_t best_m = -1;
+  if (ncs == 1) {
+    // a single member: its exact (Tx)_m, spread over the whole block
+    const int64_t mm = member(0);
+    if (exact_int) {
+      long long acc = 0;
+      for (int i = tid; i < K; i += kCorrThreads) {
+        int64_t n = mm + i;
+        if (n >= N) n -= N;
+        acc += (long long)__float2int_rn(t[i]) * sig.ival(n);
+      }
+      best_v = double(block_sum(acc, redl));
+    } else {
+      double acc = 0.0;
+      for (int i = tid; i < K; i += kCorrThreads) {
+        int64_t n = mm + i;
+        if (n >= N) n -= N;
+        acc = fma(double(t[i]), double(sig.val(n)), acc);
+      }
+      best_v = block_sum(acc, redd);
+    }
+    best_m = mm;
+  } else if (ncs > 1) {
+    double wv = -INFINITY;
+    int64_t wi = 0x7fffffffffffffffll;
+    for (int64_t c = warp; c < ncs; c += kWarps) {
+      const int64_t mm = member(c);
+      const double v = warp_dot(t, K, exact_int, false, [&](int i) {
+        int64_t n = mm + i;
+        if (n >= N) n -= N;
+        return ints ? double(sig.ival(n)) : double(sig.val(n));
+      });
+      betterd(wv, wi, v, mm);
+    }
+    if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
+    __syncthreads();
+    best_v = wbest_v[0];
+    best_m = wbest_i[0];
+    for (int w = 1; w < kWarps; ++w) betterd(best_v, best_m, wbest_v[w], wbest_i[w]);
   }
-  if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
-  __syncthreads();
   if (tid == 0) {
     tm_result res;
-    double v = wbest_v[0];
-    int64_t i = wbest_i[0];
-    for (int w = 1; w < kWarps; ++w) betterd(v, i, wbest_v[w], wbest_i[w]);
     res.n_cand = int32_t(ncs > 0x7fffffff ? 0x7fffffff : ncs);
     if (ncs == 0) { res.shift = -1; res.status = TM_EMPTY; res.score = 0.0; }
-    else { res.shift = i; res.status = ncs == 1 ? TM_FOUND : TM_RESOLVED; res.score = v; }
+    else { res.shift = best_m; res.status = ncs == 1 ? TM_FOUND : TM_RESOLVED; res.score = best_v; }
     res.status |= s_flags;
     if (*a.err) res.status |= TM_RF_DEVICE_ERROR;
     res.m1 = s_m[0];
@@ -476,16 +578,20 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   }
 }
 
+// Shared memory of a launch whose largest FFT is P: the padded work buffer,
+// the half twiddle table and, for P <= 8192, the template spectrum.
+int corr_smem_bytes(int P) { return (P + P / 16 + P / 2 + (P <= 8192 ? P : 0)) * int(sizeof(float2)); }
+
 }  // namespace
 
 cudaError_t corr_configure() {
-  const int smem = (kPMax + kPMax / 16) * int(sizeof(float2));
-  return cudaFuncSetAttribute(corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaFuncSetAttribute(corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, corr_smem_bytes(kPMax));
 }
 
 cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s) {
-  const int smem = (maxP + maxP / 16) * int(sizeof(float2));
-  corr_kernel<<<a.nq, kCorrThreads, smem, s>>>(a);
+  CorrArgs b = a;
+  b.smem_bytes = corr_smem_bytes(maxP);
+  corr_kernel<<<a.nq, kCorrThreads, b.smem_bytes, s>>>(b);
   return cudaGetLastError();
 }
 

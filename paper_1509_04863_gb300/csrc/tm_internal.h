@@ -102,6 +102,7 @@ struct CorrArgs {
   const float2* tw;       // twiddles W_{kPMax}^m, m < kPMax
   tm_result* out;
   int32_t* err;
+  int32_t smem_bytes;     // dynamic shared memory of the launch (set by the launcher)
 };
 
 // ---------------------------------------------------------------- kernels' host launchers
