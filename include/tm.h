@@ -201,6 +201,38 @@ TM_API tm_status tm_match_batch(const tm_query* q, int32_t n, tm_result* out_dev
 TM_API int32_t tm_crt_candidates(int64_t N, int32_t M1, int32_t M2, int32_t m1, int32_t m2,
                           int64_t* out, int32_t cap);
 
+/* ------------------------------------------------- no-allocation variant */
+
+/* The paper has no counterpart to this entry point: it is a deployment
+ * variant of tm_match for callers that must not allocate GPU memory, such
+ * as real-time receiver loops (cudaMalloc / cudaFree can synchronise the
+ * whole device and take unbounded time), processes whose device memory is
+ * already claimed by another allocator's pool, and code that may only
+ * allocate at start-up.
+ *
+ * It runs one query (Algorithm 1 steps 3-9, the same kernels and results as
+ * tm_match) with every scratch buffer carved from one fixed device array of
+ * TM_NOALLOC_SCRATCH_BYTES that the library holds on every GPU it is loaded
+ * on until the process exits. The caller passes x_dev, t_dev and out_dev as
+ * for tm_match. Signals above TM_NOALLOC_MAX_SIGNAL_BYTES return
+ * TM_EUNSUPPORTED with a message (checked before any GPU work); invalid
+ * problems TM_EINVAL. The fold runs on as many shares as the array holds
+ * (fewer than tm_match uses for long signals, so it can be slower). No
+ * cudaMalloc, cudaFree or other allocating call is made.
+ *
+ * The first call on a device sets that device up (finds the array's device
+ * address, configures the kernels, uploads the FFT twiddles with a
+ * synchronous copy); make that first call before any stream capture.
+ * Every call reuses the same array, which keeps the previous call's
+ * contents: calls that overlap on the GPU (different streams, or other
+ * threads) race and corrupt each other's results. Calls on one stream are
+ * ordered: each call's small descriptor upload waits for the stream's
+ * earlier work. */
+#define TM_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define TM_NOALLOC_MAX_SIGNAL_BYTES (1ll << 28)
+TM_API tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x_dev, const float* t_dev,
+                                  tm_result* out_dev, tm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -544,3 +544,147 @@ int32_t tm_crt_candidates(int64_t N, int32_t M1, int32_t M2, int32_t m1, int32_t
 }
 
 }  // extern "C"
+
+// ================================================================ no-allocation entry point
+// tm_match_noalloc: one query whose scratch lives in a fixed device array
+// instead of buffers from cudaMalloc (see tm.h for who needs this).
+
+// The scratch array. In host code its name is only a stand-in: host code
+// must use the device address from cudaGetSymbolAddress (noalloc_setup).
+static __device__ __align__(256) unsigned char g_tm_noalloc_scratch[TM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Layout of the scratch array (byte offsets, 256-aligned).
+constexpr size_t kNaErr = 0;                 // int32 error word (cleared by every call)
+constexpr size_t kNaOrder = 16;              // int32 processing order (one query: 0)
+constexpr size_t kNaFoldQ = 256;             // FoldQ descriptor
+constexpr size_t kNaCorrQ = 512;             // CorrQ descriptor
+constexpr size_t kNaTw = 1024;               // twiddles W_16384^m, written once per device
+constexpr size_t kNaY = kNaTw + size_t(kPMax) * sizeof(float2);      // folds [2][P] int32
+constexpr size_t kNaSpec = kNaY + 2 * size_t(kPMax) * sizeof(int32_t);  // template spectrum
+constexpr size_t kNaPart = kNaSpec + size_t(kPMax) * sizeof(float2);    // partial fold counts
+constexpr size_t kNaPartBytes = TM_NOALLOC_SCRATCH_BYTES - kNaPart;
+static_assert(sizeof(FoldQ) <= 256 && sizeof(CorrQ) <= 512, "descriptor slots");
+
+std::mutex g_na_mu;
+unsigned char* g_na_base[128] = {};   // device address of the array, per device
+float2 g_na_tw_host[kPMax];           // host copy of the twiddles (static storage)
+bool g_na_tw_ready = false;
+
+// Once per device, with that device current: device address of the array,
+// kernel attributes, twiddles.
+tm_status noalloc_setup(int dev, unsigned char** base) {
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (dev < 0 || dev >= 128) return fail(TM_EUNSUPPORTED, "device index above 127");
+  if (!g_na_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_tm_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    TM_CUDA(fold_configure());
+    TM_CUDA(corr_configure());
+    if (!g_na_tw_ready) {
+      const double two_pi = 6.283185307179586476925286766559;
+      for (int m = 0; m < kPMax; ++m) {
+        const double ang = two_pi * double(m) / double(kPMax);
+        g_na_tw_host[m] = make_float2(float(std::cos(ang)), float(-std::sin(ang)));
+      }
+      g_na_tw_ready = true;
+    }
+    TM_CUDA(cudaMemcpy(static_cast<unsigned char*>(p) + kNaTw, g_na_tw_host, sizeof(g_na_tw_host),
+                       cudaMemcpyHostToDevice));
+    g_na_base[dev] = static_cast<unsigned char*>(p);
+  }
+  *base = g_na_base[dev];
+  return TM_OK;
+}
+
+}  // namespace
+
+extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, const float* t, tm_result* out,
+                                      tm_stream_t stream) {
+  if (!desc || !x || !t || !out) return fail(TM_EINVAL, "null argument");
+  if (reinterpret_cast<uintptr_t>(x) & 15) return fail(TM_EINVAL, "x must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(t) & 3) return fail(TM_EINVAL, "t must be 4-byte aligned");
+  PlanCore p;
+  tm_status st = make_plan(desc->N, desc->K, desc->xdtype, desc->mode, desc->M1, desc->M2, desc->flags, p);
+  if (st != TM_OK) return st;
+  if (signal_bytes(p.xdtype, p.N) > TM_NOALLOC_MAX_SIGNAL_BYTES)
+    return fail(TM_EUNSUPPORTED, "signal larger than the " + std::to_string(TM_NOALLOC_MAX_SIGNAL_BYTES) +
+                                     " bytes the no-allocation entry point accepts (use tm_match)");
+
+  // fold geometry for one signal: equal shares, as many as the array holds
+  const int64_t W = signal_bytes(p.xdtype, p.N) & ~int64_t(15);
+  const int64_t stride = pad16(p.Mp[0]) + pad16(p.Mp[1]);
+  const int64_t max_slots = int64_t(kNaPartBytes / sizeof(int32_t)) / stride;
+  const int64_t rows_cap = int64_t(kFoldMaxRowsPerSlot - 2) * std::min(p.Mp[0], p.Mp[1]);
+  int dev = 0, sms = 0;
+  TM_CUDA(cudaGetDevice(&dev));
+  TM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int64_t nctas = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(W, 65536)));
+  nctas = std::min(nctas, max_slots);
+  if (W > 0 && (nctas < 1 || nctas < ceil_div(W, rows_cap)))
+    return fail(TM_EUNSUPPORTED, "query needs more scratch than the " + std::to_string(TM_NOALLOC_SCRATCH_BYTES) +
+                                     "-byte no-allocation array holds (use tm_match)");
+  unsigned char* base = nullptr;
+  st = noalloc_setup(dev, &base);
+  if (st != TM_OK) return st;
+
+  FoldQ f;
+  f.x = static_cast<const uint8_t*>(x);
+  f.goff = 0;
+  f.nbytes = int32_t(W);
+  f.Mp[0] = p.Mp[0]; f.Mp[1] = p.Mp[1];
+  f.moff[0] = 0; f.moff[1] = int32_t(pad16(p.Mp[0]));
+  f.stride = int32_t(stride);
+  f.first_cta = 0;
+  f.part = 0;
+  f.nslots = 0;
+  if (W > 0) {
+    int32_t lo = 0, hi = int32_t(nctas) - 1;   // CTA whose share holds the last byte
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) / 2;
+      if (fold_cta_begin(W, int32_t(nctas), mid) <= W - 1) lo = mid; else hi = mid - 1;
+    }
+    f.nslots = lo + 1;
+  }
+  CorrQ c;
+  c.x = x; c.t = t; c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
+  for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
+  c.P = p.P; c.logP = p.logP; c.inv = p.inv;
+  c.nelem16 = int32_t(p.xdtype == TM_I8_PM1 ? W : p.xdtype == TM_BITS_PM1 ? std::min<int64_t>(p.N, 8 * W)
+                      : p.xdtype == TM_F16 ? W / 2 : W / 4);
+  c.nslots = f.nslots; c.stride = f.stride; c.part = 0;
+  c.y_off = 0; c.spec_off = 0; c.r_off = -1;
+  const int32_t order0 = 0;
+
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int32_t* err = reinterpret_cast<int32_t*>(base + kNaErr);
+  TM_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));   // the previous call's error word is stale
+  // pageable-source copies: each returns once the source has been staged
+  TM_CUDA(cudaMemcpyAsync(base + kNaOrder, &order0, sizeof(order0), cudaMemcpyHostToDevice, s));
+  TM_CUDA(cudaMemcpyAsync(base + kNaFoldQ, &f, sizeof(f), cudaMemcpyHostToDevice, s));
+  TM_CUDA(cudaMemcpyAsync(base + kNaCorrQ, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+  if (W > 0) {
+    FoldArgs fa;
+    fa.q = reinterpret_cast<const FoldQ*>(base + kNaFoldQ);
+    fa.nq = 1; fa.nctas = int32_t(nctas); fa.W = W;
+    fa.partial = reinterpret_cast<int32_t*>(base + kNaPart);
+    fa.err = err;
+    const int jmax = std::max(fold_units_per_lane(p.Mp[0], kFoldWarps0), fold_units_per_lane(p.Mp[1], kFoldWarps1));
+    TM_CUDA(launch_fold_i8(fa, jmax, s));
+  }
+  CorrArgs ca;
+  ca.q = reinterpret_cast<const CorrQ*>(base + kNaCorrQ);
+  ca.order = reinterpret_cast<const int32_t*>(base + kNaOrder);
+  ca.nq = 1;
+  ca.partial = reinterpret_cast<const int32_t*>(base + kNaPart);
+  ca.y = base + kNaY;
+  ca.spec = reinterpret_cast<float2*>(base + kNaSpec);
+  ca.r = nullptr;
+  ca.tw = reinterpret_cast<const float2*>(base + kNaTw);
+  ca.out = out;
+  ca.err = err;
+  TM_CUDA(launch_correlate(ca, p.P, s));
+  return TM_OK;
+}
