@@ -96,15 +96,35 @@ tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t 
   pc.L[0] = ceil_div(N, m1); pc.L[1] = ceil_div(N, m2);
   pc.logP = logP; pc.P = 1 << logP;
   pc.inv = int32_t(mod_inverse(m1, m2));
+  if (xdtype == TM_BITS_PM1 && N > kMaxQueryBytes)
+    return fail(TM_EUNSUPPORTED, "bit-packed signal longer than 2^31-2^16 elements");
+  const FoldGeom g = fold_geom(xdtype);
   for (int j = 0; j < 2; ++j) {
-    pc.R[j] = int32_t(std::max<int64_t>(1, ceil_div(kFoldMinMp, pc.M[j])));
+    pc.R[j] = int32_t(std::max<int64_t>(1, ceil_div(g.min_mp, pc.M[j])));
     pc.Mp[j] = pc.R[j] * pc.M[j];
-    if (fold_units_per_lane(pc.Mp[j], j == 0 ? kFoldWarps0 : kFoldWarps1) > kFoldJMax)
-      return fail(TM_EUNSUPPORTED, "modulus above 20480 not supported by the fold kernel");
+    if (fold_units_per_lane(pc.Mp[j], j == 0 ? kFoldWarps0 : kFoldWarps1, g.E) > g.jmax)
+      return fail(TM_EUNSUPPORTED, "modulus too large for the fold kernel of this signal type");
   }
   pc.max_cand = ceil_div(N, m1 * m2) + 2;
-  if (xdtype != TM_I8_PM1) return fail(TM_EUNSUPPORTED, "only TM_I8_PM1 signals are folded by this build");
   return TM_OK;
+}
+
+// Bytes of a signal the fold kernel streams: a multiple of 16 holding whole
+// elements (the correlation kernel adds the few elements after it).
+int64_t fold_bytes(int32_t dtype, int64_t N) {
+  const int64_t b = dtype == TM_BITS_PM1 ? N / 8 : signal_bytes(dtype, N);
+  return b & ~int64_t(15);
+}
+
+// Elements covered by fold_bytes.
+int64_t fold_elems(int32_t dtype, int64_t N) {
+  const int64_t b = fold_bytes(dtype, N);
+  switch (dtype) {
+    case TM_I8_PM1: return b;
+    case TM_BITS_PM1: return 8 * b;
+    case TM_F16: return b / 2;
+    default: return b / 4;
+  }
 }
 
 // ---------------------------------------------------------------- per-device state
@@ -147,10 +167,18 @@ struct tm_batch_s {
   std::vector<CorrQ> cq;
   std::vector<int32_t> order;
   std::vector<int64_t> xoff, toff;   // device input copies (TM_BATCH_HOST_INPUTS)
-  int32_t nctas = 0;
-  int64_t W = 0;
+  // One fold launch per signal storage type present: its queries occupy
+  // fq[first, first + count) (fq is ordered by group), fold_of[i] is the
+  // fq position of query i.
+  struct FoldGroup {
+    int32_t dtype, first, count, nctas, jmax;
+    int64_t W;
+  };
+  std::vector<FoldGroup> groups;
+  std::vector<int32_t> fold_of;
+  int32_t nctas = 0;   // largest fold grid
+  int64_t W = 0;       // bytes folded in total
   int32_t maxP = 0;
-  int32_t jmax = 1;   // most 16-column units per fold consumer
   int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
   FoldQ* d_fq = nullptr;
   CorrQ* d_cq = nullptr;
@@ -198,7 +226,7 @@ void bind_pointers(tm_batch_t b) {
   for (int i = 0; i < b->n; ++i) {
     const void* x = (b->flags & TM_BATCH_HOST_INPUTS) ? static_cast<const void*>(b->d_x + b->xoff[i]) : b->q[i].x;
     const float* t = (b->flags & TM_BATCH_HOST_INPUTS) ? b->d_t + b->toff[i] : b->q[i].t;
-    b->fq[i].x = static_cast<const uint8_t*>(x);
+    b->fq[b->fold_of[i]].x = static_cast<const uint8_t*>(x);
     b->cq[i].x = x;
     b->cq[i].t = t;
   }
@@ -249,45 +277,64 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
   tm_status st = device_setup(b->device, &b->tw);
   if (st != TM_OK) { delete b; return st; }
 
-  // ---- fold geometry: flattened byte space, equal shares per CTA
+  // ---- fold geometry: per storage type, a flattened byte space split into
+  // equal shares, one per CTA
   b->fq.resize(n);
   b->cq.resize(n);
-  int64_t W = 0, max_share = INT64_MAX;
-  for (int i = 0; i < n; ++i) {
-    const PlanCore& p = b->pc[i];
-    const int64_t nb = signal_bytes(p.xdtype, p.N) & ~int64_t(15);
-    FoldQ& f = b->fq[i];
-    f.goff = W;
-    f.nbytes = int32_t(nb);
-    for (int j = 0; j < 2; ++j) f.Mp[j] = p.Mp[j];
-    f.moff[0] = 0;
-    f.moff[1] = int32_t(pad16(p.Mp[0]));
-    f.stride = int32_t(pad16(p.Mp[0]) + pad16(p.Mp[1]));
-    W += nb;
-    max_share = std::min<int64_t>(max_share, int64_t(kFoldMaxRowsPerSlot - 2) * std::min(p.Mp[0], p.Mp[1]));
-    for (int j = 0; j < 2; ++j)
-      b->jmax = std::max<int32_t>(b->jmax, fold_units_per_lane(p.Mp[j], j == 0 ? kFoldWarps0 : kFoldWarps1));
-  }
-  b->W = W;
-  int64_t nctas = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(W, 65536)));
-  if (W > 0) nctas = std::max<int64_t>(nctas, ceil_div(W, max_share));
-  b->nctas = int32_t(nctas);
-  auto cta_of = [&](int64_t pos) {   // CTA whose share holds byte pos
-    int32_t lo = 0, hi = b->nctas - 1;
-    while (lo < hi) {
-      const int32_t mid = (lo + hi + 1) / 2;
-      if (fold_cta_begin(W, b->nctas, mid) <= pos) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-  };
+  b->fold_of.assign(n, 0);
   int64_t part = 0;
-  for (int i = 0; i < n; ++i) {
-    FoldQ& f = b->fq[i];
-    if (f.nbytes == 0) { f.first_cta = 0; f.nslots = 0; f.part = part; continue; }
-    f.first_cta = cta_of(f.goff);
-    f.nslots = cta_of(f.goff + f.nbytes - 1) - f.first_cta + 1;
-    f.part = part;
-    part += int64_t(f.nslots) * f.stride;
+  for (int32_t dt = TM_I8_PM1; dt <= TM_F32; ++dt) {
+    tm_batch_s::FoldGroup gr;
+    gr.dtype = dt;
+    gr.first = int32_t(b->groups.empty() ? 0 : b->groups.back().first + b->groups.back().count);
+    gr.count = 0;
+    gr.jmax = 1;
+    const FoldGeom geo = fold_geom(dt);
+    int64_t W = 0, max_share = INT64_MAX;
+    for (int i = 0; i < n; ++i) {
+      const PlanCore& p = b->pc[i];
+      if (p.xdtype != dt) continue;
+      const int32_t pos = gr.first + gr.count++;
+      b->fold_of[i] = pos;
+      const int64_t nb = fold_bytes(p.xdtype, p.N);
+      FoldQ& f = b->fq[pos];
+      f.goff = W;
+      f.nbytes = int32_t(nb);
+      for (int j = 0; j < 2; ++j) f.Mp[j] = p.Mp[j];
+      f.moff[0] = 0;
+      f.moff[1] = int32_t(pad16(p.Mp[0]));
+      f.stride = int32_t(pad16(p.Mp[0]) + pad16(p.Mp[1]));
+      W += nb;
+      // rows of Mp elements per share stay below the lane counters' capacity
+      max_share = std::min<int64_t>(max_share, int64_t(kFoldMaxRowsPerSlot - 2) *
+                                                   std::min(p.Mp[0], p.Mp[1]) * geo.bits / 8);
+      for (int j = 0; j < 2; ++j)
+        gr.jmax = std::max<int32_t>(gr.jmax, fold_units_per_lane(p.Mp[j], j == 0 ? kFoldWarps0 : kFoldWarps1, geo.E));
+    }
+    if (gr.count == 0) continue;
+    gr.W = W;
+    int64_t nctas = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(W, 65536)));
+    if (W > 0) nctas = std::max<int64_t>(nctas, ceil_div(W, max_share));
+    gr.nctas = int32_t(nctas);
+    auto cta_of = [&](int64_t pos) {   // CTA whose share holds byte pos
+      int32_t lo = 0, hi = gr.nctas - 1;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) / 2;
+        if (fold_cta_begin(W, gr.nctas, mid) <= pos) lo = mid; else hi = mid - 1;
+      }
+      return lo;
+    };
+    for (int32_t k = gr.first; k < gr.first + gr.count; ++k) {
+      FoldQ& f = b->fq[k];
+      if (f.nbytes == 0) { f.first_cta = 0; f.nslots = 0; f.part = part; continue; }
+      f.first_cta = cta_of(f.goff);
+      f.nslots = cta_of(f.goff + f.nbytes - 1) - f.first_cta + 1;
+      f.part = part;
+      part += int64_t(f.nslots) * f.stride;
+    }
+    b->W += W;
+    b->nctas = std::max(b->nctas, gr.nctas);
+    b->groups.push_back(gr);
   }
   b->part_elems = std::max<int64_t>(part, 16);
 
@@ -295,13 +342,12 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
   int64_t yo = 0, so = 0, ro = 0;
   for (int i = 0; i < n; ++i) {
     const PlanCore& p = b->pc[i];
-    const FoldQ& f = b->fq[i];
+    const FoldQ& f = b->fq[b->fold_of[i]];
     CorrQ& c = b->cq[i];
     c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
     for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
     c.P = p.P; c.logP = p.logP; c.inv = p.inv;
-    c.nelem16 = int32_t(p.xdtype == TM_I8_PM1 ? f.nbytes : p.xdtype == TM_BITS_PM1 ? std::min<int64_t>(p.N, 8ll * f.nbytes)
-                        : p.xdtype == TM_F16 ? f.nbytes / 2 : f.nbytes / 4);
+    c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
     c.nslots = f.nslots; c.stride = f.stride; c.part = f.part;
     c.y_off = yo; yo += 2ll * p.P;
     c.spec_off = so; so += p.P;
@@ -358,11 +404,13 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
 
 tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
   TM_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int32_t), s));
-  if (b->W == 0) return TM_OK;
-  FoldArgs a;
-  a.q = b->d_fq; a.nq = b->n; a.nctas = b->nctas; a.W = b->W;
-  a.partial = b->d_partial; a.err = b->d_err;
-  TM_CUDA(launch_fold_i8(a, b->jmax, s));
+  for (const auto& g : b->groups) {
+    if (g.W == 0) continue;
+    FoldArgs a;
+    a.q = b->d_fq + g.first; a.nq = g.count; a.dtype = g.dtype; a.nctas = g.nctas; a.W = g.W;
+    a.partial = b->d_partial; a.err = b->d_err;
+    TM_CUDA(launch_fold(a, g.jmax, s));
+  }
   return TM_OK;
 }
 
@@ -501,7 +549,11 @@ tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r) {
 
 tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, int64_t* ws) {
   if (!b) return fail(TM_EINVAL, "null batch");
-  if (launches) *launches = (b->W > 0 ? 1 : 0) + 1;
+  if (launches) {
+    int32_t l = 1;
+    for (const auto& g : b->groups) l += g.W > 0 ? 1 : 0;
+    *launches = l;
+  }
   if (fold_ctas) *fold_ctas = b->nctas;
   if (ws) *ws = b->ws_bytes;
   return TM_OK;
@@ -614,10 +666,10 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
                                      " bytes the no-allocation entry point accepts (use tm_match)");
 
   // fold geometry for one signal: equal shares, as many as the array holds
-  const int64_t W = signal_bytes(p.xdtype, p.N) & ~int64_t(15);
+  const int64_t W = fold_bytes(p.xdtype, p.N);
   const int64_t stride = pad16(p.Mp[0]) + pad16(p.Mp[1]);
   const int64_t max_slots = int64_t(kNaPartBytes / sizeof(int32_t)) / stride;
-  const int64_t rows_cap = int64_t(kFoldMaxRowsPerSlot - 2) * std::min(p.Mp[0], p.Mp[1]);
+  const int64_t rows_cap = int64_t(kFoldMaxRowsPerSlot - 2) * std::min(p.Mp[0], p.Mp[1]) * fold_geom(p.xdtype).bits / 8;
   int dev = 0, sms = 0;
   TM_CUDA(cudaGetDevice(&dev));
   TM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -652,8 +704,7 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   c.x = x; c.t = t; c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
   for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
   c.P = p.P; c.logP = p.logP; c.inv = p.inv;
-  c.nelem16 = int32_t(p.xdtype == TM_I8_PM1 ? W : p.xdtype == TM_BITS_PM1 ? std::min<int64_t>(p.N, 8 * W)
-                      : p.xdtype == TM_F16 ? W / 2 : W / 4);
+  c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
   c.nslots = f.nslots; c.stride = f.stride; c.part = 0;
   c.y_off = 0; c.spec_off = 0; c.r_off = -1;
   const int32_t order0 = 0;
@@ -668,11 +719,12 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   if (W > 0) {
     FoldArgs fa;
     fa.q = reinterpret_cast<const FoldQ*>(base + kNaFoldQ);
-    fa.nq = 1; fa.nctas = int32_t(nctas); fa.W = W;
+    fa.nq = 1; fa.dtype = p.xdtype; fa.nctas = int32_t(nctas); fa.W = W;
     fa.partial = reinterpret_cast<int32_t*>(base + kNaPart);
     fa.err = err;
-    const int jmax = std::max(fold_units_per_lane(p.Mp[0], kFoldWarps0), fold_units_per_lane(p.Mp[1], kFoldWarps1));
-    TM_CUDA(launch_fold_i8(fa, jmax, s));
+    const int E = fold_geom(p.xdtype).E;
+    const int jmax = std::max(fold_units_per_lane(p.Mp[0], kFoldWarps0, E), fold_units_per_lane(p.Mp[1], kFoldWarps1, E));
+    TM_CUDA(launch_fold(fa, jmax, s));
   }
   CorrArgs ca;
   ca.q = reinterpret_cast<const CorrQ*>(base + kNaCorrQ);

@@ -354,10 +354,12 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
         }
       }
       __syncthreads();
+      const bool ones = Q.xdtype == TM_BITS_PM1;   // bit-packed slots count +1 entries, int8 slots -1 entries
       for (int k = tid; k < M; k += kCorrThreads) {
         // entries n < N with n = k (mod M): L of them for k < Rw, else L-1
         const int e = 2 * pad_idx(k) + j;
-        int yk = (L - 1 + (k < Rw ? 1 : 0)) - 2 * ib[e];
+        const int nk = L - 1 + (k < Rw ? 1 : 0);
+        int yk = ones ? 2 * ib[e] - nk : nk - 2 * ib[e];
         if (k >= Rw) yk += sig.ival(k - Rw);
         ib[e] = yk;
       }
@@ -380,8 +382,10 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
     for (int64_t n = Q.nelem16; n < N; ++n) {
       for (int j = 0; j < 2; ++j) {
         const int e = 2 * pad_idx(int(n % Q.M[j])) + j;
-        // the count L or L-1 above already includes this entry as +1
-        if (ints) ib[e] -= sig.ival(n) < 0 ? 2 : 0;
+        // the count L or L-1 above includes this entry: as +1 for int8
+        // (counted -1 entries), as -1 for bits (counted +1 entries)
+        if (Q.xdtype == TM_I8_PM1) ib[e] -= sig.ival(n) < 0 ? 2 : 0;
+        else if (Q.xdtype == TM_BITS_PM1) ib[e] += sig.ival(n) > 0 ? 2 : 0;
         else fb[e] += sig.val(n);
       }
     }

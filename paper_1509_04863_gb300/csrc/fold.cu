@@ -1,0 +1,527 @@
+// Step 3 of Algorithm 1 (Eq. (2)): column sums of x viewed as rows of
+// length M, for both moduli, from a single read of x.
+//
+// Design: the signals of one storage type in a batch are concatenated
+// (16-byte-aligned prefixes) into one byte space that is split into equal
+// contiguous shares, one per CTA. A producer warp streams a CTA's share
+// through a ring of shared-memory stages with bulk asynchronous copies (TMA,
+// cp.async.bulk, L2 evict-first). Consumer lanes own fixed units of E
+// consecutive columns of one modulus, dealt out in chunks of 32 consecutive
+// units per warp (8 warps for M1, 9 for M2, so that K and K+1 columns both
+// come to one chunk per warp for the paper's moduli). For a stage holding
+// elements [s, e) of a signal every lane of a warp walks the same rows l of
+// its modulus: rows strictly inside the stage take the fast path, the first
+// and last row a masked path that keeps only the part inside the stage.
+// Stages carry 16 bytes of slack on both sides so every read stays in
+// bounds. A unit narrower than E (the last one of a row) still reads E
+// columns; the columns past its width see the next row and are never
+// written out. Each CTA writes one slot of per-column results per signal
+// share; the correlation kernel adds the slots, the wrap-around term and
+// the extension k >= M.
+//
+// Units (one per storage type):
+//  int8 +-1 : 16 bytes; a byte holding -1 (0xFF) has bit 1 set and +1 (0x01)
+//             has not, so w & 0x02020202 adds 2 per -1 into packed byte
+//             lanes, widened into 16-bit lanes every few stages; output:
+//             count of -1 entries.
+//  bits     : 32 columns in one word (LSB first, 1 = +1); bit-sliced
+//             vertical counters (5 planes, up to 31 rows) flushed into byte
+//             then 16-bit lanes; output: count of +1 entries.
+//  fp16/fp32: 8 / 4 columns, fp32 accumulators added row by row in a fixed
+//             order (the result does not depend on timing); output: sums.
+//
+// To keep every lane busy the fold runs with an effective modulus
+// Mp = R*M >= fold_geom(dtype).min_mp; the correlation kernel sums the R
+// columns k + rM of the Mp-fold into column k of the M-fold.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "device_util.cuh"
+#include "tm_internal.h"
+
+namespace ftm {
+namespace {
+
+constexpr int kStageBytes = kFoldTile + 32;   // 16 bytes of slack before and after the data
+constexpr uint32_t kNegBit = 0x02020202u;
+
+__device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, uint32_t sh) {
+  return __funnelshift_r(lo, hi, sh);
+}
+
+// Bytes [o, o+16) of a stage as 4 words, -16 < o < valid + 16 (the slack
+// keeps both aligned reads inside the stage); r = o & 15 must be the same
+// in every lane of the warp.
+__device__ __forceinline__ void load16(const uint8_t* buf, int o, uint32_t (&w)[4]) {
+  const uint4* p = reinterpret_cast<const uint4*>(buf + (o & ~15));
+  const uint4 a = p[0];
+  const int r = o & 15;
+  if (r == 0) {
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    return;
+  }
+  const uint4 b = p[1];
+  const uint32_t sh = uint32_t(r & 3) * 8u;
+  switch (r >> 2) {
+    case 0: w[0] = fsr(a.x, a.y, sh); w[1] = fsr(a.y, a.z, sh); w[2] = fsr(a.z, a.w, sh); w[3] = fsr(a.w, b.x, sh); break;
+    case 1: w[0] = fsr(a.y, a.z, sh); w[1] = fsr(a.z, a.w, sh); w[2] = fsr(a.w, b.x, sh); w[3] = fsr(b.x, b.y, sh); break;
+    case 2: w[0] = fsr(a.z, a.w, sh); w[1] = fsr(a.w, b.x, sh); w[2] = fsr(b.x, b.y, sh); w[3] = fsr(b.y, b.z, sh); break;
+    default: w[0] = fsr(a.w, b.x, sh); w[1] = fsr(b.x, b.y, sh); w[2] = fsr(b.y, b.z, sh); w[3] = fsr(b.z, b.w, sh); break;
+  }
+}
+
+// Low n bytes of a word set (n clamped to [0, 4]).
+__device__ __forceinline__ uint32_t low_bytes(int n) {
+  return n <= 0 ? 0u : n >= 4 ? 0xFFFFFFFFu : (1u << (8 * n)) - 1u;
+}
+
+// ---------------------------------------------------------------- int8 +-1
+struct UnitI8 {
+  static constexpr int kE = 16, kBits = 8;
+  uint32_t c8[4], c16[8];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c8[i] = 0u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c16[i] = 0u;
+  }
+  // stages between widenings: a unit meets at most tile/Mp + 2 rows per
+  // stage and a byte lane holds up to 127 of them (2 per -1 entry)
+  static __device__ __forceinline__ int widen_every(int Mp) { return max(1, 127 / (kFoldTile / Mp + 2)); }
+  __device__ __forceinline__ void add(const uint8_t* buf, int o) {
+    uint32_t w[4];
+    load16(buf, o, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c8[i] += w[i] & kNegBit;
+  }
+  __device__ __forceinline__ void add2(const uint8_t* buf, int o, int o2) {
+    uint32_t w[4], v[4];
+    load16(buf, o, w);
+    load16(buf, o2, v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c8[i] += (w[i] & kNegBit) + (v[i] & kNegBit);
+  }
+  // elements of [o, o+16) inside [0, len)
+  __device__ __forceinline__ void add_masked(const uint8_t* buf, int o, int len) {
+    uint32_t w[4];
+    load16(buf, o, w);
+    const int lo = -o, hi = len - o;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c8[k] += w[k] & (kNegBit & low_bytes(hi - 4 * k) & ~low_bytes(lo - 4 * k));
+  }
+  __device__ __forceinline__ void end_row_block() {}
+  __device__ __forceinline__ void widen() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c16[2 * i] += c8[i] & 0x00FF00FFu;
+      c16[2 * i + 1] += (c8[i] >> 8) & 0x00FF00FFu;
+      c8[i] = 0u;
+    }
+  }
+  __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
+    int32_t cnt[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t e0 = c16[2 * i] + (c8[i] & 0x00FF00FFu);
+      const uint32_t e1 = c16[2 * i + 1] + ((c8[i] >> 8) & 0x00FF00FFu);
+      cnt[4 * i + 0] = int32_t((e0 & 0xFFFFu) >> 1);
+      cnt[4 * i + 2] = int32_t(e0 >> 17);
+      cnt[4 * i + 1] = int32_t((e1 & 0xFFFFu) >> 1);
+      cnt[4 * i + 3] = int32_t(e1 >> 17);
+    }
+    if (width == 16) {
+      int4* d4 = reinterpret_cast<int4*>(dst + col);
+      d4[0] = make_int4(cnt[0], cnt[1], cnt[2], cnt[3]);
+      d4[1] = make_int4(cnt[4], cnt[5], cnt[6], cnt[7]);
+      d4[2] = make_int4(cnt[8], cnt[9], cnt[10], cnt[11]);
+      d4[3] = make_int4(cnt[12], cnt[13], cnt[14], cnt[15]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (i < width) dst[col + i] = cnt[i];
+    }
+  }
+};
+
+// ---------------------------------------------------------------- bit-packed +-1
+struct UnitBits {
+  static constexpr int kE = 32, kBits = 1;
+  static constexpr int kPlanes = 5;       // vertical counter: up to 31 rows
+  uint32_t p[kPlanes];
+  uint32_t c8[8];                         // byte lanes: word k holds columns k, k+8, k+16, k+24
+  uint32_t c16[16];                       // 16-bit lanes: word 2k (cols k, k+16), 2k+1 (k+8, k+24)
+  int rows, flushes;
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < kPlanes; ++i) p[i] = 0u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c8[i] = 0u;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) c16[i] = 0u;
+    rows = 0;
+    flushes = 0;
+  }
+  static __device__ __forceinline__ int widen_every(int) { return 1 << 30; }   // planes flush themselves
+  // 32 bits starting at bit o of the stage (o > -32; the word before the
+  // stage lies in the 16-byte slack); o & 31 is warp-uniform
+  static __device__ __forceinline__ uint32_t load32(const uint8_t* buf, int o) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(buf);
+    const int q = o >> 5;
+    return fsr(w[q], w[q + 1], uint32_t(o & 31));
+  }
+  // add a value v (0/1 per column) of weight 1 to the planes
+  __device__ __forceinline__ void plane_add(uint32_t v) {
+#pragma unroll
+    for (int b = 0; b < kPlanes; ++b) {
+      const uint32_t c = p[b] & v;
+      p[b] ^= v;
+      v = c;
+    }
+  }
+  // add s (weight 1) and c (weight 2): one full-adder step per plane
+  __device__ __forceinline__ void plane_add2(uint32_t s, uint32_t c) {
+    const uint32_t k0 = p[0] & s;
+    p[0] ^= s;
+    // plane 1 gets c + k0 (both weight 2)
+    uint32_t carry = (p[1] & c) | (p[1] & k0) | (c & k0);
+    p[1] ^= c ^ k0;
+#pragma unroll
+    for (int b = 2; b < kPlanes; ++b) {
+      const uint32_t nc = p[b] & carry;
+      p[b] ^= carry;
+      carry = nc;
+    }
+  }
+  __device__ __forceinline__ void flush_planes() {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      uint32_t v = 0u;
+#pragma unroll
+      for (int b = 0; b < kPlanes; ++b) v |= ((p[b] >> k) & 0x01010101u) << b;
+      c8[k] += v;
+    }
+#pragma unroll
+    for (int b = 0; b < kPlanes; ++b) p[b] = 0u;
+    rows = 0;
+    if (++flushes == 8) {   // 8 x 31 rows fit a byte lane
+      flushes = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        c16[2 * k] += c8[k] & 0x00FF00FFu;
+        c16[2 * k + 1] += (c8[k] >> 8) & 0x00FF00FFu;
+        c8[k] = 0u;
+      }
+    }
+  }
+  __device__ __forceinline__ void add(const uint8_t* buf, int o) {
+    plane_add(load32(buf, o));
+    if (++rows >= 30) flush_planes();
+  }
+  __device__ __forceinline__ void add2(const uint8_t* buf, int o, int o2) {
+    const uint32_t a = load32(buf, o), b = load32(buf, o2);
+    plane_add2(a ^ b, a & b);
+    rows += 2;
+    if (rows >= 30) flush_planes();
+  }
+  __device__ __forceinline__ void add_masked(const uint8_t* buf, int o, int len) {
+    uint32_t v = load32(buf, o);
+    // keep bits i with 0 <= o + i < len
+    if (o < 0) v &= 0xFFFFFFFFu << (-o);
+    if (len - o < 32) v &= (len - o) <= 0 ? 0u : (0xFFFFFFFFu >> (32 - (len - o)));
+    plane_add(v);
+    if (++rows >= 30) flush_planes();
+  }
+  __device__ __forceinline__ void end_row_block() {}
+  __device__ __forceinline__ void widen() {}
+  __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
+    flush_planes();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t e0 = c16[2 * k] + (c8[k] & 0x00FF00FFu);
+      const uint32_t e1 = c16[2 * k + 1] + ((c8[k] >> 8) & 0x00FF00FFu);
+      const int cols[4] = {k, k + 16, k + 8, k + 24};
+      const int32_t v[4] = {int32_t(e0 & 0xFFFFu), int32_t(e0 >> 16), int32_t(e1 & 0xFFFFu), int32_t(e1 >> 16)};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (cols[i] < width) dst[col + cols[i]] = v[i];
+    }
+  }
+};
+
+// ---------------------------------------------------------------- fp32
+struct UnitF32 {
+  static constexpr int kE = 4, kBits = 32;
+  float acc[4];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = 0.f;
+  }
+  static __device__ __forceinline__ int widen_every(int) { return 1 << 30; }
+  __device__ __forceinline__ void add(const uint8_t* buf, int o) {
+    uint32_t w[4];
+    load16(buf, 4 * o, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] += __uint_as_float(w[i]);
+  }
+  __device__ __forceinline__ void add2(const uint8_t* buf, int o, int o2) {
+    add(buf, o);
+    add(buf, o2);
+  }
+  __device__ __forceinline__ void add_masked(const uint8_t* buf, int o, int len) {
+    uint32_t w[4];
+    load16(buf, 4 * o, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (o + i >= 0 && o + i < len) acc[i] += __uint_as_float(w[i]);
+  }
+  __device__ __forceinline__ void end_row_block() {}
+  __device__ __forceinline__ void widen() {}
+  __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
+    float* d = reinterpret_cast<float*>(dst) + col;
+    if (width == 4) *reinterpret_cast<float4*>(d) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < width) d[i] = acc[i];
+    }
+  }
+};
+
+// ---------------------------------------------------------------- fp16
+struct UnitF16 {
+  static constexpr int kE = 8, kBits = 16;
+  float acc[8];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+  }
+  static __device__ __forceinline__ int widen_every(int) { return 1 << 30; }
+  __device__ __forceinline__ void add(const uint8_t* buf, int o) {
+    uint32_t w[4];
+    load16(buf, 2 * o, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+      acc[2 * i] += f.x;
+      acc[2 * i + 1] += f.y;
+    }
+  }
+  __device__ __forceinline__ void add2(const uint8_t* buf, int o, int o2) {
+    add(buf, o);
+    add(buf, o2);
+  }
+  __device__ __forceinline__ void add_masked(const uint8_t* buf, int o, int len) {
+    uint32_t w[4];
+    load16(buf, 2 * o, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+      if (o + 2 * i >= 0 && o + 2 * i < len) acc[2 * i] += f.x;
+      if (o + 2 * i + 1 >= 0 && o + 2 * i + 1 < len) acc[2 * i + 1] += f.y;
+    }
+  }
+  __device__ __forceinline__ void end_row_block() {}
+  __device__ __forceinline__ void widen() {}
+  __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
+    float* d = reinterpret_cast<float*>(dst) + col;
+    if (width == 8) {
+      reinterpret_cast<float4*>(d)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      reinterpret_cast<float4*>(d)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < width) d[i] = acc[i];
+    }
+  }
+};
+
+// First query whose byte range ends after `pos`.
+__device__ __forceinline__ int first_query(const FoldQ* q, int nq, int64_t pos) {
+  int lo = 0, hi = nq;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (q[mid].goff + q[mid].nbytes > pos) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// One consumer lane's work on one share [lo, hi) (signal-local bytes) for
+// the effective modulus Mp (in elements): units lane + 32 (wig + W j), j < J,
+// where wig is the warp's index among the W warps of its modulus. Returns
+// false when a bounded wait ran out.
+template <class U, int J>
+__device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* full, uint64_t* empty, int lo, int hi,
+                                              int Mp, int W, int wig, int32_t* dst, uint32_t& it) {
+  const int lane = threadIdx.x & 31;
+  const int F = U::widen_every(Mp);
+  // unit j of this lane starts at column col(j); it exists when col(j) < Mp
+  auto col = [&](int j) { return U::kE * (lane + 32 * (wig + W * j)); };
+  U u[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) u[j].clear();
+
+  int since = 0;
+  for (int s = lo; s < hi; s += kFoldTile) {
+    const uint32_t st = it % kFoldStages;
+    // every lane waits; the warp gives up together so no lane is left
+    // behind at the __syncwarp below
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (it / kFoldStages) & 1u))) return false;
+    const uint8_t* buf = smem + st * kStageBytes + 16;
+    const int len = min(kFoldTile, hi - s);
+    // the stage in elements: [es, es + el)
+    const int es = int((int64_t(s) * 8) / U::kBits);
+    const int el = int((int64_t(len) * 8) / U::kBits);
+    const int l0 = es / Mp;               // rows meeting the stage
+    const int l1 = (es + el - 1) / Mp;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int cj = col(j);
+      if (cj >= Mp) continue;
+      // first row: the unit may start before the stage (or end after it)
+      {
+        const int o = l0 * Mp + cj - es;
+        if (o > -U::kE && o < el) u[j].add_masked(buf, o, el);
+      }
+      if (l1 > l0) {
+        // rows strictly inside the stage: all E columns are present (a
+        // narrow last unit reads past its width into the next row or the
+        // slack, in columns that are never written)
+        int l = l0 + 1;
+        for (; l + 1 < l1; l += 2) {
+          const int o = l * Mp + cj - es;
+          u[j].add2(buf, o, o + Mp);
+        }
+        if (l < l1) u[j].add(buf, l * Mp + cj - es);
+        // last row: the unit may run past the stage
+        const int o = l1 * Mp + cj - es;
+        if (o < el) u[j].add_masked(buf, o, el);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    ++it;
+    if (++since == F) {
+      since = 0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) u[j].widen();
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+    if (col(j) < Mp) u[j].write(dst, col(j), min(U::kE, Mp - col(j)));
+  return true;
+}
+
+template <class U, int JMAX>
+__global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kFoldStages * kStageBytes);
+  uint64_t* empty = full + kFoldStages;
+
+  const int tid = threadIdx.x;
+  const int64_t cb = fold_cta_begin(a.W, a.nctas, blockIdx.x);
+  const int64_t ce = fold_cta_begin(a.W, a.nctas, blockIdx.x + 1);
+
+  if (tid == 0) {
+    for (int s = 0; s < kFoldStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kFoldConsumers / 32);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (cb >= ce) return;
+  const int q0 = first_query(a.q, a.nq, cb);
+
+  // ---------------------------------------------------------------- producer
+  if (tid >= kFoldConsumers) {
+    if (tid == kFoldConsumers) {
+      const uint64_t pol = l2_policy_evict_first();
+      uint32_t it = 0;
+      bool ok = true;
+      for (int qi = q0; qi < a.nq && ok; ++qi) {
+        const int64_t goff = a.q[qi].goff;
+        const int32_t nbytes = a.q[qi].nbytes;
+        const uint8_t* x = a.q[qi].x;
+        if (goff >= ce) break;
+        if (nbytes == 0) continue;
+        const int64_t lo = max(cb, goff) - goff;
+        const int64_t hi = min(ce, goff + nbytes) - goff;
+        for (int64_t s = lo; s < hi; s += kFoldTile) {
+          const uint32_t st = it % kFoldStages;
+          if (it >= kFoldStages && !mbar_wait(&empty[st], ((it / kFoldStages) & 1u) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          const uint32_t len = uint32_t(hi - s < kFoldTile ? hi - s : int64_t(kFoldTile));
+          mbar_arrive_expect_tx(&full[st], len);
+          bulk_load(smem + st * kStageBytes + 16, x + s, len, &full[st], pol);
+          ++it;
+        }
+      }
+      if (!ok) atomicOr(a.err, 1);
+      // Let every copy this thread issued land before the CTA may exit.
+      for (uint32_t k = it > kFoldStages ? it - kFoldStages : 0; k < it; ++k)
+        (void)mbar_wait(&full[k % kFoldStages], (k / kFoldStages) & 1u);
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------------- consumers
+  const int warp = tid >> 5;
+  const int m = warp < kFoldWarps0 ? 0 : 1;         // modulus handled by this warp
+  const int W = m == 0 ? kFoldWarps0 : kFoldWarps1;
+  const int wig = m == 0 ? warp : warp - kFoldWarps0;
+  uint32_t it = 0;
+  bool ok = true;
+  for (int qi = q0; qi < a.nq && ok; ++qi) {
+    const int64_t goff = a.q[qi].goff;
+    const int32_t nbytes = a.q[qi].nbytes;
+    if (goff >= ce) break;
+    if (nbytes == 0) continue;
+    const int lo = int(max(cb, goff) - goff);
+    const int hi = int(min(ce, goff + nbytes) - goff);
+    const int Mp = a.q[qi].Mp[m];
+    int32_t* dst = a.partial + a.q[qi].part + int64_t(blockIdx.x - a.q[qi].first_cta) * a.q[qi].stride +
+                   a.q[qi].moff[m];
+    const int J = fold_units_per_lane(Mp, W, U::kE);
+    if (J <= 1) ok = consume_share<U, 1>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    else if (J == 2 || JMAX == 2) ok = consume_share<U, 2>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    else if (J <= 4 || JMAX <= 4) ok = consume_share<U, (JMAX < 4 ? JMAX : 4)>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    else ok = consume_share<U, JMAX>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+  }
+  if (!ok) atomicOr(a.err, 1);
+}
+
+constexpr int kFoldSmem = kFoldStages * kStageBytes + 2 * kFoldStages * 8;
+
+template <class K>
+cudaError_t set_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmem);
+}
+
+}  // namespace
+
+cudaError_t fold_configure() {
+  cudaError_t e;
+  if ((e = set_smem(fold_kernel<UnitI8, 3>)) != cudaSuccess) return e;
+  if ((e = set_smem(fold_kernel<UnitI8, 5>)) != cudaSuccess) return e;
+  if ((e = set_smem(fold_kernel<UnitBits, 2>)) != cudaSuccess) return e;
+  if ((e = set_smem(fold_kernel<UnitF16, 4>)) != cudaSuccess) return e;
+  return set_smem(fold_kernel<UnitF32, 8>);
+}
+
+cudaError_t launch_fold(const FoldArgs& a, int jmax, cudaStream_t s) {
+  switch (a.dtype) {
+    case TM_I8_PM1:
+      if (jmax <= 3) fold_kernel<UnitI8, 3><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a);
+      else fold_kernel<UnitI8, 5><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a);
+      break;
+    case TM_BITS_PM1: fold_kernel<UnitBits, 2><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a); break;
+    case TM_F16: fold_kernel<UnitF16, 4><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a); break;
+    default: fold_kernel<UnitF32, 8><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ftm

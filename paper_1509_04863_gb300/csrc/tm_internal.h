@@ -25,16 +25,32 @@ constexpr int kFoldConsumers = 32 * (kFoldWarps0 + kFoldWarps1);
 constexpr int kFoldThreads = kFoldConsumers + 32;    // + producer warp
 constexpr int kFoldStages = 3;
 constexpr int kFoldTile = 65536;                     // bytes per stage
-constexpr int kFoldJMax = 5;                         // 16-column units per consumer lane
-constexpr int kFoldMinMp = 4096;                     // effective modulus floor
-constexpr int kFoldMaxMp = 32 * kFoldWarps0 * kFoldJMax * 16;   // 20480
 // A consumer's 16-bit lane counters hold twice the number of -1 entries;
 // the host caps a CTA's share so that no column sees more rows than this.
 constexpr int kFoldMaxRowsPerSlot = 32000;
 
-// 16-column units per lane needed for an effective modulus Mp on `warps` warps.
-__host__ __device__ inline int fold_units_per_lane(int Mp, int warps) {
-  const int chunks = ((Mp + 15) / 16 + 31) / 32;
+// Per signal storage type: columns per consumer unit (a unit is 16 bytes of
+// a row, 4 bytes for bit-packed signals), bits per element, the floor of the
+// effective modulus Mp = R M, and the most units per lane a launch supports.
+struct FoldGeom {
+  int E;
+  int bits;
+  int min_mp;
+  int jmax;
+};
+__host__ __device__ inline FoldGeom fold_geom(int dtype) {
+  switch (dtype) {
+    case TM_BITS_PM1: return FoldGeom{32, 1, 8192, 2};
+    case TM_F16: return FoldGeom{8, 16, 4096, 4};
+    case TM_F32: return FoldGeom{4, 32, 4096, 8};
+    default: return FoldGeom{16, 8, 4096, 5};
+  }
+}
+
+// Units per lane needed for an effective modulus Mp on `warps` warps, with
+// units of E columns dealt out in chunks of 32 consecutive units per warp.
+__host__ __device__ inline int fold_units_per_lane(int Mp, int warps, int E) {
+  const int chunks = ((Mp + E - 1) / E + 31) / 32;
   return (chunks + warps - 1) / warps;
 }
 
@@ -42,7 +58,7 @@ struct FoldQ {
   const uint8_t* x;   // signal bytes, 16-byte aligned
   int64_t goff;       // first byte of this signal in the flattened space
   int32_t nbytes;     // bytes folded by the kernel (multiple of 16)
-  int32_t Mp[2];      // effective moduli R_j * M_j >= kFoldMinMp
+  int32_t Mp[2];      // effective moduli R_j * M_j (>= fold_geom(dtype).min_mp)
   int32_t moff[2];    // offset of modulus j inside a slot (int32 units)
   int32_t stride;     // slot length (int32 units)
   int32_t first_cta;  // CTA whose share holds goff
@@ -51,11 +67,13 @@ struct FoldQ {
 };
 
 struct FoldArgs {
-  const FoldQ* q;
+  const FoldQ* q;     // the signals of one storage type, in byte-space order
   int32_t nq;
+  int32_t dtype;      // tm_dtype shared by all of them
   int32_t nctas;
   int64_t W;          // total bytes (multiple of 16)
-  int32_t* partial;   // int32 counts of -1 entries per (slot, modulus, column)
+  int32_t* partial;   // per (slot, modulus, column): int32 counts of -1 (int8) or
+                      // +1 (bits) entries, or fp32 sums (real signals)
   int32_t* err;       // device error word
 };
 
@@ -106,7 +124,7 @@ struct CorrArgs {
 };
 
 // ---------------------------------------------------------------- kernels' host launchers
-cudaError_t launch_fold_i8(const FoldArgs& a, int jmax, cudaStream_t s);
+cudaError_t launch_fold(const FoldArgs& a, int jmax, cudaStream_t s);
 cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s);
 cudaError_t fold_configure();   // one-time kernel attributes
 cudaError_t corr_configure();
