@@ -89,7 +89,7 @@ tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t 
   const int64_t need = std::max(m1, m2) + K - 1;
   int32_t logP = 0;
   while ((int64_t(1) << logP) < need) ++logP;
-  if (logP > kLogPMax) return fail(TM_EUNSUPPORTED, "FFT length above 16384 (max(M1,M2)+K-1 > 16384)");
+  if (logP > kLogPMaxBlocked) return fail(TM_EUNSUPPORTED, "FFT length above 65536 (max(M1,M2)+K-1 > 65536)");
   if (signal_bytes(xdtype, N) > kMaxQueryBytes) return fail(TM_EUNSUPPORTED, "signal larger than 2^31-2^16 bytes");
   pc.N = N; pc.K = K; pc.xdtype = xdtype;
   pc.M[0] = int32_t(m1); pc.M[1] = int32_t(m2);
@@ -178,7 +178,8 @@ struct tm_batch_s {
   std::vector<int32_t> fold_of;
   int32_t nctas = 0;   // largest fold grid
   int64_t W = 0;       // bytes folded in total
-  int32_t maxP = 0;
+  int32_t maxP = 0;        // largest FFT of the shared-memory correlation launch
+  int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_blocked, n))
   int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
   FoldQ* d_fq = nullptr;
   CorrQ* d_cq = nullptr;
@@ -350,15 +351,24 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
     c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
     c.nslots = f.nslots; c.stride = f.stride; c.part = f.part;
     c.y_off = yo; yo += 2ll * p.P;
-    c.spec_off = so; so += p.P;
-    c.r_off = (flags & TM_BATCH_KEEP_CORR) ? ro : -1;
-    if (flags & TM_BATCH_KEEP_CORR) ro += 2ll * p.P;
-    b->maxP = std::max(b->maxP, p.P);
+    const bool blocked = p.P > kPMax;   // correlation in blocks (overlap-save), r kept in global memory
+    c.spec_off = so;
+    so += blocked ? int64_t(blocked_spectra(p.K, std::max(p.M[0], p.M[1]))) * kPMax : p.P;
+    c.r_off = ((flags & TM_BATCH_KEEP_CORR) || blocked) ? ro : -1;
+    if (c.r_off >= 0) ro += 2ll * p.P;
+    if (!blocked) b->maxP = std::max(b->maxP, p.P);
   }
   b->y_elems = yo; b->spec_elems = so; b->r_elems = ro;
+  // processing order: shared-memory queries (largest P first), then blocked ones
   b->order.resize(n);
   for (int i = 0; i < n; ++i) b->order[i] = i;
-  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return b->pc[a].P > b->pc[c].P; });
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) {
+    const bool ba = b->pc[a].P > kPMax, bc = b->pc[c].P > kPMax;
+    if (ba != bc) return bc;
+    return b->pc[a].P > b->pc[c].P;
+  });
+  b->n_blocked = 0;
+  for (int i = 0; i < n; ++i) b->n_blocked += b->pc[i].P > kPMax ? 1 : 0;
 
   // ---- device allocations
   auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
@@ -373,7 +383,7 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
             alloc((void**)&b->d_spec, b->spec_elems * sizeof(float2)) == cudaSuccess &&
             alloc((void**)&b->d_err, 16) == cudaSuccess &&
             alloc((void**)&b->d_out, n * sizeof(tm_result)) == cudaSuccess;
-  if (ok && (flags & TM_BATCH_KEEP_CORR)) ok = alloc((void**)&b->d_r, b->r_elems * sizeof(float)) == cudaSuccess;
+  if (ok && b->r_elems > 0) ok = alloc((void**)&b->d_r, b->r_elems * sizeof(float)) == cudaSuccess;
   if (ok && (flags & TM_BATCH_HOST_INPUTS)) {
     int64_t xb = 0, tb = 0;
     b->xoff.resize(n); b->toff.resize(n);
@@ -416,10 +426,15 @@ tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
 
 tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s) {
   CorrArgs a;
-  a.q = b->d_cq; a.order = b->d_order; a.nq = b->n;
+  a.q = b->d_cq; a.order = b->d_order; a.nq = b->n - b->n_blocked;
   a.partial = b->d_partial; a.y = b->d_y; a.spec = b->d_spec; a.r = b->d_r; a.tw = b->tw;
   a.out = out; a.err = b->d_err;
-  TM_CUDA(launch_correlate(a, b->maxP, s));
+  if (a.nq > 0) TM_CUDA(launch_correlate(a, b->maxP, s));
+  if (b->n_blocked > 0) {
+    a.order = b->d_order + (b->n - b->n_blocked);
+    a.nq = b->n_blocked;
+    TM_CUDA(launch_correlate_blocked(a, s));
+  }
   return TM_OK;
 }
 
@@ -542,7 +557,7 @@ tm_status tm_batch_folds(tm_batch_t b, int32_t i, void** y, int32_t* is_float) {
 
 tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r) {
   if (!b || !r || i < 0 || i >= b->n) return fail(TM_EINVAL, "bad query index");
-  if (!b->d_r) return fail(TM_EINVAL, "batch was created without TM_BATCH_KEEP_CORR");
+  if (b->cq[i].r_off < 0) return fail(TM_EINVAL, "batch was created without TM_BATCH_KEEP_CORR");
   *r = b->d_r + b->cq[i].r_off;
   return TM_OK;
 }
@@ -550,7 +565,7 @@ tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r) {
 tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, int64_t* ws) {
   if (!b) return fail(TM_EINVAL, "null batch");
   if (launches) {
-    int32_t l = 1;
+    int32_t l = (b->n > b->n_blocked ? 1 : 0) + (b->n_blocked > 0 ? 1 : 0);
     for (const auto& g : b->groups) l += g.W > 0 ? 1 : 0;
     *launches = l;
   }
@@ -661,6 +676,8 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   PlanCore p;
   tm_status st = make_plan(desc->N, desc->K, desc->xdtype, desc->mode, desc->M1, desc->M2, desc->flags, p);
   if (st != TM_OK) return st;
+  if (p.P > kPMax)
+    return fail(TM_EUNSUPPORTED, "the no-allocation entry point handles FFT lengths up to 16384 (use tm_match)");
   if (signal_bytes(p.xdtype, p.N) > TM_NOALLOC_MAX_SIGNAL_BYTES)
     return fail(TM_EUNSUPPORTED, "signal larger than the " + std::to_string(TM_NOALLOC_MAX_SIGNAL_BYTES) +
                                      " bytes the no-allocation entry point accepts (use tm_match)");

@@ -259,9 +259,21 @@ __device__ __forceinline__ double warp_dot(const float* __restrict__ t, int K, b
   return acc;
 }
 
-__global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a) {
-  extern __shared__ __align__(16) float2 sbuf[];
-  __shared__ float redf[kWarps];
+// Bound on max_j |r~_j - r_j| for correlations computed by length-2^logP
+// FFTs (see the kernel comment), times the number of spectra summed.
+__device__ __forceinline__ float fft_corr_error_bound(int logP, float t1, float t2, float z1, float z2, int terms) {
+  const float u = 5.9604644775390625e-08f;
+  const float epsF = 14.0f * u * float(logP > 0 ? logP : 1);
+  return 1.02f * float(terms) * (epsF * (t2 * z1 + 2.0f * t1 * z2) + 3.0f * u * t1 * z2) + 1e-30f;
+}
+
+// Steps 7-9 for one query, shared by both correlation kernels: argmax of
+// r_j (rval(j, k) = r_j[k], j = 0 for M1, 1 for M2) with exact rescoring of
+// every entry within 2 delta of the maximum, the closed-form intersection
+// S1 ∩ S2 (crt.h), the exact (Tx)_m of its member(s) and the result record.
+template <class RFn>
+__device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, float delta, bool t_integral, float t1,
+                                   int maxy, RFn rval) {
   __shared__ long long redl[kWarps];
   __shared__ double redd[kWarps];
   __shared__ float redv[kWarps];
@@ -273,8 +285,135 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   __shared__ int s_m[2];
   __shared__ double s_r[2];
   __shared__ int s_flags;
-
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int P = Q.P, K = Q.K;
+  const int64_t N = Q.N;
+  const Sig sig{Q.x, Q.xdtype};
+  const bool ints = is_int_dtype(Q.xdtype);
+  const float* __restrict__ t = Q.t;
+  if (tid == 0) s_flags = 0;
+  __syncthreads();
+  const bool exact_int = ints && t_integral;
+  // int32 rescoring is exact when every partial sum stays below 2^31:
+  // |sum| <= ||t||_1 max|y|
+  const bool small = exact_int && double(t1) * double(maxy) < 2.0e9;
+  const void* yv = static_cast<const char*>(a.y) + Q.y_off * 4;
+
+  for (int j = 0; j < 2; ++j) {
+    const int M = Q.M[j];
+    float bv = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int k = tid; k < M; k += kCorrThreads) {
+      better(bv, bi, rval(j, k), k);
+    }
+    block_argmax(bv, bi, redv, redi);
+    if (tid == 0) ncand[j] = 0;
+    __syncthreads();
+    const float thr = bv - 2.0f * delta;
+    for (int k = tid; k < M; k += kCorrThreads) {
+      if (rval(j, k) >= thr) {
+        const int c = atomicAdd(&ncand[j], 1);
+        if (c < kCandCap) cand[j][c] = k;
+      }
+    }
+    __syncthreads();
+    const int nc = ncand[j];
+    const bool all = nc > kCandCap;
+    const int ncheck = all ? M : nc;
+    double wv = -INFINITY;
+    int64_t wi = 0x7fffffffffffffffll;
+    for (int c = warp; c < ncheck; c += kWarps) {
+      const int jj = all ? c : cand[j][c];
+      double v;
+      if (ints) {
+        const int32_t* y = static_cast<const int32_t*>(yv) + int64_t(j) * P + jj;
+        v = warp_dot(t, K, exact_int, small, [&](int i) { return y[i]; });
+      } else {
+        const float* y = static_cast<const float*>(yv) + int64_t(j) * P + jj;
+        v = warp_dot(t, K, false, false, [&](int i) { return y[i]; });
+      }
+      betterd(wv, wi, v, jj);
+    }
+    if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
+    __syncthreads();
+    if (tid == 0) {
+      double v = wbest_v[0];
+      int64_t i = wbest_i[0];
+      for (int w = 1; w < kWarps; ++w) betterd(v, i, wbest_v[w], wbest_i[w]);
+      s_m[j] = int(i);
+      s_r[j] = v;
+      if (all) s_flags |= TM_RF_FULL_RESCORE;
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------ e. steps 8-9
+  const CrtSet cs = crt_intersect(N, Q.M[0], Q.M[1], Q.inv, s_m[0], s_m[1]);
+  const int64_t ncs = cs.nnat + cs.nw;
+  auto member = [&](int64_t c) -> int64_t { return c < cs.nnat ? cs.m0 + c * cs.step : cs.w[c - cs.nnat]; };
+  double best_v = 0.0;
+  int64_t best_m = -1;
+  if (ncs == 1) {
+    // a single member: its exact (Tx)_m, spread over the whole block
+    const int64_t mm = member(0);
+    if (exact_int) {
+      long long acc = 0;
+      for (int i = tid; i < K; i += kCorrThreads) {
+        int64_t n = mm + i;
+        if (n >= N) n -= N;
+        acc += (long long)__float2int_rn(t[i]) * sig.ival(n);
+      }
+      best_v = double(block_sum(acc, redl));
+    } else {
+      double acc = 0.0;
+      for (int i = tid; i < K; i += kCorrThreads) {
+        int64_t n = mm + i;
+        if (n >= N) n -= N;
+        acc = fma(double(t[i]), double(sig.val(n)), acc);
+      }
+      best_v = block_sum(acc, redd);
+    }
+    best_m = mm;
+  } else if (ncs > 1) {
+    double wv = -INFINITY;
+    int64_t wi = 0x7fffffffffffffffll;
+    for (int64_t c = warp; c < ncs; c += kWarps) {
+      const int64_t mm = member(c);
+      const double v = warp_dot(t, K, exact_int, false, [&](int i) {
+        int64_t n = mm + i;
+        if (n >= N) n -= N;
+        return ints ? double(sig.ival(n)) : double(sig.val(n));
+      });
+      betterd(wv, wi, v, mm);
+    }
+    if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
+    __syncthreads();
+    best_v = wbest_v[0];
+    best_m = wbest_i[0];
+    for (int w = 1; w < kWarps; ++w) betterd(best_v, best_m, wbest_v[w], wbest_i[w]);
+  }
+  if (tid == 0) {
+    tm_result res;
+    res.n_cand = int32_t(ncs > 0x7fffffff ? 0x7fffffff : ncs);
+    if (ncs == 0) { res.shift = -1; res.status = TM_EMPTY; res.score = 0.0; }
+    else { res.shift = best_m; res.status = ncs == 1 ? TM_FOUND : TM_RESOLVED; res.score = best_v; }
+    res.status |= s_flags;
+    if (*a.err) res.status |= TM_RF_DEVICE_ERROR;
+    res.m1 = s_m[0];
+    res.m2 = s_m[1];
+    res.r1 = s_r[0];
+    res.r2 = s_r[1];
+    a.out[qi] = res;
+  }
+}
+
+__global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a) {
+  extern __shared__ __align__(16) float2 sbuf[];
+  __shared__ float redf[kWarps];
+  __shared__ long long redl[kWarps];
+  __shared__ int redi[kWarps];
+
+  const int tid = threadIdx.x;
   const int qi = a.order[blockIdx.x];
   const CorrQ Q = a.q[qi];
   const int P = Q.P, logP = Q.logP, K = Q.K;
@@ -285,7 +424,6 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   const int npad = P + (P >> 4);
   const int halfP = P >> 1;
   float2* tw = sbuf + npad;   // W_P^m, m < P/2
-  if (tid == 0) s_flags = 0;
 
   // ------------------------------------------------ twiddles, a. template spectrum
   {
@@ -454,7 +592,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
     for (int k = tid; k < Q.M[1]; k += kCorrThreads) r[P + k] = -sbuf[pad_idx(k)].y * invP;
   }
 
-  // ------------------------------------------------ d. step 7 with exact rescoring
+  // ------------------------------------------------ d-e. steps 7-9
   // Rounding bound (normwise, fp32 unit roundoff u): one length-P FFT has
   // relative 2-norm error <= epsF = 14 u log2 P (the radix-2 bound
   // log2(P) (mu + gamma_4 (sqrt 2 + mu)) with a safety factor of two); with
@@ -462,125 +600,205 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   // max_j |dr_j| <= ||dw||_2 <= epsF (||t||_2 ||z||_1 + 2 ||t||_1 ||z||_2) + 3u ||t||_1 ||z||_2.
   // The norms are fp32 sums (relative error below (K + 2P) u < 1e-2); the
   // factor 1.02 covers them.
-  const float u = 5.9604644775390625e-08f;
-  const float epsF = 14.0f * u * float(logP > 0 ? logP : 1);
-  const float delta = 1.02f * (epsF * (t2 * z1 + 2.0f * t1 * z2) + 3.0f * u * t1 * z2) + 1e-30f;
-  const bool exact_int = ints && t_integral;
-  // int32 rescoring is exact when every partial sum stays below 2^31:
-  // |sum| <= ||t||_1 max|y|
-  const bool small = exact_int && double(t1) * double(maxy) < 2.0e9;
-  const void* yv = static_cast<const char*>(a.y) + Q.y_off * 4;
+  const float delta = fft_corr_error_bound(logP, t1, t2, z1, z2, 1);
+  select_and_resolve(a, Q, qi, delta, t_integral, t1, maxy, [&](int j, int k) {
+    const float2 w = sbuf[pad_idx(k)];
+    return j == 0 ? w.x * invP : -w.y * invP;
+  });
+}
 
+// ---------------------------------------------------------------- blocked correlation
+// For max(M)+K-1 > 16384 the correlation is cut into blocks of B = 8192
+// (overlap-save): with t_b = t[bB, bB+B), the y-segments seg_s = y[sB, sB+2B)
+// and output blocks j = aB + jj, jj < B,
+//   r_j = sum_b sum_{ii<B} t_b[ii] seg_{a+b}[jj + ii],
+// a linear correlation of length-2B arrays that a 2B-point FFT computes
+// without wrap-around. All spectra go to global scratch: T_b (b < Bt), Z_s
+// (s < A+Bt-1, z = y_1 + i y_2 as above); block a is the inverse transform
+// of sum_b T_b conj(Z_{a+b}). The folds are built straight into global memory.
+constexpr int kBlk = 8192;
+constexpr int kBlkLog = 14;   // FFT length 2 kBlk
+
+__global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const CorrArgs a) {
+  extern __shared__ __align__(16) float2 sbuf[];
+  __shared__ float redf[kWarps];
+  __shared__ long long redl[kWarps];
+  __shared__ int redi[kWarps];
+
+  const int tid = threadIdx.x;
+  const int qi = a.order[blockIdx.x];
+  const CorrQ Q = a.q[qi];
+  const int P = Q.P, K = Q.K;
+  const int64_t N = Q.N;
+  const Sig sig{Q.x, Q.xdtype};
+  const bool ints = is_int_dtype(Q.xdtype);
+  const float* __restrict__ t = Q.t;
+  constexpr int PB = 2 * kBlk;
+  constexpr int npad = PB + (PB >> 4);
+  float2* tw = sbuf + npad;   // W_PB^m, m < PB/2
+  const int Bt = (K + kBlk - 1) / kBlk;
+  const int A = (max(Q.M[0], Q.M[1]) + kBlk - 1) / kBlk;
+  const int S = A + Bt - 1;
+  float2* spec = a.spec + Q.spec_off;   // [Bt + S][PB]
+  float* rb = a.r + Q.r_off;            // [2][P]: r_1 then r_2
+
+  {
+    const int stride = kPMax >> kBlkLog;
+    for (int m = tid; m < PB / 2; m += kCorrThreads) tw[m] = __ldg(&a.tw[m * stride]);
+  }
+  // template norms
+  float t1 = 0.f, t2 = 0.f;
+  int tint = 1;
+  for (int k = tid; k < K; k += kCorrThreads) {
+    const float v = t[k];
+    t1 += fabsf(v);
+    t2 = fmaf(v, v, t2);
+    tint &= (v == rintf(v) && fabsf(v) <= 1048576.f) ? 1 : 0;
+  }
+  t1 = block_sum(t1, redf);
+  t2 = sqrtf(block_sum(t2, redf));
+  const bool t_integral = block_and(tint, redi) != 0;
+
+  // ------------------------------------------------ folds, straight to global memory
+  int32_t* yi = static_cast<int32_t*>(a.y) + Q.y_off;
+  float* yf = static_cast<float*>(a.y) + Q.y_off;
+  for (int j = 0; j < 2; ++j) {
+    const int M = Q.M[j], Rr = Q.R[j];
+    const int L = int(Q.L[j]);
+    const int Rw = int(N - int64_t(L - 1) * M);
+    const int32_t* part = a.partial + Q.part + Q.moff[j];
+    for (int k = tid; k < M; k += kCorrThreads) {
+      if (ints) {
+        int c = 0;
+        for (int s = 0; s < Q.nslots; ++s) {
+          const int32_t* ps = part + int64_t(s) * Q.stride;
+          for (int r = 0; r < Rr; ++r) c += ps[k + r * M];
+        }
+        const int nk = L - 1 + (k < Rw ? 1 : 0);
+        int yk = Q.xdtype == TM_BITS_PM1 ? 2 * c - nk : nk - 2 * c;
+        if (k >= Rw) yk += sig.ival(k - Rw);
+        yi[int64_t(j) * P + k] = yk;
+      } else {
+        const float* pf = reinterpret_cast<const float*>(part);
+        float yk = 0.f;
+        for (int s = 0; s < Q.nslots; ++s) {
+          const float* ps = pf + int64_t(s) * Q.stride;
+          for (int r = 0; r < Rr; ++r) yk += ps[k + r * M];
+        }
+        if (k >= Rw) yk += sig.val(k - Rw);
+        yf[int64_t(j) * P + k] = yk;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int64_t n = Q.nelem16; n < N; ++n) {
+      for (int j = 0; j < 2; ++j) {
+        const int64_t e = int64_t(j) * P + n % Q.M[j];
+        if (Q.xdtype == TM_I8_PM1) yi[e] -= sig.ival(n) < 0 ? 2 : 0;
+        else if (Q.xdtype == TM_BITS_PM1) yi[e] += sig.ival(n) > 0 ? 2 : 0;
+        else yf[e] += sig.val(n);
+      }
+    }
+  }
+  __syncthreads();
   for (int j = 0; j < 2; ++j) {
     const int M = Q.M[j];
-    float bv = -INFINITY;
-    int bi = 0x7fffffff;
-    for (int k = tid; k < M; k += kCorrThreads) {
-      const float2 w = sbuf[pad_idx(k)];
-      better(bv, bi, j == 0 ? w.x * invP : -w.y * invP, k);
+    const int64_t LM = Q.L[j] * M;
+    for (int i = tid; i < K - 1; i += kCorrThreads) {
+      int64_t w = i + LM - N;
+      if (w >= N) w %= N;
+      const int64_t e = int64_t(j) * P + M + i, e0 = int64_t(j) * P + i;
+      if (ints) yi[e] = yi[e0] - sig.ival(i) + sig.ival(w);
+      else yf[e] = yf[e0] - sig.val(i) + sig.val(w);
     }
-    block_argmax(bv, bi, redv, redi);
-    if (tid == 0) ncand[j] = 0;
-    __syncthreads();
-    const float thr = bv - 2.0f * delta;
-    for (int k = tid; k < M; k += kCorrThreads) {
-      const float2 w = sbuf[pad_idx(k)];
-      const float rv = j == 0 ? w.x * invP : -w.y * invP;
-      if (rv >= thr) {
-        const int c = atomicAdd(&ncand[j], 1);
-        if (c < kCandCap) cand[j][c] = k;
+  }
+  __syncthreads();
+  // norms of z = y_1 + i y_2
+  auto yval = [&](int j, int64_t k) -> float {
+    if (k >= Q.M[j] + K - 1) return 0.f;
+    return ints ? float(yi[int64_t(j) * P + k]) : yf[int64_t(j) * P + k];
+  };
+  float z1 = 0.f, z2 = 0.f;
+  int maxy = 0;
+  {
+    long long s1 = 0, s2 = 0;
+    float f1 = 0.f, f2 = 0.f;
+    for (int j = 0; j < 2; ++j) {
+      for (int k = tid; k < Q.M[j] + K - 1; k += kCorrThreads) {
+        if (ints) {
+          const int v = yi[int64_t(j) * P + k];
+          s1 += abs(v);
+          s2 += (long long)v * v;
+          maxy = max(maxy, abs(v));
+        } else {
+          const float v = yf[int64_t(j) * P + k];
+          f1 += fabsf(v);
+          f2 = fmaf(v, v, f2);
+        }
       }
     }
-    __syncthreads();
-    const int nc = ncand[j];
-    const bool all = nc > kCandCap;
-    const int ncheck = all ? M : nc;
-    double wv = -INFINITY;
-    int64_t wi = 0x7fffffffffffffffll;
-    for (int c = warp; c < ncheck; c += kWarps) {
-      const int jj = all ? c : cand[j][c];
-      double v;
-      if (ints) {
-        const int32_t* y = static_cast<const int32_t*>(yv) + int64_t(j) * P + jj;
-        v = warp_dot(t, K, exact_int, small, [&](int i) { return y[i]; });
-      } else {
-        const float* y = static_cast<const float*>(yv) + int64_t(j) * P + jj;
-        v = warp_dot(t, K, false, false, [&](int i) { return y[i]; });
-      }
-      betterd(wv, wi, v, jj);
+    if (ints) {
+      s1 = block_sum(s1, redl);
+      s2 = block_sum(s2, redl);
+      z1 = float(s1);
+      z2 = sqrtf(float(s2));
+      maxy = block_max(maxy, redi);
+    } else {
+      z1 = block_sum(f1, redf);
+      z2 = sqrtf(block_sum(f2, redf));
     }
-    if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
-    __syncthreads();
-    if (tid == 0) {
-      double v = wbest_v[0];
-      int64_t i = wbest_i[0];
-      for (int w = 1; w < kWarps; ++w) betterd(v, i, wbest_v[w], wbest_i[w]);
-      s_m[j] = int(i);
-      s_r[j] = v;
-      if (all) s_flags |= TM_RF_FULL_RESCORE;
-    }
-    __syncthreads();
   }
 
-  // ------------------------------------------------ e. steps 8-9
-  const CrtSet cs = crt_intersect(N, Q.M[0], Q.M[1], Q.inv, s_m[0], s_m[1]);
-  const int64_t ncs = cs.nnat + cs.nw;
-  auto member = [&](int64_t c) -> int64_t { return c < cs.nnat ? cs.m0 + c * cs.step : cs.w[c - cs.nnat]; };
-  double best_v = 0.0;
-  int64_t best_m = -1;
-  if (ncs == 1) {
-    // a single member: its exact (Tx)_m, spread over the whole block
-    const int64_t mm = member(0);
-    if (exact_int) {
-      long long acc = 0;
-      for (int i = tid; i < K; i += kCorrThreads) {
-        int64_t n = mm + i;
-        if (n >= N) n -= N;
-        acc += (long long)__float2int_rn(t[i]) * sig.ival(n);
-      }
-      best_v = double(block_sum(acc, redl));
-    } else {
-      double acc = 0.0;
-      for (int i = tid; i < K; i += kCorrThreads) {
-        int64_t n = mm + i;
-        if (n >= N) n -= N;
-        acc = fma(double(t[i]), double(sig.val(n)), acc);
-      }
-      best_v = block_sum(acc, redd);
-    }
-    best_m = mm;
-  } else if (ncs > 1) {
-    double wv = -INFINITY;
-    int64_t wi = 0x7fffffffffffffffll;
-    for (int64_t c = warp; c < ncs; c += kWarps) {
-      const int64_t mm = member(c);
-      const double v = warp_dot(t, K, exact_int, false, [&](int i) {
-        int64_t n = mm + i;
-        if (n >= N) n -= N;
-        return ints ? double(sig.ival(n)) : double(sig.val(n));
-      });
-      betterd(wv, wi, v, mm);
-    }
-    if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
+  // ------------------------------------------------ spectra of template blocks and signal segments
+  for (int b = 0; b < Bt; ++b) {
+    for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
     __syncthreads();
-    best_v = wbest_v[0];
-    best_m = wbest_i[0];
-    for (int w = 1; w < kWarps; ++w) betterd(best_v, best_m, wbest_v[w], wbest_i[w]);
+    for (int i = tid; i < kBlk && b * kBlk + i < K; i += kCorrThreads) sbuf[pad_idx(i)].x = t[b * kBlk + i];
+    __syncthreads();
+    fft(sbuf, kBlkLog, tw);
+    for (int k = tid; k < PB; k += kCorrThreads) spec[int64_t(b) * PB + k] = sbuf[pad_idx(k)];
+    __syncthreads();
   }
-  if (tid == 0) {
-    tm_result res;
-    res.n_cand = int32_t(ncs > 0x7fffffff ? 0x7fffffff : ncs);
-    if (ncs == 0) { res.shift = -1; res.status = TM_EMPTY; res.score = 0.0; }
-    else { res.shift = best_m; res.status = ncs == 1 ? TM_FOUND : TM_RESOLVED; res.score = best_v; }
-    res.status |= s_flags;
-    if (*a.err) res.status |= TM_RF_DEVICE_ERROR;
-    res.m1 = s_m[0];
-    res.m2 = s_m[1];
-    res.r1 = s_r[0];
-    res.r2 = s_r[1];
-    a.out[qi] = res;
+  for (int s = 0; s < S; ++s) {
+    for (int i = tid; i < PB; i += kCorrThreads) {
+      const int64_t k = int64_t(s) * kBlk + i;
+      sbuf[pad_idx(i)] = make_float2(yval(0, k), yval(1, k));
+    }
+    __syncthreads();
+    fft(sbuf, kBlkLog, tw);
+    for (int k = tid; k < PB; k += kCorrThreads) spec[int64_t(Bt + s) * PB + k] = sbuf[pad_idx(k)];
+    __syncthreads();
   }
+  // ------------------------------------------------ output blocks
+  const float invPB = 1.0f / float(PB);
+  for (int ab = 0; ab < A; ++ab) {
+    for (int k = tid; k < PB; k += kCorrThreads) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int b = 0; b < Bt; ++b) {
+        const float2 T = spec[int64_t(b) * PB + k], z = spec[int64_t(Bt + ab + b) * PB + k];
+        acc.x += T.x * z.x + T.y * z.y;   // T conj(Z)
+        acc.y += T.y * z.x - T.x * z.y;
+      }
+      sbuf[pad_idx(k)] = acc;
+    }
+    __syncthreads();
+    fft(sbuf, kBlkLog, tw);
+    for (int i = tid; i < kBlk; i += kCorrThreads) {
+      const int jj = ab * kBlk + i;
+      const float2 w = sbuf[pad_idx(i)];
+      if (jj < Q.M[0]) rb[jj] = w.x * invPB;
+      if (jj < Q.M[1]) rb[P + jj] = -w.y * invPB;
+    }
+    __syncthreads();
+  }
+  // ------------------------------------------------ steps 7-9
+  const float delta = fft_corr_error_bound(kBlkLog, t1, t2, z1, z2, Bt);
+  select_and_resolve(a, Q, qi, delta, t_integral, t1, maxy,
+                     [&](int j, int k) { return rb[int64_t(j) * P + k]; });
 }
+
+int corr_blocked_smem_bytes() { return (2 * kBlk + 2 * kBlk / 16 + kBlk) * int(sizeof(float2)); }
 
 // Shared memory of a launch whose largest FFT is P: the padded work buffer,
 // the half twiddle table and, for P <= 8192, the template spectrum.
@@ -589,7 +807,10 @@ int corr_smem_bytes(int P) { return (P + P / 16 + P / 2 + (P <= 8192 ? P : 0)) *
 }  // namespace
 
 cudaError_t corr_configure() {
-  return cudaFuncSetAttribute(corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, corr_smem_bytes(kPMax));
+  cudaError_t e = cudaFuncSetAttribute(corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, corr_smem_bytes(kPMax));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(corr_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              corr_blocked_smem_bytes());
 }
 
 cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s) {
@@ -597,6 +818,18 @@ cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s) {
   b.smem_bytes = corr_smem_bytes(maxP);
   corr_kernel<<<a.nq, kCorrThreads, b.smem_bytes, s>>>(b);
   return cudaGetLastError();
+}
+
+cudaError_t launch_correlate_blocked(const CorrArgs& a, cudaStream_t s) {
+  CorrArgs b = a;
+  b.smem_bytes = corr_blocked_smem_bytes();
+  corr_blocked_kernel<<<a.nq, kCorrThreads, b.smem_bytes, s>>>(b);
+  return cudaGetLastError();
+}
+
+int blocked_spectra(int K, int maxM) {
+  const int Bt = (K + kBlk - 1) / kBlk, A = (maxM + kBlk - 1) / kBlk;
+  return Bt + A + Bt - 1;
 }
 
 }  // namespace ftm

@@ -508,9 +508,13 @@ cudaError_t fold_configure() {
   if ((e = set_smem(fold_kernel<UnitI8, 5>)) != cudaSuccess) return e;
   if ((e = set_smem(fold_kernel<UnitBits, 2>)) != cudaSuccess) return e;
   if ((e = set_smem(fold_kernel<UnitF16, 4>)) != cudaSuccess) return e;
-  return set_smem(fold_kernel<UnitF32, 8>);
+  if ((e = set_smem(fold_kernel<UnitF16, 8>)) != cudaSuccess) return e;
+  if ((e = set_smem(fold_kernel<UnitF32, 8>)) != cudaSuccess) return e;
+  return set_smem(fold_kernel<UnitF32, 16>);
 }
 
+// Each storage type has a register-lean instantiation for the common moduli
+// and a wider one (moduli up to fold_geom().jmax units per lane).
 cudaError_t launch_fold(const FoldArgs& a, int jmax, cudaStream_t s) {
   switch (a.dtype) {
     case TM_I8_PM1:
@@ -518,8 +522,14 @@ cudaError_t launch_fold(const FoldArgs& a, int jmax, cudaStream_t s) {
       else fold_kernel<UnitI8, 5><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a);
       break;
     case TM_BITS_PM1: fold_kernel<UnitBits, 2><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a); break;
-    case TM_F16: fold_kernel<UnitF16, 4><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a); break;
-    default: fold_kernel<UnitF32, 8><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a); break;
+    case TM_F16:
+      if (jmax <= 4) fold_kernel<UnitF16, 4><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a);
+      else fold_kernel<UnitF16, 8><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a);
+      break;
+    default:
+      if (jmax <= 8) fold_kernel<UnitF32, 8><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a);
+      else fold_kernel<UnitF32, 16><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a);
+      break;
   }
   return cudaGetLastError();
 }

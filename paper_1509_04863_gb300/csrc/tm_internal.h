@@ -41,8 +41,8 @@ struct FoldGeom {
 __host__ __device__ inline FoldGeom fold_geom(int dtype) {
   switch (dtype) {
     case TM_BITS_PM1: return FoldGeom{32, 1, 8192, 2};
-    case TM_F16: return FoldGeom{8, 16, 4096, 4};
-    case TM_F32: return FoldGeom{4, 32, 4096, 8};
+    case TM_F16: return FoldGeom{8, 16, 4096, 8};
+    case TM_F32: return FoldGeom{4, 32, 4096, 16};
     default: return FoldGeom{16, 8, 4096, 5};
   }
 }
@@ -126,6 +126,12 @@ struct CorrArgs {
 // ---------------------------------------------------------------- kernels' host launchers
 cudaError_t launch_fold(const FoldArgs& a, int jmax, cudaStream_t s);
 cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s);
+// Queries with max(M)+K-1 > kPMax: blocked correlation with 2*8192-point
+// FFTs; needs spectra scratch of blocked_spectra(K, max M) * 16384 complex
+// and an r buffer [2][P] (r_off >= 0).
+cudaError_t launch_correlate_blocked(const CorrArgs& a, cudaStream_t s);
+int blocked_spectra(int K, int maxM);
+constexpr int kLogPMaxBlocked = 16;   // largest FFT length the planner accepts: 65536
 cudaError_t fold_configure();   // one-time kernel attributes
 cudaError_t corr_configure();
 

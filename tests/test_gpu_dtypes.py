@@ -104,7 +104,8 @@ def test_bitpacked_batch64_shape(tm):
 
 
 @pytest.mark.parametrize("xdtype", ["f32", "f16"])
-@pytest.mark.parametrize("N,K", [(1 << 20, 2048), ((1 << 18) + 5, 512), (3000, 200), (1 << 22, 8000)])
+@pytest.mark.parametrize("N,K", [(1 << 20, 2048), ((1 << 18) + 5, 512), (3000, 200), (1 << 22, 8000),
+                                 ((1 << 20) + 3, 12000)])
 def test_real_signals(tm, xdtype, N, K):
     qs = [W.planted_query(500 + s + N % 89, N, K, xdtype, t_sigma=0.3, mode="auto") for s in range(3)]
     b, res = _run(tm, qs)

@@ -89,6 +89,9 @@ RAGGED = [
     (1 << 22, 256, "paper", True, 0, 0),          # several CRT solutions
     (1 << 18, 8192, "paper", False, 0, 0),        # P = 16384, J = 2/3 units
     (50000, 8000, "auto", False, 0, 0),
+    (300007, 100, "explicit", False, 20011, 20021),   # M + K - 1 > 16384 with one template block
+    (1 << 20, 12000, "auto", False, 0, 0),            # FFT length 32768, blocked
+    (200000, 20000, "paper", False, 0, 0),            # FFT length 65536: 3 template blocks
 ]
 
 
@@ -164,10 +167,11 @@ def test_batch64_full_size(tm):
         check(b, i, q, res[i], ref, check_r=(i % 16 == 0))
 
 
-@pytest.mark.parametrize("K", [256, 1024, 4096, 8192])
+@pytest.mark.parametrize("K", [256, 1024, 4096, 8192, 16384])
 def test_sweep_shapes(tm, K):
     """N = 2^22, flips p = 0.1, M1 = K, M2 = K+1 (several CRT solutions for
-    K <= 1024): shifts identical to the oracle."""
+    K <= 1024; FFT length 2K = 32768 for K = 16384, correlated in blocks):
+    shifts identical to the oracle."""
     qs = W.sweep(seed=1000 + K, K=K, n=6)
     b, res, _ = run_batch(tm, qs, keep_corr=False)
     for i, q in enumerate(qs):
