@@ -192,6 +192,62 @@ TM_API tm_status tm_batch_destroy(tm_batch_t b);
 /* One-shot batch: create, run, destroy (synchronises the stream). */
 TM_API tm_status tm_match_batch(const tm_query* q, int32_t n, tm_result* out_dev, tm_stream_t stream);
 
+/* ---------------------------------------------------------------- server */
+
+/* Continuous-batching server for a synchronisation-receiver style use of the
+ * method (Sec. 3.5: a known code x is resident, templates arrive and their
+ * shift is wanted). Signals are registered once and stay in device memory;
+ * clients submit (signal, template) requests from any thread; a worker
+ * thread gathers the pending requests into an iteration that fits a fixed
+ * device arena (admission by memory), runs it as a batch (tm_batch_run) on
+ * one of n_streams streams while further requests keep arriving, and posts
+ * results with per-request latency. Results are those of tm_match. */
+
+typedef struct tm_server_s* tm_server_t;
+
+typedef struct {
+  int32_t n_streams;          /* iterations in flight, 1..4 (0: 2) */
+  int32_t max_batch;          /* requests per iteration (0: 512) */
+  int32_t queue_capacity;     /* pending requests before TM_EAGAIN (0: 65536) */
+  uint32_t flags;             /* reserved, 0 */
+  int64_t arena_bytes;        /* device workspace per stream (0: share of free memory) */
+  int64_t hbm_reserve_bytes;  /* left free when arena_bytes is 0 (0: 4 GiB) */
+} tm_serve_cfg;
+
+typedef struct {
+  uint64_t tag;        /* the caller's tag from tm_serve_submit */
+  int32_t status;      /* TM_OK, or why the request failed (e.g. TM_ENOMEM) */
+  int32_t reserved;
+  double latency_us;   /* submission to result, host clock */
+  tm_result r;
+} tm_result_tagged;
+
+typedef struct {
+  int64_t submitted, completed, failed, iterations, pending, in_flight;
+  double mean_batch;   /* requests per iteration */
+  double p50_us, p99_us, max_us;   /* latency over the completed requests */
+} tm_serve_stats;
+
+/* Signal registration flag: x is device memory to use in place (the caller
+ * keeps it alive until tm_serve_destroy); otherwise x is host memory and
+ * the server keeps its own device copy. */
+#define TM_SERVE_SIGNAL_DEVICE 0x1u
+
+TM_API tm_status tm_serve_create(const tm_serve_cfg* cfg, tm_server_t* out);
+TM_API tm_status tm_serve_register_signal(tm_server_t s, const void* x, int64_t N, int32_t xdtype, uint32_t flags,
+                                          int32_t* sig_id);
+/* Copies t_host (K floats) and queues the request; TM_EAGAIN when the queue
+ * is full, TM_EINVAL for an unknown signal or an invalid plan, TM_ENOMEM when
+ * the request alone exceeds the arena. mode/M1/M2/plan_flags as tm_plan_desc. */
+TM_API tm_status tm_serve_submit(tm_server_t s, int32_t sig_id, const float* t_host, int32_t K, int32_t mode,
+                                 int32_t M1, int32_t M2, uint32_t plan_flags, uint64_t tag);
+/* Up to max finished results; waits up to timeout_us for the first one.
+ * Returns the number written (0 on timeout) or -tm_status on error. */
+TM_API int32_t tm_serve_poll(tm_server_t s, tm_result_tagged* out, int32_t max, int64_t timeout_us);
+TM_API tm_status tm_serve_stats_get(tm_server_t s, tm_serve_stats* st);
+/* Stops the worker after the in-flight iterations, frees everything. */
+TM_API tm_status tm_serve_destroy(tm_server_t s);
+
 /* ----------------------------------------------------------- host helper */
 
 /* Steps 8-9 in closed form on the host: the elements of

@@ -312,3 +312,100 @@ def device_view(ptr: int, n: int, typestr: str):
 def result_buffer(n: int, device="cuda"):
     import torch
     return torch.zeros(n * RESULT_BYTES // 8, dtype=torch.int64, device=device)
+
+
+# ---------------------------------------------------------------- server (tm_serve_*)
+class tm_serve_cfg(C.Structure):
+    _fields_ = [("n_streams", C.c_int32), ("max_batch", C.c_int32), ("queue_capacity", C.c_int32),
+                ("flags", C.c_uint32), ("arena_bytes", C.c_int64), ("hbm_reserve_bytes", C.c_int64)]
+
+
+class tm_result_tagged(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("reserved", C.c_int32), ("latency_us", C.c_double),
+                ("r", tm_result)]
+
+
+class tm_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("iterations", C.c_int64), ("pending", C.c_int64), ("in_flight", C.c_int64),
+                ("mean_batch", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double)]
+
+
+TM_SERVE_SIGNAL_DEVICE = 0x1
+_SIGS.update({
+    "tm_serve_create": (C.c_int, [C.POINTER(tm_serve_cfg), C.POINTER(C.c_void_p)]),
+    "tm_serve_register_signal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_uint32,
+                                           C.POINTER(C.c_int32)]),
+    "tm_serve_submit": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                  C.c_uint32, C.c_uint64]),
+    "tm_serve_poll": (C.c_int32, [C.c_void_p, C.POINTER(tm_result_tagged), C.c_int32, C.c_int64]),
+    "tm_serve_stats_get": (C.c_int, [C.c_void_p, C.POINTER(tm_serve_stats)]),
+    "tm_serve_destroy": (C.c_int, [C.c_void_p]),
+})
+
+
+class Server:
+    """tm_serve_create / register_signal / submit / poll / stats / destroy."""
+
+    def __init__(self, n_streams: int = 2, max_batch: int = 512, queue_capacity: int = 65536,
+                 arena_bytes: int = 0, hbm_reserve_bytes: int = 0):
+        L = lib()
+        cfg = tm_serve_cfg(n_streams, max_batch, queue_capacity, 0, arena_bytes, hbm_reserve_bytes)
+        h = C.c_void_p()
+        _check(L.tm_serve_create(C.byref(cfg), C.byref(h)), "tm_serve_create")
+        self._h = h
+        self._keep = []
+
+    def register_signal(self, x, N: int, xdtype: str = "i8") -> int:
+        """x: numpy array / CPU tensor (copied to the device) or CUDA tensor (used in place)."""
+        import numpy as np
+        sid = C.c_int32()
+        if hasattr(x, "is_cuda") and x.is_cuda:
+            self._keep.append(x)
+            st = lib().tm_serve_register_signal(self._h, x.data_ptr(), N, DTYPE_CODES[xdtype],
+                                                TM_SERVE_SIGNAL_DEVICE, C.byref(sid))
+        else:
+            arr = np.ascontiguousarray(x.numpy() if hasattr(x, "numpy") else x)
+            st = lib().tm_serve_register_signal(self._h, arr.ctypes.data, N, DTYPE_CODES[xdtype], 0, C.byref(sid))
+        _check(st, "tm_serve_register_signal")
+        return sid.value
+
+    def submit(self, sig_id: int, t, tag: int, mode: str = "paper", M1: int = 0, M2: int = 0,
+               allow_ambig: bool = False) -> int:
+        """Queue one request; returns the status (TM_OK, TM_EAGAIN, ...) without raising for TM_EAGAIN."""
+        import numpy as np
+        tt = np.ascontiguousarray(t, dtype=np.float32)
+        st = lib().tm_serve_submit(self._h, sig_id, tt.ctypes.data, int(tt.shape[0]), MODE_CODES[mode], M1, M2,
+                                   TM_ALLOW_AMBIG if allow_ambig else 0, tag)
+        if st not in (TM_OK, TM_EAGAIN):
+            raise TMError(st, "tm_serve_submit")
+        return st
+
+    def poll(self, max_results: int = 1024, timeout_us: int = 0):
+        buf = (tm_result_tagged * max_results)()
+        k = lib().tm_serve_poll(self._h, buf, max_results, timeout_us)
+        if k < 0:
+            raise TMError(-k, "tm_serve_poll")
+        out = []
+        for i in range(k):
+            r = buf[i]
+            d = {f: getattr(r.r, f) for f, _ in tm_result._fields_}
+            d.update(tag=r.tag, req_status=r.status, latency_us=r.latency_us)
+            out.append(d)
+        return out
+
+    def stats(self) -> dict:
+        s = tm_serve_stats()
+        _check(lib().tm_serve_stats_get(self._h, C.byref(s)), "tm_serve_stats_get")
+        return {f: getattr(s, f) for f, _ in tm_serve_stats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().tm_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

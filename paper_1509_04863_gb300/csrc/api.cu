@@ -12,13 +12,15 @@
 #include <vector>
 
 #include "crt.h"
-#include "tm_internal.h"
+#include "runtime.h"
+
+namespace ftm {
 
 namespace {
-
-using namespace ftm;
-
 thread_local std::string g_err;
+}  // namespace
+
+std::string& last_error() { return g_err; }
 
 tm_status fail(tm_status s, const std::string& msg) {
   g_err = msg;
@@ -29,14 +31,7 @@ tm_status cuda_fail(cudaError_t e, const char* what) {
   return fail(TM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define TM_CUDA(call)                                   \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-
-int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-int64_t pad16(int64_t v) { return (v + 15) & ~int64_t(15); }
+namespace {
 
 int64_t gcd64(int64_t a, int64_t b) {
   while (b) { const int64_t t = a % b; a = b; b = t; }
@@ -51,6 +46,8 @@ int64_t least_s(int64_t N) {
   return s;
 }
 
+}  // namespace
+
 int64_t signal_bytes(int32_t dtype, int64_t N) {
   switch (dtype) {
     case TM_I8_PM1: return N;
@@ -59,17 +56,6 @@ int64_t signal_bytes(int32_t dtype, int64_t N) {
     default: return 4 * N;
   }
 }
-
-struct PlanCore {
-  int64_t N = 0;
-  int32_t K = 0, xdtype = 0;
-  int32_t M[2] = {0, 0};
-  int64_t L[2] = {0, 0};
-  int32_t P = 0, logP = 0;
-  int32_t inv = 0;
-  int32_t R[2] = {1, 1}, Mp[2] = {0, 0};
-  int64_t max_cand = 0;
-};
 
 // Algorithm 1 step 2 and the derived sizes.
 tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t M1, int32_t M2, uint32_t flags,
@@ -128,9 +114,11 @@ int64_t fold_elems(int32_t dtype, int64_t N) {
 }
 
 // ---------------------------------------------------------------- per-device state
+namespace {
 std::mutex g_mu;
 std::vector<float2*> g_twiddles;   // per device
 std::vector<int> g_configured;
+}  // namespace
 
 tm_status device_setup(int dev, float2** tw) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -154,59 +142,16 @@ tm_status device_setup(int dev, float2** tw) {
   return TM_OK;
 }
 
-}  // namespace
+}  // namespace ftm
 
 // ---------------------------------------------------------------- objects
-struct tm_batch_s {
-  int device = 0;
-  uint32_t flags = 0;
-  int32_t n = 0;
-  std::vector<PlanCore> pc;
-  std::vector<tm_query> q;
-  std::vector<FoldQ> fq;
-  std::vector<CorrQ> cq;
-  std::vector<int32_t> order;
-  std::vector<int64_t> xoff, toff;   // device input copies (TM_BATCH_HOST_INPUTS)
-  // One fold launch per signal storage type present: its queries occupy
-  // fq[first, first + count) (fq is ordered by group), fold_of[i] is the
-  // fq position of query i.
-  struct FoldGroup {
-    int32_t dtype, first, count, nctas, jmax;
-    int64_t W;
-  };
-  std::vector<FoldGroup> groups;
-  std::vector<int32_t> fold_of;
-  int32_t nctas = 0;   // largest fold grid
-  int64_t W = 0;       // bytes folded in total
-  int32_t maxP = 0;        // largest FFT of the shared-memory correlation launch
-  int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_blocked, n))
-  int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
-  FoldQ* d_fq = nullptr;
-  CorrQ* d_cq = nullptr;
-  int32_t* d_order = nullptr;
-  int32_t* d_partial = nullptr;
-  void* d_y = nullptr;
-  float2* d_spec = nullptr;
-  float* d_r = nullptr;
-  int32_t* d_err = nullptr;
-  tm_result* d_out = nullptr;
-  uint8_t* d_x = nullptr;
-  float* d_t = nullptr;
-  float2* tw = nullptr;
-  // pinned staging for descriptor uploads, guarded by an event
-  void* h_stage = nullptr;
-  size_t stage_bytes = 0;
-  cudaEvent_t ev_stage = nullptr;
-  int64_t ws_bytes = 0;
-};
-
 struct tm_plan_s {
   tm_plan_desc d;
-  PlanCore pc;
+  ftm::PlanCore pc;
   tm_batch_t b = nullptr;
 };
 
-namespace {
+namespace ftm {
 
 void batch_free(tm_batch_t b) {
   if (!b) return;
@@ -214,10 +159,12 @@ void batch_free(tm_batch_t b) {
   cudaGetDevice(&cur);
   cudaSetDevice(b->device);
   if (b->ev_stage) { cudaEventSynchronize(b->ev_stage); cudaEventDestroy(b->ev_stage); }
-  cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_order); cudaFree(b->d_partial);
-  cudaFree(b->d_y); cudaFree(b->d_spec); cudaFree(b->d_r); cudaFree(b->d_err); cudaFree(b->d_out);
-  cudaFree(b->d_x); cudaFree(b->d_t);
-  if (b->h_stage) cudaFreeHost(b->h_stage);
+  if (b->owns_memory) {
+    cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_order); cudaFree(b->d_partial);
+    cudaFree(b->d_y); cudaFree(b->d_spec); cudaFree(b->d_r); cudaFree(b->d_err); cudaFree(b->d_out);
+    cudaFree(b->d_x); cudaFree(b->d_t);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+  }
   cudaSetDevice(cur);
   delete b;
 }
@@ -247,12 +194,8 @@ tm_status upload_descriptors(tm_batch_t b, cudaStream_t s) {
   return TM_OK;
 }
 
-tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* out) {
-  if (!out) return fail(TM_EINVAL, "null output handle");
-  *out = nullptr;
+tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags) {
   if (n < 1 || !q) return fail(TM_EINVAL, "empty batch");
-  tm_batch_t b = new (std::nothrow) tm_batch_s();
-  if (!b) return fail(TM_ENOMEM, "host allocation");
   b->flags = flags;
   b->n = n;
   b->q.assign(q, q + n);
@@ -261,22 +204,19 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
     tm_status st = make_plan(q[i].N, q[i].K, q[i].xdtype, q[i].mode, q[i].M1, q[i].M2, q[i].flags, b->pc[i]);
     if (st != TM_OK) {
       g_err = "query " + std::to_string(i) + ": " + g_err;
-      delete b;
       return st;
     }
     if (!(flags & TM_BATCH_HOST_INPUTS)) {
-      if (!q[i].x || !q[i].t) { delete b; return fail(TM_EINVAL, "null x or t pointer"); }
-      if (reinterpret_cast<uintptr_t>(q[i].x) & 15) { delete b; return fail(TM_EINVAL, "x must be 16-byte aligned"); }
-      if (reinterpret_cast<uintptr_t>(q[i].t) & 3) { delete b; return fail(TM_EINVAL, "t must be 4-byte aligned"); }
+      if (!q[i].x || !q[i].t) return fail(TM_EINVAL, "null x or t pointer");
+      if (reinterpret_cast<uintptr_t>(q[i].x) & 15) return fail(TM_EINVAL, "x must be 16-byte aligned");
+      if (reinterpret_cast<uintptr_t>(q[i].t) & 3) return fail(TM_EINVAL, "t must be 4-byte aligned");
     }
   }
-  cudaError_t e = cudaGetDevice(&b->device);
-  if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaGetDevice"); }
+  TM_CUDA(cudaGetDevice(&b->device));
   int sms = 0;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+  TM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   tm_status st = device_setup(b->device, &b->tw);
-  if (st != TM_OK) { delete b; return st; }
+  if (st != TM_OK) return st;
 
   // ---- fold geometry: per storage type, a flattened byte space split into
   // equal shares, one per CTA
@@ -370,7 +310,12 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
   b->n_blocked = 0;
   for (int i = 0; i < n; ++i) b->n_blocked += b->pc[i].P > kPMax ? 1 : 0;
 
-  // ---- device allocations
+  return TM_OK;
+}
+
+tm_status batch_alloc(tm_batch_s* b) {
+  const int32_t n = b->n;
+  const uint32_t flags = b->flags;
   auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
     b->ws_bytes += int64_t(bytes);
     return cudaMalloc(ptr, std::max<size_t>(bytes, 16));
@@ -398,16 +343,32 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
   if (ok) ok = cudaEventCreateWithFlags(&b->ev_stage, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
-    batch_free(b);
     return fail(TM_ENOMEM, "device workspace allocation failed");
   }
-  cudaMemset(b->d_err, 0, 16);
-  cudaMemcpy(b->d_order, b->order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
-  bind_pointers(b);
-  st = upload_descriptors(b, nullptr);
-  if (st != TM_OK) { batch_free(b); return st; }
-  e = cudaStreamSynchronize(nullptr);
-  if (e != cudaSuccess) { batch_free(b); return cuda_fail(e, "descriptor upload"); }
+  TM_CUDA(cudaMemset(b->d_err, 0, 16));
+  TM_CUDA(cudaMemcpy(b->d_order, b->order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return TM_OK;
+}
+
+tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* out) {
+  if (!out) return fail(TM_EINVAL, "null output handle");
+  *out = nullptr;
+  tm_batch_t b = new (std::nothrow) tm_batch_s();
+  if (!b) return fail(TM_ENOMEM, "host allocation");
+  tm_status st = batch_plan(b, q, n, flags);
+  if (st == TM_OK) st = batch_alloc(b);
+  if (st == TM_OK) {
+    bind_pointers(b);
+    st = upload_descriptors(b, nullptr);
+  }
+  if (st == TM_OK) {
+    const cudaError_t e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) st = cuda_fail(e, "descriptor upload");
+  }
+  if (st != TM_OK) {
+    batch_free(b);
+    return st;
+  }
   *out = b;
   return TM_OK;
 }
@@ -438,7 +399,9 @@ tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s) {
   return TM_OK;
 }
 
-}  // namespace
+}  // namespace ftm
+
+using namespace ftm;
 
 // ================================================================ C ABI
 extern "C" {

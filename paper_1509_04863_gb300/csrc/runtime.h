@@ -1,0 +1,109 @@
+// Host runtime shared by the C ABI (api.cu) and the server (serve.cu):
+// planning, batch layouts and launches.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "tm_internal.h"
+
+namespace ftm {
+
+// Error reporting: sets the calling thread's message (tm_last_error).
+tm_status fail(tm_status s, const std::string& msg);
+tm_status cuda_fail(cudaError_t e, const char* what);
+std::string& last_error();
+
+#define TM_CUDA(call)                                           \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return ::ftm::cuda_fail(e_, #call);  \
+  } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t pad16(int64_t v) { return (v + 15) & ~int64_t(15); }
+
+struct PlanCore {
+  int64_t N = 0;
+  int32_t K = 0, xdtype = 0;
+  int32_t M[2] = {0, 0};
+  int64_t L[2] = {0, 0};
+  int32_t P = 0, logP = 0;
+  int32_t inv = 0;
+  int32_t R[2] = {1, 1}, Mp[2] = {0, 0};
+  int64_t max_cand = 0;
+};
+
+
+// Algorithm 1 step 2 and the derived sizes (host only).
+tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t M1, int32_t M2, uint32_t flags,
+                    PlanCore& pc);
+int64_t signal_bytes(int32_t dtype, int64_t N);
+int64_t fold_bytes(int32_t dtype, int64_t N);
+int64_t fold_elems(int32_t dtype, int64_t N);
+// Once per device: kernel attributes and the twiddle table.
+tm_status device_setup(int dev, float2** tw);
+
+}  // namespace ftm
+
+struct tm_batch_s {
+  bool owns_memory = true;   // false: device buffers belong to a server arena
+  int device = 0;
+  uint32_t flags = 0;
+  int32_t n = 0;
+  std::vector<ftm::PlanCore> pc;
+  std::vector<tm_query> q;
+  std::vector<ftm::FoldQ> fq;
+  std::vector<ftm::CorrQ> cq;
+  std::vector<int32_t> order;
+  std::vector<int64_t> xoff, toff;   // device input copies (TM_BATCH_HOST_INPUTS)
+  // One fold launch per signal storage type present: its queries occupy
+  // fq[first, first + count) (fq is ordered by group), fold_of[i] is the
+  // fq position of query i.
+  struct FoldGroup {
+    int32_t dtype, first, count, nctas, jmax;
+    int64_t W;
+  };
+  std::vector<FoldGroup> groups;
+  std::vector<int32_t> fold_of;
+  int32_t nctas = 0;   // largest fold grid
+  int64_t W = 0;       // bytes folded in total
+  int32_t maxP = 0;        // largest FFT of the shared-memory correlation launch
+  int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_blocked, n))
+  int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
+  ftm::FoldQ* d_fq = nullptr;
+  ftm::CorrQ* d_cq = nullptr;
+  int32_t* d_order = nullptr;
+  int32_t* d_partial = nullptr;
+  void* d_y = nullptr;
+  float2* d_spec = nullptr;
+  float* d_r = nullptr;
+  int32_t* d_err = nullptr;
+  tm_result* d_out = nullptr;
+  uint8_t* d_x = nullptr;
+  float* d_t = nullptr;
+  float2* tw = nullptr;
+  // pinned staging for descriptor uploads, guarded by an event
+  void* h_stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t ev_stage = nullptr;
+  int64_t ws_bytes = 0;
+};
+
+
+namespace ftm {
+
+// Host layout of a batch (plans, fold groups, descriptors, order, sizes);
+// needs the device that will run it to be current (SM count, twiddles).
+tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags);
+// Device buffers from cudaMalloc (owns_memory) and pinned staging.
+tm_status batch_alloc(tm_batch_s* b);
+void batch_free(tm_batch_s* b);
+void bind_pointers(tm_batch_s* b);
+tm_status upload_descriptors(tm_batch_s* b, cudaStream_t s);
+tm_status batch_fold(tm_batch_s* b, cudaStream_t s);
+tm_status batch_correlate(tm_batch_s* b, tm_result* out, cudaStream_t s);
+
+}  // namespace ftm

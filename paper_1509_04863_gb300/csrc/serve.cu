@@ -1,0 +1,496 @@
+// Continuous-batching server (tm_serve_*), see include/tm.h.
+//
+// A worker thread owns the device work. Each in-flight iteration has a
+// stream, a device arena (one allocation at start-up), pinned staging for
+// templates, descriptors and results, and an event. The worker loop:
+//   1. retire iterations whose event completed: post their results with
+//      latencies to the completion queue;
+//   2. for each idle stream, take pending requests in arrival order, as many
+//      as fit the arena (planned on the host; the batch shrinks until its
+//      buffers fit), copy their templates, upload the batch descriptors and
+//      launch fold + correlation + result copy on that stream;
+//   3. spin briefly while iterations are in flight, otherwise sleep on the
+//      submission condition variable.
+// Requests that arrive while others run join the next iteration, so work of
+// consecutive iterations overlaps on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace ftm;
+
+namespace {
+
+double now_us() {
+  return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+  uint64_t tag;
+  int32_t sig;
+  tm_query q;      // x filled from the signal, t set per iteration
+  PlanCore plan;
+  std::vector<float> t;
+  double t_submit;
+};
+
+struct Signal {
+  const void* x;
+  int64_t N;
+  int32_t dtype;
+  bool owned;
+};
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+struct Slot {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  char* arena = nullptr;
+  int64_t arena_bytes = 0;
+  float* h_t = nullptr;         // pinned template staging
+  int64_t h_t_cap = 0;          // floats
+  tm_result* h_out = nullptr;   // pinned results
+  void* h_stage = nullptr;      // pinned descriptor staging
+  size_t h_stage_cap = 0;
+  int32_t* h_order = nullptr;   // pinned processing order
+  tm_batch_s* b = nullptr;
+  std::vector<Req> reqs;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct tm_server_s {
+  tm_serve_cfg cfg{};
+  int device = 0;
+  std::vector<Slot> slots;
+  std::vector<Signal> signals;
+  std::mutex mu;                       // pending, signals
+  std::condition_variable cv;
+  std::deque<Req> pending;
+  std::mutex cmu;                      // completed, stats
+  std::condition_variable ccv;
+  std::deque<tm_result_tagged> done;
+  std::vector<double> lat;             // completed latencies (bounded)
+  int64_t submitted = 0, completed = 0, failed = 0, iterations = 0, batched = 0;
+  std::atomic<bool> stop{false};
+  std::atomic<int> busy{0};            // iterations in flight
+  std::thread worker;
+};
+
+namespace {
+
+// Device bytes of a planned batch when carved from an arena.
+size_t batch_bytes(const tm_batch_s* b, int64_t t_floats) {
+  const size_t n = size_t(b->n);
+  return align_up(n * sizeof(FoldQ)) + align_up(n * sizeof(CorrQ)) + align_up(n * sizeof(int32_t)) +
+         align_up(size_t(b->part_elems) * 4) + align_up(size_t(b->y_elems) * 4) +
+         align_up(size_t(b->spec_elems) * sizeof(float2)) + align_up(size_t(b->r_elems) * 4) + align_up(16) +
+         align_up(n * sizeof(tm_result)) + align_up(size_t(t_floats) * 4);
+}
+
+void carve(tm_batch_s* b, char* base, int64_t t_floats) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base + o;
+    o += align_up(bytes);
+    return p;
+  };
+  const size_t n = size_t(b->n);
+  b->d_fq = reinterpret_cast<FoldQ*>(take(n * sizeof(FoldQ)));
+  b->d_cq = reinterpret_cast<CorrQ*>(take(n * sizeof(CorrQ)));
+  b->d_order = reinterpret_cast<int32_t*>(take(n * sizeof(int32_t)));
+  b->d_partial = reinterpret_cast<int32_t*>(take(size_t(b->part_elems) * 4));
+  b->d_y = take(size_t(b->y_elems) * 4);
+  b->d_spec = reinterpret_cast<float2*>(take(size_t(b->spec_elems) * sizeof(float2)));
+  b->d_r = b->r_elems > 0 ? reinterpret_cast<float*>(take(size_t(b->r_elems) * 4)) : nullptr;
+  b->d_err = reinterpret_cast<int32_t*>(take(16));
+  b->d_out = reinterpret_cast<tm_result*>(take(n * sizeof(tm_result)));
+  b->d_t = reinterpret_cast<float*>(take(size_t(t_floats) * 4));
+}
+
+void reset_batch(tm_batch_s* b) {
+  tm_batch_s fresh;
+  fresh.owns_memory = false;
+  fresh.h_stage = b->h_stage;
+  fresh.stage_bytes = b->stage_bytes;
+  fresh.ev_stage = b->ev_stage;
+  *b = std::move(fresh);
+}
+
+void post(tm_server_t sv, std::vector<tm_result_tagged>& out) {
+  std::lock_guard<std::mutex> lk(sv->cmu);
+  for (auto& r : out) {
+    sv->done.push_back(r);
+    if (r.status == TM_OK) {
+      ++sv->completed;
+      if (sv->lat.size() < (size_t(1) << 22)) sv->lat.push_back(r.latency_us);
+    } else {
+      ++sv->failed;
+    }
+  }
+  sv->ccv.notify_all();
+}
+
+void fail_reqs(tm_server_t sv, std::vector<Req>& reqs, tm_status st) {
+  std::vector<tm_result_tagged> out;
+  const double t = now_us();
+  for (auto& q : reqs) {
+    tm_result_tagged r{};
+    r.tag = q.tag;
+    r.status = st;
+    r.latency_us = t - q.t_submit;
+    r.r.shift = -1;
+    out.push_back(r);
+  }
+  reqs.clear();
+  post(sv, out);
+}
+
+// Launch one iteration of `reqs` on slot `sl`; false if it could not be set up.
+tm_status launch_iteration(tm_server_t sv, Slot& sl) {
+  std::vector<Req>& reqs = sl.reqs;
+  const int n = int(reqs.size());
+  std::vector<tm_query> qs(n);
+  int64_t t_floats = 0;
+  std::vector<int64_t> toff(n);
+  for (int i = 0; i < n; ++i) {
+    toff[i] = t_floats;
+    t_floats += pad16(reqs[i].q.K);
+  }
+  if (t_floats > sl.h_t_cap) return TM_ENOMEM;
+  // the template pointers are only known after carving; plan with
+  // placeholders (planning reads shapes only), then bind
+  for (int i = 0; i < n; ++i) {
+    qs[i] = reqs[i].q;
+    qs[i].t = reinterpret_cast<const float*>(uintptr_t(16));
+  }
+  reset_batch(sl.b);
+  tm_status st = batch_plan(sl.b, qs.data(), n, 0);
+  if (st != TM_OK) return st;
+  if (batch_bytes(sl.b, t_floats) > size_t(sl.arena_bytes)) return TM_ENOMEM;
+  carve(sl.b, sl.arena, t_floats);
+  for (int i = 0; i < n; ++i) {
+    sl.b->q[i].t = sl.b->d_t + toff[i];
+    std::memcpy(sl.h_t + toff[i], reqs[i].t.data(), size_t(reqs[i].q.K) * sizeof(float));
+  }
+  std::memcpy(sl.h_order, sl.b->order.data(), size_t(n) * sizeof(int32_t));
+  bind_pointers(sl.b);
+  TM_CUDA(cudaMemcpyAsync(sl.b->d_t, sl.h_t, size_t(t_floats) * sizeof(float), cudaMemcpyHostToDevice, sl.s));
+  TM_CUDA(cudaMemcpyAsync(sl.b->d_order, sl.h_order, size_t(n) * sizeof(int32_t), cudaMemcpyHostToDevice, sl.s));
+  st = upload_descriptors(sl.b, sl.s);
+  if (st != TM_OK) return st;
+  st = batch_fold(sl.b, sl.s);
+  if (st != TM_OK) return st;
+  st = batch_correlate(sl.b, sl.b->d_out, sl.s);
+  if (st != TM_OK) return st;
+  TM_CUDA(cudaMemcpyAsync(sl.h_out, sl.b->d_out, size_t(n) * sizeof(tm_result), cudaMemcpyDeviceToHost, sl.s));
+  TM_CUDA(cudaEventRecord(sl.ev, sl.s));
+  return TM_OK;
+}
+
+// Take the next requests that fit the arena of `sl` (in arrival order).
+void admit(tm_server_t sv, Slot& sl) {
+  std::vector<Req> take;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const size_t k = std::min<size_t>(sv->pending.size(), size_t(sv->cfg.max_batch));
+    for (size_t i = 0; i < k; ++i) {
+      take.push_back(std::move(sv->pending.front()));
+      sv->pending.pop_front();
+    }
+  }
+  while (!take.empty()) {
+    sl.reqs = std::move(take);
+    take.clear();
+    const tm_status st = launch_iteration(sv, sl);
+    if (st == TM_OK) {
+      sl.busy = true;
+      sv->busy.fetch_add(1);
+      std::lock_guard<std::mutex> lk(sv->cmu);
+      ++sv->iterations;
+      sv->batched += int64_t(sl.reqs.size());
+      return;
+    }
+    if (st == TM_ENOMEM && sl.reqs.size() > 1) {
+      // too large for the arena: return the newer half to the queue front
+      const size_t keep = sl.reqs.size() / 2;
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (size_t i = sl.reqs.size(); i-- > keep;) sv->pending.push_front(std::move(sl.reqs[i]));
+      sl.reqs.resize(keep);
+      take = std::move(sl.reqs);
+      continue;
+    }
+    fail_reqs(sv, sl.reqs, st);
+    return;
+  }
+}
+
+void retire(tm_server_t sv, Slot& sl) {
+  const double t = now_us();
+  std::vector<tm_result_tagged> out(sl.reqs.size());
+  for (size_t i = 0; i < sl.reqs.size(); ++i) {
+    out[i].tag = sl.reqs[i].tag;
+    out[i].status = TM_OK;
+    out[i].latency_us = t - sl.reqs[i].t_submit;
+    out[i].r = sl.h_out[i];
+  }
+  sl.reqs.clear();
+  sl.busy = false;
+  sv->busy.fetch_sub(1);
+  post(sv, out);
+}
+
+void worker_main(tm_server_t sv) {
+  cudaSetDevice(sv->device);
+  while (true) {
+    bool progressed = false, any_busy = false;
+    for (auto& sl : sv->slots) {
+      if (!sl.busy) continue;
+      const cudaError_t e = cudaEventQuery(sl.ev);
+      if (e == cudaSuccess) {
+        retire(sv, sl);
+        progressed = true;
+      } else if (e != cudaErrorNotReady) {
+        cudaGetLastError();
+        sl.busy = false;
+        sv->busy.fetch_sub(1);
+        fail_reqs(sv, sl.reqs, TM_ECUDA);
+        progressed = true;
+      } else {
+        any_busy = true;
+      }
+    }
+    bool have_pending;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      have_pending = !sv->pending.empty();
+    }
+    if (have_pending) {
+      for (auto& sl : sv->slots) {
+        if (sl.busy) continue;
+        admit(sv, sl);
+        progressed = true;
+        break;
+      }
+    }
+    if (sv->stop.load() && !have_pending && !any_busy) break;
+    if (!progressed) {
+      if (any_busy) {
+        std::this_thread::yield();
+      } else {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        sv->cv.wait_for(lk, std::chrono::milliseconds(2),
+                        [&] { return !sv->pending.empty() || sv->stop.load(); });
+      }
+    }
+  }
+}
+
+void server_free(tm_server_t sv) {
+  for (auto& sl : sv->slots) {
+    if (sl.s) cudaStreamSynchronize(sl.s);
+    if (sl.b) batch_free(sl.b);   // destroys the staging event, not the arena
+    if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.s) cudaStreamDestroy(sl.s);
+    cudaFree(sl.arena);
+    if (sl.h_t) cudaFreeHost(sl.h_t);
+    if (sl.h_out) cudaFreeHost(sl.h_out);
+    if (sl.h_stage) cudaFreeHost(sl.h_stage);
+    if (sl.h_order) cudaFreeHost(sl.h_order);
+  }
+  for (auto& sg : sv->signals)
+    if (sg.owned) cudaFree(const_cast<void*>(sg.x));
+  delete sv;
+}
+
+}  // namespace
+
+extern "C" {
+
+tm_status tm_serve_create(const tm_serve_cfg* cfg_in, tm_server_t* out) {
+  if (!out) return fail(TM_EINVAL, "null output handle");
+  *out = nullptr;
+  tm_serve_cfg cfg = cfg_in ? *cfg_in : tm_serve_cfg{};
+  if (cfg.n_streams <= 0) cfg.n_streams = 2;
+  if (cfg.n_streams > 4) return fail(TM_EINVAL, "n_streams must be 1..4");
+  if (cfg.max_batch <= 0) cfg.max_batch = 512;
+  if (cfg.queue_capacity <= 0) cfg.queue_capacity = 65536;
+  if (cfg.hbm_reserve_bytes <= 0) cfg.hbm_reserve_bytes = int64_t(4) << 30;
+  tm_server_t sv = new (std::nothrow) tm_server_s();
+  if (!sv) return fail(TM_ENOMEM, "host allocation");
+  cudaError_t e = cudaGetDevice(&sv->device);
+  if (e != cudaSuccess) { delete sv; return cuda_fail(e, "cudaGetDevice"); }
+  float2* tw = nullptr;
+  tm_status st = device_setup(sv->device, &tw);
+  if (st != TM_OK) { delete sv; return st; }
+  if (cfg.arena_bytes <= 0) {
+    size_t freeb = 0, total = 0;
+    e = cudaMemGetInfo(&freeb, &total);
+    if (e != cudaSuccess) { delete sv; return cuda_fail(e, "cudaMemGetInfo"); }
+    const int64_t usable = int64_t(freeb) - cfg.hbm_reserve_bytes;
+    if (usable < (int64_t(64) << 20)) { delete sv; return fail(TM_ENOMEM, "not enough free device memory"); }
+    cfg.arena_bytes = std::min<int64_t>(usable / cfg.n_streams, int64_t(8) << 30);
+  }
+  sv->cfg = cfg;
+  sv->slots.resize(cfg.n_streams);
+  const size_t stage_cap = size_t(cfg.max_batch) * (sizeof(FoldQ) + sizeof(CorrQ));
+  // template staging: max_batch templates of 8192 entries on average; a
+  // larger iteration is split
+  const int64_t t_cap = std::max<int64_t>(int64_t(cfg.max_batch) * 8192, 65536);
+  for (auto& sl : sv->slots) {
+    bool ok = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc(&sl.arena, size_t(cfg.arena_bytes)) == cudaSuccess &&
+              cudaMallocHost(&sl.h_t, size_t(t_cap) * sizeof(float)) == cudaSuccess &&
+              cudaMallocHost(&sl.h_out, size_t(cfg.max_batch) * sizeof(tm_result)) == cudaSuccess &&
+              cudaMallocHost(&sl.h_stage, stage_cap) == cudaSuccess &&
+              cudaMallocHost(&sl.h_order, size_t(cfg.max_batch) * sizeof(int32_t)) == cudaSuccess;
+    sl.arena_bytes = cfg.arena_bytes;
+    sl.h_t_cap = t_cap;
+    sl.h_stage_cap = stage_cap;
+    if (ok) {
+      sl.b = new (std::nothrow) tm_batch_s();
+      ok = sl.b != nullptr && cudaEventCreateWithFlags(&sl.b->ev_stage, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) {
+        sl.b->owns_memory = false;
+        sl.b->h_stage = sl.h_stage;
+        sl.b->stage_bytes = stage_cap;
+      }
+    }
+    if (!ok) {
+      cudaGetLastError();
+      server_free(sv);
+      return fail(TM_ENOMEM, "server allocation failed");
+    }
+  }
+  sv->worker = std::thread(worker_main, sv);
+  *out = sv;
+  return TM_OK;
+}
+
+tm_status tm_serve_register_signal(tm_server_t sv, const void* x, int64_t N, int32_t xdtype, uint32_t flags,
+                                   int32_t* sig_id) {
+  if (!sv || !x || !sig_id) return fail(TM_EINVAL, "null argument");
+  if (N < 1 || xdtype < TM_I8_PM1 || xdtype > TM_F32) return fail(TM_EINVAL, "bad signal shape");
+  Signal sg{x, N, xdtype, false};
+  if (!(flags & TM_SERVE_SIGNAL_DEVICE)) {
+    void* d = nullptr;
+    const size_t bytes = size_t(signal_bytes(xdtype, N));
+    TM_CUDA(cudaSetDevice(sv->device));
+    TM_CUDA(cudaMalloc(&d, bytes));
+    const cudaError_t e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "signal upload"); }
+    sg.x = d;
+    sg.owned = true;
+  } else if (reinterpret_cast<uintptr_t>(x) & 15) {
+    return fail(TM_EINVAL, "x must be 16-byte aligned");
+  }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->signals.push_back(sg);
+  *sig_id = int32_t(sv->signals.size() - 1);
+  return TM_OK;
+}
+
+tm_status tm_serve_submit(tm_server_t sv, int32_t sig_id, const float* t_host, int32_t K, int32_t mode, int32_t M1,
+                          int32_t M2, uint32_t plan_flags, uint64_t tag) {
+  if (!sv || !t_host) return fail(TM_EINVAL, "null argument");
+  if (K > 65536) return fail(TM_EINVAL, "template longer than 65536");
+  Req r;
+  r.tag = tag;
+  r.sig = sig_id;
+  Signal sg;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sig_id < 0 || sig_id >= int32_t(sv->signals.size())) return fail(TM_EINVAL, "unknown signal id");
+    sg = sv->signals[sig_id];
+  }
+  tm_status st = make_plan(sg.N, K, sg.dtype, mode, M1, M2, plan_flags, r.plan);
+  if (st != TM_OK) return st;
+  r.q.x = sg.x;
+  r.q.t = nullptr;
+  r.q.N = sg.N;
+  r.q.K = K;
+  r.q.xdtype = sg.dtype;
+  r.q.mode = mode;
+  r.q.M1 = M1;
+  r.q.M2 = M2;
+  r.q.flags = plan_flags;
+  r.t.assign(t_host, t_host + K);
+  r.t_submit = now_us();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (int64_t(sv->pending.size()) >= sv->cfg.queue_capacity) return fail(TM_EAGAIN, "queue full");
+    sv->pending.push_back(std::move(r));
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->cmu);
+    ++sv->submitted;
+  }
+  sv->cv.notify_one();
+  return TM_OK;
+}
+
+int32_t tm_serve_poll(tm_server_t sv, tm_result_tagged* out, int32_t max, int64_t timeout_us) {
+  if (!sv || !out || max < 1) return -int32_t(fail(TM_EINVAL, "bad poll arguments"));
+  std::unique_lock<std::mutex> lk(sv->cmu);
+  if (sv->done.empty() && timeout_us > 0)
+    sv->ccv.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return !sv->done.empty(); });
+  int32_t k = 0;
+  while (k < max && !sv->done.empty()) {
+    out[k++] = sv->done.front();
+    sv->done.pop_front();
+  }
+  return k;
+}
+
+tm_status tm_serve_stats_get(tm_server_t sv, tm_serve_stats* st) {
+  if (!sv || !st) return fail(TM_EINVAL, "null argument");
+  std::vector<double> lat;
+  {
+    std::lock_guard<std::mutex> lk(sv->cmu);
+    st->submitted = sv->submitted;
+    st->completed = sv->completed;
+    st->failed = sv->failed;
+    st->iterations = sv->iterations;
+    st->mean_batch = sv->iterations ? double(sv->batched) / double(sv->iterations) : 0.0;
+    lat = sv->lat;
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    st->pending = int64_t(sv->pending.size());
+  }
+  st->in_flight = sv->busy.load();
+  st->p50_us = st->p99_us = st->max_us = 0.0;
+  if (!lat.empty()) {
+    std::sort(lat.begin(), lat.end());
+    st->p50_us = lat[lat.size() / 2];
+    st->p99_us = lat[std::min(lat.size() - 1, size_t(double(lat.size()) * 0.99))];
+    st->max_us = lat.back();
+  }
+  return TM_OK;
+}
+
+tm_status tm_serve_destroy(tm_server_t sv) {
+  if (!sv) return TM_OK;
+  sv->stop.store(true);
+  sv->cv.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  server_free(sv);
+  return TM_OK;
+}
+
+}  // extern "C"

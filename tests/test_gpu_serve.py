@@ -1,0 +1,147 @@
+"""The continuous-batching server (tm_serve_*) on the GPU.
+
+Requests on resident signals of every storage type go through the server
+and come back equal to the same queries run as standalone batches (bit-equal
+for +-1 signals; for real signals the fold sums may round differently when
+the rows fall into other shares, so the step-7 maxima must agree or be
+near-tied); the same request alone and inside a mix gives the same result;
+an arena too small for the whole queue splits it into several iterations;
+a request too large for the arena alone fails with TM_ENOMEM.
+"""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tm():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1509_04863_gb300 import _build
+    _build.build()
+    import paper_1509_04863_gb300 as tm
+    return tm
+
+
+def _collect(srv, n, timeout_s=60.0):
+    got = {}
+    t0 = time.time()
+    while len(got) < n and time.time() - t0 < timeout_s:
+        for r in srv.poll(1024, timeout_us=20000):
+            got[r["tag"]] = r
+    assert len(got) == n, (len(got), n)
+    return got
+
+
+def _standalone(tm, q, x_dev):
+    b = tm.Batch([dict(x=x_dev, t=torch.from_numpy(q.t).cuda(), N=q.N, K=q.K, xdtype=q.xdtype, mode=q.mode)])
+    out = tm.result_buffer(1)
+    b.run(out)
+    torch.cuda.synchronize()
+    return tm.decode_results(out)[0]
+
+
+SIGNALS = [((1 << 20) + 3, "i8"), (1 << 20, "bits"), ((1 << 19) + 1, "f32"), ((1 << 18) + 5, "f16")]
+
+
+def test_server_matches_standalone(tm):
+    srv = tm.Server(n_streams=2, max_batch=32, arena_bytes=1 << 30)
+    sigs, xs = [], []
+    for k, (N, dt) in enumerate(SIGNALS):
+        base = W.planted_query(9000 + k, N, 512, dt, mode="auto")
+        # the device copy the standalone runs use
+        xs.append(torch.from_numpy(base.x).cuda())
+        sid = srv.register_signal(base.x, N, dt)   # host copy: the server keeps its own
+        sigs.append((sid, base))
+    reqs = {}
+    rng = np.random.default_rng(3)
+    tag = 0
+    for rep in range(12):
+        for k, (sid, base) in enumerate(sigs):
+            # the registered signal, a new template window at a random shift
+            K = int(rng.choice([256, 700, 1024, 2048]))
+            k_star = int(rng.integers(0, base.N))
+            t = W.flip_entries(rng, W.cyclic_window(_values(base), k_star, K), 0.03)
+            q = W.Query(x=base.x, xdtype=base.xdtype, N=base.N, K=K, t=t, k_star=k_star, mode="auto")
+            assert srv.submit(sid, q.t, tag=tag, mode="auto") == tm.TM_OK
+            reqs[tag] = (k, q)
+            tag += 1
+    got = _collect(srv, len(reqs))
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["iterations"] >= 2
+    assert st["p50_us"] > 0 and st["p99_us"] >= st["p50_us"]
+    for t_, (k, q) in reqs.items():
+        r = got[t_]
+        assert r["req_status"] == tm.TM_OK and r["latency_us"] > 0
+        ref = _standalone(tm, q, xs[k])
+        if q.xdtype in ("i8", "bits"):
+            assert {f: r[f] for f in ref} == ref, (t_, r, ref)
+        else:
+            same = (r["m1"], r["m2"], r["shift"]) == (ref["m1"], ref["m2"], ref["shift"])
+            near = abs(r["r1"] - ref["r1"]) <= 1e-5 * max(1.0, abs(ref["r1"])) and \
+                abs(r["r2"] - ref["r2"]) <= 1e-5 * max(1.0, abs(ref["r2"]))
+            assert same or near, (t_, r, ref)
+    srv.close()
+
+
+def _values(q):
+    import oracle.ftm as O
+    return O.decode(q.x, q.xdtype, q.N).astype(np.float32)
+
+
+def test_alone_and_in_the_mix(tm):
+    srv = tm.Server(n_streams=2, max_batch=64, arena_bytes=1 << 30)
+    qa = W.planted_query(77, (1 << 20) + 16, 1024, "i8", flip_p=0.05, mode="paper")
+    sid = srv.register_signal(qa.x, qa.N, "i8")
+    qb = W.planted_query(78, 1 << 19, 2048, "bits", flip_p=0.05, mode="auto")
+    sid2 = srv.register_signal(qb.x, qb.N, "bits")
+    srv.submit(sid, qa.t, tag=1, mode="paper")
+    alone = _collect(srv, 1)[1]
+    rng = np.random.default_rng(5)
+    for i in range(40):
+        srv.submit(sid2, qb.t, tag=100 + i, mode="auto")
+        if i == 20:
+            srv.submit(sid, qa.t, tag=2, mode="paper")
+    mixed = _collect(srv, 41)
+    a = {k: v for k, v in alone.items() if k not in ("tag", "latency_us")}
+    m = {k: v for k, v in mixed[2].items() if k not in ("tag", "latency_us")}
+    assert a == m
+    srv.close()
+
+
+def test_arena_admission(tm):
+    """A small arena runs the queue as several iterations; a request that
+    alone exceeds it fails with TM_ENOMEM while the others complete."""
+    srv = tm.Server(n_streams=1, max_batch=64, arena_bytes=4 << 20)
+    q = W.planted_query(5, 1 << 20, 1024, "i8", flip_p=0.05, mode="paper")
+    sid = srv.register_signal(q.x, q.N, "i8")
+    big = W.planted_query(6, 1 << 22, 16384, "i8", mode="paper", allow_ambig=True)
+    sid_big = srv.register_signal(big.x, big.N, "i8")
+    for i in range(30):
+        srv.submit(sid, q.t, tag=i, mode="paper")
+    srv.submit(sid_big, big.t, tag=999, mode="paper", allow_ambig=True)
+    got = _collect(srv, 31)
+    assert got[999]["req_status"] == tm.TM_ENOMEM
+    ok = [got[i] for i in range(30)]
+    assert all(r["req_status"] == tm.TM_OK for r in ok)
+    assert len({(r["shift"], r["m1"], r["m2"]) for r in ok}) == 1
+    assert srv.stats()["iterations"] >= 2
+    srv.close()
+
+
+def test_submit_validation(tm):
+    srv = tm.Server(n_streams=1, max_batch=8, arena_bytes=64 << 20)
+    q = W.planted_query(1, 4096, 64, "i8")
+    sid = srv.register_signal(q.x, q.N, "i8")
+    with pytest.raises(tm.TMError) as e:
+        srv.submit(sid + 7, q.t, tag=0)
+    assert e.value.status == tm.TM_EINVAL
+    with pytest.raises(tm.TMError) as e:
+        srv.submit(sid, q.t[:16], tag=0, mode="paper")    # 16 * 17 <= 4096: needs allow_ambig
+    assert e.value.status == tm.TM_EINVAL
+    srv.close()
