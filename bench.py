@@ -64,7 +64,10 @@ def profile_traffic(kernel_src: str, summary: str):
     if not os.path.exists(path):
         return None
     import re
-    sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()[:16]
+    src = os.path.join(ROOT, kernel_src)
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     text = open(path).read()
     m_sha = re.search(r"kernel_source_sha:\s*`?([0-9a-f]+)", text)
     m_bytes = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
@@ -299,7 +302,7 @@ def run_native(args):
             done, dt = cpu_oracle_sample(qs)
             cpu = {"value": done / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
                    "sample": f"{done} of the 64 batch64 queries, numpy oracle (Algorithm 1 in int64), 1 thread"}
-        traffic = profile_traffic("paper_1509_04863_gb300/csrc/fold_i8.cu", "fold_i8_batch64.md")
+        traffic = profile_traffic("paper_1509_04863_gb300/csrc/fold.cu", "fold_kernel_batch64.md")
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -308,7 +311,7 @@ def run_native(args):
             "input_GBps": world * in_bytes / (ms_per_step / 1e3) / 1e9,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "what": "one batch64 step (64 queries), device time"},
-            "roofline": {"bound": "hbm", "kernel": "fold_i8_kernel", "achieved": achieved, "peak": hbm_peak,
+            "roofline": {"bound": "hbm", "kernel": "fold_kernel<UnitI8,3>", "achieved": achieved, "peak": hbm_peak,
                          "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": in_bytes,
                          "fold_ms": float(fold_ms.mean()), "corr_ms": float((step_ms - fold_ms).mean())},
