@@ -48,6 +48,8 @@ def _compile(src: str, extra) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    if extra and r.stderr:
+        print(r.stderr, file=sys.stderr)
     return obj
 
 

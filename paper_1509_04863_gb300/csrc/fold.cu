@@ -10,20 +10,23 @@
 // units per warp (8 warps for M1, 9 for M2, so that K and K+1 columns both
 // come to one chunk per warp for the paper's moduli). For a stage holding
 // elements [s, e) of a signal every lane of a warp walks the same rows l of
-// its modulus: rows strictly inside the stage take the fast path, the first
-// and last row a masked path that keeps only the part inside the stage.
-// Stages carry 16 bytes of slack on both sides so every read stays in
-// bounds. A unit narrower than E (the last one of a row) still reads E
-// columns; the columns past its width see the next row and are never
-// written out. Each CTA writes one slot of per-column results per signal
-// share; the correlation kernel adds the slots, the wrap-around term and
-// the extension k >= M.
+// its modulus. Int8 units read whole rows through row walkers that keep
+// each unit's next row offset from stage to stage; a row cut by a stage
+// edge is read in two parts, the bytes past either edge being slack that
+// reads as +1. The other units take a fast path for rows strictly inside
+// the stage and a masked path for the first and last row. Stages carry 16
+// bytes of slack on both sides so every read stays in bounds. A unit
+// narrower than E (the last one of a row) still reads E columns; the
+// columns past its width see the next row and are never written out. Each
+// CTA writes one slot of per-column results per signal share; the
+// correlation kernel adds the slots, the wrap-around term and the
+// extension k >= M.
 //
 // Units (one per storage type):
-//  int8 +-1 : 16 bytes; a byte holding -1 (0xFF) has bit 1 set and +1 (0x01)
-//             has not, so w & 0x02020202 adds 2 per -1 into packed byte
-//             lanes, widened into 16-bit lanes every few stages; output:
-//             count of -1 entries.
+//  int8 +-1 : 16 bytes; whole words added (raw sums, carries included)
+//             and decoded into per-column counts every few stages (see
+//             UnitI8), widened into 16-bit lanes; output: count of -1
+//             entries.
 //  bits     : 32 columns in one word (LSB first, 1 = +1); bit-sliced
 //             vertical counters (5 planes, up to 31 rows) flushed into byte
 //             then 16-bit lanes; output: count of +1 entries.
@@ -43,7 +46,6 @@ namespace ftm {
 namespace {
 
 constexpr int kStageBytes = kFoldTile + 32;   // 16 bytes of slack before and after the data
-constexpr uint32_t kNegBit = 0x02020202u;
 
 __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, uint32_t sh) {
   return __funnelshift_r(lo, hi, sh);
@@ -70,64 +72,95 @@ __device__ __forceinline__ void load16(const uint8_t* buf, int o, uint32_t (&w)[
   }
 }
 
-// Low n bytes of a word set (n clamped to [0, 4]).
-__device__ __forceinline__ uint32_t low_bytes(int n) {
-  return n <= 0 ? 0u : n >= 4 ? 0xFFFFFFFFu : (1u << (8 * n)) - 1u;
+// Bytes [o, o+16) of a stage whose phase o & 15 == P is known at compile
+// time (o - P is 16-byte aligned).
+template <int P>
+__device__ __forceinline__ void load16p(const uint8_t* buf, int o, uint32_t (&w)[4]) {
+  const uint4* p = reinterpret_cast<const uint4*>(buf + (o - P));
+  const uint4 a = p[0];
+  if constexpr (P == 0) {
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+  } else {
+    const uint4 b = p[1];
+    const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    constexpr int q = P >> 2;
+    constexpr uint32_t sh = uint32_t(P & 3) * 8u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[k] = sh == 0 ? v[q + k] : fsr(v[q + k], v[q + k + 1], sh);
+  }
 }
 
 // ---------------------------------------------------------------- int8 +-1
+// An entry is 0x01 (+1) or 0xFF (-1), i.e. 1 + 254 [entry = -1]. Whole
+// 32-bit words are added, carries between byte lanes included, so after R
+// row reads a lane word holds
+//   S = R * 0x01010101 + 254 * C  (mod 2^32),   C = sum_b n_b 256^b,
+// n_b the number of -1 entries in byte lane b. While R <= 127 each n_b
+// fits 7 bits, C < 2^31, and C = ((S - R * 0x01010101) >> 1) * 127^-1
+// (mod 2^31) gives the four counts back exactly. Bytes just outside a
+// stage read as 0x01 (the stage slack holds that value), which adds to R
+// but not to the counts: a row cut by a stage boundary is read in two
+// parts, one per stage, with no mask.
 struct UnitI8 {
   static constexpr int kE = 16, kBits = 8;
-  uint32_t c8[4], c16[8];
+  static constexpr bool kWalk = true;
+  static constexpr uint32_t kInv127 = 0x6FDFBF7Fu;   // 127 * kInv127 = 1 (mod 2^31)
+  uint32_t s[4];      // raw word sums since the last widening
+  uint32_t c16[8];    // counts in 16-bit lanes: word 2i columns 4i, 4i+2; word 2i+1 columns 4i+1, 4i+3
+  uint32_t rows;      // row reads since the last widening
   __device__ __forceinline__ void clear() {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) c8[i] = 0u;
+    for (int i = 0; i < 4; ++i) s[i] = 0u;
 #pragma unroll
     for (int i = 0; i < 8; ++i) c16[i] = 0u;
+    rows = 0u;
   }
-  // stages between widenings: a unit meets at most tile/Mp + 2 rows per
-  // stage and a byte lane holds up to 127 of them (2 per -1 entry)
+  // stages between widenings: a unit reads at most tile/Mp + 2 rows per stage
   static __device__ __forceinline__ int widen_every(int Mp) { return max(1, 127 / (kFoldTile / Mp + 2)); }
+  template <int P>
+  __device__ __forceinline__ void addp(const uint8_t* buf, int o) {
+    uint32_t w[4];
+    load16p<P>(buf, o, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s[i] += w[i];
+    ++rows;
+  }
   __device__ __forceinline__ void add(const uint8_t* buf, int o) {
     uint32_t w[4];
     load16(buf, o, w);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) c8[i] += w[i] & kNegBit;
+    for (int i = 0; i < 4; ++i) s[i] += w[i];
+    ++rows;
   }
-  __device__ __forceinline__ void add2(const uint8_t* buf, int o, int o2) {
-    uint32_t w[4], v[4];
-    load16(buf, o, w);
-    load16(buf, o2, v);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) c8[i] += (w[i] & kNegBit) + (v[i] & kNegBit);
+  // two rows at 16-byte aligned offsets
+  __device__ __forceinline__ void add2_aligned(const uint8_t* buf, int o, int o2) {
+    const uint4 a = *reinterpret_cast<const uint4*>(buf + o);
+    const uint4 b = *reinterpret_cast<const uint4*>(buf + o2);
+    s[0] += a.x + b.x;
+    s[1] += a.y + b.y;
+    s[2] += a.z + b.z;
+    s[3] += a.w + b.w;
+    rows += 2u;
   }
-  // elements of [o, o+16) inside [0, len)
-  __device__ __forceinline__ void add_masked(const uint8_t* buf, int o, int len) {
-    uint32_t w[4];
-    load16(buf, o, w);
-    const int lo = -o, hi = len - o;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) c8[k] += w[k] & (kNegBit & low_bytes(hi - 4 * k) & ~low_bytes(lo - 4 * k));
-  }
-  __device__ __forceinline__ void end_row_block() {}
   __device__ __forceinline__ void widen() {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      c16[2 * i] += c8[i] & 0x00FF00FFu;
-      c16[2 * i + 1] += (c8[i] >> 8) & 0x00FF00FFu;
-      c8[i] = 0u;
+      const uint32_t c = (((s[i] - rows * 0x01010101u) >> 1) * kInv127) & 0x7FFFFFFFu;
+      c16[2 * i] += c & 0x00FF00FFu;
+      c16[2 * i + 1] += (c >> 8) & 0x00FF00FFu;
+      s[i] = 0u;
     }
+    rows = 0u;
   }
   __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
+    widen();
     int32_t cnt[16];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const uint32_t e0 = c16[2 * i] + (c8[i] & 0x00FF00FFu);
-      const uint32_t e1 = c16[2 * i + 1] + ((c8[i] >> 8) & 0x00FF00FFu);
-      cnt[4 * i + 0] = int32_t((e0 & 0xFFFFu) >> 1);
-      cnt[4 * i + 2] = int32_t(e0 >> 17);
-      cnt[4 * i + 1] = int32_t((e1 & 0xFFFFu) >> 1);
-      cnt[4 * i + 3] = int32_t(e1 >> 17);
+      cnt[4 * i + 0] = int32_t(c16[2 * i] & 0xFFFFu);
+      cnt[4 * i + 2] = int32_t(c16[2 * i] >> 16);
+      cnt[4 * i + 1] = int32_t(c16[2 * i + 1] & 0xFFFFu);
+      cnt[4 * i + 3] = int32_t(c16[2 * i + 1] >> 16);
     }
     if (width == 16) {
       int4* d4 = reinterpret_cast<int4*>(dst + col);
@@ -143,9 +176,50 @@ struct UnitI8 {
   }
 };
 
+// Row walkers for units that read past stage edges without masks: read
+// the rows o, o + Mp, ... with o < el and return the first offset >= el.
+// Offsets and Mp multiples of 16: aligned loads, two rows per step.
+template <class U>
+__device__ __forceinline__ int walk_aligned(U& u, const uint8_t* buf, int o, int el, int Mp) {
+  for (; o + Mp < el; o += 2 * Mp) u.add2_aligned(buf, o, o + Mp);
+  if (o < el) {
+    u.template addp<0>(buf, o);
+    o += Mp;
+  }
+  return o;
+}
+
+// Mp = 1 (mod 16), as for the modulus K+1 with K a multiple of 16: the
+// phase o & 15 advances by one per row, so the rows are visited through a
+// cycle of 16 compile-time phases entered at the first row's phase.
+template <class U>
+__device__ __forceinline__ int walk_step1(U& u, const uint8_t* buf, int o, int el, int Mp) {
+#define FTM_ROW(P)            \
+  case P:                     \
+    if (o >= el) return o;    \
+    u.template addp<P>(buf, o); \
+    o += Mp;
+  switch (o & 15) {
+    for (;;) {
+      FTM_ROW(0) FTM_ROW(1) FTM_ROW(2) FTM_ROW(3) FTM_ROW(4) FTM_ROW(5) FTM_ROW(6) FTM_ROW(7)
+      FTM_ROW(8) FTM_ROW(9) FTM_ROW(10) FTM_ROW(11) FTM_ROW(12) FTM_ROW(13) FTM_ROW(14) FTM_ROW(15)
+    }
+  }
+#undef FTM_ROW
+  return o;
+}
+
+// Any other Mp: the phase is taken at run time.
+template <class U>
+__device__ __forceinline__ int walk_any(U& u, const uint8_t* buf, int o, int el, int Mp) {
+  for (; o < el; o += Mp) u.add(buf, o);
+  return o;
+}
+
 // ---------------------------------------------------------------- bit-packed +-1
 struct UnitBits {
   static constexpr int kE = 32, kBits = 1;
+  static constexpr bool kWalk = false;
   static constexpr int kPlanes = 5;       // vertical counter: up to 31 rows
   uint32_t p[kPlanes];
   uint32_t c8[8];                         // byte lanes: word k holds columns k, k+8, k+16, k+24
@@ -251,6 +325,7 @@ struct UnitBits {
 // ---------------------------------------------------------------- fp32
 struct UnitF32 {
   static constexpr int kE = 4, kBits = 32;
+  static constexpr bool kWalk = false;
   float acc[4];
   __device__ __forceinline__ void clear() {
 #pragma unroll
@@ -290,6 +365,7 @@ struct UnitF32 {
 // ---------------------------------------------------------------- fp16
 struct UnitF16 {
   static constexpr int kE = 8, kBits = 16;
+  static constexpr bool kWalk = false;
   float acc[8];
   __device__ __forceinline__ void clear() {
 #pragma unroll
@@ -412,6 +488,57 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
   return true;
 }
 
+// The same for units read through the row walkers (kWalk): each unit keeps
+// the offset of its next row relative to the next stage, so no row index
+// is recomputed per stage and no read is masked.
+template <class U, int J>
+__device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t* full, uint64_t* empty, int lo,
+                                                   int hi, int Mp, int W, int wig, int32_t* dst, uint32_t& it) {
+  static_assert(U::kBits == 8, "walkers step in bytes");
+  const int lane = threadIdx.x & 31;
+  const int F = U::widen_every(Mp);
+  auto col = [&](int j) { return U::kE * (lane + 32 * (wig + W * j)); };
+  U u[J];
+  int o[J];   // next row of unit j, relative to the current stage
+  const int l = lo / Mp;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    u[j].clear();
+    o[j] = l * Mp + col(j) - lo;
+    if (o[j] <= -U::kE) o[j] += Mp;
+  }
+  const int step = Mp & 15;
+  int since = 0;
+  for (int s = lo; s < hi; s += kFoldTile) {
+    const uint32_t st = it % kFoldStages;
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (it / kFoldStages) & 1u))) return false;
+    const uint8_t* buf = smem + st * kStageBytes + 16;
+    const int el = min(kFoldTile, hi - s);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      if (col(j) >= Mp) continue;
+      const int e = step == 0 ? walk_aligned(u[j], buf, o[j], el, Mp)
+                  : step == 1 ? walk_step1(u[j], buf, o[j], el, Mp)
+                              : walk_any(u[j], buf, o[j], el, Mp);
+      // a last row that started within kE bytes of the end continues in
+      // the next stage (its first bytes there fall at negative offsets)
+      o[j] = e - Mp > el - U::kE ? e - Mp - el : e - el;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    ++it;
+    if (++since == F) {
+      since = 0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) u[j].widen();
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+    if (col(j) < Mp) u[j].write(dst, col(j), min(U::kE, Mp - col(j)));
+  return true;
+}
+
 template <class U, int JMAX>
 __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -428,6 +555,14 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
       mbar_init(&empty[s], kFoldConsumers / 32);
     }
     mbar_init_fence();
+  }
+  // The 16 bytes before and after each stage's data read as +1 entries of
+  // an int8 signal (walker units read across stage edges); bulk copies
+  // never write there.
+  if (tid < 8 * kFoldStages) {
+    const int st = tid >> 3, k = tid & 7;
+    uint32_t* w = reinterpret_cast<uint32_t*>(smem + st * kStageBytes + (k < 4 ? 0 : 16 + kFoldTile));
+    w[k & 3] = 0x01010101u;
   }
   __syncthreads();
   if (cb >= ce) return;
@@ -454,6 +589,14 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
             break;
           }
           const uint32_t len = uint32_t(hi - s < kFoldTile ? hi - s : int64_t(kFoldTile));
+          if (len < uint32_t(kFoldTile)) {
+            // a short stage: the 16 bytes after its data read as +1 too; a
+            // later bulk copy into this stage overwrites them, so order the
+            // store before the async proxy's writes
+            *reinterpret_cast<uint4*>(smem + st * kStageBytes + 16 + len) =
+                make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          }
           mbar_arrive_expect_tx(&full[st], len);
           bulk_load(smem + st * kStageBytes + 16, x + s, len, &full[st], pol);
           ++it;
@@ -485,10 +628,17 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
     int32_t* dst = a.partial + a.q[qi].part + int64_t(blockIdx.x - a.q[qi].first_cta) * a.q[qi].stride +
                    a.q[qi].moff[m];
     const int J = fold_units_per_lane(Mp, W, U::kE);
-    if (J <= 1) ok = consume_share<U, 1>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-    else if (J == 2 || JMAX == 2) ok = consume_share<U, 2>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-    else if (J <= 4 || JMAX <= 4) ok = consume_share<U, (JMAX < 4 ? JMAX : 4)>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-    else ok = consume_share<U, JMAX>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    if constexpr (U::kWalk) {
+      if (J <= 1) ok = consume_share_walk<U, 1>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+      else if (J == 2 || JMAX == 2) ok = consume_share_walk<U, 2>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+      else if (J <= 3 || JMAX <= 3) ok = consume_share_walk<U, (JMAX < 3 ? JMAX : 3)>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+      else ok = consume_share_walk<U, JMAX>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    } else {
+      if (J <= 1) ok = consume_share<U, 1>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+      else if (J == 2 || JMAX == 2) ok = consume_share<U, 2>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+      else if (J <= 4 || JMAX <= 4) ok = consume_share<U, (JMAX < 4 ? JMAX : 4)>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+      else ok = consume_share<U, JMAX>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+    }
   }
   if (!ok) atomicOr(a.err, 1);
 }
