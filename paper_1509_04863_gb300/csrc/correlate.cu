@@ -102,9 +102,12 @@ __device__ __forceinline__ float2 twiddle(const float2* tw, int e, int halfP) {
 
 // One Stockham pass of radix R over P points whose sub-transforms of length
 // Ns are done: butterfly j takes x[j + r P/R], twiddles by W_{Ns R}^{r (j mod Ns)},
-// and writes to (j - j mod Ns) R + j mod Ns + r Ns.
+// and writes to (j - j mod Ns) R + j mod Ns + r Ns. The twiddles come from
+// the pass table stab[(r-1) Ns + k] = W_{16 Ns}^{r k} when given (lanes with
+// consecutive k read consecutive entries), else from the half table tw.
 template <int R>
-__device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift, const float2* tw) {
+__device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift, const float2* tw,
+                                         const float2* stab) {
   constexpr int NB = (kPMax / R + kCorrThreads - 1) / kCorrThreads;
   const int nbf = P / R;
   float2 v[NB][R];
@@ -116,8 +119,13 @@ __device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift
 #pragma unroll
       for (int r = 0; r < R; ++r) v[b][r] = buf[pad_idx(j + r * nbf)];
       if (Ns > 1) {
+        if (stab != nullptr) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], twiddle(tw, (r * k) << twshift, P >> 1));
+          for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], stab[(r - 1) * Ns + k]);
+        } else {
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], twiddle(tw, (r * k) << twshift, P >> 1));
+        }
       }
       dft<R>(v[b]);
     }
@@ -136,21 +144,47 @@ __device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift
   __syncthreads();
 }
 
+// Pass tables for every radix-16 pass but the last (16 Ns < P), packed one
+// after the other: 15 Ns entries W_{16 Ns}^{r k}, r = 1..15, k < Ns. At most
+// 15 (4 + 64) = 1020 entries for P <= 16384.
+constexpr int kPassTw = 1024;
+__device__ __forceinline__ int pass_first(int logP) { return logP & 3; }
+
+// Fills the pass tables from the global table gtw[m] = W_{kPMax}^m.
+__device__ void build_pass_twiddles(float2* stw, int logP, const float2* __restrict__ gtw) {
+  const int P = 1 << logP;
+  int off = 0;
+  for (int Ns = 1 << pass_first(logP); 16 * Ns < P; Ns <<= 4) {
+    if (Ns > 1) {
+      const int stride = kPMax / (16 * Ns);
+      for (int i = threadIdx.x; i < 15 * Ns; i += kCorrThreads) {
+        const int r = i / Ns + 1, k = i - (r - 1) * Ns;
+        stw[off + i] = __ldg(&gtw[r * k * stride]);
+      }
+      off += 15 * Ns;
+    }
+  }
+}
+
 // Forward FFT of length 2^logP in place (padded layout, natural order);
-// tw holds W_P^m for m < P/2.
-__device__ void fft(float2* buf, int logP, const float2* tw) {
+// tw holds W_P^m for m < P/2, stw the pass tables of build_pass_twiddles.
+__device__ void fft(float2* buf, int logP, const float2* tw, const float2* stw) {
   const int P = 1 << logP;
   int logNs = 0;
-  const int first = logP & 3;
+  const int first = pass_first(logP);
   if (first) {
     const int twshift = logP - first;
-    if (first == 1) fft_pass<2>(buf, P, 1, twshift, tw);
-    else if (first == 2) fft_pass<4>(buf, P, 1, twshift, tw);
-    else fft_pass<8>(buf, P, 1, twshift, tw);
+    if (first == 1) fft_pass<2>(buf, P, 1, twshift, tw, nullptr);
+    else if (first == 2) fft_pass<4>(buf, P, 1, twshift, tw, nullptr);
+    else fft_pass<8>(buf, P, 1, twshift, tw, nullptr);
     logNs = first;
   }
+  int off = 0;
   while (logNs < logP) {
-    fft_pass<16>(buf, P, 1 << logNs, logP - (logNs + 4), tw);
+    const int Ns = 1 << logNs;
+    const bool last = logNs + 4 == logP;
+    fft_pass<16>(buf, P, Ns, logP - (logNs + 4), tw, (last || Ns == 1) ? nullptr : stw + off);
+    if (!last && Ns > 1) off += 15 * Ns;
     logNs += 4;
   }
 }
@@ -167,6 +201,53 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) s += red[w];
   return s;
+}
+
+// Two float sums and an AND over the block in one exchange (red: 2 kWarps floats).
+__device__ __forceinline__ void block_sum2_and(float& a, float& b, int& c, float* red, int* redi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  c = __all_sync(0xffffffffu, c);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = a;
+    red[kWarps + (threadIdx.x >> 5)] = b;
+    redi[threadIdx.x >> 5] = c;
+  }
+  __syncthreads();
+  a = 0.f;
+  b = 0.f;
+  c = 1;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    a += red[w];
+    b += red[kWarps + w];
+    c &= redi[w];
+  }
+}
+
+// Four 64-bit sums over the block in one exchange (red: 4 kWarps entries).
+template <class T>
+__device__ __forceinline__ void block_sum4(T (&v)[4], T* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) red[4 * (threadIdx.x >> 5) + i] = v[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    T s = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += red[4 * w + i];
+    v[i] = s;
+  }
 }
 
 __device__ __forceinline__ int block_and(int v, int* redi) {
@@ -192,6 +273,18 @@ __device__ __forceinline__ int block_max(int v, int* redi) {
 }
 
 // max value, smallest index on ties
+__device__ __forceinline__ float block_maxf(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = red[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) m = fmaxf(m, red[w]);
+  return m;
+}
+
 __device__ __forceinline__ void better(float& v, int& i, float v2, int i2) {
   if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
 }
@@ -230,6 +323,31 @@ struct Sig {
 
 __device__ __forceinline__ bool is_int_dtype(int d) { return d == TM_I8_PM1 || d == TM_BITS_PM1; }
 
+// The same accessors with the storage type fixed at compile time, so that
+// batches of loads carry no branches and can all be in flight at once.
+template <int DT>
+struct SigT {
+  const void* x;
+  __device__ __forceinline__ float val(int64_t n) const {
+    if constexpr (DT == TM_I8_PM1) return (__ldg(static_cast<const uint8_t*>(x) + n) & 2u) ? -1.0f : 1.0f;
+    else if constexpr (DT == TM_BITS_PM1)
+      return ((__ldg(static_cast<const uint8_t*>(x) + (n >> 3)) >> (n & 7)) & 1u) ? 1.0f : -1.0f;
+    else if constexpr (DT == TM_F16) return __half2float(static_cast<const __half*>(x)[n]);
+    else return __ldg(static_cast<const float*>(x) + n);
+  }
+};
+
+// Calls f(SigT<dtype>{x}).
+template <class F>
+__device__ __forceinline__ void with_sig(int dtype, const void* x, F&& f) {
+  switch (dtype) {
+    case TM_I8_PM1: f(SigT<TM_I8_PM1>{x}); break;
+    case TM_BITS_PM1: f(SigT<TM_BITS_PM1>{x}); break;
+    case TM_F16: f(SigT<TM_F16>{x}); break;
+    default: f(SigT<TM_F32>{x}); break;
+  }
+}
+
 // Exact sum_{i<K} t_i * v(i) over one warp: integer terms in int32 when
 // `small` guarantees no partial sum reaches 2^31, else int64; reals in fp64.
 template <class F>
@@ -259,12 +377,35 @@ __device__ __forceinline__ double warp_dot(const float* __restrict__ t, int K, b
   return acc;
 }
 
-// Bound on max_j |r~_j - r_j| for correlations computed by length-2^logP
-// FFTs (see the kernel comment), times the number of spectra summed.
-__device__ __forceinline__ float fft_corr_error_bound(int logP, float t1, float t2, float z1, float z2, int terms) {
+// Bound on max_j |r~_j - r_j| for a correlation computed through length-P
+// FFTs as the inverse transform of a sum of `terms` spectrum products
+// T_b conj(Z_s). Inputs: t2 >= ||t_b||_2 and z2 >= ||z_s||_2 (the blocks'
+// 2-norms), Tp >= max_k |T_k| of the exact template spectra, Zc = max_k |Z~_k|
+// of the computed signal spectra. Derivation (u = 2^-24; one length-P FFT
+// has relative 2-norm error <= epsF = 14 u log2 P, the radix-2 bound
+// log2(P) (mu + gamma_4 (sqrt 2 + mu)) with a safety factor of two; the
+// unnormalised transform scales 2-norms by sqrt P):
+//   T~ Z~* - T Z* = dT Z~* + T dZ*, so each product is off by at most
+//   epsF sqrt(P) (t2 Zc + Tp z2) in 2-norm, plus its own rounding and that
+//   of the sum, (3 + terms) u |T~ Z~*| <= (3 + terms) u Tp sqrt(P) z2;
+//   the inverse transform adds epsF times the 2-norm of its input, at most
+//   epsF terms Tp sqrt(P) z2, and divides every 2-norm by sqrt(P) on the
+//   way back (the 1/P scaling is exact).
+// Hence max_j |dr_j| <= ||dr||_2 <= terms (epsF (t2 Zc + 2 Tp z2) + (3 + terms) u Tp z2).
+// The factor 1.02 covers the fp32 rounding of the norms and maxima.
+__device__ __forceinline__ float fft_corr_error_bound(int logP, float t2, float Tp, float Zc, float z2, int terms) {
   const float u = 5.9604644775390625e-08f;
   const float epsF = 14.0f * u * float(logP > 0 ? logP : 1);
-  return 1.02f * float(terms) * (epsF * (t2 * z1 + 2.0f * t1 * z2) + 3.0f * u * t1 * z2) + 1e-30f;
+  return 1.02f * float(terms) *
+             (epsF * (t2 * Zc + 2.0f * Tp * z2) + float(3 + terms) * u * Tp * z2) + 1e-30f;
+}
+
+// A rigorous bound on max_k |T_k| from the computed spectrum's maximum:
+// |T_k - T~_k| <= ||dT||_2 <= epsF sqrt(P) ||t||_2.
+__device__ __forceinline__ float spectrum_max_bound(float Tc, int logP, float t2) {
+  const float u = 5.9604644775390625e-08f;
+  const float epsF = 14.0f * u * float(logP > 0 ? logP : 1);
+  return 1.0001f * Tc + epsF * sqrtf(float(1 << logP)) * t2;
 }
 
 // Steps 7-9 for one query, shared by both correlation kernels: argmax of
@@ -276,6 +417,8 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
                                    int maxy, RFn rval) {
   __shared__ long long redl[kWarps];
   __shared__ double redd[kWarps];
+  __shared__ long long redl4[4 * kWarps];
+  __shared__ double redd4[4 * kWarps];
   __shared__ float redv[kWarps];
   __shared__ int redi[kWarps];
   __shared__ int cand[2][kCandCap];
@@ -299,6 +442,8 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
   const bool small = exact_int && double(t1) * double(maxy) < 2.0e9;
   const void* yv = static_cast<const char*>(a.y) + Q.y_off * 4;
 
+  // step 7 for both moduli: the argmax of the FFT values and every index
+  // within 2 delta of it
   for (int j = 0; j < 2; ++j) {
     const int M = Q.M[j];
     float bv = -INFINITY;
@@ -316,33 +461,97 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
         if (c < kCandCap) cand[j][c] = k;
       }
     }
-    __syncthreads();
+  }
+  __syncthreads();
+
+  // exact rescoring of the candidates
+  for (int j = 0; j < 2; ++j) {
     const int nc = ncand[j];
-    const bool all = nc > kCandCap;
-    const int ncheck = all ? M : nc;
-    double wv = -INFINITY;
-    int64_t wi = 0x7fffffffffffffffll;
-    for (int c = warp; c < ncheck; c += kWarps) {
-      const int jj = all ? c : cand[j][c];
-      double v;
-      if (ints) {
-        const int32_t* y = static_cast<const int32_t*>(yv) + int64_t(j) * P + jj;
-        v = warp_dot(t, K, exact_int, small, [&](int i) { return y[i]; });
-      } else {
-        const float* y = static_cast<const float*>(yv) + int64_t(j) * P + jj;
-        v = warp_dot(t, K, false, false, [&](int i) { return y[i]; });
+    const int32_t* yi = static_cast<const int32_t*>(yv) + int64_t(j) * P;
+    const float* yf = static_cast<const float*>(yv) + int64_t(j) * P;
+    if (nc <= kCandCap) {
+      // up to four candidates at a time, each summed by the whole block
+      double bv = -INFINITY;
+      int64_t bi = 0x7fffffffffffffffll;
+      for (int c0 = 0; c0 < nc; c0 += 4) {
+        const int nb = min(4, nc - c0);
+        int jj[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) jj[b] = cand[j][c0 + (b < nb ? b : 0)];
+        double v[4];
+        // loads for four indices i per thread go out before any is used
+        constexpr int kU = 4;
+        if (exact_int) {
+          long long acc[4] = {0, 0, 0, 0};
+          for (int i0 = tid; i0 < K; i0 += kU * kCorrThreads) {
+            float tv[kU];
+            int yv[kU][4];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              const int i = i0 + u * kCorrThreads;
+              tv[u] = i < K ? __ldg(&t[i]) : 0.f;
+#pragma unroll
+              for (int b = 0; b < 4; ++b) yv[u][b] = i < K ? yi[jj[b] + i] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              const long long ti = __float2int_rn(tv[u]);
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc[b] += ti * yv[u][b];
+            }
+          }
+          block_sum4(acc, redl4);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) v[b] = double(acc[b]);
+        } else {
+          double acc[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int i0 = tid; i0 < K; i0 += kU * kCorrThreads) {
+            float tv[kU], yv[kU][4];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              const int i = i0 + u * kCorrThreads;
+              tv[u] = i < K ? __ldg(&t[i]) : 0.f;
+#pragma unroll
+              for (int b = 0; b < 4; ++b) yv[u][b] = i < K ? (ints ? float(yi[jj[b] + i]) : yf[jj[b] + i]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc[b] = fma(double(tv[u]), double(yv[u][b]), acc[b]);
+          }
+          block_sum4(acc, redd4);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) v[b] = acc[b];
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (b < nb) betterd(bv, bi, v[b], jj[b]);
       }
-      betterd(wv, wi, v, jj);
-    }
-    if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
-    __syncthreads();
-    if (tid == 0) {
-      double v = wbest_v[0];
-      int64_t i = wbest_i[0];
-      for (int w = 1; w < kWarps; ++w) betterd(v, i, wbest_v[w], wbest_i[w]);
-      s_m[j] = int(i);
-      s_r[j] = v;
-      if (all) s_flags |= TM_RF_FULL_RESCORE;
+      if (tid == 0) {
+        s_m[j] = int(bi);
+        s_r[j] = bv;
+      }
+    } else {
+      // more candidates than the list holds: every index, one per warp
+      const int M = Q.M[j];
+      double wv = -INFINITY;
+      int64_t wi = 0x7fffffffffffffffll;
+      for (int c = warp; c < M; c += kWarps) {
+        double v;
+        if (ints) v = warp_dot(t, K, exact_int, small, [&](int i) { return yi[c + i]; });
+        else v = warp_dot(t, K, false, false, [&](int i) { return yf[c + i]; });
+        betterd(wv, wi, v, c);
+      }
+      if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
+      __syncthreads();
+      if (tid == 0) {
+        double v = wbest_v[0];
+        int64_t i = wbest_i[0];
+        for (int w = 1; w < kWarps; ++w) betterd(v, i, wbest_v[w], wbest_i[w]);
+        s_m[j] = int(i);
+        s_r[j] = v;
+        s_flags |= TM_RF_FULL_RESCORE;
+      }
     }
     __syncthreads();
   }
@@ -409,7 +618,7 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
 
 __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a) {
   extern __shared__ __align__(16) float2 sbuf[];
-  __shared__ float redf[kWarps];
+  __shared__ float redf[2 * kWarps];
   __shared__ long long redl[kWarps];
   __shared__ int redi[kWarps];
 
@@ -424,94 +633,176 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   const int npad = P + (P >> 4);
   const int halfP = P >> 1;
   float2* tw = sbuf + npad;   // W_P^m, m < P/2
+  // pass tables at the end of the launch's shared memory
+  float2* stw = reinterpret_cast<float2*>(reinterpret_cast<char*>(sbuf) + a.smem_bytes) - kPassTw;
 
   // ------------------------------------------------ twiddles, a. template spectrum
+  // Twiddles, pass tables and the template are independent loads; each
+  // loop issues a batch of them before storing any.
+  constexpr int kTB = 8;
   {
     const int stride = kPMax >> logP;
-    for (int m = tid; m < halfP; m += kCorrThreads) tw[m] = __ldg(&a.tw[m * stride]);
+    for (int m0 = tid; m0 < halfP; m0 += kTB * kCorrThreads) {
+      float2 v[kTB];
+#pragma unroll
+      for (int b = 0; b < kTB; ++b) {
+        const int m = m0 + b * kCorrThreads;
+        v[b] = m < halfP ? __ldg(&a.tw[m * stride]) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int b = 0; b < kTB; ++b)
+        if (m0 + b * kCorrThreads < halfP) tw[m0 + b * kCorrThreads] = v[b];
+    }
+    build_pass_twiddles(stw, logP, a.tw);
   }
   float t1 = 0.f, t2 = 0.f;
   int tint = 1;
-  for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int k = tid; k < K; k += kCorrThreads) {
-    const float v = t[k];
-    sbuf[pad_idx(k)].x = v;
-    t1 += fabsf(v);
-    t2 = fmaf(v, v, t2);
-    tint &= (v == rintf(v) && fabsf(v) <= 1048576.f) ? 1 : 0;
+  // the padded template (the padding slots of sbuf are never read)
+  for (int k0 = tid; k0 < P; k0 += kTB * kCorrThreads) {
+    float v[kTB];
+#pragma unroll
+    for (int b = 0; b < kTB; ++b) {
+      const int k = k0 + b * kCorrThreads;
+      v[b] = k < K ? __ldg(&t[k]) : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < kTB; ++b) {
+      const int k = k0 + b * kCorrThreads;
+      if (k < P) sbuf[pad_idx(k)] = make_float2(v[b], 0.f);
+      t1 += fabsf(v[b]);
+      t2 = fmaf(v[b], v[b], t2);
+      tint &= (v[b] == rintf(v[b]) && fabsf(v[b]) <= 1048576.f) ? 1 : 0;
+    }
   }
-  t1 = block_sum(t1, redf);
-  t2 = sqrtf(block_sum(t2, redf));
-  const bool t_integral = block_and(tint, redi) != 0;
-  fft(sbuf, logP, tw);
+  block_sum2_and(t1, t2, tint, redf, redi);
+  t2 = sqrtf(t2);
+  const bool t_integral = tint != 0;
+  fft(sbuf, logP, tw, stw);
   // the spectrum stays in shared memory when the launch left room for it
-  float2* spec = (npad + halfP + P) * int(sizeof(float2)) <= a.smem_bytes ? tw + halfP : a.spec + Q.spec_off;
-  for (int k = tid; k < P; k += kCorrThreads) spec[k] = sbuf[pad_idx(k)];
-  __syncthreads();
+  float2* spec = (npad + halfP + P + kPassTw) * int(sizeof(float2)) <= a.smem_bytes ? tw + halfP
+                                                                                   : a.spec + Q.spec_off;
+  float tc2 = 0.f;
+  for (int k = tid; k < P; k += kCorrThreads) {
+    const float2 T = sbuf[pad_idx(k)];
+    spec[k] = T;
+    tc2 = fmaxf(tc2, fmaf(T.x, T.x, T.y * T.y));
+  }
+  const float Tp = spectrum_max_bound(sqrtf(block_maxf(tc2, redf)), logP, t2);
 
   // ------------------------------------------------ b. folds
+  // Loads are issued in batches (kB per thread) before their results are
+  // used, so each pass waits for about one memory round trip.
+  constexpr int kB = 8;
   int* ib = reinterpret_cast<int*>(sbuf);     // int view: entry e -> ib[2e] (M1), ib[2e+1] (M2)
   float* fb = reinterpret_cast<float*>(sbuf);
   for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
   __syncthreads();
-  for (int j = 0; j < 2; ++j) {
-    const int M = Q.M[j], Rr = Q.R[j];
-    const int L = int(Q.L[j]);
-    const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
-    const int32_t* part = a.partial + Q.part + Q.moff[j];
-    if (ints) {
-      // Partial slots hold counts of -1 entries per column kp < Mp of the
-      // Mp-fold; column k of the M-fold gathers kp = k + r M, r < R. Four
-      // columns per pass keep enough loads in flight.
-      const int Mp = Rr * M;
-      for (int k0 = 4 * tid; k0 < Mp; k0 += 4 * kCorrThreads) {
-        int4 c = make_int4(0, 0, 0, 0);
-        if (k0 + 4 <= Mp) {
-          for (int s = 0; s < Q.nslots; ++s) {
-            const int4 v = __ldg(reinterpret_cast<const int4*>(part + int64_t(s) * Q.stride + k0));
-            c.x += v.x; c.y += v.y; c.z += v.z; c.w += v.w;
-          }
-        } else {
-          for (int s = 0; s < Q.nslots; ++s) {
-            const int32_t* ps = part + int64_t(s) * Q.stride + k0;
-            c.x += ps[0];
-            if (k0 + 1 < Mp) c.y += ps[1];
-            if (k0 + 2 < Mp) c.z += ps[2];
-          }
-        }
-        const int cc[4] = {c.x, c.y, c.z, c.w};
+  if (ints) {
+    // Partial slots hold counts of -1 (int8) or +1 (bits) entries per column
+    // kp < Mp of the Mp-fold; column k of the M-fold gathers kp = k + r M,
+    // r < R. Slot rows are padded to 16 columns, so a quad read at kp < Mp
+    // stays inside the row; columns past Mp are dropped.
+    for (int j = 0; j < 2; ++j) {
+      const int M = Q.M[j], Rr = Q.R[j], Mp = Rr * M;
+      const int32_t* part = a.partial + Q.part + Q.moff[j];
+      const int nq4 = (Mp + 3) >> 2;
+      for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
+        int4 c[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int kp = k0 + i;
-          if (kp < Mp && cc[i] != 0) {
-            const int e = 2 * pad_idx(Rr == 1 ? kp : kp % M) + j;
-            if (Rr == 1) ib[e] = cc[i];
-            else atomicAdd(&ib[e], cc[i]);
+        for (int b = 0; b < 4; ++b) c[b] = make_int4(0, 0, 0, 0);
+#pragma unroll 2
+        for (int sl = 0; sl < Q.nslots; ++sl) {
+          const int32_t* ps = part + int64_t(sl) * Q.stride;
+          int4 v[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int q = q0 + b * kCorrThreads;
+            v[b] = q < nq4 ? __ldg(reinterpret_cast<const int4*>(ps) + q) : make_int4(0, 0, 0, 0);
+          }
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            c[b].x += v[b].x; c[b].y += v[b].y; c[b].z += v[b].z; c[b].w += v[b].w;
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int k0 = 4 * (q0 + b * kCorrThreads);
+          const int cc[4] = {c[b].x, c[b].y, c[b].z, c[b].w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int kp = k0 + i;
+            if (kp < Mp && cc[i] != 0) {
+              const int e = 2 * pad_idx(Rr == 1 ? kp : kp % M) + j;
+              if (Rr == 1) ib[e] = cc[i];
+              else atomicAdd(&ib[e], cc[i]);
+            }
           }
         }
       }
-      __syncthreads();
-      const bool ones = Q.xdtype == TM_BITS_PM1;   // bit-packed slots count +1 entries, int8 slots -1 entries
-      for (int k = tid; k < M; k += kCorrThreads) {
-        // entries n < N with n = k (mod M): L of them for k < Rw, else L-1
-        const int e = 2 * pad_idx(k) + j;
-        const int nk = L - 1 + (k < Rw ? 1 : 0);
-        int yk = ones ? 2 * ib[e] - nk : nk - 2 * ib[e];
-        if (k >= Rw) yk += sig.ival(k - Rw);
-        ib[e] = yk;
-      }
-    } else {
-      for (int k = tid; k < M; k += kCorrThreads) {
-        // partial slots hold fp32 column sums, added in a fixed order
-        const float* pf = reinterpret_cast<const float*>(part);
-        float yk = 0.f;
-        for (int s = 0; s < Q.nslots; ++s) {
-          const float* ps = pf + int64_t(s) * Q.stride;
-          for (int r = 0; r < Rr; ++r) yk += ps[k + r * M];
+    }
+    __syncthreads();
+    // counts -> fold values; column k >= Rw (the last row is short) also
+    // takes the wrap-around entry x_{k-Rw}
+    const bool ones = Q.xdtype == TM_BITS_PM1;   // bit-packed slots count +1 entries, int8 slots -1 entries
+    for (int j = 0; j < 2; ++j) {
+      const int M = Q.M[j];
+      const int L = int(Q.L[j]);
+      const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
+      with_sig(Q.xdtype, Q.x, [&](auto sx) {
+        for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
+          float xv[kB];
+#pragma unroll
+          for (int b = 0; b < kB; ++b) {
+            const int k = k0 + b * kCorrThreads;
+            xv[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
+          }
+#pragma unroll
+          for (int b = 0; b < kB; ++b) {
+            const int k = k0 + b * kCorrThreads;
+            if (k < M) {
+              // entries n < N with n = k (mod M): L of them for k < Rw, else L-1
+              const int e = 2 * pad_idx(k) + j;
+              const int nk = L - 1 + (k < Rw ? 1 : 0);
+              ib[e] = (ones ? 2 * ib[e] - nk : nk - 2 * ib[e]) + int(xv[b]);
+            }
+          }
         }
-        if (k >= Rw) yk += sig.val(k - Rw);
-        fb[2 * pad_idx(k) + j] = yk;
+      });
+    }
+  } else {
+    // partial slots hold fp32 column sums, added in a fixed order
+    for (int j = 0; j < 2; ++j) {
+      const int M = Q.M[j], Rr = Q.R[j];
+      const int L = int(Q.L[j]);
+      const int Rw = int(N - int64_t(L - 1) * M);
+      const float* pf = reinterpret_cast<const float*>(a.partial + Q.part + Q.moff[j]);
+      for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
+        float acc[kB];
+        with_sig(Q.xdtype, Q.x, [&](auto sx) {
+#pragma unroll
+          for (int b = 0; b < kB; ++b) {
+            const int k = k0 + b * kCorrThreads;
+            acc[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
+          }
+        });
+        float yk[kB];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) yk[b] = 0.f;
+        for (int sl = 0; sl < Q.nslots; ++sl) {
+          const float* ps = pf + int64_t(sl) * Q.stride;
+          for (int r = 0; r < Rr; ++r) {
+#pragma unroll
+            for (int b = 0; b < kB; ++b) {
+              const int k = k0 + b * kCorrThreads;
+              if (k < M) yk[b] += __ldg(&ps[k + r * M]);
+            }
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          const int k = k0 + b * kCorrThreads;
+          if (k < M) fb[2 * pad_idx(k) + j] = yk[b] + acc[b];
+        }
       }
     }
   }
@@ -529,24 +820,43 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
     }
   }
   __syncthreads();
+  // extension y[M+i] = y[i] - x_i + x_{(i+LM) mod N}, i < K-1
   for (int j = 0; j < 2; ++j) {
     const int M = Q.M[j];
     const int64_t LM = Q.L[j] * M;
-    for (int i = tid; i < K - 1; i += kCorrThreads) {
-      const int e = 2 * pad_idx(M + i) + j, e0 = 2 * pad_idx(i) + j;
-      int64_t w = i + LM - N;   // LM >= N and i + LM - N < 2M, so one reduction is rare
-      if (w >= N) w %= N;
-      if (ints) ib[e] = ib[e0] - sig.ival(i) + sig.ival(w);
-      else fb[e] = fb[e0] - sig.val(i) + sig.val(w);
+    for (int i0 = tid; i0 < K - 1; i0 += kB * kCorrThreads) {
+      float xi[kB], xw[kB];
+      with_sig(Q.xdtype, Q.x, [&](auto sx) {
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          const int i = i0 + b * kCorrThreads;
+          xi[b] = xw[b] = 0.f;
+          if (i < K - 1) {
+            int64_t w = i + LM - N;   // LM >= N and i + LM - N < 2M, so one reduction is rare
+            if (w >= N) w %= N;
+            xi[b] = sx.val(i);
+            xw[b] = sx.val(w);
+          }
+        }
+      });
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int i = i0 + b * kCorrThreads;
+        if (i < K - 1) {
+          const int e = 2 * pad_idx(M + i) + j, e0 = 2 * pad_idx(i) + j;
+          if (ints) ib[e] = ib[e0] - int(xi[b]) + int(xw[b]);
+          else fb[e] = fb[e0] - xi[b] + xw[b];
+        }
+      }
     }
   }
   __syncthreads();
   // export exact folds, convert to float, norms of z (exact integers for +-1
   // signals; fp32 sums for reals)
-  float z1 = 0.f, z2 = 0.f;
+  float z2 = 0.f;
   int maxy = 0;
   if (ints) {
-    long long s1 = 0, s2 = 0;
+    long long s2 = 0;
     int32_t* yi = static_cast<int32_t*>(a.y) + Q.y_off;
     for (int k = tid; k < P; k += kCorrThreads) {
       const int e = 2 * pad_idx(k);
@@ -554,13 +864,10 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
       yi[k] = v0;
       yi[P + k] = v1;
       sbuf[pad_idx(k)] = make_float2(float(v0), float(v1));
-      s1 += abs(v0) + abs(v1);
       s2 += (long long)v0 * v0 + (long long)v1 * v1;
       maxy = max(maxy, max(abs(v0), abs(v1)));
     }
-    s1 = block_sum(s1, redl);
     s2 = block_sum(s2, redl);
-    z1 = float(s1);
     z2 = sqrtf(float(s2));
     maxy = block_max(maxy, redi);
   } else {
@@ -569,21 +876,21 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
       const float2 v = sbuf[pad_idx(k)];
       yf[k] = v.x;
       yf[P + k] = v.y;
-      z1 += fabsf(v.x) + fabsf(v.y);
       z2 = fmaf(v.x, v.x, fmaf(v.y, v.y, z2));
     }
-    z1 = block_sum(z1, redf);
     z2 = sqrtf(block_sum(z2, redf));
   }
 
   // ------------------------------------------------ c. correlation by FFT
-  fft(sbuf, logP, tw);
+  fft(sbuf, logP, tw, stw);
+  float zc2 = 0.f;
   for (int k = tid; k < P; k += kCorrThreads) {
     const float2 z = sbuf[pad_idx(k)], T = spec[k];
+    zc2 = fmaxf(zc2, fmaf(z.x, z.x, z.y * z.y));
     sbuf[pad_idx(k)] = make_float2(T.x * z.x + T.y * z.y, T.y * z.x - T.x * z.y);   // T conj(Z)
   }
-  __syncthreads();
-  fft(sbuf, logP, tw);
+  const float Zc = 1.0001f * sqrtf(block_maxf(zc2, redf));   // block_maxf also orders the writes above
+  fft(sbuf, logP, tw, stw);
   const float invP = 1.0f / float(P);   // exact: P is a power of two
 
   if (a.r != nullptr && Q.r_off >= 0) {
@@ -593,14 +900,8 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   }
 
   // ------------------------------------------------ d-e. steps 7-9
-  // Rounding bound (normwise, fp32 unit roundoff u): one length-P FFT has
-  // relative 2-norm error <= epsF = 14 u log2 P (the radix-2 bound
-  // log2(P) (mu + gamma_4 (sqrt 2 + mu)) with a safety factor of two); with
-  // |T_k| <= ||t||_1, |Z_k| <= ||z||_1 and the 1/P scaling of the inverse,
-  // max_j |dr_j| <= ||dw||_2 <= epsF (||t||_2 ||z||_1 + 2 ||t||_1 ||z||_2) + 3u ||t||_1 ||z||_2.
-  // The norms are fp32 sums (relative error below (K + 2P) u < 1e-2); the
-  // factor 1.02 covers them.
-  const float delta = fft_corr_error_bound(logP, t1, t2, z1, z2, 1);
+  // Rounding bound on every r_j (fft_corr_error_bound, one product term).
+  const float delta = fft_corr_error_bound(logP, t2, Tp, Zc, z2, 1);
   select_and_resolve(a, Q, qi, delta, t_integral, t1, maxy, [&](int j, int k) {
     const float2 w = sbuf[pad_idx(k)];
     return j == 0 ? w.x * invP : -w.y * invP;
@@ -641,10 +942,12 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
   const int S = A + Bt - 1;
   float2* spec = a.spec + Q.spec_off;   // [Bt + S][PB]
   float* rb = a.r + Q.r_off;            // [2][P]: r_1 then r_2
+  float2* stw = reinterpret_cast<float2*>(reinterpret_cast<char*>(sbuf) + a.smem_bytes) - kPassTw;
 
   {
     const int stride = kPMax >> kBlkLog;
     for (int m = tid; m < PB / 2; m += kCorrThreads) tw[m] = __ldg(&a.tw[m * stride]);
+    build_pass_twiddles(stw, kBlkLog, a.tw);
   }
   // template norms
   float t1 = 0.f, t2 = 0.f;
@@ -719,45 +1022,45 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
     if (k >= Q.M[j] + K - 1) return 0.f;
     return ints ? float(yi[int64_t(j) * P + k]) : yf[int64_t(j) * P + k];
   };
-  float z1 = 0.f, z2 = 0.f;
+  float z2 = 0.f;
   int maxy = 0;
   {
-    long long s1 = 0, s2 = 0;
-    float f1 = 0.f, f2 = 0.f;
+    long long s2 = 0;
+    float f2 = 0.f;
     for (int j = 0; j < 2; ++j) {
       for (int k = tid; k < Q.M[j] + K - 1; k += kCorrThreads) {
         if (ints) {
           const int v = yi[int64_t(j) * P + k];
-          s1 += abs(v);
           s2 += (long long)v * v;
           maxy = max(maxy, abs(v));
         } else {
           const float v = yf[int64_t(j) * P + k];
-          f1 += fabsf(v);
           f2 = fmaf(v, v, f2);
         }
       }
     }
     if (ints) {
-      s1 = block_sum(s1, redl);
       s2 = block_sum(s2, redl);
-      z1 = float(s1);
       z2 = sqrtf(float(s2));
       maxy = block_max(maxy, redi);
     } else {
-      z1 = block_sum(f1, redf);
       z2 = sqrtf(block_sum(f2, redf));
     }
   }
 
   // ------------------------------------------------ spectra of template blocks and signal segments
+  float tc2 = 0.f, zc2 = 0.f;   // largest |T~_k|^2, |Z~_k|^2 over all blocks
   for (int b = 0; b < Bt; ++b) {
     for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int i = tid; i < kBlk && b * kBlk + i < K; i += kCorrThreads) sbuf[pad_idx(i)].x = t[b * kBlk + i];
     __syncthreads();
-    fft(sbuf, kBlkLog, tw);
-    for (int k = tid; k < PB; k += kCorrThreads) spec[int64_t(b) * PB + k] = sbuf[pad_idx(k)];
+    fft(sbuf, kBlkLog, tw, stw);
+    for (int k = tid; k < PB; k += kCorrThreads) {
+      const float2 T = sbuf[pad_idx(k)];
+      spec[int64_t(b) * PB + k] = T;
+      tc2 = fmaxf(tc2, fmaf(T.x, T.x, T.y * T.y));
+    }
     __syncthreads();
   }
   for (int s = 0; s < S; ++s) {
@@ -766,10 +1069,16 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
       sbuf[pad_idx(i)] = make_float2(yval(0, k), yval(1, k));
     }
     __syncthreads();
-    fft(sbuf, kBlkLog, tw);
-    for (int k = tid; k < PB; k += kCorrThreads) spec[int64_t(Bt + s) * PB + k] = sbuf[pad_idx(k)];
+    fft(sbuf, kBlkLog, tw, stw);
+    for (int k = tid; k < PB; k += kCorrThreads) {
+      const float2 Z = sbuf[pad_idx(k)];
+      spec[int64_t(Bt + s) * PB + k] = Z;
+      zc2 = fmaxf(zc2, fmaf(Z.x, Z.x, Z.y * Z.y));
+    }
     __syncthreads();
   }
+  const float Tp = spectrum_max_bound(sqrtf(block_maxf(tc2, redf)), kBlkLog, t2);
+  const float Zc = 1.0001f * sqrtf(block_maxf(zc2, redf));
   // ------------------------------------------------ output blocks
   const float invPB = 1.0f / float(PB);
   for (int ab = 0; ab < A; ++ab) {
@@ -783,7 +1092,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
       sbuf[pad_idx(k)] = acc;
     }
     __syncthreads();
-    fft(sbuf, kBlkLog, tw);
+    fft(sbuf, kBlkLog, tw, stw);
     for (int i = tid; i < kBlk; i += kCorrThreads) {
       const int jj = ab * kBlk + i;
       const float2 w = sbuf[pad_idx(i)];
@@ -793,16 +1102,19 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
     __syncthreads();
   }
   // ------------------------------------------------ steps 7-9
-  const float delta = fft_corr_error_bound(kBlkLog, t1, t2, z1, z2, Bt);
+  const float delta = fft_corr_error_bound(kBlkLog, t2, Tp, Zc, z2, Bt);
   select_and_resolve(a, Q, qi, delta, t_integral, t1, maxy,
                      [&](int j, int k) { return rb[int64_t(j) * P + k]; });
 }
 
-int corr_blocked_smem_bytes() { return (2 * kBlk + 2 * kBlk / 16 + kBlk) * int(sizeof(float2)); }
+int corr_blocked_smem_bytes() { return (2 * kBlk + 2 * kBlk / 16 + kBlk + kPassTw) * int(sizeof(float2)); }
 
 // Shared memory of a launch whose largest FFT is P: the padded work buffer,
-// the half twiddle table and, for P <= 8192, the template spectrum.
-int corr_smem_bytes(int P) { return (P + P / 16 + P / 2 + (P <= 8192 ? P : 0)) * int(sizeof(float2)); }
+// the half twiddle table, for P <= 8192 the template spectrum, and the pass
+// twiddle tables.
+int corr_smem_bytes(int P) {
+  return (P + P / 16 + P / 2 + (P <= 8192 ? P : 0) + kPassTw) * int(sizeof(float2));
+}
 
 }  // namespace
 

@@ -305,7 +305,6 @@ struct UnitBits {
     plane_add(v);
     if (++rows >= 30) flush_planes();
   }
-  __device__ __forceinline__ void end_row_block() {}
   __device__ __forceinline__ void widen() {}
   __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
     flush_planes();
@@ -349,7 +348,6 @@ struct UnitF32 {
     for (int i = 0; i < 4; ++i)
       if (o + i >= 0 && o + i < len) acc[i] += __uint_as_float(w[i]);
   }
-  __device__ __forceinline__ void end_row_block() {}
   __device__ __forceinline__ void widen() {}
   __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
     float* d = reinterpret_cast<float*>(dst) + col;
@@ -396,7 +394,6 @@ struct UnitF16 {
       if (o + 2 * i + 1 >= 0 && o + 2 * i + 1 < len) acc[2 * i + 1] += f.y;
     }
   }
-  __device__ __forceinline__ void end_row_block() {}
   __device__ __forceinline__ void widen() {}
   __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
     float* d = reinterpret_cast<float*>(dst) + col;
