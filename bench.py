@@ -14,6 +14,7 @@ bounded sample, and a plain full-length FFT correlation (cuFFT via torch)
 on the same GPU for comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+  python bench.py --workload uneven|serve   (other workloads, one line each)
   N > 1: torchrun --nproc-per-node N bench.py --gpus N ... (queries sharded by
   rank, no collective on the data path: weak scaling).
 """
@@ -331,6 +332,158 @@ def run_native(args):
     return 0
 
 
+def signal_bytes(N: int, xdtype: str) -> int:
+    return {"i8": N, "bits": (N + 7) // 8, "f16": 2 * N, "f32": 4 * N}[xdtype]
+
+
+def run_uneven(args):
+    """The 4096-query uneven mix (N log-uniform in [2^14, 2^24], K in [2^8,
+    2^13], half +-1 int8 / half N(0,1) fp32 signals, automatic moduli) as one
+    CUDA graph per step. Inputs are drawn on the device (about 25 GB)."""
+    import torch
+    import paper_1509_04863_gb300 as tm
+    from workloads import device as WD
+    n = args.queries if args.queries != QUERIES else 4096
+    t0 = time.perf_counter()
+    qs = WD.uneven(seed=5000, n=n)
+    gen_s = time.perf_counter() - t0
+    specs = [dict(x=q["x"], t=q["t"], N=q["N"], K=q["K"], xdtype=q["xdtype"], mode="auto") for q in qs]
+    total_bytes = sum(signal_bytes(q["N"], q["xdtype"]) for q in qs)
+    b = tm.Batch(specs)
+    out = tm.result_buffer(n)
+    b.capture_graph(out)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.launch_graph(stream)
+    torch.cuda.synchronize()
+    assert b.device_error() == 0
+    res = tm.decode_results(out)
+    success = sum(r["shift"] == q["k_star"] for r, q in zip(res, qs)) / n
+    K = args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        b.launch_graph(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / K
+    # the fold launches alone (outside the graph) for the roofline
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nf = max(3, min(20, K))
+    f0.record(stream)
+    for _ in range(nf):
+        b.fold(stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fold_ms = f0.elapsed_time(f1) / nf
+    hbm_peak, peak_kind = measured_peaks()
+    st = b.stats()
+    line = {
+        "metric": "queries/s", "value": n / (ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32/f32 (fold), f32 (FFT), int64/f64 (rescoring)",
+        "data": "synthetic (drawn on the device with torch's seeded CUDA generator)",
+        "config": {"workload": f"uneven{n}: N log-uniform [2^14,2^24], K log-uniform [2^8,2^13], "
+                               "half int8 +-1 / half fp32 N(0,1), template noise N(0,0.3^2), auto moduli",
+                   "queries": n, "signal_bytes": total_bytes, "launch": "one CUDA graph per step",
+                   "l2": f"{total_bytes / 1e9:.1f} GB of signals per step > L2 (no flush)"},
+        "input_GBps": total_bytes / (ms / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": "fold_kernel (int8 and fp32 groups)",
+                     "achieved": total_bytes / (fold_ms / 1e3) / 1e9, "peak": hbm_peak,
+                     "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s",
+                     "frac": total_bytes / (fold_ms / 1e3) / 1e9 / hbm_peak, "traffic": None,
+                     "fold_ms": fold_ms, "corr_ms": ms - fold_ms},
+        "gpu_launches": K * st["launches_per_run"], "fold_ctas": st["fold_ctas"],
+        "clocks": clk, "success_rate": success, "generation_s": gen_s,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_serve(args):
+    """Continuous-batching server under open-loop Poisson arrivals: a pool of
+    resident signals of the uneven mix, each request a fresh template cut
+    from one of them; real signals stored as fp32, then as fp16."""
+    import threading
+
+    import torch
+    import paper_1509_04863_gb300 as tm
+    from workloads import device as WD
+    rate, dur, nsig = args.rate, args.duration, args.signals
+    sigs = WD.uneven(seed=7000, n=nsig)
+    nreq = int(rate * dur)
+    rng = np.random.default_rng(123)
+    gaps = rng.exponential(1.0 / rate, nreq)
+    arrive = np.cumsum(gaps)
+    which = rng.integers(0, nsig, nreq)
+    shifts = [int(rng.integers(0, sigs[w]["N"])) for w in which]
+    # fresh templates, cut on the device and copied to host memory before the run
+    temps = []
+    for i in range(nreq):
+        g = sigs[which[i]]
+        temps.append(WD.template(g["x"], g["K"], shifts[i], 0.3, 10 ** 6 + i).cpu().numpy())
+    out = {"offered_qps": rate, "duration_s": dur, "requests": nreq, "signals": nsig}
+    shift_by_storage = {}
+    for storage in ("f32", "f16"):
+        srv = tm.Server(n_streams=args.streams, max_batch=args.max_batch)
+        ids = []
+        for g in sigs:
+            if g["xdtype"] == "f32" and storage == "f16":
+                ids.append(srv.register_signal(g["x"].half(), g["N"], "f16"))
+            else:
+                ids.append(srv.register_signal(g["x"], g["N"], g["xdtype"]))
+        got = {}
+        done = threading.Event()
+
+        def poller():
+            while len(got) < nreq:
+                for r in srv.poll(4096, timeout_us=2000):
+                    got[r["tag"]] = r
+            done.set()
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        rejected = 0
+        t_start = time.perf_counter()
+        for i in range(nreq):
+            while time.perf_counter() - t_start < arrive[i]:
+                pass
+            while srv.submit(ids[which[i]], temps[i], tag=i, mode="auto") == tm.TM_EAGAIN:
+                rejected += 1
+        done.wait(timeout=120)
+        t_end = time.perf_counter()
+        lat = np.array([got[i]["latency_us"] for i in range(nreq) if i in got and i >= nreq // 10])
+        st = srv.stats()
+        shift_by_storage[storage] = [got[i]["shift"] if i in got else None for i in range(nreq)]
+        out[storage] = {"served_qps": len(got) / (t_end - t_start), "completed": len(got),
+                        "failed": st["failed"], "rejected_retries": rejected,
+                        "p50_us": float(np.percentile(lat, 50)) if len(lat) else None,
+                        "p99_us": float(np.percentile(lat, 99)) if len(lat) else None,
+                        "max_us": float(lat.max()) if len(lat) else None,
+                        "mean_batch": st["mean_batch"], "iterations": st["iterations"],
+                        "success_rate": float(np.mean([shift_by_storage[storage][i] == shifts[i]
+                                                       for i in range(nreq)]))}
+        srv.close()
+        del srv
+        torch.cuda.synchronize()
+    agree = np.mean([a == b for a, b in zip(shift_by_storage["f32"], shift_by_storage["f16"])])
+    line = {"metric": "served queries/s", "value": out["f32"]["served_qps"], "unit": "queries/s", "n_gpus": 1,
+            "higher_is_better": True, "vs_baseline": None, "dtype": "int32/f32 fold, f32 FFT",
+            "data": "synthetic (device-drawn)",
+            "config": {"workload": f"serve: Poisson {rate:.0f} req/s for {dur:.0f} s over {nsig} resident signals "
+                                   "of the uneven mix (half int8 +-1, half real)",
+                       "streams": args.streams, "max_batch": args.max_batch},
+            "latency_us": {"p50": out["f32"]["p50_us"], "p99": out["f32"]["p99_us"],
+                           "what": "submit to result, server clock, first 10% of requests excluded"},
+            "serve": out, "f16_vs_f32_shift_agreement": float(agree)}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,6 +495,14 @@ def main():
     ap.add_argument("--queries", type=int, default=64)
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--K", type=int, default=K_T)
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve"],
+                    help="batch64 (default line), uneven (4096-query mix as one CUDA graph), "
+                         "serve (Poisson arrivals through the continuous-batching server)")
+    ap.add_argument("--rate", type=float, default=20000.0)
+    ap.add_argument("--duration", type=float, default=3.0)
+    ap.add_argument("--signals", type=int, default=1024)
+    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--max-batch", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -349,6 +510,10 @@ def main():
         return run_reference(args)
     if args.kernels_only:
         return run_kernels_only(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_native(args)
 
 

@@ -161,8 +161,9 @@ TM_API tm_status tm_batch_set_inputs(tm_batch_t b, const tm_query* q, int32_t n)
  * writes partial column sums of both folds. */
 TM_API tm_status tm_batch_fold(tm_batch_t b, tm_stream_t stream);
 /* Steps 3 (completion: wrap term, extension k >= M), 4-9 for every query:
- * one CTA per query; writes n tm_results to out_dev. Must follow
- * tm_batch_fold on the same stream. */
+ * one CTA per query, largest FFT first, in one launch (plus one launch for
+ * queries whose FFT exceeds 16384 points); writes n tm_results to out_dev.
+ * Must follow tm_batch_fold on the same stream. */
 TM_API tm_status tm_batch_correlate(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
 /* tm_batch_fold + tm_batch_correlate. */
 TM_API tm_status tm_batch_run(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
@@ -174,6 +175,15 @@ TM_API tm_status tm_batch_run(tm_batch_t b, tm_result* out_dev, tm_stream_t stre
 TM_API tm_status tm_batch_run_host(tm_batch_t b, const void* const* x_host,
                             const float* const* t_host, tm_result* out_host,
                             tm_stream_t stream);
+/* Record one tm_batch_run(b, out_dev) - the fold launches and the
+ * correlation launches with the memsets before them - as a CUDA graph held
+ * by the batch (captured on a private stream; nothing runs). Replaces an
+ * earlier capture. The graph reads the query descriptors from device
+ * memory, so tm_batch_set_inputs still applies to it; out_dev is fixed. */
+TM_API tm_status tm_batch_graph_capture(tm_batch_t b, tm_result* out_dev);
+/* Launch the captured graph on a stream: the same work as tm_batch_run in
+ * one graph launch. TM_EINVAL without a capture. */
+TM_API tm_status tm_batch_graph_launch(tm_batch_t b, tm_stream_t stream);
 /* Device pointers to query i's folds from the last run: y[0..P) for M1 then
  * y[P..2P) for M2, entries k < M_j+K-1 valid. int32 for +-1 signals,
  * float32 for real signals (*is_float set accordingly). */

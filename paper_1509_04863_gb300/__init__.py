@@ -72,6 +72,8 @@ _SIGS = {
     "tm_batch_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "tm_batch_run_host": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p,
                                     C.c_void_p]),
+    "tm_batch_graph_capture": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tm_batch_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_folds": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]),
     "tm_batch_corr": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "tm_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
@@ -224,6 +226,13 @@ class Batch:
 
     def correlate(self, out, stream=None):
         _check(lib().tm_batch_correlate(self._h, out.data_ptr(), _stream_ptr(stream)), "tm_batch_correlate")
+
+    def capture_graph(self, out):
+        """Record one run writing to `out` as a CUDA graph (tm_batch_graph_capture)."""
+        _check(lib().tm_batch_graph_capture(self._h, out.data_ptr()), "tm_batch_graph_capture")
+
+    def launch_graph(self, stream=None):
+        _check(lib().tm_batch_graph_launch(self._h, _stream_ptr(stream)), "tm_batch_graph_launch")
 
     def run_host(self, x_host: Sequence, t_host: Sequence, out_host, stream=None):
         """x_host, t_host: CPU tensors (pinned for speed); out_host: CPU tensor of n*48 bytes."""

@@ -158,6 +158,8 @@ void batch_free(tm_batch_t b) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(b->device);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->ev_stage) { cudaEventSynchronize(b->ev_stage); cudaEventDestroy(b->ev_stage); }
   if (b->owns_memory) {
     cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_order); cudaFree(b->d_partial);
@@ -489,6 +491,39 @@ tm_status tm_batch_run(tm_batch_t b, tm_result* out, tm_stream_t stream) {
   tm_status st = tm_batch_fold(b, stream);
   if (st != TM_OK) return st;
   return tm_batch_correlate(b, out, stream);
+}
+
+tm_status tm_batch_graph_capture(tm_batch_t b, tm_result* out) {
+  if (!b || !out) return fail(TM_EINVAL, "tm_batch_graph_capture: null argument");
+  TM_CUDA(cudaSetDevice(b->device));
+  if (!b->cap_stream) TM_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  TM_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  tm_status st = batch_fold(b, b->cap_stream);
+  if (st == TM_OK) st = batch_correlate(b, out, b->cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+  if (st != TM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  const cudaError_t e2 = cudaGraphInstantiate(&b->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    b->gexec = nullptr;
+    return cuda_fail(e2, "cudaGraphInstantiate");
+  }
+  return TM_OK;
+}
+
+tm_status tm_batch_graph_launch(tm_batch_t b, tm_stream_t stream) {
+  if (!b || !b->gexec) return fail(TM_EINVAL, "tm_batch_graph_launch: no captured graph");
+  TM_CUDA(cudaGraphLaunch(b->gexec, reinterpret_cast<cudaStream_t>(stream)));
+  return TM_OK;
 }
 
 tm_status tm_batch_run_host(tm_batch_t b, const void* const* x_host, const float* const* t_host,

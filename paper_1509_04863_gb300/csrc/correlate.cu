@@ -105,10 +105,11 @@ __device__ __forceinline__ float2 twiddle(const float2* tw, int e, int halfP) {
 // and writes to (j - j mod Ns) R + j mod Ns + r Ns. The twiddles come from
 // the pass table stab[(r-1) Ns + k] = W_{16 Ns}^{r k} when given (lanes with
 // consecutive k read consecutive entries), else from the half table tw.
-template <int R>
+template <int R, int NBMAX>
 __device__ __forceinline__ void fft_pass(float2* buf, int P, int Ns, int twshift, const float2* tw,
                                          const float2* stab) {
-  constexpr int NB = (kPMax / R + kCorrThreads - 1) / kCorrThreads;
+  // butterflies per thread: NBMAX radix-16 butterflies' worth of points
+  constexpr int NB = (NBMAX * 16) / R;
   const int nbf = P / R;
   float2 v[NB][R];
 #pragma unroll
@@ -166,24 +167,26 @@ __device__ void build_pass_twiddles(float2* stw, int logP, const float2* __restr
   }
 }
 
-// Forward FFT of length 2^logP in place (padded layout, natural order);
-// tw holds W_P^m for m < P/2, stw the pass tables of build_pass_twiddles.
-__device__ void fft(float2* buf, int logP, const float2* tw, const float2* stw) {
+// Forward FFT of length 2^logP <= 8192 NBMAX in place (padded layout,
+// natural order); tw holds W_P^m for m < P/2, stw the pass tables of
+// build_pass_twiddles. Each thread holds NBMAX x 16 points per pass.
+template <int NBMAX>
+__device__ __forceinline__ void fft(float2* buf, int logP, const float2* tw, const float2* stw) {
   const int P = 1 << logP;
   int logNs = 0;
   const int first = pass_first(logP);
   if (first) {
     const int twshift = logP - first;
-    if (first == 1) fft_pass<2>(buf, P, 1, twshift, tw, nullptr);
-    else if (first == 2) fft_pass<4>(buf, P, 1, twshift, tw, nullptr);
-    else fft_pass<8>(buf, P, 1, twshift, tw, nullptr);
+    if (first == 1) fft_pass<2, NBMAX>(buf, P, 1, twshift, tw, nullptr);
+    else if (first == 2) fft_pass<4, NBMAX>(buf, P, 1, twshift, tw, nullptr);
+    else fft_pass<8, NBMAX>(buf, P, 1, twshift, tw, nullptr);
     logNs = first;
   }
   int off = 0;
   while (logNs < logP) {
     const int Ns = 1 << logNs;
     const bool last = logNs + 4 == logP;
-    fft_pass<16>(buf, P, Ns, logP - (logNs + 4), tw, (last || Ns == 1) ? nullptr : stw + off);
+    fft_pass<16, NBMAX>(buf, P, Ns, logP - (logNs + 4), tw, (last || Ns == 1) ? nullptr : stw + off);
     if (!last && Ns > 1) off += 15 * Ns;
     logNs += 4;
   }
@@ -616,14 +619,16 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
   }
 }
 
-__global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a) {
-  extern __shared__ __align__(16) float2 sbuf[];
+// Steps 3 (completion) to 9 for query qi. The twiddle table and the pass
+// tables are loaded only when logP differs from the previous query's
+// (loaded_logP).
+template <int NBMAX>
+__device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sbuf, int& loaded_logP) {
   __shared__ float redf[2 * kWarps];
   __shared__ long long redl[kWarps];
   __shared__ int redi[kWarps];
 
   const int tid = threadIdx.x;
-  const int qi = a.order[blockIdx.x];
   const CorrQ Q = a.q[qi];
   const int P = Q.P, logP = Q.logP, K = Q.K;
   const int64_t N = Q.N;
@@ -640,7 +645,8 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   // Twiddles, pass tables and the template are independent loads; each
   // loop issues a batch of them before storing any.
   constexpr int kTB = 8;
-  {
+  if (logP != loaded_logP) {
+    loaded_logP = logP;
     const int stride = kPMax >> logP;
     for (int m0 = tid; m0 < halfP; m0 += kTB * kCorrThreads) {
       float2 v[kTB];
@@ -677,7 +683,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   block_sum2_and(t1, t2, tint, redf, redi);
   t2 = sqrtf(t2);
   const bool t_integral = tint != 0;
-  fft(sbuf, logP, tw, stw);
+  fft<NBMAX>(sbuf, logP, tw, stw);
   // the spectrum stays in shared memory when the launch left room for it
   float2* spec = (npad + halfP + P + kPassTw) * int(sizeof(float2)) <= a.smem_bytes ? tw + halfP
                                                                                    : a.spec + Q.spec_off;
@@ -882,7 +888,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
   }
 
   // ------------------------------------------------ c. correlation by FFT
-  fft(sbuf, logP, tw, stw);
+  fft<NBMAX>(sbuf, logP, tw, stw);
   float zc2 = 0.f;
   for (int k = tid; k < P; k += kCorrThreads) {
     const float2 z = sbuf[pad_idx(k)], T = spec[k];
@@ -890,7 +896,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
     sbuf[pad_idx(k)] = make_float2(T.x * z.x + T.y * z.y, T.y * z.x - T.x * z.y);   // T conj(Z)
   }
   const float Zc = 1.0001f * sqrtf(block_maxf(zc2, redf));   // block_maxf also orders the writes above
-  fft(sbuf, logP, tw, stw);
+  fft<NBMAX>(sbuf, logP, tw, stw);
   const float invP = 1.0f / float(P);   // exact: P is a power of two
 
   if (a.r != nullptr && Q.r_off >= 0) {
@@ -906,6 +912,17 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a)
     const float2 w = sbuf[pad_idx(k)];
     return j == 0 ? w.x * invP : -w.y * invP;
   });
+}
+
+// One CTA per query, in a.order (largest FFT first); the hardware hands the
+// next query to whichever SM frees up. (A persistent loop over queries with
+// twiddles reused across them was tried: carrying state across iterations
+// pushes this kernel past its 128 registers and into local memory.)
+template <int NBMAX>
+__global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a) {
+  extern __shared__ __align__(16) float2 sbuf[];
+  int loaded_logP = -1;
+  corr_query<NBMAX>(a, a.order[blockIdx.x], sbuf, loaded_logP);
 }
 
 // ---------------------------------------------------------------- blocked correlation
@@ -1055,7 +1072,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
     __syncthreads();
     for (int i = tid; i < kBlk && b * kBlk + i < K; i += kCorrThreads) sbuf[pad_idx(i)].x = t[b * kBlk + i];
     __syncthreads();
-    fft(sbuf, kBlkLog, tw, stw);
+    fft<2>(sbuf, kBlkLog, tw, stw);
     for (int k = tid; k < PB; k += kCorrThreads) {
       const float2 T = sbuf[pad_idx(k)];
       spec[int64_t(b) * PB + k] = T;
@@ -1069,7 +1086,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
       sbuf[pad_idx(i)] = make_float2(yval(0, k), yval(1, k));
     }
     __syncthreads();
-    fft(sbuf, kBlkLog, tw, stw);
+    fft<2>(sbuf, kBlkLog, tw, stw);
     for (int k = tid; k < PB; k += kCorrThreads) {
       const float2 Z = sbuf[pad_idx(k)];
       spec[int64_t(Bt + s) * PB + k] = Z;
@@ -1092,7 +1109,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
       sbuf[pad_idx(k)] = acc;
     }
     __syncthreads();
-    fft(sbuf, kBlkLog, tw, stw);
+    fft<2>(sbuf, kBlkLog, tw, stw);
     for (int i = tid; i < kBlk; i += kCorrThreads) {
       const int jj = ab * kBlk + i;
       const float2 w = sbuf[pad_idx(i)];
@@ -1119,7 +1136,10 @@ int corr_smem_bytes(int P) {
 }  // namespace
 
 cudaError_t corr_configure() {
-  cudaError_t e = cudaFuncSetAttribute(corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, corr_smem_bytes(kPMax));
+  cudaError_t e = cudaFuncSetAttribute(corr_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       corr_smem_bytes(kPMax / 2));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(corr_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, corr_smem_bytes(kPMax));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(corr_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               corr_blocked_smem_bytes());
@@ -1128,7 +1148,9 @@ cudaError_t corr_configure() {
 cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s) {
   CorrArgs b = a;
   b.smem_bytes = corr_smem_bytes(maxP);
-  corr_kernel<<<a.nq, kCorrThreads, b.smem_bytes, s>>>(b);
+  // one butterfly of radix 16 per thread and pass up to P = 8192, two above
+  if (maxP <= kPMax / 2) corr_kernel<1><<<a.nq, kCorrThreads, b.smem_bytes, s>>>(b);
+  else corr_kernel<2><<<a.nq, kCorrThreads, b.smem_bytes, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -90,6 +90,9 @@ struct tm_batch_s {
   size_t stage_bytes = 0;
   cudaEvent_t ev_stage = nullptr;
   int64_t ws_bytes = 0;
+  // tm_batch_graph_capture: the captured run and the stream it was captured on
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
 };
 
 

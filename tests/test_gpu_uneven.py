@@ -1,0 +1,104 @@
+"""The uneven batch (4096 queries, N log-uniform, K log-uniform, half +-1
+int8 and half N(0,1) fp32 signals with noisy templates, automatic moduli)
+run as one CUDA graph.
+
+- the graph replays give results identical to a plain tm_batch_run
+  (every query, every field), replay after replay;
+- a seeded sample of queries equals the oracle: bit-exact folds, maxima
+  and shifts for +-1 signals, the fp32 tolerance rules for real ones;
+- the same queries sharing the batch with 4095 others give the same result
+  as alone.
+
+Signal lengths here span [2^14, 2^18] so the host generates the batch in
+seconds; the length distribution's upper end is exercised by the other
+GPU tests (N = 2^24).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle.ftm as O
+import workloads as W
+from test_gpu_dtypes import check_int, check_real
+
+pytestmark = pytest.mark.gpu
+
+NQ = 4096
+
+
+@pytest.fixture(scope="module")
+def tm():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1509_04863_gb300 import _build
+    _build.build()
+    import paper_1509_04863_gb300 as tm
+    return tm
+
+
+@pytest.fixture(scope="module")
+def uneven(tm):
+    qs = W.uneven(seed=5000, n=NQ, logN=(14.0, 18.0))
+    specs = [dict(x=torch.from_numpy(q.x).cuda(), t=torch.from_numpy(q.t).cuda(), N=q.N, K=q.K,
+                  xdtype=q.xdtype, mode=q.mode) for q in qs]
+    b = tm.Batch(specs, keep_corr=True)
+    return qs, specs, b
+
+
+def test_graph_replays_equal_plain_run(tm, uneven):
+    qs, _, b = uneven
+    plain = tm.result_buffer(NQ)
+    b.run(plain)
+    torch.cuda.synchronize()
+    want = tm.decode_results(plain)
+    assert b.device_error() == 0
+    out = tm.result_buffer(NQ)
+    b.capture_graph(out)
+    for _ in range(3):
+        out.zero_()
+        b.launch_graph()
+        torch.cuda.synchronize()
+        assert tm.decode_results(out) == want
+    assert b.device_error() == 0
+    assert sum(q.xdtype == "i8" for q in qs) > NQ // 3 and sum(q.xdtype == "f32" for q in qs) > NQ // 3
+
+
+def test_graph_sample_vs_oracle(tm, uneven):
+    qs, _, b = uneven
+    out = tm.result_buffer(NQ)
+    b.capture_graph(out)
+    b.launch_graph()
+    torch.cuda.synchronize()
+    res = tm.decode_results(out)
+    rng = np.random.default_rng(17)
+    sample = rng.choice(NQ, 160, replace=False)
+    exact_real = n_real = 0
+    for i in sample:
+        q = qs[int(i)]
+        ref = O.match_query(q)
+        if q.xdtype == "i8":
+            check_int(b, int(i), q, res[int(i)], ref)
+        else:
+            n_real += 1
+            exact_real += check_real(b, int(i), q, res[int(i)], ref)
+    assert exact_real >= n_real - 2   # near-ties are rare
+
+
+def test_alone_equals_in_batch(tm, uneven):
+    qs, specs, b = uneven
+    out = tm.result_buffer(NQ)
+    b.run(out)
+    torch.cuda.synchronize()
+    res = tm.decode_results(out)
+    for i in (0, 1, 2, 1000, NQ - 1):
+        one = tm.Batch([specs[i]])
+        o1 = tm.result_buffer(1)
+        one.run(o1)
+        torch.cuda.synchronize()
+        r1 = tm.decode_results(o1)[0]
+        if qs[i].xdtype == "i8":
+            assert r1 == res[i], (i, r1, res[i])
+        else:
+            # the fold shares fall differently alone and in the batch: fp32
+            # sums may round differently; the picks agree or are near-ties
+            assert (r1["m1"], r1["m2"]) == (res[i]["m1"], res[i]["m2"]) or \
+                abs(r1["r1"] - res[i]["r1"]) <= 1e-4 * max(1.0, abs(res[i]["r1"]))
