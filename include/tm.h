@@ -199,6 +199,14 @@ TM_API tm_status tm_batch_stats(tm_batch_t b, int32_t* launches_per_run, int32_t
 TM_API tm_status tm_batch_device_error(tm_batch_t b, tm_stream_t stream, int32_t* err);
 TM_API tm_status tm_batch_destroy(tm_batch_t b);
 
+/* Self-test of the library's bounded device-side waits: one CTA waits on
+ * an mbarrier that nothing arrives at, with the limit limit_ns (clamped to
+ * [1 us, 100 ms]); *gave_up = 1 when the wait ended at its limit (the
+ * expected outcome), 0 if it completed. The kernels' own waits use the same
+ * code with a 2 s limit and then set their device error word. Synchronises
+ * the current device. */
+TM_API tm_status tm_selftest_wait_timeout(int64_t limit_ns, int32_t* gave_up);
+
 /* One-shot batch: create, run, destroy (synchronises the stream). */
 TM_API tm_status tm_match_batch(const tm_query* q, int32_t n, tm_result* out_dev, tm_stream_t stream);
 

@@ -83,7 +83,16 @@ _SIGS = {
     "tm_crt_candidates": (C.c_int32, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                       C.POINTER(C.c_int64), C.c_int32]),
     "tm_match_noalloc": (C.c_int, [C.POINTER(tm_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tm_selftest_wait_timeout": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
 }
+
+
+def selftest_wait_timeout(limit_ns: int = 1_000_000) -> bool:
+    """True when a device-side bounded wait on a barrier nothing arrives at
+    gave up at its limit (tm_selftest_wait_timeout)."""
+    g = C.c_int32(-1)
+    _check(lib().tm_selftest_wait_timeout(int(limit_ns), C.byref(g)), "tm_selftest_wait_timeout")
+    return g.value == 1
 
 TM_NOALLOC_SCRATCH_BYTES = 4 << 20
 

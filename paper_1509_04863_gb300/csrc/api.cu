@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "crt.h"
+#include "device_util.cuh"
 #include "runtime.h"
 
 namespace ftm {
@@ -401,6 +402,23 @@ tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s) {
   return TM_OK;
 }
 
+namespace {
+
+// One CTA waits on an mbarrier that nothing arrives at: the bounded wait
+// must give up after limit_ns and report it.
+__global__ void wait_timeout_probe(uint64_t limit_ns, int32_t* gave_up) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_for(&bar, 0, limit_ns);
+  if (threadIdx.x == 0) *gave_up = ok ? 0 : 1;
+}
+
+}  // namespace
+
 }  // namespace ftm
 
 using namespace ftm;
@@ -491,6 +509,22 @@ tm_status tm_batch_run(tm_batch_t b, tm_result* out, tm_stream_t stream) {
   tm_status st = tm_batch_fold(b, stream);
   if (st != TM_OK) return st;
   return tm_batch_correlate(b, out, stream);
+}
+
+tm_status tm_selftest_wait_timeout(int64_t limit_ns, int32_t* gave_up) {
+  if (!gave_up) return fail(TM_EINVAL, "tm_selftest_wait_timeout: null argument");
+  const int64_t lim = limit_ns < 1000 ? 1000 : limit_ns > 100000000 ? 100000000 : limit_ns;
+  int32_t* d = nullptr;
+  TM_CUDA(cudaMalloc(&d, sizeof(int32_t)));
+  cudaError_t e = cudaMemset(d, 0xff, sizeof(int32_t));
+  if (e == cudaSuccess) {
+    wait_timeout_probe<<<1, 32>>>(uint64_t(lim), d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(gave_up, d, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "tm_selftest_wait_timeout");
+  return TM_OK;
 }
 
 tm_status tm_batch_graph_capture(tm_batch_t b, tm_result* out) {
