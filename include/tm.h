@@ -73,6 +73,9 @@ typedef enum { TM_MODE_AUTO = 0, TM_MODE_PAPER = 1, TM_MODE_EXPLICIT = 2 } tm_mo
 #define TM_RESOLVED 2   /* |S1 ∩ S2| > 1; best exact (Tx)_m, ties -> smallest m */
 #define TM_RF_FULL_RESCORE 0x100  /* too many near-maximal r_j: all j rescored */
 #define TM_RF_DEVICE_ERROR 0x200  /* a device-side bounded wait ran out */
+#define TM_RF_SCORE_PENDING 0x400 /* tm_correlate_folds: no signal, so the member(s)
+                                     of S1 ∩ S2 are unscored; shift = the first
+                                     member, to be resolved by the caller */
 
 typedef struct {
   int64_t N;       /* signal length, 1 <= N */
@@ -140,6 +143,37 @@ TM_API tm_status tm_plan_destroy(tm_plan_t plan);
  * on the current device); calls on one plan must not overlap on the GPU. */
 TM_API tm_status tm_match(tm_plan_t plan, const void* x_dev, const float* t_dev,
                    tm_result* out_dev, tm_stream_t stream);
+
+/* ------------------------------------------------- slices of one signal
+ * A signal too large for one GPU is cut into contiguous slices [n0, n0+len),
+ * one per GPU. Eq. (2) is a sum over the entries of x, so the slices'
+ * extended folds add up to the signal's (exactly for +-1 signals); one sum
+ * reduction brings them to one GPU, which runs steps 4-8 on the sum; the
+ * exact scores of step 9 are again sums over slices. Plans of P <= 16384. */
+
+/* Folds of the slice: y[0..P) for M1 and y[P..2P) for M2 (int32 for +-1
+ * signals, float32 for real ones; entries k >= M_j+K-1 set to 0), where
+ * y_j[k] = sum_{l<L_j} x_{(k + l M_j) mod N} keeps only the terms whose index
+ * lies in [n0, n0+len). x: the slice's storage (entry n0 first), 16-byte
+ * aligned; n0 must fall on a 16-byte boundary of the signal (n0 * bits per
+ * entry a multiple of 128). Writes all 2P entries of y (caller-owned device
+ * memory). Calls on one plan must not overlap on the GPU. */
+TM_API tm_status tm_fold_slice(tm_plan_t plan, const void* x_dev, int64_t n0, int64_t len, void* y_dev,
+                               tm_stream_t stream);
+/* Steps 4-8 from complete folds y (layout of tm_fold_slice, e.g. the sum of
+ * all slices' folds): one tm_result with m1, m2, r1, r2, n_cand. With one
+ * member of S1 ∩ S2 it is the shift; its score, and the choice among several
+ * members (step 9), need the signal: the result carries TM_RF_SCORE_PENDING,
+ * shift = the first member, score = 0 (tm_crt_candidates lists the members;
+ * tm_score_slice scores them). */
+TM_API tm_status tm_correlate_folds(tm_plan_t plan, const void* y_dev, const float* t_dev,
+                                    tm_result* out_dev, tm_stream_t stream);
+/* Partial exact scores over a slice: out[c] = sum_{i<K} t_i x_{(m[c]+i) mod N}
+ * over the terms whose index lies in [n0, n0+len) (fp64; exact for integer
+ * data). m_dev, out_dev: nm entries of device memory. */
+TM_API tm_status tm_score_slice(tm_plan_t plan, const void* x_dev, int64_t n0, int64_t len,
+                                const float* t_dev, const int64_t* m_dev, int32_t nm, double* out_dev,
+                                tm_stream_t stream);
 
 /* ----------------------------------------------------------------- batch */
 

@@ -121,6 +121,21 @@ def fold(x: np.ndarray, M: int, K: int) -> np.ndarray:
     return y
 
 
+def fold_slice(xs: np.ndarray, n0: int, N: int, M: int, K: int) -> np.ndarray:
+    """Eq. (2) keeping only the terms whose index lies in the slice
+    [n0, n0 + len(xs)) of a length-N signal (xs = x_{n0} .. x_{n0+len-1}):
+    (y_M)_k = sum_{i<L} x_{(k+iM) mod N} [n0 <= (k+iM) mod N < n0+len]."""
+    n1 = n0 + xs.shape[0]
+    L = ceil_div(N, M)
+    k = np.arange(M + K - 1, dtype=np.int64)
+    y = np.zeros(M + K - 1, dtype=xs.dtype)
+    for i in range(L):
+        idx = (k + i * M) % N
+        inside = (idx >= n0) & (idx < n1)
+        y[inside] += xs[idx[inside] - n0]
+    return y
+
+
 # ---------------------------------------------------------------------------
 # Steps 4-6: fast correlation in the low-dimensional space. Its result is
 # r_j = sum_{i<K} t_i y_{j+i} for j < M (Thm. 1 with D_{M+K}); the paper
@@ -179,6 +194,17 @@ def tx_at(x: np.ndarray, t: np.ndarray, m: int):
     if x.dtype.kind == "i" and t.dtype.kind == "i":
         return int(np.dot(t, x[idx]))
     return float(np.dot(t.astype(np.float64), x[idx].astype(np.float64)))
+
+
+def tx_slice(xs: np.ndarray, n0: int, N: int, t: np.ndarray, m: int):
+    """(Tx)_m keeping only the terms whose index lies in the slice
+    [n0, n0 + len(xs)) of a length-N signal."""
+    K = t.shape[0]
+    idx = (np.arange(K, dtype=np.int64) + m) % N
+    inside = (idx >= n0) & (idx < n0 + xs.shape[0])
+    if xs.dtype.kind == "i" and t.dtype.kind == "i":
+        return int(np.dot(t[inside], xs[idx[inside] - n0]))
+    return float(np.dot(t[inside].astype(np.float64), xs[idx[inside] - n0].astype(np.float64)))
 
 
 def ftm(x: np.ndarray, t: np.ndarray, M1: int, M2: int, corr: str = "direct") -> Dict:

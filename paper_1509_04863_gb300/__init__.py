@@ -25,6 +25,7 @@ TM_ALLOW_AMBIG = 0x1
 TM_FOUND, TM_EMPTY, TM_RESOLVED = 0, 1, 2
 TM_RF_FULL_RESCORE = 0x100
 TM_RF_DEVICE_ERROR = 0x200
+TM_RF_SCORE_PENDING = 0x400
 TM_BATCH_KEEP_CORR = 0x1
 TM_BATCH_HOST_INPUTS = 0x2
 
@@ -84,6 +85,10 @@ _SIGS = {
                                       C.POINTER(C.c_int64), C.c_int32]),
     "tm_match_noalloc": (C.c_int, [C.POINTER(tm_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tm_selftest_wait_timeout": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
+    "tm_fold_slice": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),
+    "tm_correlate_folds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tm_score_slice": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
+                                 C.c_void_p, C.c_void_p]),
 }
 
 
@@ -174,6 +179,25 @@ class Plan:
     def match(self, x, t, out, stream=None):
         """x, t, out: CUDA tensors (out: >= 48 bytes, e.g. torch.empty(6, dtype=torch.int64))."""
         _check(lib().tm_match(self._h, x.data_ptr(), t.data_ptr(), out.data_ptr(), _stream_ptr(stream)), "tm_match")
+
+    # ---- slices of one signal (tm_fold_slice / tm_correlate_folds / tm_score_slice)
+    def fold_slice(self, x_slice, n0: int, length: int, y, stream=None):
+        """Folds of entries [n0, n0+length) into y (CUDA tensor of 2P int32 or float32)."""
+        xp = x_slice.data_ptr() if length > 0 else None
+        _check(lib().tm_fold_slice(self._h, xp, int(n0), int(length), y.data_ptr(), _stream_ptr(stream)),
+               "tm_fold_slice")
+
+    def correlate_folds(self, y, t, out, stream=None):
+        """Steps 4-8 from complete folds y; out: 48-byte result buffer (CUDA)."""
+        _check(lib().tm_correlate_folds(self._h, y.data_ptr(), t.data_ptr(), out.data_ptr(), _stream_ptr(stream)),
+               "tm_correlate_folds")
+
+    def score_slice(self, x_slice, n0: int, length: int, t, m, out, stream=None):
+        """Partial exact scores over the slice for the int64 CUDA tensor of
+        positions m into the float64 CUDA tensor out."""
+        xp = x_slice.data_ptr() if length > 0 else None
+        _check(lib().tm_score_slice(self._h, xp, int(n0), int(length), t.data_ptr(), m.data_ptr(), int(m.numel()),
+                                    out.data_ptr(), _stream_ptr(stream)), "tm_score_slice")
 
     def close(self):
         if self._h:

@@ -146,10 +146,27 @@ tm_status device_setup(int dev, float2** tw) {
 }  // namespace ftm
 
 // ---------------------------------------------------------------- objects
+// Device scratch of the slice entry points (tm_fold_slice and friends),
+// allocated on first use and grown when a larger slice arrives.
+struct SliceWs {
+  int device = -1;
+  int64_t part_cap = 0;            // int32 entries of `partial`
+  ftm::FoldQ* d_fq = nullptr;
+  ftm::CorrQ* d_cq = nullptr;
+  int32_t* d_order = nullptr;
+  int32_t* d_partial = nullptr;
+  int32_t* d_err = nullptr;
+  float2* d_spec = nullptr;
+  ~SliceWs() {
+    cudaFree(d_fq); cudaFree(d_cq); cudaFree(d_order); cudaFree(d_partial); cudaFree(d_err); cudaFree(d_spec);
+  }
+};
+
 struct tm_plan_s {
   tm_plan_desc d;
   ftm::PlanCore pc;
   tm_batch_t b = nullptr;
+  SliceWs* sw = nullptr;
 };
 
 namespace ftm {
@@ -454,7 +471,151 @@ tm_status tm_plan_get_info(tm_plan_t p, tm_plan_info* info) {
 tm_status tm_plan_destroy(tm_plan_t p) {
   if (!p) return TM_OK;
   batch_free(p->b);
+  if (p->sw) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->sw->device);
+    delete p->sw;
+    cudaSetDevice(cur);
+  }
   delete p;
+  return TM_OK;
+}
+
+namespace {
+
+// The slice scratch of plan p on the current device, with room for `slots`
+// partial slots.
+tm_status slice_ws(tm_plan_t p, int64_t slots, SliceWs** out) {
+  int dev = 0;
+  TM_CUDA(cudaGetDevice(&dev));
+  if (p->sw && p->sw->device != dev) return fail(TM_EINVAL, "plan's slice scratch lives on another device");
+  if (!p->sw) {
+    SliceWs* w = new (std::nothrow) SliceWs();
+    if (!w) return fail(TM_ENOMEM, "host allocation");
+    w->device = dev;
+    const bool ok = cudaMalloc((void**)&w->d_fq, sizeof(FoldQ)) == cudaSuccess &&
+                    cudaMalloc((void**)&w->d_cq, sizeof(CorrQ)) == cudaSuccess &&
+                    cudaMalloc((void**)&w->d_order, 16) == cudaSuccess &&
+                    cudaMalloc((void**)&w->d_err, 16) == cudaSuccess &&
+                    cudaMalloc((void**)&w->d_spec, size_t(p->pc.P) * sizeof(float2)) == cudaSuccess;
+    if (!ok) {
+      delete w;
+      cudaGetLastError();
+      return fail(TM_ENOMEM, "slice scratch");
+    }
+    TM_CUDA(cudaMemset(w->d_order, 0, 16));
+    TM_CUDA(cudaMemset(w->d_err, 0, 16));
+    p->sw = w;
+  }
+  const int64_t stride = pad16(p->pc.Mp[0]) + pad16(p->pc.Mp[1]);
+  if (slots * stride > p->sw->part_cap) {
+    cudaFree(p->sw->d_partial);
+    p->sw->d_partial = nullptr;
+    p->sw->part_cap = 0;
+    if (cudaMalloc((void**)&p->sw->d_partial, size_t(slots * stride) * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TM_ENOMEM, "slice partial folds");
+    }
+    p->sw->part_cap = slots * stride;
+  }
+  *out = p->sw;
+  return TM_OK;
+}
+
+}  // namespace
+
+tm_status tm_fold_slice(tm_plan_t p, const void* x, int64_t n0, int64_t len, void* y, tm_stream_t stream) {
+  if (!p || !y || (len > 0 && !x)) return fail(TM_EINVAL, "null argument");
+  const PlanCore& pc = p->pc;
+  if (n0 < 0 || len < 0 || n0 + len > pc.N) return fail(TM_EINVAL, "slice outside [0, N)");
+  const FoldGeom geo = fold_geom(pc.xdtype);
+  if ((n0 * geo.bits) % 128 != 0) return fail(TM_EINVAL, "slice start must fall on a 16-byte boundary of the signal");
+  if (reinterpret_cast<uintptr_t>(x) & 15) return fail(TM_EINVAL, "x must be 16-byte aligned");
+  if (pc.P > kPMax) return fail(TM_EUNSUPPORTED, "slices need P <= 16384");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  TM_CUDA(cudaGetDevice(&dev));
+  TM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  float2* tw = nullptr;
+  tm_status st = device_setup(dev, &tw);
+  if (st != TM_OK) return st;
+  const int64_t W = fold_bytes(pc.xdtype, len);
+  const int64_t max_share = int64_t(kFoldMaxRowsPerSlot - 2) * std::min(pc.Mp[0], pc.Mp[1]) * geo.bits / 8;
+  int64_t nctas = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(W, 65536)));
+  if (W > 0) nctas = std::max<int64_t>(nctas, ceil_div(W, max_share));
+  SliceWs* w = nullptr;
+  if ((st = slice_ws(p, nctas, &w)) != TM_OK) return st;
+  FoldQ f{};
+  f.x = static_cast<const uint8_t*>(x);
+  f.goff = 0;
+  f.nbytes = int32_t(W);
+  f.Mp[0] = pc.Mp[0]; f.Mp[1] = pc.Mp[1];
+  f.moff[0] = 0; f.moff[1] = int32_t(pad16(pc.Mp[0]));
+  f.stride = int32_t(pad16(pc.Mp[0]) + pad16(pc.Mp[1]));
+  f.first_cta = 0;
+  f.nslots = W > 0 ? int32_t(nctas) : 0;
+  f.part = 0;
+  f.e0 = n0;
+  TM_CUDA(cudaMemcpyAsync(w->d_fq, &f, sizeof(f), cudaMemcpyHostToDevice, s));
+  if (W > 0) {
+    FoldArgs a;
+    a.q = w->d_fq; a.nq = 1; a.dtype = pc.xdtype; a.nctas = int32_t(nctas); a.W = W;
+    a.partial = w->d_partial; a.err = w->d_err;
+    const int jmax = std::max(fold_units_per_lane(pc.Mp[0], kFoldWarps0, geo.E),
+                              fold_units_per_lane(pc.Mp[1], kFoldWarps1, geo.E));
+    TM_CUDA(launch_fold(a, jmax, s));
+  }
+  SliceFoldArgs c{};
+  c.partial = w->d_partial;
+  c.nslots = f.nslots;
+  c.stride = f.stride;
+  for (int j = 0; j < 2; ++j) { c.moff[j] = f.moff[j]; c.M[j] = pc.M[j]; c.R[j] = pc.R[j]; c.L[j] = pc.L[j]; }
+  c.N = pc.N; c.K = pc.K; c.P = pc.P; c.xdtype = pc.xdtype;
+  c.x = x; c.n0 = n0; c.len = len; c.nfold = fold_elems(pc.xdtype, len);
+  c.y = y;
+  TM_CUDA(launch_fold_slice_complete(c, s));
+  return TM_OK;
+}
+
+tm_status tm_correlate_folds(tm_plan_t p, const void* y, const float* t, tm_result* out, tm_stream_t stream) {
+  if (!p || !y || !t || !out) return fail(TM_EINVAL, "null argument");
+  const PlanCore& pc = p->pc;
+  if (pc.P > kPMax) return fail(TM_EUNSUPPORTED, "folds given: P <= 16384 only");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  TM_CUDA(cudaGetDevice(&dev));
+  float2* tw = nullptr;
+  tm_status st = device_setup(dev, &tw);
+  if (st != TM_OK) return st;
+  SliceWs* w = nullptr;
+  if ((st = slice_ws(p, 0, &w)) != TM_OK) return st;
+  CorrQ c{};
+  c.x = nullptr; c.t = t; c.N = pc.N; c.K = pc.K; c.xdtype = pc.xdtype;
+  for (int j = 0; j < 2; ++j) { c.M[j] = pc.M[j]; c.R[j] = pc.R[j]; c.L[j] = pc.L[j]; }
+  c.P = pc.P; c.logP = pc.logP; c.inv = pc.inv;
+  c.nelem16 = int32_t(fold_elems(pc.xdtype, pc.N));
+  c.nslots = 0; c.stride = 0; c.part = 0; c.y_off = 0; c.spec_off = 0; c.r_off = -1;
+  c.y_in = y;
+  TM_CUDA(cudaMemcpyAsync(w->d_cq, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+  TM_CUDA(cudaMemsetAsync(w->d_err, 0, sizeof(int32_t), s));
+  CorrArgs a;
+  a.q = w->d_cq; a.order = w->d_order; a.nq = 1; a.partial = nullptr;
+  a.y = const_cast<void*>(y); a.spec = w->d_spec; a.r = nullptr; a.tw = tw; a.out = out; a.err = w->d_err;
+  TM_CUDA(launch_correlate(a, pc.P, s));
+  return TM_OK;
+}
+
+tm_status tm_score_slice(tm_plan_t p, const void* x, int64_t n0, int64_t len, const float* t, const int64_t* m,
+                         int32_t nm, double* out, tm_stream_t stream) {
+  if (!p || !t || (nm > 0 && (!m || !out)) || (len > 0 && !x)) return fail(TM_EINVAL, "null argument");
+  const PlanCore& pc = p->pc;
+  if (n0 < 0 || len < 0 || n0 + len > pc.N || nm < 0) return fail(TM_EINVAL, "slice outside [0, N)");
+  if (pc.xdtype == TM_BITS_PM1 && n0 % 8 != 0) return fail(TM_EINVAL, "bit-packed slices start on a byte");
+  SliceScoreArgs a;
+  a.x = x; a.xdtype = pc.xdtype; a.N = pc.N; a.n0 = n0; a.len = len; a.t = t; a.K = pc.K; a.m = m; a.nm = nm;
+  a.out = out;
+  TM_CUDA(launch_score_slice(a, reinterpret_cast<cudaStream_t>(stream)));
   return TM_OK;
 }
 
@@ -731,7 +892,7 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   st = noalloc_setup(dev, &base);
   if (st != TM_OK) return st;
 
-  FoldQ f;
+  FoldQ f{};
   f.x = static_cast<const uint8_t*>(x);
   f.goff = 0;
   f.nbytes = int32_t(W);
@@ -749,7 +910,7 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
     }
     f.nslots = lo + 1;
   }
-  CorrQ c;
+  CorrQ c{};
   c.x = x; c.t = t; c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
   for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
   c.P = p.P; c.logP = p.logP; c.inv = p.inv;

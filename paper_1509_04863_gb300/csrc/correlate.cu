@@ -443,7 +443,7 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
   // int32 rescoring is exact when every partial sum stays below 2^31:
   // |sum| <= ||t||_1 max|y|
   const bool small = exact_int && double(t1) * double(maxy) < 2.0e9;
-  const void* yv = static_cast<const char*>(a.y) + Q.y_off * 4;
+  const void* yv = Q.y_in != nullptr ? Q.y_in : static_cast<const void*>(static_cast<const char*>(a.y) + Q.y_off * 4);
 
   // step 7 for both moduli: the argmax of the FFT values and every index
   // within 2 delta of it
@@ -565,7 +565,11 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
   auto member = [&](int64_t c) -> int64_t { return c < cs.nnat ? cs.m0 + c * cs.step : cs.w[c - cs.nnat]; };
   double best_v = 0.0;
   int64_t best_m = -1;
-  if (ncs == 1) {
+  const bool have_x = Q.x != nullptr;
+  if (!have_x) {
+    // folds without the signal: the member(s) are reported unscored
+    best_m = ncs > 0 ? member(0) : -1;
+  } else if (ncs == 1) {
     // a single member: its exact (Tx)_m, spread over the whole block
     const int64_t mm = member(0);
     if (exact_int) {
@@ -610,6 +614,7 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
     if (ncs == 0) { res.shift = -1; res.status = TM_EMPTY; res.score = 0.0; }
     else { res.shift = best_m; res.status = ncs == 1 ? TM_FOUND : TM_RESOLVED; res.score = best_v; }
     res.status |= s_flags;
+    if (!have_x && ncs > 0) res.status |= TM_RF_SCORE_PENDING;
     if (*a.err) res.status |= TM_RF_DEVICE_ERROR;
     res.m1 = s_m[0];
     res.m2 = s_m[1];
@@ -701,157 +706,166 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   constexpr int kB = 8;
   int* ib = reinterpret_cast<int*>(sbuf);     // int view: entry e -> ib[2e] (M1), ib[2e+1] (M2)
   float* fb = reinterpret_cast<float*>(sbuf);
-  for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
-  __syncthreads();
-  if (ints) {
-    // Partial slots hold counts of -1 (int8) or +1 (bits) entries per column
-    // kp < Mp of the Mp-fold; column k of the M-fold gathers kp = k + r M,
-    // r < R. Slot rows are padded to 16 columns, so a quad read at kp < Mp
-    // stays inside the row; columns past Mp are dropped.
-    for (int j = 0; j < 2; ++j) {
-      const int M = Q.M[j], Rr = Q.R[j], Mp = Rr * M;
-      const int32_t* part = a.partial + Q.part + Q.moff[j];
-      const int nq4 = (Mp + 3) >> 2;
-      for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
-        int4 c[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) c[b] = make_int4(0, 0, 0, 0);
-#pragma unroll 2
-        for (int sl = 0; sl < Q.nslots; ++sl) {
-          const int32_t* ps = part + int64_t(sl) * Q.stride;
-          int4 v[4];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int q = q0 + b * kCorrThreads;
-            v[b] = q < nq4 ? __ldg(reinterpret_cast<const int4*>(ps) + q) : make_int4(0, 0, 0, 0);
+  if (Q.y_in != nullptr) {
+    // complete folds supplied by the caller (e.g. summed slice folds)
+    const int32_t* yin = static_cast<const int32_t*>(Q.y_in);
+    for (int k = tid; k < P; k += kCorrThreads) {
+      ib[2 * pad_idx(k)] = yin[k];           // int32 or float bits alike
+      ib[2 * pad_idx(k) + 1] = yin[P + k];
+    }
+  } else {
+    for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (ints) {
+      // Partial slots hold counts of -1 (int8) or +1 (bits) entries per column
+      // kp < Mp of the Mp-fold; column k of the M-fold gathers kp = k + r M,
+      // r < R. Slot rows are padded to 16 columns, so a quad read at kp < Mp
+      // stays inside the row; columns past Mp are dropped.
+      for (int j = 0; j < 2; ++j) {
+        const int M = Q.M[j], Rr = Q.R[j], Mp = Rr * M;
+        const int32_t* part = a.partial + Q.part + Q.moff[j];
+        const int nq4 = (Mp + 3) >> 2;
+        for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
+          int4 c[4];
+  #pragma unroll
+          for (int b = 0; b < 4; ++b) c[b] = make_int4(0, 0, 0, 0);
+  #pragma unroll 2
+          for (int sl = 0; sl < Q.nslots; ++sl) {
+            const int32_t* ps = part + int64_t(sl) * Q.stride;
+            int4 v[4];
+  #pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const int q = q0 + b * kCorrThreads;
+              v[b] = q < nq4 ? __ldg(reinterpret_cast<const int4*>(ps) + q) : make_int4(0, 0, 0, 0);
+            }
+  #pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              c[b].x += v[b].x; c[b].y += v[b].y; c[b].z += v[b].z; c[b].w += v[b].w;
+            }
           }
-#pragma unroll
+  #pragma unroll
           for (int b = 0; b < 4; ++b) {
-            c[b].x += v[b].x; c[b].y += v[b].y; c[b].z += v[b].z; c[b].w += v[b].w;
+            const int k0 = 4 * (q0 + b * kCorrThreads);
+            const int cc[4] = {c[b].x, c[b].y, c[b].z, c[b].w};
+  #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int kp = k0 + i;
+              if (kp < Mp && cc[i] != 0) {
+                const int e = 2 * pad_idx(Rr == 1 ? kp : kp % M) + j;
+                if (Rr == 1) ib[e] = cc[i];
+                else atomicAdd(&ib[e], cc[i]);
+              }
+            }
           }
         }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int k0 = 4 * (q0 + b * kCorrThreads);
-          const int cc[4] = {c[b].x, c[b].y, c[b].z, c[b].w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int kp = k0 + i;
-            if (kp < Mp && cc[i] != 0) {
-              const int e = 2 * pad_idx(Rr == 1 ? kp : kp % M) + j;
-              if (Rr == 1) ib[e] = cc[i];
-              else atomicAdd(&ib[e], cc[i]);
+      }
+      __syncthreads();
+      // counts -> fold values; column k >= Rw (the last row is short) also
+      // takes the wrap-around entry x_{k-Rw}
+      const bool ones = Q.xdtype == TM_BITS_PM1;   // bit-packed slots count +1 entries, int8 slots -1 entries
+      for (int j = 0; j < 2; ++j) {
+        const int M = Q.M[j];
+        const int L = int(Q.L[j]);
+        const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
+        with_sig(Q.xdtype, Q.x, [&](auto sx) {
+          for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
+            float xv[kB];
+  #pragma unroll
+            for (int b = 0; b < kB; ++b) {
+              const int k = k0 + b * kCorrThreads;
+              xv[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
             }
+  #pragma unroll
+            for (int b = 0; b < kB; ++b) {
+              const int k = k0 + b * kCorrThreads;
+              if (k < M) {
+                // entries n < N with n = k (mod M): L of them for k < Rw, else L-1
+                const int e = 2 * pad_idx(k) + j;
+                const int nk = L - 1 + (k < Rw ? 1 : 0);
+                ib[e] = (ones ? 2 * ib[e] - nk : nk - 2 * ib[e]) + int(xv[b]);
+              }
+            }
+          }
+        });
+      }
+    } else {
+      // partial slots hold fp32 column sums, added in a fixed order
+      for (int j = 0; j < 2; ++j) {
+        const int M = Q.M[j], Rr = Q.R[j];
+        const int L = int(Q.L[j]);
+        const int Rw = int(N - int64_t(L - 1) * M);
+        const float* pf = reinterpret_cast<const float*>(a.partial + Q.part + Q.moff[j]);
+        for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
+          float acc[kB];
+          with_sig(Q.xdtype, Q.x, [&](auto sx) {
+  #pragma unroll
+            for (int b = 0; b < kB; ++b) {
+              const int k = k0 + b * kCorrThreads;
+              acc[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
+            }
+          });
+          float yk[kB];
+  #pragma unroll
+          for (int b = 0; b < kB; ++b) yk[b] = 0.f;
+          for (int sl = 0; sl < Q.nslots; ++sl) {
+            const float* ps = pf + int64_t(sl) * Q.stride;
+            for (int r = 0; r < Rr; ++r) {
+  #pragma unroll
+              for (int b = 0; b < kB; ++b) {
+                const int k = k0 + b * kCorrThreads;
+                if (k < M) yk[b] += __ldg(&ps[k + r * M]);
+              }
+            }
+          }
+  #pragma unroll
+          for (int b = 0; b < kB; ++b) {
+            const int k = k0 + b * kCorrThreads;
+            if (k < M) fb[2 * pad_idx(k) + j] = yk[b] + acc[b];
           }
         }
       }
     }
     __syncthreads();
-    // counts -> fold values; column k >= Rw (the last row is short) also
-    // takes the wrap-around entry x_{k-Rw}
-    const bool ones = Q.xdtype == TM_BITS_PM1;   // bit-packed slots count +1 entries, int8 slots -1 entries
+    if (tid == 0) {
+      for (int64_t n = Q.nelem16; n < N; ++n) {
+        for (int j = 0; j < 2; ++j) {
+          const int e = 2 * pad_idx(int(n % Q.M[j])) + j;
+          // the count L or L-1 above includes this entry: as +1 for int8
+          // (counted -1 entries), as -1 for bits (counted +1 entries)
+          if (Q.xdtype == TM_I8_PM1) ib[e] -= sig.ival(n) < 0 ? 2 : 0;
+          else if (Q.xdtype == TM_BITS_PM1) ib[e] += sig.ival(n) > 0 ? 2 : 0;
+          else fb[e] += sig.val(n);
+        }
+      }
+    }
+    __syncthreads();
+    // extension y[M+i] = y[i] - x_i + x_{(i+LM) mod N}, i < K-1
     for (int j = 0; j < 2; ++j) {
       const int M = Q.M[j];
-      const int L = int(Q.L[j]);
-      const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
-      with_sig(Q.xdtype, Q.x, [&](auto sx) {
-        for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
-          float xv[kB];
-#pragma unroll
-          for (int b = 0; b < kB; ++b) {
-            const int k = k0 + b * kCorrThreads;
-            xv[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
-          }
-#pragma unroll
-          for (int b = 0; b < kB; ++b) {
-            const int k = k0 + b * kCorrThreads;
-            if (k < M) {
-              // entries n < N with n = k (mod M): L of them for k < Rw, else L-1
-              const int e = 2 * pad_idx(k) + j;
-              const int nk = L - 1 + (k < Rw ? 1 : 0);
-              ib[e] = (ones ? 2 * ib[e] - nk : nk - 2 * ib[e]) + int(xv[b]);
-            }
-          }
-        }
-      });
-    }
-  } else {
-    // partial slots hold fp32 column sums, added in a fixed order
-    for (int j = 0; j < 2; ++j) {
-      const int M = Q.M[j], Rr = Q.R[j];
-      const int L = int(Q.L[j]);
-      const int Rw = int(N - int64_t(L - 1) * M);
-      const float* pf = reinterpret_cast<const float*>(a.partial + Q.part + Q.moff[j]);
-      for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
-        float acc[kB];
+      const int64_t LM = Q.L[j] * M;
+      for (int i0 = tid; i0 < K - 1; i0 += kB * kCorrThreads) {
+        float xi[kB], xw[kB];
         with_sig(Q.xdtype, Q.x, [&](auto sx) {
-#pragma unroll
+  #pragma unroll
           for (int b = 0; b < kB; ++b) {
-            const int k = k0 + b * kCorrThreads;
-            acc[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
+            const int i = i0 + b * kCorrThreads;
+            xi[b] = xw[b] = 0.f;
+            if (i < K - 1) {
+              int64_t w = i + LM - N;   // LM >= N and i + LM - N < 2M, so one reduction is rare
+              if (w >= N) w %= N;
+              xi[b] = sx.val(i);
+              xw[b] = sx.val(w);
+            }
           }
         });
-        float yk[kB];
-#pragma unroll
-        for (int b = 0; b < kB; ++b) yk[b] = 0.f;
-        for (int sl = 0; sl < Q.nslots; ++sl) {
-          const float* ps = pf + int64_t(sl) * Q.stride;
-          for (int r = 0; r < Rr; ++r) {
-#pragma unroll
-            for (int b = 0; b < kB; ++b) {
-              const int k = k0 + b * kCorrThreads;
-              if (k < M) yk[b] += __ldg(&ps[k + r * M]);
-            }
-          }
-        }
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-          const int k = k0 + b * kCorrThreads;
-          if (k < M) fb[2 * pad_idx(k) + j] = yk[b] + acc[b];
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int64_t n = Q.nelem16; n < N; ++n) {
-      for (int j = 0; j < 2; ++j) {
-        const int e = 2 * pad_idx(int(n % Q.M[j])) + j;
-        // the count L or L-1 above includes this entry: as +1 for int8
-        // (counted -1 entries), as -1 for bits (counted +1 entries)
-        if (Q.xdtype == TM_I8_PM1) ib[e] -= sig.ival(n) < 0 ? 2 : 0;
-        else if (Q.xdtype == TM_BITS_PM1) ib[e] += sig.ival(n) > 0 ? 2 : 0;
-        else fb[e] += sig.val(n);
-      }
-    }
-  }
-  __syncthreads();
-  // extension y[M+i] = y[i] - x_i + x_{(i+LM) mod N}, i < K-1
-  for (int j = 0; j < 2; ++j) {
-    const int M = Q.M[j];
-    const int64_t LM = Q.L[j] * M;
-    for (int i0 = tid; i0 < K - 1; i0 += kB * kCorrThreads) {
-      float xi[kB], xw[kB];
-      with_sig(Q.xdtype, Q.x, [&](auto sx) {
-#pragma unroll
+  #pragma unroll
         for (int b = 0; b < kB; ++b) {
           const int i = i0 + b * kCorrThreads;
-          xi[b] = xw[b] = 0.f;
           if (i < K - 1) {
-            int64_t w = i + LM - N;   // LM >= N and i + LM - N < 2M, so one reduction is rare
-            if (w >= N) w %= N;
-            xi[b] = sx.val(i);
-            xw[b] = sx.val(w);
+            const int e = 2 * pad_idx(M + i) + j, e0 = 2 * pad_idx(i) + j;
+            if (ints) ib[e] = ib[e0] - int(xi[b]) + int(xw[b]);
+            else fb[e] = fb[e0] - xi[b] + xw[b];
           }
-        }
-      });
-#pragma unroll
-      for (int b = 0; b < kB; ++b) {
-        const int i = i0 + b * kCorrThreads;
-        if (i < K - 1) {
-          const int e = 2 * pad_idx(M + i) + j, e0 = 2 * pad_idx(i) + j;
-          if (ints) ib[e] = ib[e0] - int(xi[b]) + int(xw[b]);
-          else fb[e] = fb[e0] - xi[b] + xw[b];
         }
       }
     }
@@ -867,8 +881,10 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
     for (int k = tid; k < P; k += kCorrThreads) {
       const int e = 2 * pad_idx(k);
       const int v0 = ib[e], v1 = ib[e + 1];
-      yi[k] = v0;
-      yi[P + k] = v1;
+      if (Q.y_in == nullptr) {
+        yi[k] = v0;
+        yi[P + k] = v1;
+      }
       sbuf[pad_idx(k)] = make_float2(float(v0), float(v1));
       s2 += (long long)v0 * v0 + (long long)v1 * v1;
       maxy = max(maxy, max(abs(v0), abs(v1)));
@@ -880,8 +896,10 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
     float* yf = static_cast<float*>(a.y) + Q.y_off;
     for (int k = tid; k < P; k += kCorrThreads) {
       const float2 v = sbuf[pad_idx(k)];
-      yf[k] = v.x;
-      yf[P + k] = v.y;
+      if (Q.y_in == nullptr) {
+        yf[k] = v.x;
+        yf[P + k] = v.y;
+      }
       z2 = fmaf(v.x, v.x, fmaf(v.y, v.y, z2));
     }
     z2 = sqrtf(block_sum(z2, redf));

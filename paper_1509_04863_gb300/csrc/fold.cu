@@ -424,7 +424,7 @@ __device__ __forceinline__ int first_query(const FoldQ* q, int nq, int64_t pos) 
 // false when a bounded wait ran out.
 template <class U, int J>
 __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* full, uint64_t* empty, int lo, int hi,
-                                              int Mp, int W, int wig, int32_t* dst, uint32_t& it) {
+                                              int Mp, int ph, int W, int wig, int32_t* dst, uint32_t& it) {
   const int lane = threadIdx.x & 31;
   const int F = U::widen_every(Mp);
   // unit j of this lane starts at column col(j); it exists when col(j) < Mp
@@ -442,7 +442,7 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
     const uint8_t* buf = smem + st * kStageBytes + 16;
     const int len = min(kFoldTile, hi - s);
     // the stage in elements: [es, es + el)
-    const int es = int((int64_t(s) * 8) / U::kBits);
+    const int es = int((int64_t(s) * 8) / U::kBits) + ph;   // the stage's first element, row phase included
     const int el = int((int64_t(len) * 8) / U::kBits);
     const int l0 = es / Mp;               // rows meeting the stage
     const int l1 = (es + el - 1) / Mp;
@@ -490,18 +490,19 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
 // is recomputed per stage and no read is masked.
 template <class U, int J>
 __device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t* full, uint64_t* empty, int lo,
-                                                   int hi, int Mp, int W, int wig, int32_t* dst, uint32_t& it) {
+                                                   int hi, int Mp, int ph, int W, int wig, int32_t* dst,
+                                                   uint32_t& it) {
   static_assert(U::kBits == 8, "walkers step in bytes");
   const int lane = threadIdx.x & 31;
   const int F = U::widen_every(Mp);
   auto col = [&](int j) { return U::kE * (lane + 32 * (wig + W * j)); };
   U u[J];
   int o[J];   // next row of unit j, relative to the current stage
-  const int l = lo / Mp;
+  const int l = (lo + ph) / Mp;
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     u[j].clear();
-    o[j] = l * Mp + col(j) - lo;
+    o[j] = l * Mp + col(j) - (lo + ph);
     if (o[j] <= -U::kE) o[j] += Mp;
   }
   const int step = Mp & 15;
@@ -622,19 +623,21 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
     const int lo = int(max(cb, goff) - goff);
     const int hi = int(min(ce, goff + nbytes) - goff);
     const int Mp = a.q[qi].Mp[m];
+    // rows are counted from element e0 of the signal (0 unless x is a slice)
+    const int ph = int(a.q[qi].e0 % Mp);
     int32_t* dst = a.partial + a.q[qi].part + int64_t(blockIdx.x - a.q[qi].first_cta) * a.q[qi].stride +
                    a.q[qi].moff[m];
     const int J = fold_units_per_lane(Mp, W, U::kE);
     if constexpr (U::kWalk) {
-      if (J <= 1) ok = consume_share_walk<U, 1>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-      else if (J == 2 || JMAX == 2) ok = consume_share_walk<U, 2>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-      else if (J <= 3 || JMAX <= 3) ok = consume_share_walk<U, (JMAX < 3 ? JMAX : 3)>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-      else ok = consume_share_walk<U, JMAX>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+      if (J <= 1) ok = consume_share_walk<U, 1>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
+      else if (J == 2 || JMAX == 2) ok = consume_share_walk<U, 2>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
+      else if (J <= 3 || JMAX <= 3) ok = consume_share_walk<U, (JMAX < 3 ? JMAX : 3)>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
+      else ok = consume_share_walk<U, JMAX>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
     } else {
-      if (J <= 1) ok = consume_share<U, 1>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-      else if (J == 2 || JMAX == 2) ok = consume_share<U, 2>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-      else if (J <= 4 || JMAX <= 4) ok = consume_share<U, (JMAX < 4 ? JMAX : 4)>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
-      else ok = consume_share<U, JMAX>(smem, full, empty, lo, hi, Mp, W, wig, dst, it);
+      if (J <= 1) ok = consume_share<U, 1>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
+      else if (J == 2 || JMAX == 2) ok = consume_share<U, 2>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
+      else if (J <= 4 || JMAX <= 4) ok = consume_share<U, (JMAX < 4 ? JMAX : 4)>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
+      else ok = consume_share<U, JMAX>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
     }
   }
   if (!ok) atomicOr(a.err, 1);

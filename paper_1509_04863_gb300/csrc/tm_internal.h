@@ -64,6 +64,8 @@ struct FoldQ {
   int32_t first_cta;  // CTA whose share holds goff
   int32_t nslots;
   int64_t part;       // offset of this query's first slot in the partial buffer
+  int64_t e0;         // element index of x[0] within its signal (a slice), else 0;
+                      // the byte offset e0 * bits / 8 is a multiple of 16
 };
 
 struct FoldArgs {
@@ -107,6 +109,8 @@ struct CorrQ {
   int64_t y_off;      // fold output [2][P] (int32 or float), element offset
   int64_t spec_off;   // template spectrum scratch [P] float2, element offset
   int64_t r_off;      // correlation output [2][P] float, or -1
+  const void* y_in;   // complete folds [2][P] supplied by the caller (the fold
+                      // completion is skipped; x may then be null: no exact score)
 };
 
 struct CorrArgs {
@@ -132,6 +136,37 @@ cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s);
 cudaError_t launch_correlate_blocked(const CorrArgs& a, cudaStream_t s);
 int blocked_spectra(int K, int maxM);
 constexpr int kLogPMaxBlocked = 16;   // largest FFT length the planner accepts: 65536
+// ---------------------------------------------------------------- slices of one signal
+// Completion of a slice's fold: the extended folds [2][P] of Eq. (2)
+// restricted to the entries x_n with n in [n0, n0 + len), from the fold
+// kernel's slots over [n0, n0 + nfold) plus the slice's own tail, wrap-around
+// and extension terms.
+struct SliceFoldArgs {
+  const int32_t* partial;   // [nslots][stride] int32 counts or fp32 sums
+  int32_t nslots, stride;
+  int32_t moff[2], M[2], R[2];
+  int64_t L[2];
+  int64_t N;
+  int32_t K, P, xdtype;
+  const void* x;            // the slice's storage: element n0 first
+  int64_t n0, len, nfold;
+  void* y;                  // [2][P] int32 (+-1 signals) or float
+};
+cudaError_t launch_fold_slice_complete(const SliceFoldArgs& a, cudaStream_t s);
+// Partial scores sum_{i<K} t_i x_{(m+i) mod N} over the entries in the slice,
+// for each candidate m; fp64 (exact for integer data).
+struct SliceScoreArgs {
+  const void* x;
+  int32_t xdtype;
+  int64_t N, n0, len;
+  const float* t;
+  int32_t K;
+  const int64_t* m;
+  int32_t nm;
+  double* out;
+};
+cudaError_t launch_score_slice(const SliceScoreArgs& a, cudaStream_t s);
+
 cudaError_t fold_configure();   // one-time kernel attributes
 cudaError_t corr_configure();
 

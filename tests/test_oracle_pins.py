@@ -333,3 +333,36 @@ def test_table2_success_rates(snr, n):
     k = _success_rate(1 << 26, 1 << 16, n, 77000 + int(snr * 10), snr=snr)
     pp = min(max(p, 1e-3), 1 - 1e-3)
     assert _binom_two_sided_p(k, n, pp) > 1e-3, (snr, k, n, p)
+
+
+# ---------------------------------------------------------------------------
+# Slices of one signal: Eq. (2) and Eq. (1) are sums over the entries of x,
+# so restricting them to the pieces of any partition and adding the pieces
+# must give the whole (checked against fold() and tx_at(), which never
+# restrict); the single piece [0, N) is the whole.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,M,K", [(1000, 37, 20), (4096, 64, 65), (777, 800, 50), (5000, 71, 70)])
+def test_fold_slices_add_up(N, M, K):
+    rng = np.random.default_rng(N + M)
+    x = rng.integers(-3, 4, N).astype(np.int64)
+    want = O.fold(x, M, K)
+    assert np.array_equal(O.fold_slice(x, 0, N, M, K), want)
+    for _ in range(5):
+        cuts = np.sort(rng.choice(np.arange(1, N), size=int(rng.integers(1, 6)), replace=False))
+        bounds = [0, *cuts.tolist(), N]
+        got = sum(O.fold_slice(x[a:b], a, N, M, K) for a, b in zip(bounds[:-1], bounds[1:]))
+        assert np.array_equal(got, want)
+
+
+def test_score_slices_add_up():
+    rng = np.random.default_rng(5)
+    N, K = 3001, 257
+    x = rng.integers(-1, 2, N).astype(np.int64) * 2 + 1
+    t = rng.integers(-2, 3, K).astype(np.int64)
+    for m in (0, 5, N - 100, N - 1):
+        want = O.tx_at(x, t, m)
+        bounds = [0, 1000, 1016, 2990, N]
+        got = sum(O.tx_slice(x[a:b], a, N, t, m) for a, b in zip(bounds[:-1], bounds[1:]))
+        assert got == want
+        assert O.tx_slice(x, 0, N, t, m) == want
