@@ -14,7 +14,7 @@ bounded sample, and a plain full-length FFT correlation (cuFFT via torch)
 on the same GPU for comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-  python bench.py --workload uneven|serve   (other workloads, one line each)
+  python bench.py --workload uneven|serve|sweep   (other workloads, one line each)
   N > 1: torchrun --nproc-per-node N bench.py --gpus N ... (queries sharded by
   rank, no collective on the data path: weak scaling).
 """
@@ -484,6 +484,50 @@ def run_serve(args):
     return 0
 
 
+def run_sweep(args):
+    """The success-probability sweep: N = 2^22 +-1 signals, K in
+    {256 .. 16384}, 256 seeds per K with 10% template flips, moduli K and
+    K+1 (several CRT solutions accepted and resolved by exact scores). One
+    batch per K; reports the success rate against the paper's variable
+    K^2 / (ln K N) next to the time per batch."""
+    import math
+
+    import torch
+    import paper_1509_04863_gb300 as tm
+    N, n = 1 << 22, args.seeds
+    rows = []
+    for K in W.SWEEP_KS:
+        qs = W.sweep(seed=1000 + K, K=K, n=n, N=N)
+        specs = [dict(x=torch.from_numpy(q.x).cuda(), t=torch.from_numpy(q.t).cuda(), N=q.N, K=q.K, xdtype="i8",
+                      mode="paper", allow_ambig=True) for q in qs]
+        b = tm.Batch(specs)
+        out = tm.result_buffer(n)
+        b.run(out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            b.run(out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res = tm.decode_results(out)
+        ok = sum(r["shift"] == q.k_star for r, q in zip(res, qs))
+        rows.append({"K": K, "x": K * K / (math.log(K) * N), "success_rate": ok / n, "ms_per_batch": ms,
+                     "queries_per_s": n / (ms / 1e3), "blocked": b.infos[0]["P"] > 16384,
+                     "device_error": b.device_error()})
+        del b, specs
+        torch.cuda.empty_cache()
+    line = {"metric": "success rate vs K^2/(ln K N)", "value": rows[-1]["success_rate"], "unit": "fraction",
+            "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "int32 fold, f32 FFT, int64 rescoring",
+            "data": "synthetic", "config": {"workload": f"sweep: N=2^22 int8 +-1, K in {list(W.SWEEP_KS)}, {n} seeds "
+                                                        "per K, 10% template flips, M1=K, M2=K+1"},
+            "sweep": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -495,9 +539,10 @@ def main():
     ap.add_argument("--queries", type=int, default=64)
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--K", type=int, default=K_T)
-    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve"],
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve", "sweep"],
                     help="batch64 (default line), uneven (4096-query mix as one CUDA graph), "
                          "serve (Poisson arrivals through the continuous-batching server)")
+    ap.add_argument("--seeds", type=int, default=256)
     ap.add_argument("--rate", type=float, default=20000.0)
     ap.add_argument("--duration", type=float, default=3.0)
     ap.add_argument("--signals", type=int, default=1024)
@@ -514,6 +559,8 @@ def main():
         return run_uneven(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_native(args)
 
 

@@ -10,11 +10,12 @@
 // units per warp (8 warps for M1, 9 for M2, so that K and K+1 columns both
 // come to one chunk per warp for the paper's moduli). For a stage holding
 // elements [s, e) of a signal every lane of a warp walks the same rows l of
-// its modulus. Int8 units read whole rows through row walkers that keep
-// each unit's next row offset from stage to stage; a row cut by a stage
-// edge is read in two parts, the bytes past either edge being slack that
-// reads as +1. The other units take a fast path for rows strictly inside
-// the stage and a masked path for the first and last row. Stages carry 16
+// its modulus. Int8, fp16 and fp32 units read whole rows through row walkers
+// that keep each unit's next row offset from stage to stage; a row cut by a
+// stage edge is read in two parts, the bytes past either edge being slack
+// that holds a neutral value (+1 for int8, which adds to no count; +0.0 for
+// reals). Bit-packed units take a fast path for rows strictly inside the
+// stage and a masked path for the first and last row. Stages carry 16
 // bytes of slack on both sides so every read stays in bounds. A unit
 // narrower than E (the last one of a row) still reads E columns; the
 // columns past its width see the next row and are never written out. Each
@@ -324,29 +325,34 @@ struct UnitBits {
 // ---------------------------------------------------------------- fp32
 struct UnitF32 {
   static constexpr int kE = 4, kBits = 32;
-  static constexpr bool kWalk = false;
+  static constexpr bool kWalk = true;   // stage slack reads as +0.0f
   float acc[4];
   __device__ __forceinline__ void clear() {
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[i] = 0.f;
   }
   static __device__ __forceinline__ int widen_every(int) { return 1 << 30; }
-  __device__ __forceinline__ void add(const uint8_t* buf, int o) {
+  // 16 bytes at byte offset ob (a multiple of 4): whole words, no shifts
+  __device__ __forceinline__ void add(const uint8_t* buf, int ob) {
+    const uint4* p = reinterpret_cast<const uint4*>(buf + (ob & ~15));
+    const uint4 a = p[0];
     uint32_t w[4];
-    load16(buf, 4 * o, w);
+    switch ((ob >> 2) & 3) {
+      case 0: w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; break;
+      case 1: { const uint4 b = p[1]; w[0] = a.y; w[1] = a.z; w[2] = a.w; w[3] = b.x; break; }
+      case 2: { const uint4 b = p[1]; w[0] = a.z; w[1] = a.w; w[2] = b.x; w[3] = b.y; break; }
+      default: { const uint4 b = p[1]; w[0] = a.w; w[1] = b.x; w[2] = b.y; w[3] = b.z; break; }
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[i] += __uint_as_float(w[i]);
   }
-  __device__ __forceinline__ void add2(const uint8_t* buf, int o, int o2) {
-    add(buf, o);
-    add(buf, o2);
-  }
-  __device__ __forceinline__ void add_masked(const uint8_t* buf, int o, int len) {
-    uint32_t w[4];
-    load16(buf, 4 * o, w);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (o + i >= 0 && o + i < len) acc[i] += __uint_as_float(w[i]);
+  template <int P>
+  __device__ __forceinline__ void addp(const uint8_t* buf, int ob) { add(buf, ob); }
+  __device__ __forceinline__ void add2_aligned(const uint8_t* buf, int o, int o2) {
+    const float4 a = *reinterpret_cast<const float4*>(buf + o);
+    const float4 b = *reinterpret_cast<const float4*>(buf + o2);
+    acc[0] += a.x; acc[1] += a.y; acc[2] += a.z; acc[3] += a.w;
+    acc[0] += b.x; acc[1] += b.y; acc[2] += b.z; acc[3] += b.w;
   }
   __device__ __forceinline__ void widen() {}
   __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
@@ -363,16 +369,14 @@ struct UnitF32 {
 // ---------------------------------------------------------------- fp16
 struct UnitF16 {
   static constexpr int kE = 8, kBits = 16;
-  static constexpr bool kWalk = false;
+  static constexpr bool kWalk = true;   // stage slack reads as +0.0
   float acc[8];
   __device__ __forceinline__ void clear() {
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = 0.f;
   }
   static __device__ __forceinline__ int widen_every(int) { return 1 << 30; }
-  __device__ __forceinline__ void add(const uint8_t* buf, int o) {
-    uint32_t w[4];
-    load16(buf, 2 * o, w);
+  __device__ __forceinline__ void add_words(const uint32_t (&w)[4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
@@ -380,19 +384,20 @@ struct UnitF16 {
       acc[2 * i + 1] += f.y;
     }
   }
-  __device__ __forceinline__ void add2(const uint8_t* buf, int o, int o2) {
-    add(buf, o);
-    add(buf, o2);
-  }
-  __device__ __forceinline__ void add_masked(const uint8_t* buf, int o, int len) {
+  // 16 bytes at byte offset ob (a multiple of 2)
+  __device__ __forceinline__ void add(const uint8_t* buf, int ob) {
     uint32_t w[4];
-    load16(buf, 2 * o, w);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
-      if (o + 2 * i >= 0 && o + 2 * i < len) acc[2 * i] += f.x;
-      if (o + 2 * i + 1 >= 0 && o + 2 * i + 1 < len) acc[2 * i + 1] += f.y;
-    }
+    load16(buf, ob, w);
+    add_words(w);
+  }
+  template <int P>
+  __device__ __forceinline__ void addp(const uint8_t* buf, int ob) { add(buf, ob); }
+  __device__ __forceinline__ void add2_aligned(const uint8_t* buf, int o, int o2) {
+    const uint4 a = *reinterpret_cast<const uint4*>(buf + o);
+    const uint4 b = *reinterpret_cast<const uint4*>(buf + o2);
+    const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wb[4] = {b.x, b.y, b.z, b.w};
+    add_words(wa);
+    add_words(wb);
   }
   __device__ __forceinline__ void widen() {}
   __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
@@ -488,24 +493,30 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
 // The same for units read through the row walkers (kWalk): each unit keeps
 // the offset of its next row relative to the next stage, so no row index
 // is recomputed per stage and no read is masked.
+// The same for units read through the row walkers (kWalk): each unit keeps
+// the byte offset of its next row relative to the next stage, so no row
+// index is recomputed per stage and no read is masked. Rows are Mb = Mp *
+// bytes-per-element bytes long; a unit covers 16 bytes of a row.
 template <class U, int J>
 __device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t* full, uint64_t* empty, int lo,
                                                    int hi, int Mp, int ph, int W, int wig, int32_t* dst,
                                                    uint32_t& it) {
-  static_assert(U::kBits == 8, "walkers step in bytes");
+  constexpr int kEB = U::kBits / 8;   // bytes per element
   const int lane = threadIdx.x & 31;
   const int F = U::widen_every(Mp);
-  auto col = [&](int j) { return U::kE * (lane + 32 * (wig + W * j)); };
+  const int Mb = Mp * kEB;
+  auto colb = [&](int j) { return 16 * (lane + 32 * (wig + W * j)); };   // unit j's first byte in a row
   U u[J];
-  int o[J];   // next row of unit j, relative to the current stage
-  const int l = (lo + ph) / Mp;
+  int o[J];   // next row of unit j, relative to the current stage (bytes)
+  const int g = lo + ph * kEB;        // the share's first byte, counted from the row phase
+  const int l = g / Mb;
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     u[j].clear();
-    o[j] = l * Mp + col(j) - (lo + ph);
-    if (o[j] <= -U::kE) o[j] += Mp;
+    o[j] = l * Mb + colb(j) - g;
+    if (o[j] <= -16) o[j] += Mb;
   }
-  const int step = Mp & 15;
+  const int step = Mb & 15;
   int since = 0;
   for (int s = lo; s < hi; s += kFoldTile) {
     const uint32_t st = it % kFoldStages;
@@ -514,13 +525,14 @@ __device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t
     const int el = min(kFoldTile, hi - s);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      if (col(j) >= Mp) continue;
-      const int e = step == 0 ? walk_aligned(u[j], buf, o[j], el, Mp)
-                  : step == 1 ? walk_step1(u[j], buf, o[j], el, Mp)
-                              : walk_any(u[j], buf, o[j], el, Mp);
-      // a last row that started within kE bytes of the end continues in
+      if (colb(j) >= Mb) continue;
+      int e;
+      if (step == 0) e = walk_aligned(u[j], buf, o[j], el, Mb);
+      else if constexpr (kEB == 1) e = step == 1 ? walk_step1(u[j], buf, o[j], el, Mb) : walk_any(u[j], buf, o[j], el, Mb);
+      else e = walk_any(u[j], buf, o[j], el, Mb);
+      // a last row that started within 16 bytes of the end continues in
       // the next stage (its first bytes there fall at negative offsets)
-      o[j] = e - Mp > el - U::kE ? e - Mp - el : e - el;
+      o[j] = e - Mb > el - 16 ? e - Mb - el : e - el;
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
@@ -532,8 +544,10 @@ __device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t
     }
   }
 #pragma unroll
-  for (int j = 0; j < J; ++j)
-    if (col(j) < Mp) u[j].write(dst, col(j), min(U::kE, Mp - col(j)));
+  for (int j = 0; j < J; ++j) {
+    const int col = colb(j) / kEB;
+    if (col < Mp) u[j].write(dst, col, min(U::kE, Mp - col));
+  }
   return true;
 }
 
@@ -554,13 +568,15 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
     }
     mbar_init_fence();
   }
-  // The 16 bytes before and after each stage's data read as +1 entries of
-  // an int8 signal (walker units read across stage edges); bulk copies
+  // The 16 bytes before and after each stage's data hold a neutral value
+  // (walker units read across stage edges): +1 entries of an int8 signal,
+  // which add to no count; zero bytes, +0.0 for real signals. Bulk copies
   // never write there.
+  const uint32_t neutral = a.dtype == TM_I8_PM1 ? 0x01010101u : 0u;   // +1 entries / +0.0 / no bits set
   if (tid < 8 * kFoldStages) {
     const int st = tid >> 3, k = tid & 7;
     uint32_t* w = reinterpret_cast<uint32_t*>(smem + st * kStageBytes + (k < 4 ? 0 : 16 + kFoldTile));
-    w[k & 3] = 0x01010101u;
+    w[k & 3] = neutral;
   }
   __syncthreads();
   if (cb >= ce) return;
@@ -592,7 +608,7 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
             // later bulk copy into this stage overwrites them, so order the
             // store before the async proxy's writes
             *reinterpret_cast<uint4*>(smem + st * kStageBytes + 16 + len) =
-                make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+                make_uint4(neutral, neutral, neutral, neutral);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           }
           mbar_arrive_expect_tx(&full[st], len);
