@@ -351,6 +351,7 @@ def run_uneven(args):
     total_bytes = sum(signal_bytes(q["N"], q["xdtype"]) for q in qs)
     b = tm.Batch(specs)
     out = tm.result_buffer(n)
+    tiles = b.autotune(force=True)   # stage ring per storage type, timed on this batch
     b.capture_graph(out)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -390,6 +391,7 @@ def run_uneven(args):
         "config": {"workload": f"uneven{n}: N log-uniform [2^14,2^24], K log-uniform [2^8,2^13], "
                                "half int8 +-1 / half fp32 N(0,1), template noise N(0,0.3^2), auto moduli",
                    "queries": n, "signal_bytes": total_bytes, "launch": "one CUDA graph per step",
+                   "autotuned_stage_bytes": tiles,
                    "l2": f"{total_bytes / 1e9:.1f} GB of signals per step > L2 (no flush)"},
         "input_GBps": total_bytes / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "kernel": "fold_kernel (int8 and fp32 groups)",

@@ -209,6 +209,16 @@ TM_API tm_status tm_batch_run(tm_batch_t b, tm_result* out_dev, tm_stream_t stre
 TM_API tm_status tm_batch_run_host(tm_batch_t b, const void* const* x_host,
                             const float* const* t_host, tm_result* out_host,
                             tm_stream_t stream);
+/* Autotuner: for each storage type in the batch, time the fold launch with
+ * stage rings of 3 x 64 KiB, 6 x 32 KiB and 12 x 16 KiB on the batch's own
+ * inputs (a few launches each on `stream`, which it synchronises) and keep
+ * the fastest for later runs and captures. Choices are cached per process
+ * by (storage type, size class of the batch, size class of the effective
+ * modulus); TM_TUNE_FORCE re-times. tiles (optional, 4 entries indexed by
+ * tm_dtype) receives the chosen stage bytes, 0 for types not in the batch.
+ * Partial folds are overwritten: run the batch again before reading them. */
+#define TM_TUNE_FORCE 0x1u
+TM_API tm_status tm_batch_autotune(tm_batch_t b, tm_stream_t stream, uint32_t flags, int32_t* tiles);
 /* Record one tm_batch_run(b, out_dev) - the fold launches and the
  * correlation launches with the memsets before them - as a CUDA graph held
  * by the batch (captured on a private stream; nothing runs). Replaces an

@@ -73,6 +73,7 @@ _SIGS = {
     "tm_batch_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "tm_batch_run_host": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p,
                                     C.c_void_p]),
+    "tm_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
     "tm_batch_graph_capture": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_folds": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]),
@@ -259,6 +260,13 @@ class Batch:
 
     def correlate(self, out, stream=None):
         _check(lib().tm_batch_correlate(self._h, out.data_ptr(), _stream_ptr(stream)), "tm_batch_correlate")
+
+    def autotune(self, stream=None, force: bool = False) -> dict:
+        """tm_batch_autotune: pick the fold's stage ring per storage type; returns {dtype: stage bytes}."""
+        tiles = (C.c_int32 * 4)()
+        _check(lib().tm_batch_autotune(self._h, _stream_ptr(stream), 1 if force else 0, tiles), "tm_batch_autotune")
+        names = {v: k for k, v in DTYPE_CODES.items()}
+        return {names[d]: tiles[d] for d in range(4) if tiles[d]}
 
     def capture_graph(self, out):
         """Record one run writing to `out` as a CUDA graph (tm_batch_graph_capture)."""

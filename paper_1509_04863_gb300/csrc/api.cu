@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -399,7 +401,7 @@ tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
     if (g.W == 0) continue;
     FoldArgs a;
     a.q = b->d_fq + g.first; a.nq = g.count; a.dtype = g.dtype; a.nctas = g.nctas; a.W = g.W;
-    a.partial = b->d_partial; a.err = b->d_err;
+    a.partial = b->d_partial; a.err = b->d_err; a.tile = g.tile;
     TM_CUDA(launch_fold(a, g.jmax, s));
   }
   return TM_OK;
@@ -685,6 +687,81 @@ tm_status tm_selftest_wait_timeout(int64_t limit_ns, int32_t* gave_up) {
   if (e == cudaSuccess) e = cudaMemcpy(gave_up, d, sizeof(int32_t), cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(e, "tm_selftest_wait_timeout");
+  return TM_OK;
+}
+
+namespace {
+
+// Tuned stage sizes by (storage type, log2 of the group's bytes, log2 of
+// the mean effective modulus), shared by all batches of the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int32_t> g_tune;
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << (l + 1)) <= v) ++l;
+  return l;
+}
+
+}  // namespace
+
+tm_status tm_batch_autotune(tm_batch_t b, tm_stream_t stream, uint32_t flags, int32_t* tiles) {
+  if (!b) return fail(TM_EINVAL, "null batch");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TM_CUDA(cudaSetDevice(b->device));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TM_CUDA(cudaEventCreate(&e0));
+  TM_CUDA(cudaEventCreate(&e1));
+  tm_status st = TM_OK;
+  for (auto& g : b->groups) {
+    if (g.W == 0) continue;
+    int64_t mp = 0;
+    for (int32_t k = g.first; k < g.first + g.count; ++k) mp += b->fq[k].Mp[0];
+    const auto key = std::make_tuple(int(g.dtype), ilog2(g.W), ilog2(std::max<int64_t>(1, mp / g.count)));
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end() && !(flags & TM_TUNE_FORCE)) {
+        g.tile = it->second;
+        continue;
+      }
+    }
+    FoldArgs a;
+    a.q = b->d_fq + g.first; a.nq = g.count; a.dtype = g.dtype; a.nctas = g.nctas; a.W = g.W;
+    a.partial = b->d_partial; a.err = b->d_err;
+    float best = 0.f;
+    int32_t best_tile = kFoldTile;
+    for (int32_t tile : {65536, 32768, 16384}) {
+      a.tile = tile;
+      cudaError_t e = launch_fold(a, g.jmax, s);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_fold(a, g.jmax, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "tm_batch_autotune");
+        break;
+      }
+      if (tile == 65536 || ms < best) {
+        best = ms;
+        best_tile = tile;
+      }
+    }
+    if (st != TM_OK) break;
+    g.tile = best_tile;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best_tile;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TM_OK) return st;
+  if (tiles) {
+    for (int d = 0; d < 4; ++d) tiles[d] = 0;
+    for (const auto& g : b->groups)
+      if (g.dtype >= 0 && g.dtype < 4) tiles[g.dtype] = g.tile;
+  }
   return TM_OK;
 }
 

@@ -46,7 +46,20 @@
 namespace ftm {
 namespace {
 
-constexpr int kStageBytes = kFoldTile + 32;   // 16 bytes of slack before and after the data
+constexpr int kSlack = 32;   // 16 bytes of slack before and after each stage's data
+
+// Position in the ring of stages: stage index and the parity of its
+// current phase, advanced without divisions.
+struct RingPos {
+  uint32_t st = 0, ph = 0, used = 0;   // used: stages filled so far (saturates at the ring size)
+  __device__ __forceinline__ void advance(int stages) {
+    if (++st == uint32_t(stages)) {
+      st = 0;
+      ph ^= 1u;
+    }
+    if (used < uint32_t(stages)) ++used;
+  }
+};
 
 __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, uint32_t sh) {
   return __funnelshift_r(lo, hi, sh);
@@ -117,7 +130,7 @@ struct UnitI8 {
     rows = 0u;
   }
   // stages between widenings: a unit reads at most tile/Mp + 2 rows per stage
-  static __device__ __forceinline__ int widen_every(int Mp) { return max(1, 127 / (kFoldTile / Mp + 2)); }
+  static __device__ __forceinline__ int widen_every(int Mp, int tile) { return max(1, 127 / (tile / Mp + 2)); }
   template <int P>
   __device__ __forceinline__ void addp(const uint8_t* buf, int o) {
     uint32_t w[4];
@@ -236,7 +249,7 @@ struct UnitBits {
     rows = 0;
     flushes = 0;
   }
-  static __device__ __forceinline__ int widen_every(int) { return 1 << 30; }   // planes flush themselves
+  static __device__ __forceinline__ int widen_every(int, int) { return 1 << 30; }   // planes flush themselves
   // 32 bits starting at bit o of the stage (o > -32; the word before the
   // stage lies in the 16-byte slack); o & 31 is warp-uniform
   static __device__ __forceinline__ uint32_t load32(const uint8_t* buf, int o) {
@@ -331,7 +344,7 @@ struct UnitF32 {
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[i] = 0.f;
   }
-  static __device__ __forceinline__ int widen_every(int) { return 1 << 30; }
+  static __device__ __forceinline__ int widen_every(int, int) { return 1 << 30; }
   // 16 bytes at byte offset ob (a multiple of 4): whole words, no shifts
   __device__ __forceinline__ void add(const uint8_t* buf, int ob) {
     const uint4* p = reinterpret_cast<const uint4*>(buf + (ob & ~15));
@@ -375,7 +388,7 @@ struct UnitF16 {
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = 0.f;
   }
-  static __device__ __forceinline__ int widen_every(int) { return 1 << 30; }
+  static __device__ __forceinline__ int widen_every(int, int) { return 1 << 30; }
   __device__ __forceinline__ void add_words(const uint32_t (&w)[4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -428,10 +441,11 @@ __device__ __forceinline__ int first_query(const FoldQ* q, int nq, int64_t pos) 
 // where wig is the warp's index among the W warps of its modulus. Returns
 // false when a bounded wait ran out.
 template <class U, int J>
-__device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* full, uint64_t* empty, int lo, int hi,
-                                              int Mp, int ph, int W, int wig, int32_t* dst, uint32_t& it) {
+__device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* full, uint64_t* empty, int tile,
+                                              int stages, int lo, int hi, int Mp, int ph, int W, int wig,
+                                              int32_t* dst, RingPos& rp) {
   const int lane = threadIdx.x & 31;
-  const int F = U::widen_every(Mp);
+  const int F = U::widen_every(Mp, tile);
   // unit j of this lane starts at column col(j); it exists when col(j) < Mp
   auto col = [&](int j) { return U::kE * (lane + 32 * (wig + W * j)); };
   U u[J];
@@ -439,13 +453,13 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
   for (int j = 0; j < J; ++j) u[j].clear();
 
   int since = 0;
-  for (int s = lo; s < hi; s += kFoldTile) {
-    const uint32_t st = it % kFoldStages;
+  for (int s = lo; s < hi; s += tile) {
+    const uint32_t st = rp.st;
     // every lane waits; the warp gives up together so no lane is left
     // behind at the __syncwarp below
-    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (it / kFoldStages) & 1u))) return false;
-    const uint8_t* buf = smem + st * kStageBytes + 16;
-    const int len = min(kFoldTile, hi - s);
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], rp.ph))) return false;
+    const uint8_t* buf = smem + st * (tile + kSlack) + 16;
+    const int len = min(tile, hi - s);
     // the stage in elements: [es, es + el)
     const int es = int((int64_t(s) * 8) / U::kBits) + ph;   // the stage's first element, row phase included
     const int el = int((int64_t(len) * 8) / U::kBits);
@@ -477,7 +491,7 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
-    ++it;
+    rp.advance(stages);
     if (++since == F) {
       since = 0;
 #pragma unroll
@@ -498,12 +512,12 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
 // index is recomputed per stage and no read is masked. Rows are Mb = Mp *
 // bytes-per-element bytes long; a unit covers 16 bytes of a row.
 template <class U, int J>
-__device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t* full, uint64_t* empty, int lo,
-                                                   int hi, int Mp, int ph, int W, int wig, int32_t* dst,
-                                                   uint32_t& it) {
+__device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t* full, uint64_t* empty, int tile,
+                                                   int stages, int lo, int hi, int Mp, int ph, int W, int wig,
+                                                   int32_t* dst, RingPos& rp) {
   constexpr int kEB = U::kBits / 8;   // bytes per element
   const int lane = threadIdx.x & 31;
-  const int F = U::widen_every(Mp);
+  const int F = U::widen_every(Mp, tile);
   const int Mb = Mp * kEB;
   auto colb = [&](int j) { return 16 * (lane + 32 * (wig + W * j)); };   // unit j's first byte in a row
   U u[J];
@@ -518,11 +532,11 @@ __device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t
   }
   const int step = Mb & 15;
   int since = 0;
-  for (int s = lo; s < hi; s += kFoldTile) {
-    const uint32_t st = it % kFoldStages;
-    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (it / kFoldStages) & 1u))) return false;
-    const uint8_t* buf = smem + st * kStageBytes + 16;
-    const int el = min(kFoldTile, hi - s);
+  for (int s = lo; s < hi; s += tile) {
+    const uint32_t st = rp.st;
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], rp.ph))) return false;
+    const uint8_t* buf = smem + st * (tile + kSlack) + 16;
+    const int el = min(tile, hi - s);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       if (colb(j) >= Mb) continue;
@@ -536,7 +550,7 @@ __device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
-    ++it;
+    rp.advance(stages);
     if (++since == F) {
       since = 0;
 #pragma unroll
@@ -554,15 +568,16 @@ __device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t
 template <class U, int JMAX>
 __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kFoldStages * kStageBytes);
-  uint64_t* empty = full + kFoldStages;
+  const int tile = a.tile, stages = kFoldRingBytes / a.tile;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kFoldRingBytes + kFoldMaxStages * kSlack);
+  uint64_t* empty = full + kFoldMaxStages;
 
   const int tid = threadIdx.x;
   const int64_t cb = fold_cta_begin(a.W, a.nctas, blockIdx.x);
   const int64_t ce = fold_cta_begin(a.W, a.nctas, blockIdx.x + 1);
 
   if (tid == 0) {
-    for (int s = 0; s < kFoldStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kFoldConsumers / 32);
     }
@@ -573,9 +588,9 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
   // which add to no count; zero bytes, +0.0 for real signals. Bulk copies
   // never write there.
   const uint32_t neutral = a.dtype == TM_I8_PM1 ? 0x01010101u : 0u;   // +1 entries / +0.0 / no bits set
-  if (tid < 8 * kFoldStages) {
+  if (tid < 8 * stages) {
     const int st = tid >> 3, k = tid & 7;
-    uint32_t* w = reinterpret_cast<uint32_t*>(smem + st * kStageBytes + (k < 4 ? 0 : 16 + kFoldTile));
+    uint32_t* w = reinterpret_cast<uint32_t*>(smem + st * (tile + kSlack) + (k < 4 ? 0 : 16 + tile));
     w[k & 3] = neutral;
   }
   __syncthreads();
@@ -586,7 +601,8 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
   if (tid >= kFoldConsumers) {
     if (tid == kFoldConsumers) {
       const uint64_t pol = l2_policy_evict_first();
-      uint32_t it = 0;
+      RingPos rp;
+      uint32_t fills = 0;
       bool ok = true;
       for (int qi = q0; qi < a.nq && ok; ++qi) {
         const int64_t goff = a.q[qi].goff;
@@ -596,30 +612,32 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
         if (nbytes == 0) continue;
         const int64_t lo = max(cb, goff) - goff;
         const int64_t hi = min(ce, goff + nbytes) - goff;
-        for (int64_t s = lo; s < hi; s += kFoldTile) {
-          const uint32_t st = it % kFoldStages;
-          if (it >= kFoldStages && !mbar_wait(&empty[st], ((it / kFoldStages) & 1u) ^ 1u)) {
+        for (int64_t s = lo; s < hi; s += tile) {
+          const uint32_t st = rp.st;
+          // a stage filled before is free again once its consumers arrived
+          if (rp.used == uint32_t(stages) && !mbar_wait(&empty[st], rp.ph ^ 1u)) {
             ok = false;
             break;
           }
-          const uint32_t len = uint32_t(hi - s < kFoldTile ? hi - s : int64_t(kFoldTile));
-          if (len < uint32_t(kFoldTile)) {
+          const uint32_t len = uint32_t(hi - s < tile ? hi - s : int64_t(tile));
+          if (len < uint32_t(tile)) {
             // a short stage: the 16 bytes after its data read as +1 too; a
             // later bulk copy into this stage overwrites them, so order the
             // store before the async proxy's writes
-            *reinterpret_cast<uint4*>(smem + st * kStageBytes + 16 + len) =
+            *reinterpret_cast<uint4*>(smem + st * (tile + kSlack) + 16 + len) =
                 make_uint4(neutral, neutral, neutral, neutral);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           }
           mbar_arrive_expect_tx(&full[st], len);
-          bulk_load(smem + st * kStageBytes + 16, x + s, len, &full[st], pol);
-          ++it;
+          bulk_load(smem + st * (tile + kSlack) + 16, x + s, len, &full[st], pol);
+          rp.advance(stages);
+          ++fills;
         }
       }
       if (!ok) atomicOr(a.err, 1);
       // Let every copy this thread issued land before the CTA may exit.
-      for (uint32_t k = it > kFoldStages ? it - kFoldStages : 0; k < it; ++k)
-        (void)mbar_wait(&full[k % kFoldStages], (k / kFoldStages) & 1u);
+      for (uint32_t k = fills > uint32_t(stages) ? fills - stages : 0; k < fills; ++k)
+        (void)mbar_wait(&full[k % stages], (k / stages) & 1u);
     }
     return;
   }
@@ -629,7 +647,7 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
   const int m = warp < kFoldWarps0 ? 0 : 1;         // modulus handled by this warp
   const int W = m == 0 ? kFoldWarps0 : kFoldWarps1;
   const int wig = m == 0 ? warp : warp - kFoldWarps0;
-  uint32_t it = 0;
+  RingPos rp;
   bool ok = true;
   for (int qi = q0; qi < a.nq && ok; ++qi) {
     const int64_t goff = a.q[qi].goff;
@@ -645,21 +663,21 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
                    a.q[qi].moff[m];
     const int J = fold_units_per_lane(Mp, W, U::kE);
     if constexpr (U::kWalk) {
-      if (J <= 1) ok = consume_share_walk<U, 1>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
-      else if (J == 2 || JMAX == 2) ok = consume_share_walk<U, 2>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
-      else if (J <= 3 || JMAX <= 3) ok = consume_share_walk<U, (JMAX < 3 ? JMAX : 3)>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
-      else ok = consume_share_walk<U, JMAX>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
+      if (J <= 1) ok = consume_share_walk<U, 1>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
+      else if (J == 2 || JMAX == 2) ok = consume_share_walk<U, 2>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
+      else if (J <= 3 || JMAX <= 3) ok = consume_share_walk<U, (JMAX < 3 ? JMAX : 3)>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
+      else ok = consume_share_walk<U, JMAX>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
     } else {
-      if (J <= 1) ok = consume_share<U, 1>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
-      else if (J == 2 || JMAX == 2) ok = consume_share<U, 2>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
-      else if (J <= 4 || JMAX <= 4) ok = consume_share<U, (JMAX < 4 ? JMAX : 4)>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
-      else ok = consume_share<U, JMAX>(smem, full, empty, lo, hi, Mp, ph, W, wig, dst, it);
+      if (J <= 1) ok = consume_share<U, 1>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
+      else if (J == 2 || JMAX == 2) ok = consume_share<U, 2>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
+      else if (J <= 4 || JMAX <= 4) ok = consume_share<U, (JMAX < 4 ? JMAX : 4)>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
+      else ok = consume_share<U, JMAX>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
     }
   }
   if (!ok) atomicOr(a.err, 1);
 }
 
-constexpr int kFoldSmem = kFoldStages * kStageBytes + 2 * kFoldStages * 8;
+constexpr int kFoldSmem = kFoldRingBytes + kFoldMaxStages * kSlack + 2 * kFoldMaxStages * 8;
 
 template <class K>
 cudaError_t set_smem(K kernel) {
@@ -682,6 +700,7 @@ cudaError_t fold_configure() {
 // Each storage type has a register-lean instantiation for the common moduli
 // and a wider one (moduli up to fold_geom().jmax units per lane).
 cudaError_t launch_fold(const FoldArgs& a, int jmax, cudaStream_t s) {
+  if (a.tile != 16384 && a.tile != 32768 && a.tile != 65536) return cudaErrorInvalidValue;
   switch (a.dtype) {
     case TM_I8_PM1:
       if (jmax <= 3) fold_kernel<UnitI8, 3><<<a.nctas, kFoldThreads, kFoldSmem, s>>>(a);

@@ -65,6 +65,7 @@ struct tm_batch_s {
   struct FoldGroup {
     int32_t dtype, first, count, nctas, jmax;
     int64_t W;
+    int32_t tile = ftm::kFoldTile;   // stage bytes (tm_batch_autotune may change it)
   };
   std::vector<FoldGroup> groups;
   std::vector<int32_t> fold_of;

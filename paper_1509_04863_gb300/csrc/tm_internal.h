@@ -23,8 +23,13 @@ constexpr int kFoldWarps0 = 8;                       // consumer warps of modulu
 constexpr int kFoldWarps1 = 9;                       // consumer warps of modulus M2
 constexpr int kFoldConsumers = 32 * (kFoldWarps0 + kFoldWarps1);
 constexpr int kFoldThreads = kFoldConsumers + 32;    // + producer warp
+// The ring of shared-memory stages: 3 x 64 KiB by default; an autotuner
+// may pick 6 x 32 KiB or 12 x 16 KiB for a batch (same ring bytes).
 constexpr int kFoldStages = 3;
-constexpr int kFoldTile = 65536;                     // bytes per stage
+constexpr int kFoldTile = 65536;                     // bytes per stage (default)
+constexpr int kFoldRingBytes = kFoldStages * kFoldTile;
+constexpr int kFoldMinTile = 16384;
+constexpr int kFoldMaxStages = kFoldRingBytes / kFoldMinTile;
 // A consumer's 16-bit lane counters hold twice the number of -1 entries;
 // the host caps a CTA's share so that no column sees more rows than this.
 constexpr int kFoldMaxRowsPerSlot = 32000;
@@ -77,6 +82,7 @@ struct FoldArgs {
   int32_t* partial;   // per (slot, modulus, column): int32 counts of -1 (int8) or
                       // +1 (bits) entries, or fp32 sums (real signals)
   int32_t* err;       // device error word
+  int32_t tile = kFoldTile;   // bytes per stage: 16384, 32768 or 65536
 };
 
 // Start of CTA c's share of W bytes (multiple of 16). Shared by the host

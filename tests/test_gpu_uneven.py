@@ -102,3 +102,21 @@ def test_alone_equals_in_batch(tm, uneven):
             # sums may round differently; the picks agree or are near-ties
             assert (r1["m1"], r1["m2"]) == (res[i]["m1"], res[i]["m2"]) or \
                 abs(r1["r1"] - res[i]["r1"]) <= 1e-4 * max(1.0, abs(res[i]["r1"]))
+
+
+def test_autotuned_batch_gives_the_same_results(tm, uneven):
+    """The autotuner only changes the fold's stage ring: every result, real
+    signals included, stays bit-identical (stage edges add +0.0 / +1 entries
+    that count for nothing)."""
+    qs, _, b = uneven
+    plain = tm.result_buffer(NQ)
+    b.run(plain)
+    torch.cuda.synchronize()
+    tiles = b.autotune(force=True)
+    assert set(tiles) == {"i8", "f32"} and all(v in (16384, 32768, 65536) for v in tiles.values())
+    out = tm.result_buffer(NQ)
+    b.capture_graph(out)
+    b.launch_graph()
+    torch.cuda.synchronize()
+    assert tm.decode_results(out) == tm.decode_results(plain)
+    assert b.device_error() == 0
