@@ -430,8 +430,9 @@ def run_serve(args):
         temps.append(WD.template(g["x"], g["K"], shifts[i], 0.3, 10 ** 6 + i).cpu().numpy())
     out = {"offered_qps": rate, "duration_s": dur, "requests": nreq, "signals": nsig}
     shift_by_storage = {}
-    for storage in ("f32", "f16"):
-        srv = tm.Server(n_streams=args.streams, max_batch=args.max_batch)
+    for storage in ("f32", "f16", "f32+fold_cache"):
+        cache = (1 << 30) if storage.endswith("fold_cache") else 0
+        srv = tm.Server(n_streams=args.streams, max_batch=args.max_batch, fold_cache_bytes=cache)
         ids = []
         for g in sigs:
             if g["xdtype"] == "f32" and storage == "f16":
@@ -467,6 +468,7 @@ def run_serve(args):
                         "p99_us": float(np.percentile(lat, 99)) if len(lat) else None,
                         "max_us": float(lat.max()) if len(lat) else None,
                         "mean_batch": st["mean_batch"], "iterations": st["iterations"],
+                        "fold_cache_hits": st["fold_cache_hits"], "fold_cache_misses": st["fold_cache_misses"],
                         "success_rate": float(np.mean([shift_by_storage[storage][i] == shifts[i]
                                                        for i in range(nreq)]))}
         srv.close()
@@ -481,7 +483,9 @@ def run_serve(args):
                        "streams": args.streams, "max_batch": args.max_batch},
             "latency_us": {"p50": out["f32"]["p50_us"], "p99": out["f32"]["p99_us"],
                            "what": "submit to result, server clock, first 10% of requests excluded"},
-            "serve": out, "f16_vs_f32_shift_agreement": float(agree)}
+            "serve": out, "f16_vs_f32_shift_agreement": float(agree),
+            "fold_cache_variant": "serve['f32+fold_cache']: folds of (signal, M1, M2) reused across requests; "
+                                  "a labelled variant, not the primary number"}
     print(json.dumps(line))
     return 0
 

@@ -274,6 +274,13 @@ typedef struct {
   uint32_t flags;             /* reserved, 0 */
   int64_t arena_bytes;        /* device workspace per stream (0: share of free memory) */
   int64_t hbm_reserve_bytes;  /* left free when arena_bytes is 0 (0: 4 GiB) */
+  int64_t fold_cache_bytes;   /* fold cache (0: off): the folds of a resident signal
+                                 over k < M_j depend only on (signal, M1, M2), so a
+                                 request whose pair was folded before skips the O(N)
+                                 fold and pays only steps 4-9 (Sec. 3.5: a known code,
+                                 many templates). Least recently used pairs are
+                                 dropped beyond this many device bytes. Requests with
+                                 FFT lengths above 16384 are not cached. */
 } tm_serve_cfg;
 
 typedef struct {
@@ -288,6 +295,7 @@ typedef struct {
   int64_t submitted, completed, failed, iterations, pending, in_flight;
   double mean_batch;   /* requests per iteration */
   double p50_us, p99_us, max_us;   /* latency over the completed requests */
+  int64_t fold_cache_hits, fold_cache_misses;   /* requests served from / missing the fold cache */
 } tm_serve_stats;
 
 /* Signal registration flag: x is device memory to use in place (the caller

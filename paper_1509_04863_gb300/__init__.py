@@ -367,7 +367,8 @@ def result_buffer(n: int, device="cuda"):
 # ---------------------------------------------------------------- server (tm_serve_*)
 class tm_serve_cfg(C.Structure):
     _fields_ = [("n_streams", C.c_int32), ("max_batch", C.c_int32), ("queue_capacity", C.c_int32),
-                ("flags", C.c_uint32), ("arena_bytes", C.c_int64), ("hbm_reserve_bytes", C.c_int64)]
+                ("flags", C.c_uint32), ("arena_bytes", C.c_int64), ("hbm_reserve_bytes", C.c_int64),
+                ("fold_cache_bytes", C.c_int64)]
 
 
 class tm_result_tagged(C.Structure):
@@ -378,7 +379,8 @@ class tm_result_tagged(C.Structure):
 class tm_serve_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("iterations", C.c_int64), ("pending", C.c_int64), ("in_flight", C.c_int64),
-                ("mean_batch", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double)]
+                ("mean_batch", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
+                ("fold_cache_hits", C.c_int64), ("fold_cache_misses", C.c_int64)]
 
 
 TM_SERVE_SIGNAL_DEVICE = 0x1
@@ -398,9 +400,9 @@ class Server:
     """tm_serve_create / register_signal / submit / poll / stats / destroy."""
 
     def __init__(self, n_streams: int = 2, max_batch: int = 512, queue_capacity: int = 65536,
-                 arena_bytes: int = 0, hbm_reserve_bytes: int = 0):
+                 arena_bytes: int = 0, hbm_reserve_bytes: int = 0, fold_cache_bytes: int = 0):
         L = lib()
-        cfg = tm_serve_cfg(n_streams, max_batch, queue_capacity, 0, arena_bytes, hbm_reserve_bytes)
+        cfg = tm_serve_cfg(n_streams, max_batch, queue_capacity, 0, arena_bytes, hbm_reserve_bytes, fold_cache_bytes)
         h = C.c_void_p()
         _check(L.tm_serve_create(C.byref(cfg), C.byref(h)), "tm_serve_create")
         self._h = h

@@ -216,7 +216,7 @@ tm_status upload_descriptors(tm_batch_t b, cudaStream_t s) {
   return TM_OK;
 }
 
-tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags) {
+tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags, const uint8_t* nofold) {
   if (n < 1 || !q) return fail(TM_EINVAL, "empty batch");
   b->flags = flags;
   b->n = n;
@@ -259,7 +259,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
       if (p.xdtype != dt) continue;
       const int32_t pos = gr.first + gr.count++;
       b->fold_of[i] = pos;
-      const int64_t nb = fold_bytes(p.xdtype, p.N);
+      const int64_t nb = (nofold && nofold[i]) ? 0 : fold_bytes(p.xdtype, p.N);
       FoldQ& f = b->fq[pos];
       f.goff = W;
       f.nbytes = int32_t(nb);

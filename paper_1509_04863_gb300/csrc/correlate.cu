@@ -716,7 +716,13 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   } else {
     for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
     __syncthreads();
-    if (ints) {
+    if (Q.y_core != nullptr) {
+      // the folds over k < M_j from a cache of this signal's folds (int32 or
+      // float bits alike)
+      const int32_t* yc = static_cast<const int32_t*>(Q.y_core);
+      for (int j = 0; j < 2; ++j)
+        for (int k = tid; k < Q.M[j]; k += kCorrThreads) ib[2 * pad_idx(k) + j] = yc[int64_t(j) * Q.core_pitch + k];
+    } else if (ints) {
       // Partial slots hold counts of -1 (int8) or +1 (bits) entries per column
       // kp < Mp of the Mp-fold; column k of the M-fold gathers kp = k + r M,
       // r < R. Slot rows are padded to 16 columns, so a quad read at kp < Mp
@@ -727,27 +733,27 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
         const int nq4 = (Mp + 3) >> 2;
         for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
           int4 c[4];
-  #pragma unroll
+#pragma unroll
           for (int b = 0; b < 4; ++b) c[b] = make_int4(0, 0, 0, 0);
-  #pragma unroll 2
+#pragma unroll 2
           for (int sl = 0; sl < Q.nslots; ++sl) {
             const int32_t* ps = part + int64_t(sl) * Q.stride;
             int4 v[4];
-  #pragma unroll
+#pragma unroll
             for (int b = 0; b < 4; ++b) {
               const int q = q0 + b * kCorrThreads;
               v[b] = q < nq4 ? __ldg(reinterpret_cast<const int4*>(ps) + q) : make_int4(0, 0, 0, 0);
             }
-  #pragma unroll
+#pragma unroll
             for (int b = 0; b < 4; ++b) {
               c[b].x += v[b].x; c[b].y += v[b].y; c[b].z += v[b].z; c[b].w += v[b].w;
             }
           }
-  #pragma unroll
+#pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int k0 = 4 * (q0 + b * kCorrThreads);
             const int cc[4] = {c[b].x, c[b].y, c[b].z, c[b].w};
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < 4; ++i) {
               const int kp = k0 + i;
               if (kp < Mp && cc[i] != 0) {
@@ -770,12 +776,12 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
         with_sig(Q.xdtype, Q.x, [&](auto sx) {
           for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
             float xv[kB];
-  #pragma unroll
+#pragma unroll
             for (int b = 0; b < kB; ++b) {
               const int k = k0 + b * kCorrThreads;
               xv[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
             }
-  #pragma unroll
+#pragma unroll
             for (int b = 0; b < kB; ++b) {
               const int k = k0 + b * kCorrThreads;
               if (k < M) {
@@ -798,26 +804,26 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
         for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
           float acc[kB];
           with_sig(Q.xdtype, Q.x, [&](auto sx) {
-  #pragma unroll
+#pragma unroll
             for (int b = 0; b < kB; ++b) {
               const int k = k0 + b * kCorrThreads;
               acc[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
             }
           });
           float yk[kB];
-  #pragma unroll
+#pragma unroll
           for (int b = 0; b < kB; ++b) yk[b] = 0.f;
           for (int sl = 0; sl < Q.nslots; ++sl) {
             const float* ps = pf + int64_t(sl) * Q.stride;
             for (int r = 0; r < Rr; ++r) {
-  #pragma unroll
+#pragma unroll
               for (int b = 0; b < kB; ++b) {
                 const int k = k0 + b * kCorrThreads;
                 if (k < M) yk[b] += __ldg(&ps[k + r * M]);
               }
             }
           }
-  #pragma unroll
+#pragma unroll
           for (int b = 0; b < kB; ++b) {
             const int k = k0 + b * kCorrThreads;
             if (k < M) fb[2 * pad_idx(k) + j] = yk[b] + acc[b];
@@ -826,7 +832,7 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       }
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && Q.y_core == nullptr) {
       for (int64_t n = Q.nelem16; n < N; ++n) {
         for (int j = 0; j < 2; ++j) {
           const int e = 2 * pad_idx(int(n % Q.M[j])) + j;
@@ -846,7 +852,7 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       for (int i0 = tid; i0 < K - 1; i0 += kB * kCorrThreads) {
         float xi[kB], xw[kB];
         with_sig(Q.xdtype, Q.x, [&](auto sx) {
-  #pragma unroll
+#pragma unroll
           for (int b = 0; b < kB; ++b) {
             const int i = i0 + b * kCorrThreads;
             xi[b] = xw[b] = 0.f;
@@ -858,7 +864,7 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
             }
           }
         });
-  #pragma unroll
+#pragma unroll
         for (int b = 0; b < kB; ++b) {
           const int i = i0 + b * kCorrThreads;
           if (i < K - 1) {

@@ -101,7 +101,10 @@ namespace ftm {
 
 // Host layout of a batch (plans, fold groups, descriptors, order, sizes);
 // needs the device that will run it to be current (SM count, twiddles).
-tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags);
+// nofold (optional, n entries): queries whose folds come from elsewhere
+// (CorrQ::y_core); the fold kernel does not read their signals.
+tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags,
+                     const uint8_t* nofold = nullptr);
 // Device buffers from cudaMalloc (owns_memory) and pinned staging.
 tm_status batch_alloc(tm_batch_s* b);
 void batch_free(tm_batch_s* b);

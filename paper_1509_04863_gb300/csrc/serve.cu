@@ -21,9 +21,11 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "runtime.h"
@@ -52,6 +54,21 @@ struct Signal {
   bool owned;
 };
 
+// Fold cache: the folds over k < M_j of (signal, M1, M2), rows of `pitch`
+// entries; `ev` completes when they are written; refs counts in-flight
+// iterations reading them, pending is set until the writing iteration
+// retires (an entry is dropped only with neither).
+using CacheKey = std::tuple<int32_t, int32_t, int32_t>;
+struct CacheEntry {
+  void* y = nullptr;
+  int32_t pitch = 0;
+  int64_t bytes = 0;
+  cudaEvent_t ev = nullptr;
+  int refs = 0;
+  bool pending = true;
+  uint64_t last = 0;
+};
+
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -68,6 +85,7 @@ struct Slot {
   int32_t* h_order = nullptr;   // pinned processing order
   tm_batch_s* b = nullptr;
   std::vector<Req> reqs;
+  std::vector<CacheKey> hits, made;   // fold-cache entries read / written by the iteration
   bool busy = false;
 };
 
@@ -86,6 +104,10 @@ struct tm_server_s {
   std::deque<tm_result_tagged> done;
   std::vector<double> lat;             // completed latencies (bounded)
   int64_t submitted = 0, completed = 0, failed = 0, iterations = 0, batched = 0;
+  std::map<CacheKey, CacheEntry> fcache;   // worker thread only
+  int64_t fcache_bytes = 0;
+  uint64_t fclock = 0;
+  int64_t fc_hits = 0, fc_misses = 0;
   std::atomic<bool> stop{false};
   std::atomic<int> busy{0};            // iterations in flight
   std::thread worker;
@@ -178,8 +200,22 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
     qs[i] = reqs[i].q;
     qs[i].t = reinterpret_cast<const float*>(uintptr_t(16));
   }
+  // fold cache lookups: hits skip the fold kernel
+  const bool cache_on = sv->cfg.fold_cache_bytes > 0;
+  std::vector<uint8_t> nofold(size_t(n), 0);
+  std::vector<CacheEntry*> hit(size_t(n), nullptr);
+  if (cache_on) {
+    for (int i = 0; i < n; ++i) {
+      if (reqs[i].plan.P > kPMax) continue;
+      auto it = sv->fcache.find(CacheKey(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1]));
+      if (it != sv->fcache.end()) {
+        nofold[i] = 1;
+        hit[i] = &it->second;
+      }
+    }
+  }
   reset_batch(sl.b);
-  tm_status st = batch_plan(sl.b, qs.data(), n, 0);
+  tm_status st = batch_plan(sl.b, qs.data(), n, 0, nofold.data());
   if (st != TM_OK) return st;
   if (batch_bytes(sl.b, t_floats) > size_t(sl.arena_bytes)) return TM_ENOMEM;
   carve(sl.b, sl.arena, t_floats);
@@ -189,6 +225,12 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
   }
   std::memcpy(sl.h_order, sl.b->order.data(), size_t(n) * sizeof(int32_t));
   bind_pointers(sl.b);
+  for (int i = 0; i < n; ++i) {
+    if (!hit[i]) continue;
+    sl.b->cq[i].y_core = hit[i]->y;
+    sl.b->cq[i].core_pitch = hit[i]->pitch;
+    TM_CUDA(cudaStreamWaitEvent(sl.s, hit[i]->ev, 0));
+  }
   TM_CUDA(cudaMemcpyAsync(sl.b->d_t, sl.h_t, size_t(t_floats) * sizeof(float), cudaMemcpyHostToDevice, sl.s));
   TM_CUDA(cudaMemcpyAsync(sl.b->d_order, sl.h_order, size_t(n) * sizeof(int32_t), cudaMemcpyHostToDevice, sl.s));
   st = upload_descriptors(sl.b, sl.s);
@@ -199,6 +241,66 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
   if (st != TM_OK) return st;
   TM_CUDA(cudaMemcpyAsync(sl.h_out, sl.b->d_out, size_t(n) * sizeof(tm_result), cudaMemcpyDeviceToHost, sl.s));
   TM_CUDA(cudaEventRecord(sl.ev, sl.s));
+  if (cache_on) {
+    sl.hits.clear();
+    sl.made.clear();
+    for (int i = 0; i < n; ++i) {
+      if (!hit[i]) continue;
+      ++hit[i]->refs;
+      hit[i]->last = ++sv->fclock;
+      sl.hits.emplace_back(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1]);
+    }
+    int64_t nh = 0;
+    for (int i = 0; i < n; ++i) nh += hit[i] ? 1 : 0;
+    {
+      std::lock_guard<std::mutex> lk(sv->cmu);
+      sv->fc_hits += nh;
+      sv->fc_misses += n - nh;
+    }
+    // new entries from this iteration's folds (copied once it has run)
+    for (int i = 0; i < n; ++i) {
+      if (hit[i] || reqs[i].plan.P > kPMax) continue;
+      const CacheKey key(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1]);
+      if (sv->fcache.count(key)) continue;
+      const int32_t pitch = std::max(reqs[i].plan.M[0], reqs[i].plan.M[1]);
+      const int64_t bytes = 2 * int64_t(pitch) * 4;
+      // drop least recently used entries that nothing reads or writes
+      while (sv->fcache_bytes + bytes > sv->cfg.fold_cache_bytes) {
+        auto victim = sv->fcache.end();
+        for (auto it = sv->fcache.begin(); it != sv->fcache.end(); ++it)
+          if (it->second.refs == 0 && !it->second.pending &&
+              (victim == sv->fcache.end() || it->second.last < victim->second.last))
+            victim = it;
+        if (victim == sv->fcache.end()) break;
+        cudaFreeAsync(victim->second.y, sl.s);
+        cudaEventDestroy(victim->second.ev);
+        sv->fcache_bytes -= victim->second.bytes;
+        sv->fcache.erase(victim);
+      }
+      if (sv->fcache_bytes + bytes > sv->cfg.fold_cache_bytes) continue;
+      CacheEntry e;
+      e.pitch = pitch;
+      e.bytes = bytes;
+      e.last = ++sv->fclock;
+      if (cudaMallocAsync(&e.y, size_t(bytes), sl.s) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      const char* src = static_cast<const char*>(sl.b->d_y) + sl.b->cq[i].y_off * 4;
+      if (cudaMemcpy2DAsync(e.y, size_t(pitch) * 4, src, size_t(sl.b->cq[i].P) * 4, size_t(pitch) * 4, 2,
+                            cudaMemcpyDeviceToDevice, sl.s) != cudaSuccess ||
+          cudaEventCreateWithFlags(&e.ev, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventRecord(e.ev, sl.s) != cudaSuccess) {
+        cudaGetLastError();
+        if (e.ev) cudaEventDestroy(e.ev);
+        cudaFreeAsync(e.y, sl.s);
+        continue;
+      }
+      sv->fcache_bytes += bytes;
+      sv->fcache.emplace(key, e);
+      sl.made.push_back(key);
+    }
+  }
   return TM_OK;
 }
 
@@ -239,7 +341,22 @@ void admit(tm_server_t sv, Slot& sl) {
   }
 }
 
+// The iteration on `sl` no longer reads or writes its fold-cache entries.
+void release_cache(tm_server_t sv, Slot& sl) {
+  for (const auto& k : sl.hits) {
+    auto it = sv->fcache.find(k);
+    if (it != sv->fcache.end()) --it->second.refs;
+  }
+  for (const auto& k : sl.made) {
+    auto it = sv->fcache.find(k);
+    if (it != sv->fcache.end()) it->second.pending = false;
+  }
+  sl.hits.clear();
+  sl.made.clear();
+}
+
 void retire(tm_server_t sv, Slot& sl) {
+  release_cache(sv, sl);
   const double t = now_us();
   std::vector<tm_result_tagged> out(sl.reqs.size());
   for (size_t i = 0; i < sl.reqs.size(); ++i) {
@@ -266,6 +383,7 @@ void worker_main(tm_server_t sv) {
         progressed = true;
       } else if (e != cudaErrorNotReady) {
         cudaGetLastError();
+        release_cache(sv, sl);
         sl.busy = false;
         sv->busy.fetch_sub(1);
         fail_reqs(sv, sl.reqs, TM_ECUDA);
@@ -311,6 +429,10 @@ void server_free(tm_server_t sv) {
     if (sl.h_out) cudaFreeHost(sl.h_out);
     if (sl.h_stage) cudaFreeHost(sl.h_stage);
     if (sl.h_order) cudaFreeHost(sl.h_order);
+  }
+  for (auto& kv : sv->fcache) {
+    cudaFree(kv.second.y);
+    if (kv.second.ev) cudaEventDestroy(kv.second.ev);
   }
   for (auto& sg : sv->signals)
     if (sg.owned) cudaFree(const_cast<void*>(sg.x));
@@ -467,6 +589,8 @@ tm_status tm_serve_stats_get(tm_server_t sv, tm_serve_stats* st) {
     st->failed = sv->failed;
     st->iterations = sv->iterations;
     st->mean_batch = sv->iterations ? double(sv->batched) / double(sv->iterations) : 0.0;
+    st->fold_cache_hits = sv->fc_hits;
+    st->fold_cache_misses = sv->fc_misses;
     lat = sv->lat;
   }
   {

@@ -117,6 +117,10 @@ struct CorrQ {
   int64_t r_off;      // correlation output [2][P] float, or -1
   const void* y_in;   // complete folds [2][P] supplied by the caller (the fold
                       // completion is skipped; x may then be null: no exact score)
+  const void* y_core; // cached folds over k < M_j (wrap-around and last entries
+                      // included), row j at y_core + j core_pitch; the fold
+                      // kernel skips the signal, only the extension is added
+  int32_t core_pitch;
 };
 
 struct CorrArgs {

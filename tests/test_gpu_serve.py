@@ -145,3 +145,46 @@ def test_submit_validation(tm):
         srv.submit(sid, q.t[:16], tag=0, mode="paper")    # 16 * 17 <= 4096: needs allow_ambig
     assert e.value.status == tm.TM_EINVAL
     srv.close()
+
+
+def test_fold_cache(tm):
+    """Requests on resident signals whose moduli repeat are served from the
+    fold cache (no O(N) fold): the same results as a server without it
+    (bit-equal for +-1 signals, near for real ones), and the cache reports
+    hits after the first fold of each (signal, M1, M2)."""
+    # N = 2^20 + 3: automatic moduli M1 = max(K, 1024), so every K <= 1024
+    # shares one pair
+    N = (1 << 20) + 3
+    base = [W.planted_query(4000 + k, N, 512, dt, mode="auto") for k, dt in enumerate(["i8", "f32", "bits"])]
+    rng = np.random.default_rng(9)
+    reqs = []
+    for rnd in range(3):
+        for k, q in enumerate(base):
+            for K in (256, 700, 1000, 1024):
+                k_star = int(rng.integers(0, N))
+                t = W.flip_entries(rng, W.cyclic_window(_values(q), k_star, K), 0.03)
+                reqs.append((k, K, t))
+    outs = []
+    for cache in (0, 64 << 20):
+        srv = tm.Server(n_streams=2, max_batch=8, arena_bytes=1 << 28, fold_cache_bytes=cache)
+        ids = [srv.register_signal(q.x, q.N, q.xdtype) for q in base]
+        got = {}
+        for i, (k, K, t) in enumerate(reqs):
+            assert srv.submit(ids[k], t, tag=i, mode="auto") == tm.TM_OK
+            if i % 12 == 11:   # let earlier rounds finish so later ones can hit
+                got.update(_collect(srv, i + 1 - len(got)))
+        got.update(_collect(srv, len(reqs) - len(got)))
+        st = srv.stats()
+        outs.append((got, st))
+        srv.close()
+    (plain, st0), (cached, st1) = outs
+    assert st0["fold_cache_hits"] == 0
+    assert st1["fold_cache_hits"] >= len(reqs) // 2 and st1["failed"] == 0
+    for i, (k, K, t) in enumerate(reqs):
+        a, b = plain[i], cached[i]
+        assert a["req_status"] == b["req_status"] == tm.TM_OK
+        if base[k].xdtype in ("i8", "bits"):
+            assert {f: a[f] for f in ("shift", "status", "m1", "m2", "r1", "r2", "score", "n_cand")} == \
+                {f: b[f] for f in ("shift", "status", "m1", "m2", "r1", "r2", "score", "n_cand")}, (i, a, b)
+        else:
+            assert (a["m1"], a["m2"]) == (b["m1"], b["m2"]) or abs(a["r1"] - b["r1"]) <= 1e-4 * max(1.0, abs(a["r1"]))
