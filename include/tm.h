@@ -66,6 +66,12 @@ typedef enum { TM_MODE_AUTO = 0, TM_MODE_PAPER = 1, TM_MODE_EXPLICIT = 2 } tm_mo
 /* Plan flag: accept M1*M2 <= N. The intersection of step 9 may then hold
  * several shifts; they are resolved by their exact (Tx)_m. */
 #define TM_ALLOW_AMBIG 0x1u
+/* Plan flag: step 3 with the second sampling matrix of Thm. 2, Phi =
+ * [I_M ... I_M] on x zero-padded to a multiple of M (no wrap-around term),
+ * and steps 4-6 as the circular correlation of period M with the template
+ * (y extended periodically); candidate positions in the padding are
+ * dropped in step 8. */
+#define TM_THM2_SAMPLING 0x2u
 
 /* tm_result.status values (low byte) and flag bits. */
 #define TM_FOUND 0      /* |S1 ∩ S2| = 1 */

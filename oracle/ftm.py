@@ -26,6 +26,9 @@ listed again in the design notes):
                         mode "auto" uses M1 = max(K, s), M2 = M1+1 with s the
                         least integer such that s(s+1) > N.
   R8 (Sec. 4, Table 2)  SNR = 10 log10(E[x^2] / s^2) with noise on x only.
+  R13 (Thm. 2)          the second sampling matrix uses Phi_M = I_M on x
+                        zero-padded to a multiple of M, a circular correlation
+                        of period M, and candidate positions below N only.
 """
 from __future__ import annotations
 
@@ -243,10 +246,68 @@ def ftm(x: np.ndarray, t: np.ndarray, M1: int, M2: int, corr: str = "direct") ->
                 n_cand=len(I), score=score)
 
 
+# ---------------------------------------------------------------------------
+# The second sampling matrix of Thm. 2: Phi = [Phi_M ... Phi_M] with Phi_M = I_M
+# acting on x zero-padded to a multiple of M (the paper pads when M does not
+# divide N). The fold has length M and the correlation with the template is
+# circular with period M: T^ = circ([t 0]) of size M x M (reading R13).
+# ---------------------------------------------------------------------------
+
+def fold_thm2(x: np.ndarray, M: int) -> np.ndarray:
+    """y = Phi x' (Thm. 2): y_k = sum_l x'_{k + l M}, k < M, x' = x padded with zeros to L M."""
+    N = x.shape[0]
+    L = ceil_div(N, M)
+    xp = np.zeros(L * M, dtype=x.dtype)
+    xp[:N] = x
+    return xp.reshape(L, M).sum(axis=0)
+
+
+def correlate_circular(y: np.ndarray, t: np.ndarray, M: int) -> np.ndarray:
+    """(T^ y)_j = sum_{i<K} t_i y_{(j+i) mod M}, j < M, T^ = circ([t 0_{M-K}])."""
+    K = t.shape[0]
+    kind = np.int64 if (y.dtype.kind == "i" and t.dtype.kind == "i") else np.float64
+    r = np.zeros(M, dtype=kind)
+    for i in range(K):
+        r += t[i].astype(kind) * np.roll(y, -i).astype(kind)
+    return r
+
+
+def candidate_set_thm2(m_tilde: int, M: int, N: int) -> Set[int]:
+    """{m~ + l M : l < ceil(N/M)} inside the signal (positions in the zero
+    padding are not shifts of x) (R13)."""
+    return {int(m_tilde + i * M) for i in range(ceil_div(N, M)) if m_tilde + i * M < N}
+
+
+def ftm_thm2(x: np.ndarray, t: np.ndarray, M1: int, M2: int) -> Dict:
+    """Algorithm 1 with the Thm. 2 sampling matrix in step 3 (fold of the
+    zero-padded signal, length M) and the circular correlation of period M
+    in steps 4-6; steps 7-9 as in ftm()."""
+    N = x.shape[0]
+    t = template_values(t) if t.dtype.kind == "f" else t
+    y1, y2 = fold_thm2(x, M1), fold_thm2(x, M2)
+    r1, r2 = correlate_circular(y1, t, M1), correlate_circular(y2, t, M2)
+    m1, m2 = argmax_first(r1), argmax_first(r2)
+    S1, S2 = candidate_set_thm2(m1, M1, N), candidate_set_thm2(m2, M2, N)
+    I = sorted(S1 & S2)
+    if len(I) == 0:
+        shift, status = -1, EMPTY
+    elif len(I) == 1:
+        shift, status = I[0], FOUND
+    else:
+        scores = [tx_at(x, t, m) for m in I]
+        shift, status = I[scores.index(max(scores))], RESOLVED
+    score = tx_at(x, t, shift) if shift >= 0 else 0
+    return dict(M1=M1, M2=M2, y1=y1, y2=y2, r1=r1, r2=r2, m1=m1, m2=m2, S1=S1, S2=S2, I=I,
+                shift=int(shift), status=status, n_cand=len(I), score=score)
+
+
 def match_query(q, corr: str = "direct") -> Dict:
-    """Plan + FTM for a workloads.Query-like object."""
+    """Plan + FTM for a workloads.Query-like object (q.meta["thm2"]: the
+    Thm. 2 sampling variant)."""
     M1, M2 = plan(q.N, q.K, q.mode, q.M1, q.M2, q.allow_ambig)
     x = decode(q.x, q.xdtype, q.N)
+    if q.meta.get("thm2"):
+        return ftm_thm2(x, q.t, M1, M2)
     return ftm(x, q.t, M1, M2, corr=corr)
 
 

@@ -22,6 +22,7 @@ TM_OK, TM_EINVAL, TM_ENOMEM, TM_ECUDA, TM_EBUSY, TM_ETIMEDOUT, TM_EAGAIN, TM_EUN
 TM_I8_PM1, TM_BITS_PM1, TM_F16, TM_F32 = range(4)
 TM_MODE_AUTO, TM_MODE_PAPER, TM_MODE_EXPLICIT = range(3)
 TM_ALLOW_AMBIG = 0x1
+TM_THM2_SAMPLING = 0x2
 TM_FOUND, TM_EMPTY, TM_RESOLVED = 0, 1, 2
 TM_RF_FULL_RESCORE = 0x100
 TM_RF_DEVICE_ERROR = 0x200
@@ -167,9 +168,8 @@ class Plan:
     """tm_plan_create / tm_plan_get_info / tm_match / tm_plan_destroy."""
 
     def __init__(self, N: int, K: int, xdtype: str = "i8", mode: str = "paper", M1: int = 0, M2: int = 0,
-                 allow_ambig: bool = False):
-        d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2,
-                         TM_ALLOW_AMBIG if allow_ambig else 0)
+                 allow_ambig: bool = False, thm2: bool = False):
+        d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2, _plan_flags(allow_ambig, thm2))
         h = C.c_void_p()
         _check(lib().tm_plan_create(C.byref(d), C.byref(h)), "tm_plan_create")
         self._h = h
@@ -216,9 +216,13 @@ def tm_plan_create(N, K, xdtype="i8", mode="paper", M1=0, M2=0, allow_ambig=Fals
     return Plan(N, K, xdtype, mode, M1, M2, allow_ambig)
 
 
-def _query_struct(x_ptr, t_ptr, N, K, xdtype, mode, M1=0, M2=0, allow_ambig=False) -> tm_query:
+def _plan_flags(allow_ambig=False, thm2=False) -> int:
+    return (TM_ALLOW_AMBIG if allow_ambig else 0) | (TM_THM2_SAMPLING if thm2 else 0)
+
+
+def _query_struct(x_ptr, t_ptr, N, K, xdtype, mode, M1=0, M2=0, allow_ambig=False, thm2=False) -> tm_query:
     return tm_query(x_ptr, t_ptr, int(N), int(K), DTYPE_CODES[xdtype], MODE_CODES[mode], int(M1), int(M2),
-                    TM_ALLOW_AMBIG if allow_ambig else 0)
+                    _plan_flags(allow_ambig, thm2))
 
 
 class Batch:
@@ -236,7 +240,7 @@ class Batch:
             xp = s["x"].data_ptr() if s.get("x") is not None else None
             tp = s["t"].data_ptr() if s.get("t") is not None else None
             arr[i] = _query_struct(xp, tp, s["N"], s["K"], s.get("xdtype", "i8"), s.get("mode", "paper"),
-                                   s.get("M1", 0), s.get("M2", 0), s.get("allow_ambig", False))
+                                   s.get("M1", 0), s.get("M2", 0), s.get("allow_ambig", False), s.get("thm2", False))
         self._arr = arr
         flags = (TM_BATCH_KEEP_CORR if keep_corr else 0) | (TM_BATCH_HOST_INPUTS if host_inputs else 0)
         h = C.c_void_p()
@@ -244,7 +248,7 @@ class Batch:
         self._h = h
         # per-query plan information (host-only planner calls)
         self.infos = [Plan(s["N"], s["K"], s.get("xdtype", "i8"), s.get("mode", "paper"), s.get("M1", 0),
-                           s.get("M2", 0), s.get("allow_ambig", False)).info for s in specs]
+                           s.get("M2", 0), s.get("allow_ambig", False), s.get("thm2", False)).info for s in specs]
 
     def set_inputs(self, xs, ts):
         for i in range(self.n):
@@ -423,12 +427,12 @@ class Server:
         return sid.value
 
     def submit(self, sig_id: int, t, tag: int, mode: str = "paper", M1: int = 0, M2: int = 0,
-               allow_ambig: bool = False) -> int:
+               allow_ambig: bool = False, thm2: bool = False) -> int:
         """Queue one request; returns the status (TM_OK, TM_EAGAIN, ...) without raising for TM_EAGAIN."""
         import numpy as np
         tt = np.ascontiguousarray(t, dtype=np.float32)
         st = lib().tm_serve_submit(self._h, sig_id, tt.ctypes.data, int(tt.shape[0]), MODE_CODES[mode], M1, M2,
-                                   TM_ALLOW_AMBIG if allow_ambig else 0, tag)
+                                   _plan_flags(allow_ambig, thm2), tag)
         if st not in (TM_OK, TM_EAGAIN):
             raise TMError(st, "tm_serve_submit")
         return st

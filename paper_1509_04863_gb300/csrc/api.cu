@@ -95,6 +95,7 @@ tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t 
       return fail(TM_EUNSUPPORTED, "modulus too large for the fold kernel of this signal type");
   }
   pc.max_cand = ceil_div(N, m1 * m2) + 2;
+  pc.flags = flags;
   return TM_OK;
 }
 
@@ -310,6 +311,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
     for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
     c.P = p.P; c.logP = p.logP; c.inv = p.inv;
+    c.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
     c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
     c.nslots = f.nslots; c.stride = f.stride; c.part = f.part;
     c.y_off = yo; yo += 2ll * p.P;
@@ -535,6 +537,7 @@ tm_status tm_fold_slice(tm_plan_t p, const void* x, int64_t n0, int64_t len, voi
   if ((n0 * geo.bits) % 128 != 0) return fail(TM_EINVAL, "slice start must fall on a 16-byte boundary of the signal");
   if (reinterpret_cast<uintptr_t>(x) & 15) return fail(TM_EINVAL, "x must be 16-byte aligned");
   if (pc.P > kPMax) return fail(TM_EUNSUPPORTED, "slices need P <= 16384");
+  if (pc.flags & TM_THM2_SAMPLING) return fail(TM_EUNSUPPORTED, "slices use the sampling of Eq. (3)");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0, sms = 0;
   TM_CUDA(cudaGetDevice(&dev));
@@ -596,6 +599,7 @@ tm_status tm_correlate_folds(tm_plan_t p, const void* y, const float* t, tm_resu
   c.x = nullptr; c.t = t; c.N = pc.N; c.K = pc.K; c.xdtype = pc.xdtype;
   for (int j = 0; j < 2; ++j) { c.M[j] = pc.M[j]; c.R[j] = pc.R[j]; c.L[j] = pc.L[j]; }
   c.P = pc.P; c.logP = pc.logP; c.inv = pc.inv;
+  c.thm2 = (pc.flags & TM_THM2_SAMPLING) ? 1 : 0;
   c.nelem16 = int32_t(fold_elems(pc.xdtype, pc.N));
   c.nslots = 0; c.stride = 0; c.part = 0; c.y_off = 0; c.spec_off = 0; c.r_off = -1;
   c.y_in = y;
@@ -991,6 +995,7 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   c.x = x; c.t = t; c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
   for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
   c.P = p.P; c.logP = p.logP; c.inv = p.inv;
+  c.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
   c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
   c.nslots = f.nslots; c.stride = f.stride; c.part = 0;
   c.y_off = 0; c.spec_off = 0; c.r_off = -1;

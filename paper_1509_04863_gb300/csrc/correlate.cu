@@ -560,7 +560,8 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
   }
 
   // ------------------------------------------------ e. steps 8-9
-  const CrtSet cs = crt_intersect(N, Q.M[0], Q.M[1], Q.inv, s_m[0], s_m[1]);
+  CrtSet cs = crt_intersect(N, Q.M[0], Q.M[1], Q.inv, s_m[0], s_m[1]);
+  if (Q.thm2) cs.nw = 0;   // wrapped members fall in the zero padding
   const int64_t ncs = cs.nnat + cs.nw;
   auto member = [&](int64_t c) -> int64_t { return c < cs.nnat ? cs.m0 + c * cs.step : cs.w[c - cs.nnat]; };
   double best_v = 0.0;
@@ -779,7 +780,7 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
 #pragma unroll
             for (int b = 0; b < kB; ++b) {
               const int k = k0 + b * kCorrThreads;
-              xv[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
+              xv[b] = (k < M && k >= Rw && !Q.thm2) ? sx.val(k - Rw) : 0.f;
             }
 #pragma unroll
             for (int b = 0; b < kB; ++b) {
@@ -807,7 +808,7 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
 #pragma unroll
             for (int b = 0; b < kB; ++b) {
               const int k = k0 + b * kCorrThreads;
-              acc[b] = (k < M && k >= Rw) ? sx.val(k - Rw) : 0.f;
+              acc[b] = (k < M && k >= Rw && !Q.thm2) ? sx.val(k - Rw) : 0.f;
             }
           });
           float yk[kB];
@@ -856,7 +857,7 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
           for (int b = 0; b < kB; ++b) {
             const int i = i0 + b * kCorrThreads;
             xi[b] = xw[b] = 0.f;
-            if (i < K - 1) {
+            if (i < K - 1 && !Q.thm2) {   // Thm. 2: periodic, y[M+i] = y[i]
               int64_t w = i + LM - N;   // LM >= N and i + LM - N < 2M, so one reduction is rare
               if (w >= N) w %= N;
               xi[b] = sx.val(i);
@@ -1020,7 +1021,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
         }
         const int nk = L - 1 + (k < Rw ? 1 : 0);
         int yk = Q.xdtype == TM_BITS_PM1 ? 2 * c - nk : nk - 2 * c;
-        if (k >= Rw) yk += sig.ival(k - Rw);
+        if (k >= Rw && !Q.thm2) yk += sig.ival(k - Rw);
         yi[int64_t(j) * P + k] = yk;
       } else {
         const float* pf = reinterpret_cast<const float*>(part);
@@ -1029,7 +1030,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
           const float* ps = pf + int64_t(s) * Q.stride;
           for (int r = 0; r < Rr; ++r) yk += ps[k + r * M];
         }
-        if (k >= Rw) yk += sig.val(k - Rw);
+        if (k >= Rw && !Q.thm2) yk += sig.val(k - Rw);
         yf[int64_t(j) * P + k] = yk;
       }
     }
@@ -1053,8 +1054,14 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
       int64_t w = i + LM - N;
       if (w >= N) w %= N;
       const int64_t e = int64_t(j) * P + M + i, e0 = int64_t(j) * P + i;
-      if (ints) yi[e] = yi[e0] - sig.ival(i) + sig.ival(w);
-      else yf[e] = yf[e0] - sig.val(i) + sig.val(w);
+      if (Q.thm2) {   // periodic extension
+        if (ints) yi[e] = yi[e0];
+        else yf[e] = yf[e0];
+      } else if (ints) {
+        yi[e] = yi[e0] - sig.ival(i) + sig.ival(w);
+      } else {
+        yf[e] = yf[e0] - sig.val(i) + sig.val(w);
+      }
     }
   }
   __syncthreads();

@@ -34,6 +34,7 @@ struct PlanCore {
   int32_t inv = 0;
   int32_t R[2] = {1, 1}, Mp[2] = {0, 0};
   int64_t max_cand = 0;
+  uint32_t flags = 0;   // TM_ALLOW_AMBIG, TM_THM2_SAMPLING
 };
 
 

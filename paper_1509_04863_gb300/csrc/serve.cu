@@ -58,7 +58,7 @@ struct Signal {
 // entries; `ev` completes when they are written; refs counts in-flight
 // iterations reading them, pending is set until the writing iteration
 // retires (an entry is dropped only with neither).
-using CacheKey = std::tuple<int32_t, int32_t, int32_t>;
+using CacheKey = std::tuple<int32_t, int32_t, int32_t, uint32_t>;   // signal, M1, M2, sampling flag
 struct CacheEntry {
   void* y = nullptr;
   int32_t pitch = 0;
@@ -207,7 +207,7 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
   if (cache_on) {
     for (int i = 0; i < n; ++i) {
       if (reqs[i].plan.P > kPMax) continue;
-      auto it = sv->fcache.find(CacheKey(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1]));
+      auto it = sv->fcache.find(CacheKey(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & TM_THM2_SAMPLING));
       if (it != sv->fcache.end()) {
         nofold[i] = 1;
         hit[i] = &it->second;
@@ -248,7 +248,7 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
       if (!hit[i]) continue;
       ++hit[i]->refs;
       hit[i]->last = ++sv->fclock;
-      sl.hits.emplace_back(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1]);
+      sl.hits.emplace_back(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & TM_THM2_SAMPLING);
     }
     int64_t nh = 0;
     for (int i = 0; i < n; ++i) nh += hit[i] ? 1 : 0;
@@ -260,7 +260,7 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
     // new entries from this iteration's folds (copied once it has run)
     for (int i = 0; i < n; ++i) {
       if (hit[i] || reqs[i].plan.P > kPMax) continue;
-      const CacheKey key(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1]);
+      const CacheKey key(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & TM_THM2_SAMPLING);
       if (sv->fcache.count(key)) continue;
       const int32_t pitch = std::max(reqs[i].plan.M[0], reqs[i].plan.M[1]);
       const int64_t bytes = 2 * int64_t(pitch) * 4;

@@ -107,6 +107,7 @@ struct CorrQ {
   int64_t L[2];       // ceil(N / M_j)
   int32_t P, logP;
   int32_t inv;        // M1^{-1} mod M2
+  int32_t thm2;       // Thm. 2 sampling: no wrap-around term, periodic extension
   int32_t nelem16;    // elements covered by the fold kernel
   int32_t nslots;
   int32_t moff[2];

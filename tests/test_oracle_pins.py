@@ -366,3 +366,48 @@ def test_score_slices_add_up():
         got = sum(O.tx_slice(x[a:b], a, N, t, m) for a, b in zip(bounds[:-1], bounds[1:]))
         assert got == want
         assert O.tx_slice(x, 0, N, t, m) == want
+
+
+# ---------------------------------------------------------------------------
+# Thm. 2 (the second sampling matrix): fold_thm2 against Phi = [I ... I]
+# built as a matrix; the theorem's identity T^ Phi x = Phi T_bar x with the
+# block-diagonal T_bar, from explicit matrices; the circular correlation by
+# an FFT of length M; a window inside one block reads the true (Tx)_m.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,M,K", [(60, 12, 5), (61, 12, 5), (100, 7, 7), (128, 32, 9)])
+def test_thm2_fold_and_identity(N, M, K):
+    rng = np.random.default_rng(N * M)
+    x = rng.integers(-5, 6, N).astype(np.int64)
+    t = rng.integers(-3, 4, K).astype(np.int64)
+    L = -(-N // M)
+    xp = np.concatenate([x, np.zeros(L * M - N, dtype=np.int64)])
+    Phi = np.hstack([np.eye(M, dtype=np.int64)] * L)
+    y = O.fold_thm2(x, M)
+    assert np.array_equal(y, Phi @ xp)
+    tM = np.concatenate([t, np.zeros(M - K, dtype=np.int64)])
+    That = O.circ(tM)
+    Tbar = np.kron(np.eye(L, dtype=np.int64), That)
+    assert np.array_equal(That @ (Phi @ xp), Phi @ (Tbar @ xp))
+    r = O.correlate_circular(y, t, M)
+    assert np.array_equal(r, That @ y)
+    rf = np.real(np.fft.ifft(np.conj(np.fft.fft(tM)) * np.fft.fft(y)))
+    assert np.allclose(rf, r)
+
+
+def test_thm2_window_inside_a_block():
+    rng = np.random.default_rng(3)
+    N, M, K = 4096, 256, 64
+    x = np.where(rng.random(N) < 0.5, 1, -1).astype(np.int64)
+    k_star = 5 * M + 100                     # the window [k*, k*+K) stays in block 5
+    t = x[k_star:k_star + K].copy()
+    L = N // M
+    blocks = x.reshape(L, M)
+    # block-diagonal correlation at k* mod M, block 5 alone, equals (Tx)_{k*} = K
+    tM = np.concatenate([t, np.zeros(M - K, dtype=np.int64)])
+    assert int((O.circ(tM) @ blocks[5])[k_star % M]) == O.tx_at(x, t, k_star) == K
+    # and the whole Thm. 2 fold correlation is the sum of the blocks' terms
+    r = O.correlate_circular(O.fold_thm2(x, M), t, M)
+    assert r[k_star % M] == sum(int((O.circ(tM) @ b)[k_star % M]) for b in blocks)
+    assert k_star in O.candidate_set_thm2(k_star % M, M, N)
+    assert all(v < N for v in O.candidate_set_thm2(M - 1, M, N - 3))
