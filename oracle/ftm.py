@@ -26,6 +26,9 @@ listed again in the design notes):
                         mode "auto" uses M1 = max(K, s), M2 = M1+1 with s the
                         least integer such that s(s+1) > N.
   R8 (Sec. 4, Table 2)  SNR = 10 log10(E[x^2] / s^2) with noise on x only.
+  R14 (Thm. 4)          three moduli: consecutive integers c, c+1, c+2 from
+                        the least odd c >= K (PAPER) or >= max(K, s) with
+                        s(s+1)(s+2) > N (AUTO), pairwise co-prime.
   R13 (Thm. 2)          the second sampling matrix uses Phi_M = I_M on x
                         zero-padded to a multiple of M, a circular correlation
                         of period M, and candidate positions below N only.
@@ -301,11 +304,83 @@ def ftm_thm2(x: np.ndarray, t: np.ndarray, M1: int, M2: int) -> Dict:
                 shift=int(shift), status=status, n_cand=len(I), score=score)
 
 
+# ---------------------------------------------------------------------------
+# Steps 2-9 with alpha > 2 pairwise co-prime moduli (Thm. 4: a residue
+# system whose product reaches N determines the shift uniquely), reading R14
+# for their choice.
+# ---------------------------------------------------------------------------
+
+def least_s3(N: int) -> int:
+    """Least integer s with s (s+1) (s+2) > N."""
+    s = max(1, int(round(N ** (1.0 / 3.0))) - 2)
+    while s * (s + 1) * (s + 2) <= N:
+        s += 1
+    while s > 1 and (s - 1) * s * (s + 1) > N:
+        s -= 1
+    return s
+
+
+def plan3(N: int, K: int, mode: str = "paper", M1: int = 0, M2: int = 0, M3: int = 0,
+          allow_ambig: bool = False) -> Tuple[int, int, int]:
+    """Three moduli (R14): "paper" the consecutive integers c, c+1, c+2 from
+    the least odd c >= K (pairwise co-prime); "auto" the same from the least
+    odd c >= max(K, s), s(s+1)(s+2) > N; "explicit" the caller's."""
+    if mode in ("paper", "auto"):
+        c = K if mode == "paper" else max(K, least_s3(N))
+        c += 1 - c % 2
+        M1, M2, M3 = c, c + 1, c + 2
+    elif mode != "explicit":
+        raise ValueError(mode)
+    Ms = (M1, M2, M3)
+    if min(Ms) < K:
+        raise ValueError("moduli must be >= K")
+    for i in range(3):
+        for j in range(i + 1, 3):
+            if math.gcd(Ms[i], Ms[j]) != 1:
+                raise ValueError("moduli must be pairwise co-prime")
+    if M1 * M2 * M3 <= N and not allow_ambig:
+        raise ValueError("M1*M2*M3 must exceed N")
+    return M1, M2, M3
+
+
+def ftm_multi(x: np.ndarray, t: np.ndarray, moduli, corr: str = "direct") -> Dict:
+    """Algorithm 1 with any number of moduli: steps 3-8 for each modulus and
+    the intersection of all candidate sets in step 9 (Thm. 4)."""
+    N = x.shape[0]
+    t = template_values(t) if t.dtype.kind == "f" else t
+    K = t.shape[0]
+    ys, rs, ms, Ss = [], [], [], []
+    for M in moduli:
+        y = fold(x, M, K)
+        r = correlate(y, t, M) if corr == "direct" else correlate_fft(y, t, M)
+        if corr != "direct" and x.dtype.kind == "i" and t.dtype.kind == "i":
+            r = np.rint(r).astype(np.int64)
+        m = argmax_first(r)
+        ys.append(y)
+        rs.append(r)
+        ms.append(m)
+        Ss.append(candidate_set(m, M, N))
+    I = sorted(set.intersection(*Ss))
+    if len(I) == 0:
+        shift, status = -1, EMPTY
+    elif len(I) == 1:
+        shift, status = I[0], FOUND
+    else:
+        scores = [tx_at(x, t, m) for m in I]
+        shift, status = I[scores.index(max(scores))], RESOLVED
+    score = tx_at(x, t, shift) if shift >= 0 else 0
+    return dict(moduli=tuple(moduli), ys=ys, rs=rs, ms=ms, Ss=Ss, I=I, shift=int(shift), status=status,
+                n_cand=len(I), score=score)
+
+
 def match_query(q, corr: str = "direct") -> Dict:
     """Plan + FTM for a workloads.Query-like object (q.meta["thm2"]: the
     Thm. 2 sampling variant)."""
-    M1, M2 = plan(q.N, q.K, q.mode, q.M1, q.M2, q.allow_ambig)
     x = decode(q.x, q.xdtype, q.N)
+    if q.meta.get("three"):
+        Ms = plan3(q.N, q.K, q.mode, q.M1, q.M2, q.meta.get("M3", 0), q.allow_ambig)
+        return ftm_multi(x, q.t, Ms, corr=corr)
+    M1, M2 = plan(q.N, q.K, q.mode, q.M1, q.M2, q.allow_ambig)
     if q.meta.get("thm2"):
         return ftm_thm2(x, q.t, M1, M2)
     return ftm(x, q.t, M1, M2, corr=corr)

@@ -411,3 +411,55 @@ def test_thm2_window_inside_a_block():
     assert r[k_star % M] == sum(int((O.circ(tM) @ b)[k_star % M]) for b in blocks)
     assert k_star in O.candidate_set_thm2(k_star % M, M, N)
     assert all(v < N for v in O.candidate_set_thm2(M - 1, M, N - 3))
+
+
+# ---------------------------------------------------------------------------
+# Thm. 4 with three moduli: the intersection of the three candidate sets is
+# checked exhaustively against the CRT (every shift of small signals is
+# recovered, and only it when M1 M2 M3 >= N); the chosen moduli are pairwise
+# co-prime and reach N; three moduli recover a planted shift where K(K+1) <= N
+# leaves two moduli ambiguous.
+# ---------------------------------------------------------------------------
+
+def test_three_moduli_crt_exhaustive():
+    for (M1, M2, M3) in [(3, 4, 5), (5, 6, 7), (7, 8, 9)]:
+        for N in (M1 * M2 * M3 - 5, M1 * M2 * M3, M1 * M2 * M3 + 9):
+            for m in range(0, N, max(1, N // 37)):
+                Ss = [O.candidate_set(m % M, M, N) for M in (M1, M2, M3)]
+                I = set.intersection(*Ss)
+                assert m in I
+                if M1 * M2 * M3 >= N:
+                    # naturals are unique mod M1 M2 M3 (Thm. 4); any other
+                    # member is the wrapped member of one of the sets
+                    nat = [v for v in I if v % M1 == m % M1 and v % M2 == m % M2 and v % M3 == m % M3]
+                    assert nat == [m]
+                    wrapped = {m % M + (-(-N // M) - 1) * M - N for M in (M1, M2, M3)}
+                    assert all(v == m or v in wrapped for v in I)
+
+
+@pytest.mark.parametrize("N,K,mode", [(10 ** 6, 64, "paper"), (10 ** 6, 100, "auto"), (5000, 7, "paper")])
+def test_three_moduli_plan(N, K, mode):
+    M1, M2, M3 = O.plan3(N, K, mode, allow_ambig=True)
+    assert min(M1, M2, M3) >= K and M1 % 2 == 1
+    assert math.gcd(M1, M2) == math.gcd(M1, M3) == math.gcd(M2, M3) == 1
+    if mode == "auto":
+        assert M1 * M2 * M3 > N
+
+
+def test_three_moduli_recover_where_two_are_ambiguous():
+    # a strong planted window in weak noise, so that step 7 succeeds for
+    # every modulus although K (K+1) = 66306 < N: two moduli then leave
+    # several members of S1 ∩ S2, three leave exactly the planted shift
+    rng = np.random.default_rng(8)
+    N, K = 300000, 257
+    x = 0.01 * rng.standard_normal(N)
+    k_star = 123457
+    t = np.where(rng.random(K) < 0.5, 1.0, -1.0)
+    x[(np.arange(K) + k_star) % N] = t
+    two = O.ftm(x, t, K, K + 1)
+    assert two["m1"] == k_star % K and two["m2"] == k_star % (K + 1)
+    assert two["n_cand"] > 1 and k_star in two["I"]
+    M1, M2, M3 = O.plan3(N, K, "paper", allow_ambig=True)   # 257 * 258 * 259 > N
+    assert M1 * M2 * M3 > N
+    three = O.ftm_multi(x, t, (M1, M2, M3))
+    assert three["n_cand"] == 1 and three["shift"] == k_star and three["status"] == O.FOUND
