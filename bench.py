@@ -279,7 +279,7 @@ def run_native(args):
     bh = tm.Batch([dict(x=None, t=None, N=q.N, K=q.K, xdtype="i8", mode="paper") for q in qs], host_inputs=True)
     xh = [torch.from_numpy(q.x).pin_memory() for q in qs]
     th = [torch.from_numpy(q.t).pin_memory() for q in qs]
-    oh = torch.zeros(QUERIES * 6, dtype=torch.int64).pin_memory()
+    oh = torch.zeros(QUERIES * tm.RESULT_BYTES // 8, dtype=torch.int64).pin_memory()
     bh.run_host(xh, th, oh)
     e2e_steps = max(3, min(20, K // 50))
     if world > 1:
@@ -317,7 +317,7 @@ def run_native(args):
                          "traffic": traffic, "algorithmic_bytes_per_launch": in_bytes,
                          "fold_ms": float(fold_ms.mean()), "corr_ms": float((step_ms - fold_ms).mean())},
             "e2e": {"value": world * QUERIES * e2e_steps / e2e_s, "unit": "queries/s",
-                    "h2d_bytes_per_step": in_bytes + QUERIES * K_T * 4, "d2h_bytes_per_step": QUERIES * 48,
+                    "h2d_bytes_per_step": in_bytes + QUERIES * K_T * 4, "d2h_bytes_per_step": QUERIES * tm.RESULT_BYTES,
                     "api": "tm_batch_run_host (pinned host buffers)", "matches_device_run": e2e_ok},
             "gpu_launches": K * launches,
             "clocks": clk,

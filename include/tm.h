@@ -72,6 +72,14 @@ typedef enum { TM_MODE_AUTO = 0, TM_MODE_PAPER = 1, TM_MODE_EXPLICIT = 2 } tm_mo
  * (y extended periodically); candidate positions in the padding are
  * dropped in step 8. */
 #define TM_THM2_SAMPLING 0x2u
+/* Plan flag: step 2 with three pairwise co-prime moduli M1 < M2 < M3 (Thm.
+ * 4: the residues determine the shift once M1 M2 M3 > N, which holds for
+ * much smaller K than M1 M2 > N). PAPER: c, c+1, c+2 from the least odd
+ * c >= K; AUTO: from the least odd c >= max(K, s), s(s+1)(s+2) > N;
+ * EXPLICIT: M1, M2, M3 as given. Steps 3-8 run for each modulus and step 9
+ * intersects the three candidate sets. FFT lengths up to 16384; no
+ * slices, no Thm. 2 sampling with it. */
+#define TM_THREE_MODULI 0x4u
 
 /* tm_result.status values (low byte) and flag bits. */
 #define TM_FOUND 0      /* |S1 ∩ S2| = 1 */
@@ -89,7 +97,9 @@ typedef struct {
   int32_t xdtype;  /* tm_dtype */
   int32_t mode;    /* tm_mode */
   int32_t M1, M2;  /* only read for TM_MODE_EXPLICIT */
-  uint32_t flags;  /* TM_ALLOW_AMBIG */
+  uint32_t flags;  /* TM_ALLOW_AMBIG, TM_THM2_SAMPLING, TM_THREE_MODULI */
+  int32_t M3;      /* only read for TM_MODE_EXPLICIT with TM_THREE_MODULI */
+  int32_t reserved;
 } tm_plan_desc;
 
 typedef struct {
@@ -99,16 +109,22 @@ typedef struct {
   int64_t L1, L2;  /* ceil(N/M1), ceil(N/M2): terms per fold entry (Eq. (2)) */
   int32_t P;       /* FFT length: the least power of two >= max(M1,M2)+K-1 */
   int32_t max_cand;/* bound on |S1 ∩ S2|: ceil(N/(M1*M2)) + 2 */
+  int32_t M3;      /* third modulus (TM_THREE_MODULI), else 0 */
+  int32_t reserved;
+  int64_t L3;
 } tm_plan_info;
 
-/* One matching result (48 bytes), written to device memory. */
+/* One matching result (64 bytes), written to device memory. */
 typedef struct {
   int64_t shift;   /* recovered m^ in [0, N), or -1 (TM_EMPTY) */
   int32_t status;  /* TM_FOUND / TM_EMPTY / TM_RESOLVED | TM_RF_* flags */
-  int32_t n_cand;  /* |S1 ∩ S2| */
+  int32_t n_cand;  /* |S1 ∩ S2| (∩ S3 with TM_THREE_MODULI) */
   int32_t m1, m2;  /* step-7 maxima m~1 < M1, m~2 < M2 */
   double r1, r2;   /* exact r_{M1}[m~1], r_{M2}[m~2] (rescored, see below) */
   double score;    /* exact (Tx)_shift, 0 when shift = -1 */
+  int32_t m3;      /* TM_THREE_MODULI: m~3 < M3 and its exact r; else 0 */
+  int32_t reserved;
+  double r3;
 } tm_result;
 
 /* One query of a batch. */
@@ -121,6 +137,8 @@ typedef struct {
   int32_t mode;
   int32_t M1, M2;
   uint32_t flags;
+  int32_t M3;
+  int32_t reserved;
 } tm_query;
 
 /* ------------------------------------------------------------------ misc */
@@ -234,12 +252,13 @@ TM_API tm_status tm_batch_graph_capture(tm_batch_t b, tm_result* out_dev);
 /* Launch the captured graph on a stream: the same work as tm_batch_run in
  * one graph launch. TM_EINVAL without a capture. */
 TM_API tm_status tm_batch_graph_launch(tm_batch_t b, tm_stream_t stream);
-/* Device pointers to query i's folds from the last run: y[0..P) for M1 then
- * y[P..2P) for M2, entries k < M_j+K-1 valid. int32 for +-1 signals,
- * float32 for real signals (*is_float set accordingly). */
+/* Device pointers to query i's folds from the last run: y[0..P) for M1,
+ * y[P..2P) for M2 (and y[2P..3P) for M3 with TM_THREE_MODULI), entries
+ * k < M_j+K-1 valid. int32 for +-1 signals, float32 for real signals
+ * (*is_float set accordingly). */
 TM_API tm_status tm_batch_folds(tm_batch_t b, int32_t i, void** y_dev, int32_t* is_float);
 /* Device pointer to query i's FFT correlations from the last run (needs
- * TM_BATCH_KEEP_CORR): r[0..M1) then r[P..P+M2), float32. */
+ * TM_BATCH_KEEP_CORR): r[0..M1), r[P..P+M2) (and r[2P..2P+M3)), float32. */
 TM_API tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r_dev);
 /* Number of CUDA kernels one tm_batch_run launches, and fold CTAs. */
 TM_API tm_status tm_batch_stats(tm_batch_t b, int32_t* launches_per_run, int32_t* fold_ctas,

@@ -23,6 +23,7 @@ TM_I8_PM1, TM_BITS_PM1, TM_F16, TM_F32 = range(4)
 TM_MODE_AUTO, TM_MODE_PAPER, TM_MODE_EXPLICIT = range(3)
 TM_ALLOW_AMBIG = 0x1
 TM_THM2_SAMPLING = 0x2
+TM_THREE_MODULI = 0x4
 TM_FOUND, TM_EMPTY, TM_RESOLVED = 0, 1, 2
 TM_RF_FULL_RESCORE = 0x100
 TM_RF_DEVICE_ERROR = 0x200
@@ -36,28 +37,30 @@ MODE_CODES = {"auto": TM_MODE_AUTO, "paper": TM_MODE_PAPER, "explicit": TM_MODE_
 
 class tm_plan_desc(C.Structure):
     _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("xdtype", C.c_int32), ("mode", C.c_int32),
-                ("M1", C.c_int32), ("M2", C.c_int32), ("flags", C.c_uint32)]
+                ("M1", C.c_int32), ("M2", C.c_int32), ("flags", C.c_uint32), ("M3", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class tm_plan_info(C.Structure):
     _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("xdtype", C.c_int32), ("M1", C.c_int32),
                 ("M2", C.c_int32), ("L1", C.c_int64), ("L2", C.c_int64), ("P", C.c_int32),
-                ("max_cand", C.c_int32)]
+                ("max_cand", C.c_int32), ("M3", C.c_int32), ("reserved", C.c_int32), ("L3", C.c_int64)]
 
 
 class tm_result(C.Structure):
     _fields_ = [("shift", C.c_int64), ("status", C.c_int32), ("n_cand", C.c_int32), ("m1", C.c_int32),
-                ("m2", C.c_int32), ("r1", C.c_double), ("r2", C.c_double), ("score", C.c_double)]
+                ("m2", C.c_int32), ("r1", C.c_double), ("r2", C.c_double), ("score", C.c_double),
+                ("m3", C.c_int32), ("reserved", C.c_int32), ("r3", C.c_double)]
 
 
 class tm_query(C.Structure):
     _fields_ = [("x", C.c_void_p), ("t", C.c_void_p), ("N", C.c_int64), ("K", C.c_int32),
                 ("xdtype", C.c_int32), ("mode", C.c_int32), ("M1", C.c_int32), ("M2", C.c_int32),
-                ("flags", C.c_uint32)]
+                ("flags", C.c_uint32), ("M3", C.c_int32), ("reserved", C.c_int32)]
 
 
 RESULT_BYTES = C.sizeof(tm_result)
-assert RESULT_BYTES == 48
+assert RESULT_BYTES == 64
 
 # name -> (restype, argtypes)
 _SIGS = {
@@ -110,7 +113,7 @@ def tm_match_noalloc(x, t, out, N: int, K: int, xdtype: str = "i8", mode: str = 
     (its scratch is a fixed array inside the library; calls must not
     overlap on the GPU). x, t, out: CUDA tensors as for Plan.match."""
     import torch
-    d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2, TM_ALLOW_AMBIG if allow_ambig else 0)
+    d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2, TM_ALLOW_AMBIG if allow_ambig else 0, 0, 0)
     sp = _stream_ptr(stream) if (stream is not None or torch.cuda.is_available()) else None
     _check(lib().tm_match_noalloc(C.byref(d), x.data_ptr(), t.data_ptr(), out.data_ptr(), sp), "tm_match_noalloc")
 
@@ -168,8 +171,9 @@ class Plan:
     """tm_plan_create / tm_plan_get_info / tm_match / tm_plan_destroy."""
 
     def __init__(self, N: int, K: int, xdtype: str = "i8", mode: str = "paper", M1: int = 0, M2: int = 0,
-                 allow_ambig: bool = False, thm2: bool = False):
-        d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2, _plan_flags(allow_ambig, thm2))
+                 allow_ambig: bool = False, thm2: bool = False, three: bool = False, M3: int = 0):
+        d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2, _plan_flags(allow_ambig, thm2, three),
+                         M3, 0)
         h = C.c_void_p()
         _check(lib().tm_plan_create(C.byref(d), C.byref(h)), "tm_plan_create")
         self._h = h
@@ -178,7 +182,7 @@ class Plan:
         self.info = {f: getattr(info, f) for f, _ in tm_plan_info._fields_}
 
     def match(self, x, t, out, stream=None):
-        """x, t, out: CUDA tensors (out: >= 48 bytes, e.g. torch.empty(6, dtype=torch.int64))."""
+        """x, t, out: CUDA tensors (out: >= 64 bytes, e.g. result_buffer(1))."""
         _check(lib().tm_match(self._h, x.data_ptr(), t.data_ptr(), out.data_ptr(), _stream_ptr(stream)), "tm_match")
 
     # ---- slices of one signal (tm_fold_slice / tm_correlate_folds / tm_score_slice)
@@ -189,7 +193,7 @@ class Plan:
                "tm_fold_slice")
 
     def correlate_folds(self, y, t, out, stream=None):
-        """Steps 4-8 from complete folds y; out: 48-byte result buffer (CUDA)."""
+        """Steps 4-8 from complete folds y; out: one-result buffer (CUDA)."""
         _check(lib().tm_correlate_folds(self._h, y.data_ptr(), t.data_ptr(), out.data_ptr(), _stream_ptr(stream)),
                "tm_correlate_folds")
 
@@ -216,13 +220,15 @@ def tm_plan_create(N, K, xdtype="i8", mode="paper", M1=0, M2=0, allow_ambig=Fals
     return Plan(N, K, xdtype, mode, M1, M2, allow_ambig)
 
 
-def _plan_flags(allow_ambig=False, thm2=False) -> int:
-    return (TM_ALLOW_AMBIG if allow_ambig else 0) | (TM_THM2_SAMPLING if thm2 else 0)
+def _plan_flags(allow_ambig=False, thm2=False, three=False) -> int:
+    return (TM_ALLOW_AMBIG if allow_ambig else 0) | (TM_THM2_SAMPLING if thm2 else 0) | \
+        (TM_THREE_MODULI if three else 0)
 
 
-def _query_struct(x_ptr, t_ptr, N, K, xdtype, mode, M1=0, M2=0, allow_ambig=False, thm2=False) -> tm_query:
+def _query_struct(x_ptr, t_ptr, N, K, xdtype, mode, M1=0, M2=0, allow_ambig=False, thm2=False, three=False,
+                  M3=0) -> tm_query:
     return tm_query(x_ptr, t_ptr, int(N), int(K), DTYPE_CODES[xdtype], MODE_CODES[mode], int(M1), int(M2),
-                    _plan_flags(allow_ambig, thm2))
+                    _plan_flags(allow_ambig, thm2, three), int(M3), 0)
 
 
 class Batch:
@@ -240,7 +246,8 @@ class Batch:
             xp = s["x"].data_ptr() if s.get("x") is not None else None
             tp = s["t"].data_ptr() if s.get("t") is not None else None
             arr[i] = _query_struct(xp, tp, s["N"], s["K"], s.get("xdtype", "i8"), s.get("mode", "paper"),
-                                   s.get("M1", 0), s.get("M2", 0), s.get("allow_ambig", False), s.get("thm2", False))
+                                   s.get("M1", 0), s.get("M2", 0), s.get("allow_ambig", False), s.get("thm2", False),
+                                   s.get("three", False), s.get("M3", 0))
         self._arr = arr
         flags = (TM_BATCH_KEEP_CORR if keep_corr else 0) | (TM_BATCH_HOST_INPUTS if host_inputs else 0)
         h = C.c_void_p()
@@ -248,7 +255,8 @@ class Batch:
         self._h = h
         # per-query plan information (host-only planner calls)
         self.infos = [Plan(s["N"], s["K"], s.get("xdtype", "i8"), s.get("mode", "paper"), s.get("M1", 0),
-                           s.get("M2", 0), s.get("allow_ambig", False), s.get("thm2", False)).info for s in specs]
+                           s.get("M2", 0), s.get("allow_ambig", False), s.get("thm2", False), s.get("three", False),
+                           s.get("M3", 0)).info for s in specs]
 
     def set_inputs(self, xs, ts):
         for i in range(self.n):
@@ -280,7 +288,7 @@ class Batch:
         _check(lib().tm_batch_graph_launch(self._h, _stream_ptr(stream)), "tm_batch_graph_launch")
 
     def run_host(self, x_host: Sequence, t_host: Sequence, out_host, stream=None):
-        """x_host, t_host: CPU tensors (pinned for speed); out_host: CPU tensor of n*48 bytes."""
+        """x_host, t_host: CPU tensors (pinned for speed); out_host: CPU tensor of n*RESULT_BYTES bytes."""
         xs = (C.c_void_p * self.n)(*[x.data_ptr() for x in x_host])
         ts = (C.c_void_p * self.n)(*[t.data_ptr() for t in t_host])
         _check(lib().tm_batch_run_host(self._h, xs, ts, out_host.data_ptr(), _stream_ptr(stream)),
@@ -292,14 +300,17 @@ class Batch:
         _check(lib().tm_batch_folds(self._h, i, C.byref(p), C.byref(f)), "tm_batch_folds")
         return p.value, bool(f.value)
 
+    def _nmod(self, i: int) -> int:
+        return 3 if self.infos[i]["M3"] else 2
+
     def folds(self, i: int):
-        """Query i's folds as a device tensor view: [0, P) for M1, [P, 2P) for M2."""
+        """Query i's folds as a device tensor view: [0, P) for M1, [P, 2P) for M2 (and [2P, 3P) for M3)."""
         ptr, is_float = self.folds_ptr(i)
-        return device_view(ptr, 2 * self.infos[i]["P"], "<f4" if is_float else "<i4")
+        return device_view(ptr, self._nmod(i) * self.infos[i]["P"], "<f4" if is_float else "<i4")
 
     def corr(self, i: int):
-        """Query i's FFT correlations (float32 view): r1 at [0, M1), r2 at [P, P+M2)."""
-        return device_view(self.corr_ptr(i), 2 * self.infos[i]["P"], "<f4")
+        """Query i's FFT correlations (float32 view): r1 at [0, M1), r2 at [P, P+M2) (r3 at [2P, 2P+M3))."""
+        return device_view(self.corr_ptr(i), self._nmod(i) * self.infos[i]["P"], "<f4")
 
     def corr_ptr(self, i: int):
         p = C.c_void_p()
@@ -341,7 +352,7 @@ def tm_match_batch(specs, out, stream=None):
 
 
 def decode_results(buf) -> List[dict]:
-    """tm_result records from a CPU tensor / bytes-like of n*48 bytes."""
+    """tm_result records from a CPU tensor / bytes-like of n*RESULT_BYTES bytes."""
     import numpy as np
     raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
     n = len(raw) // RESULT_BYTES
@@ -427,12 +438,12 @@ class Server:
         return sid.value
 
     def submit(self, sig_id: int, t, tag: int, mode: str = "paper", M1: int = 0, M2: int = 0,
-               allow_ambig: bool = False, thm2: bool = False) -> int:
+               allow_ambig: bool = False, thm2: bool = False, three: bool = False) -> int:
         """Queue one request; returns the status (TM_OK, TM_EAGAIN, ...) without raising for TM_EAGAIN."""
         import numpy as np
         tt = np.ascontiguousarray(t, dtype=np.float32)
         st = lib().tm_serve_submit(self._h, sig_id, tt.ctypes.data, int(tt.shape[0]), MODE_CODES[mode], M1, M2,
-                                   _plan_flags(allow_ambig, thm2), tag)
+                                   _plan_flags(allow_ambig, thm2, three), tag)
         if st not in (TM_OK, TM_EAGAIN):
             raise TMError(st, "tm_serve_submit")
         return st

@@ -61,40 +61,76 @@ int64_t signal_bytes(int32_t dtype, int64_t N) {
 }
 
 // Algorithm 1 step 2 and the derived sizes.
+// Least integer s with s (s+1) (s+2) > N.
+int64_t least_s3(int64_t N) {
+  int64_t s = std::max<int64_t>(1, int64_t(std::cbrt(double(N))) - 2);
+  while (s * (s + 1) * (s + 2) <= N) ++s;
+  while (s > 1 && (s - 1) * s * (s + 1) > N) --s;
+  return s;
+}
+
 tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t M1, int32_t M2, uint32_t flags,
-                    PlanCore& pc) {
+                    PlanCore& pc, int32_t M3) {
   if (N < 1 || K < 1 || K > N) return fail(TM_EINVAL, "need 1 <= K <= N");
   if (xdtype < TM_I8_PM1 || xdtype > TM_F32) return fail(TM_EINVAL, "unknown signal dtype");
-  int64_t m1, m2;
-  if (mode == TM_MODE_PAPER) { m1 = K; m2 = int64_t(K) + 1; }
-  else if (mode == TM_MODE_AUTO) { m1 = std::max<int64_t>(K, least_s(N)); m2 = m1 + 1; }
-  else if (mode == TM_MODE_EXPLICIT) { m1 = M1; m2 = M2; }
+  const bool three = (flags & TM_THREE_MODULI) != 0;
+  if (three && (flags & TM_THM2_SAMPLING)) return fail(TM_EUNSUPPORTED, "three moduli with the Thm. 2 sampling");
+  int64_t m[3] = {0, 0, 0};
+  if (three) {
+    if (mode == TM_MODE_PAPER || mode == TM_MODE_AUTO) {
+      int64_t c = mode == TM_MODE_PAPER ? K : std::max<int64_t>(K, least_s3(N));
+      c += 1 - (c & 1);   // odd: c, c+1, c+2 pairwise co-prime
+      m[0] = c; m[1] = c + 1; m[2] = c + 2;
+    } else if (mode == TM_MODE_EXPLICIT) {
+      m[0] = M1; m[1] = M2; m[2] = M3;
+    } else {
+      return fail(TM_EINVAL, "unknown mode");
+    }
+  } else if (mode == TM_MODE_PAPER) { m[0] = K; m[1] = int64_t(K) + 1; }
+  else if (mode == TM_MODE_AUTO) { m[0] = std::max<int64_t>(K, least_s(N)); m[1] = m[0] + 1; }
+  else if (mode == TM_MODE_EXPLICIT) { m[0] = M1; m[1] = M2; }
   else return fail(TM_EINVAL, "unknown mode");
-  if (m1 < K || m2 < K) return fail(TM_EINVAL, "step 2 needs M1 >= K and M2 >= K");
-  if (m1 > 2 * N || m2 > 2 * N) return fail(TM_EINVAL, "moduli above 2N are not meaningful");
-  if (gcd64(m1, m2) != 1) return fail(TM_EINVAL, "step 2 needs co-prime M1 and M2");
-  if (m1 * m2 <= N && !(flags & TM_ALLOW_AMBIG))
-    return fail(TM_EINVAL, "step 2 needs M1*M2 > N (set TM_ALLOW_AMBIG to accept several solutions)");
-  const int64_t need = std::max(m1, m2) + K - 1;
+  const int nm = three ? 3 : 2;
+  for (int j = 0; j < nm; ++j) {
+    if (m[j] < K) return fail(TM_EINVAL, "step 2 needs every modulus >= K");
+    if (m[j] > 2 * N) return fail(TM_EINVAL, "moduli above 2N are not meaningful");
+  }
+  for (int i = 0; i < nm; ++i)
+    for (int j = i + 1; j < nm; ++j)
+      if (gcd64(m[i], m[j]) != 1) return fail(TM_EINVAL, "step 2 needs pairwise co-prime moduli");
+  // the product of the moduli must exceed N (checked without overflow)
+  bool above = m[0] > N / m[1] || m[0] * m[1] > N;
+  if (three && !above) above = m[0] * m[1] > N / m[2] || m[0] * m[1] * m[2] > N;
+  if (!above && !(flags & TM_ALLOW_AMBIG))
+    return fail(TM_EINVAL, "step 2 needs the moduli's product above N (set TM_ALLOW_AMBIG to accept several solutions)");
+  int64_t mmax = 0;
+  for (int j = 0; j < nm; ++j) mmax = std::max(mmax, m[j]);
+  const int64_t need = mmax + K - 1;
   int32_t logP = 0;
   while ((int64_t(1) << logP) < need) ++logP;
-  if (logP > kLogPMaxBlocked) return fail(TM_EUNSUPPORTED, "FFT length above 65536 (max(M1,M2)+K-1 > 65536)");
+  if (logP > kLogPMaxBlocked) return fail(TM_EUNSUPPORTED, "FFT length above 65536 (max(M)+K-1 > 65536)");
+  if (three && logP > kLogPMax) return fail(TM_EUNSUPPORTED, "three moduli: FFT lengths up to 16384");
   if (signal_bytes(xdtype, N) > kMaxQueryBytes) return fail(TM_EUNSUPPORTED, "signal larger than 2^31-2^16 bytes");
-  pc.N = N; pc.K = K; pc.xdtype = xdtype;
-  pc.M[0] = int32_t(m1); pc.M[1] = int32_t(m2);
-  pc.L[0] = ceil_div(N, m1); pc.L[1] = ceil_div(N, m2);
+  pc.N = N; pc.K = K; pc.xdtype = xdtype; pc.nmod = nm;
+  for (int j = 0; j < 3; ++j) {
+    pc.M[j] = int32_t(m[j]);
+    pc.L[j] = j < nm ? ceil_div(N, m[j]) : 0;
+  }
   pc.logP = logP; pc.P = 1 << logP;
-  pc.inv = int32_t(mod_inverse(m1, m2));
+  pc.inv = int32_t(mod_inverse(m[0], m[1]));
+  pc.inv3 = three ? int32_t(mod_inverse((m[0] % m[2]) * (m[1] % m[2]) % m[2], m[2])) : 0;
   if (xdtype == TM_BITS_PM1 && N > kMaxQueryBytes)
     return fail(TM_EUNSUPPORTED, "bit-packed signal longer than 2^31-2^16 elements");
   const FoldGeom g = fold_geom(xdtype);
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < 3; ++j) {
+    if (j >= nm) { pc.R[j] = 1; pc.Mp[j] = 0; continue; }
     pc.R[j] = int32_t(std::max<int64_t>(1, ceil_div(g.min_mp, pc.M[j])));
     pc.Mp[j] = pc.R[j] * pc.M[j];
-    if (fold_units_per_lane(pc.Mp[j], j == 0 ? kFoldWarps0 : kFoldWarps1, g.E) > g.jmax)
+    if (fold_units_per_lane(pc.Mp[j], fold_warp_count(nm, j), g.E) > g.jmax)
       return fail(TM_EUNSUPPORTED, "modulus too large for the fold kernel of this signal type");
   }
-  pc.max_cand = ceil_div(N, m1 * m2) + 2;
+  const long double prod = (long double)m[0] * (long double)m[1] * (three ? (long double)m[2] : 1.0L);
+  pc.max_cand = int64_t(std::ceil((long double)N / prod)) + 3;
   pc.flags = flags;
   return TM_OK;
 }
@@ -224,7 +260,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
   b->q.assign(q, q + n);
   b->pc.resize(n);
   for (int i = 0; i < n; ++i) {
-    tm_status st = make_plan(q[i].N, q[i].K, q[i].xdtype, q[i].mode, q[i].M1, q[i].M2, q[i].flags, b->pc[i]);
+    tm_status st = make_plan(q[i].N, q[i].K, q[i].xdtype, q[i].mode, q[i].M1, q[i].M2, q[i].flags, b->pc[i], q[i].M3);
     if (st != TM_OK) {
       g_err = "query " + std::to_string(i) + ": " + g_err;
       return st;
@@ -264,16 +300,21 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
       FoldQ& f = b->fq[pos];
       f.goff = W;
       f.nbytes = int32_t(nb);
-      for (int j = 0; j < 2; ++j) f.Mp[j] = p.Mp[j];
-      f.moff[0] = 0;
-      f.moff[1] = int32_t(pad16(p.Mp[0]));
-      f.stride = int32_t(pad16(p.Mp[0]) + pad16(p.Mp[1]));
+      f.nmod = p.nmod;
+      int32_t off = 0;
+      for (int j = 0; j < 3; ++j) {
+        f.Mp[j] = j < p.nmod ? p.Mp[j] : 0;
+        f.moff[j] = off;
+        off += j < p.nmod ? int32_t(pad16(p.Mp[j])) : 0;
+      }
+      f.stride = off;
       W += nb;
       // rows of Mp elements per share stay below the lane counters' capacity
       max_share = std::min<int64_t>(max_share, int64_t(kFoldMaxRowsPerSlot - 2) *
-                                                   std::min(p.Mp[0], p.Mp[1]) * geo.bits / 8);
-      for (int j = 0; j < 2; ++j)
-        gr.jmax = std::max<int32_t>(gr.jmax, fold_units_per_lane(p.Mp[j], j == 0 ? kFoldWarps0 : kFoldWarps1, geo.E));
+                                                   std::min(p.Mp[0], p.nmod == 3 ? std::min(p.Mp[1], p.Mp[2]) : p.Mp[1]) *
+                                                   geo.bits / 8);
+      for (int j = 0; j < p.nmod; ++j)
+        gr.jmax = std::max<int32_t>(gr.jmax, fold_units_per_lane(p.Mp[j], fold_warp_count(p.nmod, j), geo.E));
     }
     if (gr.count == 0) continue;
     gr.W = W;
@@ -309,17 +350,18 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     const FoldQ& f = b->fq[b->fold_of[i]];
     CorrQ& c = b->cq[i];
     c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
-    for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
-    c.P = p.P; c.logP = p.logP; c.inv = p.inv;
+    c.nmod = p.nmod;
+    for (int j = 0; j < 3; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
+    c.P = p.P; c.logP = p.logP; c.inv = p.inv; c.inv3 = p.inv3;
     c.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
     c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
     c.nslots = f.nslots; c.stride = f.stride; c.part = f.part;
-    c.y_off = yo; yo += 2ll * p.P;
+    c.y_off = yo; yo += int64_t(p.nmod) * p.P;
     const bool blocked = p.P > kPMax;   // correlation in blocks (overlap-save), r kept in global memory
     c.spec_off = so;
     so += blocked ? int64_t(blocked_spectra(p.K, std::max(p.M[0], p.M[1]))) * kPMax : p.P;
     c.r_off = ((flags & TM_BATCH_KEEP_CORR) || blocked) ? ro : -1;
-    if (c.r_off >= 0) ro += 2ll * p.P;
+    if (c.r_off >= 0) ro += int64_t(p.nmod) * p.P;
     if (!blocked) b->maxP = std::max(b->maxP, p.P);
   }
   b->y_elems = yo; b->spec_elems = so; b->r_elems = ro;
@@ -456,7 +498,8 @@ tm_status tm_plan_create(const tm_plan_desc* desc, tm_plan_t* out) {
   tm_plan_t p = new (std::nothrow) tm_plan_s();
   if (!p) return fail(TM_ENOMEM, "host allocation");
   p->d = *desc;
-  tm_status st = make_plan(desc->N, desc->K, desc->xdtype, desc->mode, desc->M1, desc->M2, desc->flags, p->pc);
+  tm_status st = make_plan(desc->N, desc->K, desc->xdtype, desc->mode, desc->M1, desc->M2, desc->flags, p->pc,
+                           desc->M3);
   if (st != TM_OK) { delete p; return st; }
   *out = p;
   return TM_OK;
@@ -467,6 +510,9 @@ tm_status tm_plan_get_info(tm_plan_t p, tm_plan_info* info) {
   info->N = p->pc.N; info->K = p->pc.K; info->xdtype = p->pc.xdtype;
   info->M1 = p->pc.M[0]; info->M2 = p->pc.M[1];
   info->L1 = p->pc.L[0]; info->L2 = p->pc.L[1];
+  info->M3 = p->pc.nmod == 3 ? p->pc.M[2] : 0;
+  info->reserved = 0;
+  info->L3 = p->pc.nmod == 3 ? p->pc.L[2] : 0;
   info->P = p->pc.P;
   info->max_cand = int32_t(std::min<int64_t>(p->pc.max_cand, INT32_MAX));
   return TM_OK;
@@ -538,6 +584,7 @@ tm_status tm_fold_slice(tm_plan_t p, const void* x, int64_t n0, int64_t len, voi
   if (reinterpret_cast<uintptr_t>(x) & 15) return fail(TM_EINVAL, "x must be 16-byte aligned");
   if (pc.P > kPMax) return fail(TM_EUNSUPPORTED, "slices need P <= 16384");
   if (pc.flags & TM_THM2_SAMPLING) return fail(TM_EUNSUPPORTED, "slices use the sampling of Eq. (3)");
+  if (pc.nmod != 2) return fail(TM_EUNSUPPORTED, "slices use two moduli");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0, sms = 0;
   TM_CUDA(cudaGetDevice(&dev));
@@ -558,6 +605,7 @@ tm_status tm_fold_slice(tm_plan_t p, const void* x, int64_t n0, int64_t len, voi
   f.Mp[0] = pc.Mp[0]; f.Mp[1] = pc.Mp[1];
   f.moff[0] = 0; f.moff[1] = int32_t(pad16(pc.Mp[0]));
   f.stride = int32_t(pad16(pc.Mp[0]) + pad16(pc.Mp[1]));
+  f.nmod = 2;
   f.first_cta = 0;
   f.nslots = W > 0 ? int32_t(nctas) : 0;
   f.part = 0;
@@ -587,6 +635,7 @@ tm_status tm_correlate_folds(tm_plan_t p, const void* y, const float* t, tm_resu
   if (!p || !y || !t || !out) return fail(TM_EINVAL, "null argument");
   const PlanCore& pc = p->pc;
   if (pc.P > kPMax) return fail(TM_EUNSUPPORTED, "folds given: P <= 16384 only");
+  if (pc.nmod != 2) return fail(TM_EUNSUPPORTED, "folds given: two moduli");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0;
   TM_CUDA(cudaGetDevice(&dev));
@@ -596,7 +645,7 @@ tm_status tm_correlate_folds(tm_plan_t p, const void* y, const float* t, tm_resu
   SliceWs* w = nullptr;
   if ((st = slice_ws(p, 0, &w)) != TM_OK) return st;
   CorrQ c{};
-  c.x = nullptr; c.t = t; c.N = pc.N; c.K = pc.K; c.xdtype = pc.xdtype;
+  c.x = nullptr; c.t = t; c.N = pc.N; c.K = pc.K; c.xdtype = pc.xdtype; c.nmod = 2;
   for (int j = 0; j < 2; ++j) { c.M[j] = pc.M[j]; c.R[j] = pc.R[j]; c.L[j] = pc.L[j]; }
   c.P = pc.P; c.logP = pc.logP; c.inv = pc.inv;
   c.thm2 = (pc.flags & TM_THM2_SAMPLING) ? 1 : 0;
@@ -629,7 +678,7 @@ tm_status tm_match(tm_plan_t p, const void* x, const float* t, tm_result* out, t
   if (!p || !x || !t || !out) return fail(TM_EINVAL, "null argument");
   tm_query q;
   q.x = x; q.t = t; q.N = p->d.N; q.K = p->d.K; q.xdtype = p->d.xdtype; q.mode = p->d.mode;
-  q.M1 = p->d.M1; q.M2 = p->d.M2; q.flags = p->d.flags;
+  q.M1 = p->d.M1; q.M2 = p->d.M2; q.flags = p->d.flags; q.M3 = p->d.M3; q.reserved = 0;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!p->b) {
     tm_status st = batch_build(&q, 1, 0, &p->b);
@@ -948,8 +997,9 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   if (reinterpret_cast<uintptr_t>(x) & 15) return fail(TM_EINVAL, "x must be 16-byte aligned");
   if (reinterpret_cast<uintptr_t>(t) & 3) return fail(TM_EINVAL, "t must be 4-byte aligned");
   PlanCore p;
-  tm_status st = make_plan(desc->N, desc->K, desc->xdtype, desc->mode, desc->M1, desc->M2, desc->flags, p);
+  tm_status st = make_plan(desc->N, desc->K, desc->xdtype, desc->mode, desc->M1, desc->M2, desc->flags, p, desc->M3);
   if (st != TM_OK) return st;
+  if (p.nmod != 2) return fail(TM_EUNSUPPORTED, "the no-allocation entry point uses two moduli (use tm_match)");
   if (p.P > kPMax)
     return fail(TM_EUNSUPPORTED, "the no-allocation entry point handles FFT lengths up to 16384 (use tm_match)");
   if (signal_bytes(p.xdtype, p.N) > TM_NOALLOC_MAX_SIGNAL_BYTES)
@@ -979,6 +1029,7 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   f.nbytes = int32_t(W);
   f.Mp[0] = p.Mp[0]; f.Mp[1] = p.Mp[1];
   f.moff[0] = 0; f.moff[1] = int32_t(pad16(p.Mp[0]));
+  f.nmod = 2;
   f.stride = int32_t(stride);
   f.first_cta = 0;
   f.part = 0;
@@ -992,7 +1043,7 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
     f.nslots = lo + 1;
   }
   CorrQ c{};
-  c.x = x; c.t = t; c.N = p.N; c.K = p.K; c.xdtype = p.xdtype;
+  c.x = x; c.t = t; c.N = p.N; c.K = p.K; c.xdtype = p.xdtype; c.nmod = 2;
   for (int j = 0; j < 2; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
   c.P = p.P; c.logP = p.logP; c.inv = p.inv;
   c.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;

@@ -411,25 +411,48 @@ __device__ __forceinline__ float spectrum_max_bound(float Tc, int logP, float t2
   return 1.0001f * Tc + epsF * sqrtf(float(1 << logP)) * t2;
 }
 
-// Steps 7-9 for one query, shared by both correlation kernels: argmax of
-// r_j (rval(j, k) = r_j[k], j = 0 for M1, 1 for M2) with exact rescoring of
-// every entry within 2 delta of the maximum, the closed-form intersection
-// S1 ∩ S2 (crt.h), the exact (Tx)_m of its member(s) and the result record.
+// Step 7 candidates of each modulus of a query: the argmax of the FFT
+// values and every index within 2 delta of it.
+struct Cands {
+  int cand[3][kCandCap];
+  int ncand[3];
+};
+
+// Step 7 for modulus mj (rv(k) = r~_mj[k], k < M).
 template <class RFn>
-__device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, float delta, bool t_integral, float t1,
-                                   int maxy, RFn rval) {
+__device__ void collect_candidates(Cands& cs, int mj, int M, float delta, RFn rv) {
+  __shared__ float redv[kWarps];
+  __shared__ int redi[kWarps];
+  const int tid = threadIdx.x;
+  float bv = -INFINITY;
+  int bi = 0x7fffffff;
+  for (int k = tid; k < M; k += kCorrThreads) better(bv, bi, rv(k), k);
+  block_argmax(bv, bi, redv, redi);
+  if (tid == 0) cs.ncand[mj] = 0;
+  __syncthreads();
+  const float thr = bv - 2.0f * delta;
+  for (int k = tid; k < M; k += kCorrThreads) {
+    if (rv(k) >= thr) {
+      const int c = atomicAdd(&cs.ncand[mj], 1);
+      if (c < kCandCap) cs.cand[mj][c] = k;
+    }
+  }
+  __syncthreads();
+}
+
+// Steps 7-9 after the candidates of every modulus are collected: exact
+// rescoring of each candidate from the exported folds (the chosen index is
+// the exact argmax), the closed-form intersection of the candidate sets
+// (crt.h), the exact (Tx)_m of its member(s) and the result record.
+__device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integral, float t1, int maxy, Cands& cs) {
   __shared__ long long redl[kWarps];
   __shared__ double redd[kWarps];
   __shared__ long long redl4[4 * kWarps];
   __shared__ double redd4[4 * kWarps];
-  __shared__ float redv[kWarps];
-  __shared__ int redi[kWarps];
-  __shared__ int cand[2][kCandCap];
-  __shared__ int ncand[2];
   __shared__ double wbest_v[kWarps];
   __shared__ int64_t wbest_i[kWarps];
-  __shared__ int s_m[2];
-  __shared__ double s_r[2];
+  __shared__ int s_m[3];
+  __shared__ double s_r[3];
   __shared__ int s_flags;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int P = Q.P, K = Q.K;
@@ -437,7 +460,11 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
   const Sig sig{Q.x, Q.xdtype};
   const bool ints = is_int_dtype(Q.xdtype);
   const float* __restrict__ t = Q.t;
-  if (tid == 0) s_flags = 0;
+  if (tid == 0) {
+    s_flags = 0;
+    s_m[2] = 0;
+    s_r[2] = 0.0;
+  }
   __syncthreads();
   const bool exact_int = ints && t_integral;
   // int32 rescoring is exact when every partial sum stays below 2^31:
@@ -445,31 +472,9 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
   const bool small = exact_int && double(t1) * double(maxy) < 2.0e9;
   const void* yv = Q.y_in != nullptr ? Q.y_in : static_cast<const void*>(static_cast<const char*>(a.y) + Q.y_off * 4);
 
-  // step 7 for both moduli: the argmax of the FFT values and every index
-  // within 2 delta of it
-  for (int j = 0; j < 2; ++j) {
-    const int M = Q.M[j];
-    float bv = -INFINITY;
-    int bi = 0x7fffffff;
-    for (int k = tid; k < M; k += kCorrThreads) {
-      better(bv, bi, rval(j, k), k);
-    }
-    block_argmax(bv, bi, redv, redi);
-    if (tid == 0) ncand[j] = 0;
-    __syncthreads();
-    const float thr = bv - 2.0f * delta;
-    for (int k = tid; k < M; k += kCorrThreads) {
-      if (rval(j, k) >= thr) {
-        const int c = atomicAdd(&ncand[j], 1);
-        if (c < kCandCap) cand[j][c] = k;
-      }
-    }
-  }
-  __syncthreads();
-
   // exact rescoring of the candidates
-  for (int j = 0; j < 2; ++j) {
-    const int nc = ncand[j];
+  for (int j = 0; j < Q.nmod; ++j) {
+    const int nc = cs.ncand[j];
     const int32_t* yi = static_cast<const int32_t*>(yv) + int64_t(j) * P;
     const float* yf = static_cast<const float*>(yv) + int64_t(j) * P;
     if (nc <= kCandCap) {
@@ -480,7 +485,7 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
         const int nb = min(4, nc - c0);
         int jj[4];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) jj[b] = cand[j][c0 + (b < nb ? b : 0)];
+        for (int b = 0; b < 4; ++b) jj[b] = cs.cand[j][c0 + (b < nb ? b : 0)];
         double v[4];
         // loads for four indices i per thread go out before any is used
         constexpr int kU = 4;
@@ -560,10 +565,16 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
   }
 
   // ------------------------------------------------ e. steps 8-9
-  CrtSet cs = crt_intersect(N, Q.M[0], Q.M[1], Q.inv, s_m[0], s_m[1]);
-  if (Q.thm2) cs.nw = 0;   // wrapped members fall in the zero padding
-  const int64_t ncs = cs.nnat + cs.nw;
-  auto member = [&](int64_t c) -> int64_t { return c < cs.nnat ? cs.m0 + c * cs.step : cs.w[c - cs.nnat]; };
+  CrtSet crt;
+  if (Q.nmod == 3) {
+    const int64_t Ms[3] = {Q.M[0], Q.M[1], Q.M[2]}, ms[3] = {s_m[0], s_m[1], s_m[2]};
+    crt = crt_intersect3(N, Ms, Q.inv, Q.inv3, ms);
+  } else {
+    crt = crt_intersect(N, Q.M[0], Q.M[1], Q.inv, s_m[0], s_m[1]);
+  }
+  if (Q.thm2) crt.nw = 0;   // wrapped members fall in the zero padding
+  const int64_t ncs = crt.nnat + crt.nw;
+  auto member = [&](int64_t c) -> int64_t { return c < crt.nnat ? crt.m0 + c * crt.step : crt.w[c - crt.nnat]; };
   double best_v = 0.0;
   int64_t best_m = -1;
   const bool have_x = Q.x != nullptr;
@@ -621,8 +632,22 @@ __device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, fl
     res.m2 = s_m[1];
     res.r1 = s_r[0];
     res.r2 = s_r[1];
+    res.m3 = s_m[2];
+    res.reserved = 0;
+    res.r3 = s_r[2];
     a.out[qi] = res;
   }
+}
+
+// Steps 7-9 for two moduli whose FFT values are all available at once
+// (rval(j, k) = r~_j[k]).
+template <class RFn>
+__device__ void select_and_resolve(const CorrArgs& a, const CorrQ& Q, int qi, float delta, bool t_integral, float t1,
+                                   int maxy, RFn rval) {
+  __shared__ Cands cs;
+  collect_candidates(cs, 0, Q.M[0], delta, [&](int k) { return rval(0, k); });
+  collect_candidates(cs, 1, Q.M[1], delta, [&](int k) { return rval(1, k); });
+  resolve(a, Q, qi, t_integral, t1, maxy, cs);
 }
 
 // Steps 3 (completion) to 9 for query qi. The twiddle table and the pass
@@ -701,6 +726,12 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   }
   const float Tp = spectrum_max_bound(sqrtf(block_maxf(tc2, redf)), logP, t2);
 
+  // ------------------------------------------------ b-d, per pass: the first
+  // pass carries M1 (real part) and M2 (imaginary part) through one complex
+  // FFT pipeline, a second pass (three moduli) carries M3
+  __shared__ Cands cands;
+  int maxy_all = 0;
+  auto run_pass = [&](const int pass) {
   // ------------------------------------------------ b. folds
   // Loads are issued in batches (kB per thread) before their results are
   // used, so each pass waits for about one memory round trip.
@@ -721,16 +752,21 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       // the folds over k < M_j from a cache of this signal's folds (int32 or
       // float bits alike)
       const int32_t* yc = static_cast<const int32_t*>(Q.y_core);
-      for (int j = 0; j < 2; ++j)
-        for (int k = tid; k < Q.M[j]; k += kCorrThreads) ib[2 * pad_idx(k) + j] = yc[int64_t(j) * Q.core_pitch + k];
+      for (int j = 0; j < 2; ++j) {
+        const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);
+        if (mj < 0) continue;
+        for (int k = tid; k < Q.M[mj]; k += kCorrThreads) ib[2 * pad_idx(k) + j] = yc[int64_t(mj) * Q.core_pitch + k];
+      }
     } else if (ints) {
       // Partial slots hold counts of -1 (int8) or +1 (bits) entries per column
       // kp < Mp of the Mp-fold; column k of the M-fold gathers kp = k + r M,
       // r < R. Slot rows are padded to 16 columns, so a quad read at kp < Mp
       // stays inside the row; columns past Mp are dropped.
       for (int j = 0; j < 2; ++j) {
-        const int M = Q.M[j], Rr = Q.R[j], Mp = Rr * M;
-        const int32_t* part = a.partial + Q.part + Q.moff[j];
+      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
+      if (mj < 0) continue;
+        const int M = Q.M[mj], Rr = Q.R[mj], Mp = Rr * M;
+        const int32_t* part = a.partial + Q.part + Q.moff[mj];
         const int nq4 = (Mp + 3) >> 2;
         for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
           int4 c[4];
@@ -771,8 +807,10 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       // takes the wrap-around entry x_{k-Rw}
       const bool ones = Q.xdtype == TM_BITS_PM1;   // bit-packed slots count +1 entries, int8 slots -1 entries
       for (int j = 0; j < 2; ++j) {
-        const int M = Q.M[j];
-        const int L = int(Q.L[j]);
+      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
+      if (mj < 0) continue;
+        const int M = Q.M[mj];
+        const int L = int(Q.L[mj]);
         const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
         with_sig(Q.xdtype, Q.x, [&](auto sx) {
           for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
@@ -798,10 +836,12 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
     } else {
       // partial slots hold fp32 column sums, added in a fixed order
       for (int j = 0; j < 2; ++j) {
-        const int M = Q.M[j], Rr = Q.R[j];
-        const int L = int(Q.L[j]);
+      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
+      if (mj < 0) continue;
+        const int M = Q.M[mj], Rr = Q.R[mj];
+        const int L = int(Q.L[mj]);
         const int Rw = int(N - int64_t(L - 1) * M);
-        const float* pf = reinterpret_cast<const float*>(a.partial + Q.part + Q.moff[j]);
+        const float* pf = reinterpret_cast<const float*>(a.partial + Q.part + Q.moff[mj]);
         for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
           float acc[kB];
           with_sig(Q.xdtype, Q.x, [&](auto sx) {
@@ -836,7 +876,9 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
     if (tid == 0 && Q.y_core == nullptr) {
       for (int64_t n = Q.nelem16; n < N; ++n) {
         for (int j = 0; j < 2; ++j) {
-          const int e = 2 * pad_idx(int(n % Q.M[j])) + j;
+      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
+      if (mj < 0) continue;
+          const int e = 2 * pad_idx(int(n % Q.M[mj])) + j;
           // the count L or L-1 above includes this entry: as +1 for int8
           // (counted -1 entries), as -1 for bits (counted +1 entries)
           if (Q.xdtype == TM_I8_PM1) ib[e] -= sig.ival(n) < 0 ? 2 : 0;
@@ -848,8 +890,10 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
     __syncthreads();
     // extension y[M+i] = y[i] - x_i + x_{(i+LM) mod N}, i < K-1
     for (int j = 0; j < 2; ++j) {
-      const int M = Q.M[j];
-      const int64_t LM = Q.L[j] * M;
+      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
+      if (mj < 0) continue;
+      const int M = Q.M[mj];
+      const int64_t LM = Q.L[mj] * M;
       for (int i0 = tid; i0 < K - 1; i0 += kB * kCorrThreads) {
         float xi[kB], xw[kB];
         with_sig(Q.xdtype, Q.x, [&](auto sx) {
@@ -889,8 +933,8 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       const int e = 2 * pad_idx(k);
       const int v0 = ib[e], v1 = ib[e + 1];
       if (Q.y_in == nullptr) {
-        yi[k] = v0;
-        yi[P + k] = v1;
+        yi[(pass == 0 ? 0 : 2) * P + k] = v0;
+        if (pass == 0) yi[P + k] = v1;
       }
       sbuf[pad_idx(k)] = make_float2(float(v0), float(v1));
       s2 += (long long)v0 * v0 + (long long)v1 * v1;
@@ -904,8 +948,8 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
     for (int k = tid; k < P; k += kCorrThreads) {
       const float2 v = sbuf[pad_idx(k)];
       if (Q.y_in == nullptr) {
-        yf[k] = v.x;
-        yf[P + k] = v.y;
+        yf[(pass == 0 ? 0 : 2) * P + k] = v.x;
+        if (pass == 0) yf[P + k] = v.y;
       }
       z2 = fmaf(v.x, v.x, fmaf(v.y, v.y, z2));
     }
@@ -926,17 +970,32 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
 
   if (a.r != nullptr && Q.r_off >= 0) {
     float* r = a.r + Q.r_off;
-    for (int k = tid; k < Q.M[0]; k += kCorrThreads) r[k] = sbuf[pad_idx(k)].x * invP;
-    for (int k = tid; k < Q.M[1]; k += kCorrThreads) r[P + k] = -sbuf[pad_idx(k)].y * invP;
+    if (pass == 0) {
+      for (int k = tid; k < Q.M[0]; k += kCorrThreads) r[k] = sbuf[pad_idx(k)].x * invP;
+      for (int k = tid; k < Q.M[1]; k += kCorrThreads) r[P + k] = -sbuf[pad_idx(k)].y * invP;
+    } else {
+      for (int k = tid; k < Q.M[2]; k += kCorrThreads) r[2 * P + k] = sbuf[pad_idx(k)].x * invP;
+    }
   }
 
-  // ------------------------------------------------ d-e. steps 7-9
+  // ------------------------------------------------ d. step 7 candidates
   // Rounding bound on every r_j (fft_corr_error_bound, one product term).
   const float delta = fft_corr_error_bound(logP, t2, Tp, Zc, z2, 1);
-  select_and_resolve(a, Q, qi, delta, t_integral, t1, maxy, [&](int j, int k) {
-    const float2 w = sbuf[pad_idx(k)];
-    return j == 0 ? w.x * invP : -w.y * invP;
-  });
+  if (pass == 0) {
+    collect_candidates(cands, 0, Q.M[0], delta, [&](int k) { return sbuf[pad_idx(k)].x * invP; });
+    collect_candidates(cands, 1, Q.M[1], delta, [&](int k) { return -sbuf[pad_idx(k)].y * invP; });
+  } else {
+    collect_candidates(cands, 2, Q.M[2], delta, [&](int k) { return sbuf[pad_idx(k)].x * invP; });
+  }
+  maxy_all = max(maxy_all, maxy);
+  };
+  run_pass(0);
+  if (Q.nmod == 3) {
+    __syncthreads();   // the first pass's values are no longer read
+    run_pass(1);
+  }
+  // ------------------------------------------------ e. steps 7-9
+  resolve(a, Q, qi, t_integral, t1, maxy_all, cands);
 }
 
 // One CTA per query, in a.order (largest FFT first); the hardware hands the

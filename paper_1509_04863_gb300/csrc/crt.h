@@ -16,9 +16,9 @@ namespace ftm {
 
 struct CrtSet {
   int64_t m0;      // first natural solution (>= N when there is none)
-  int64_t step;    // M1 * M2
+  int64_t step;    // M1 * M2 (M1 * M2 * M3)
   int64_t nnat;    // number of natural solutions below N
-  int64_t w[2];    // wrapped members in the intersection
+  int64_t w[3];    // wrapped members in the intersection
   int32_t nw;
 };
 
@@ -54,6 +54,32 @@ TM_HD CrtSet crt_intersect(int64_t N, int64_t M1, int64_t M2, int64_t inv, int64
   c.nw = 0;
   if (w1 >= 0 && (w1 % M2 == m2 || w1 == w2)) c.w[c.nw++] = w1;
   if (w2 >= 0 && w2 != w1 && w2 % M1 == m1) c.w[c.nw++] = w2;
+  return c;
+}
+
+// Three moduli (Thm. 4): the naturals solve v = m_i (mod M_i), i = 1..3,
+// the progression m0 + j M1 M2 M3 (m0 from the two-modulus solution and
+// inv3 = (M1 M2)^{-1} mod M3); a wrapped member w_i joins when it lies in
+// the other two sets (congruent to their m_j, or equal to their w_j).
+TM_HD CrtSet crt_intersect3(int64_t N, const int64_t (&M)[3], int64_t inv, int64_t inv3, const int64_t (&m)[3]) {
+  CrtSet c = crt_intersect(N, M[0], M[1], inv, m[0], m[1]);
+  const int64_t M12 = M[0] * M[1];
+  const int64_t d = ((m[2] - c.m0) % M[2] + M[2]) % M[2];
+  const int64_t k = (d * inv3) % M[2];
+  c.m0 = c.m0 + M12 * k;
+  c.step = M12 * M[2];
+  c.nnat = c.m0 < N ? (N - 1 - c.m0) / c.step + 1 : 0;
+  int64_t w[3];
+  for (int i = 0; i < 3; ++i) w[i] = m[i] + ((N + M[i] - 1) / M[i] - 1) * M[i] - N;
+  c.nw = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (w[i] < 0) continue;
+    bool all = true, dup = false;
+    for (int j = 0; j < 3; ++j)
+      if (j != i && !(w[i] % M[j] == m[j] || w[i] == w[j])) all = false;
+    for (int q = 0; q < c.nw; ++q) dup = dup || c.w[q] == w[i];
+    if (all && !dup) c.w[c.nw++] = w[i];
+  }
   return c;
 }
 

@@ -644,9 +644,6 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
 
   // ---------------------------------------------------------------- consumers
   const int warp = tid >> 5;
-  const int m = warp < kFoldWarps0 ? 0 : 1;         // modulus handled by this warp
-  const int W = m == 0 ? kFoldWarps0 : kFoldWarps1;
-  const int wig = m == 0 ? warp : warp - kFoldWarps0;
   RingPos rp;
   bool ok = true;
   for (int qi = q0; qi < a.nq && ok; ++qi) {
@@ -654,6 +651,12 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
     const int32_t nbytes = a.q[qi].nbytes;
     if (goff >= ce) break;
     if (nbytes == 0) continue;
+    // the modulus this warp folds for this signal (warps split 8/9 between
+    // two moduli, 6/6/5 between three)
+    const int nm = a.q[qi].nmod;
+    const int m = nm == 3 ? (warp < 6 ? 0 : warp < 12 ? 1 : 2) : (warp < kFoldWarps0 ? 0 : 1);
+    const int W = fold_warp_count(nm, m);
+    const int wig = warp - fold_warp_first(nm, m);
     const int lo = int(max(cb, goff) - goff);
     const int hi = int(min(ce, goff + nbytes) - goff);
     const int Mp = a.q[qi].Mp[m];

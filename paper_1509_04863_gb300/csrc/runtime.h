@@ -28,19 +28,21 @@ inline int64_t pad16(int64_t v) { return (v + 15) & ~int64_t(15); }
 struct PlanCore {
   int64_t N = 0;
   int32_t K = 0, xdtype = 0;
-  int32_t M[2] = {0, 0};
-  int64_t L[2] = {0, 0};
+  int32_t nmod = 2;                 // moduli of step 2 (3 with TM_THREE_MODULI)
+  int32_t M[3] = {0, 0, 0};
+  int64_t L[3] = {0, 0, 0};
   int32_t P = 0, logP = 0;
-  int32_t inv = 0;
-  int32_t R[2] = {1, 1}, Mp[2] = {0, 0};
+  int32_t inv = 0;                  // M1^-1 mod M2
+  int32_t inv3 = 0;                 // (M1 M2)^-1 mod M3
+  int32_t R[3] = {1, 1, 1}, Mp[3] = {0, 0, 0};
   int64_t max_cand = 0;
-  uint32_t flags = 0;   // TM_ALLOW_AMBIG, TM_THM2_SAMPLING
+  uint32_t flags = 0;   // TM_ALLOW_AMBIG, TM_THM2_SAMPLING, TM_THREE_MODULI
 };
 
 
 // Algorithm 1 step 2 and the derived sizes (host only).
 tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t M1, int32_t M2, uint32_t flags,
-                    PlanCore& pc);
+                    PlanCore& pc, int32_t M3 = 0);
 int64_t signal_bytes(int32_t dtype, int64_t N);
 int64_t fold_bytes(int32_t dtype, int64_t N);
 int64_t fold_elems(int32_t dtype, int64_t N);

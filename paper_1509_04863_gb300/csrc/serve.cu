@@ -58,7 +58,7 @@ struct Signal {
 // entries; `ev` completes when they are written; refs counts in-flight
 // iterations reading them, pending is set until the writing iteration
 // retires (an entry is dropped only with neither).
-using CacheKey = std::tuple<int32_t, int32_t, int32_t, uint32_t>;   // signal, M1, M2, sampling flag
+using CacheKey = std::tuple<int32_t, int32_t, int32_t, uint32_t>;   // signal, M1, M2, sampling / moduli flags
 struct CacheEntry {
   void* y = nullptr;
   int32_t pitch = 0;
@@ -207,7 +207,7 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
   if (cache_on) {
     for (int i = 0; i < n; ++i) {
       if (reqs[i].plan.P > kPMax) continue;
-      auto it = sv->fcache.find(CacheKey(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & TM_THM2_SAMPLING));
+      auto it = sv->fcache.find(CacheKey(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & (TM_THM2_SAMPLING | TM_THREE_MODULI)));
       if (it != sv->fcache.end()) {
         nofold[i] = 1;
         hit[i] = &it->second;
@@ -248,7 +248,7 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
       if (!hit[i]) continue;
       ++hit[i]->refs;
       hit[i]->last = ++sv->fclock;
-      sl.hits.emplace_back(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & TM_THM2_SAMPLING);
+      sl.hits.emplace_back(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & (TM_THM2_SAMPLING | TM_THREE_MODULI));
     }
     int64_t nh = 0;
     for (int i = 0; i < n; ++i) nh += hit[i] ? 1 : 0;
@@ -260,10 +260,11 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
     // new entries from this iteration's folds (copied once it has run)
     for (int i = 0; i < n; ++i) {
       if (hit[i] || reqs[i].plan.P > kPMax) continue;
-      const CacheKey key(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & TM_THM2_SAMPLING);
+      const CacheKey key(reqs[i].sig, reqs[i].plan.M[0], reqs[i].plan.M[1], reqs[i].plan.flags & (TM_THM2_SAMPLING | TM_THREE_MODULI));
       if (sv->fcache.count(key)) continue;
-      const int32_t pitch = std::max(reqs[i].plan.M[0], reqs[i].plan.M[1]);
-      const int64_t bytes = 2 * int64_t(pitch) * 4;
+      const int rows = reqs[i].plan.nmod;
+      const int32_t pitch = std::max(std::max(reqs[i].plan.M[0], reqs[i].plan.M[1]), rows == 3 ? reqs[i].plan.M[2] : 0);
+      const int64_t bytes = rows * int64_t(pitch) * 4;
       // drop least recently used entries that nothing reads or writes
       while (sv->fcache_bytes + bytes > sv->cfg.fold_cache_bytes) {
         auto victim = sv->fcache.end();
@@ -287,7 +288,7 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
         continue;
       }
       const char* src = static_cast<const char*>(sl.b->d_y) + sl.b->cq[i].y_off * 4;
-      if (cudaMemcpy2DAsync(e.y, size_t(pitch) * 4, src, size_t(sl.b->cq[i].P) * 4, size_t(pitch) * 4, 2,
+      if (cudaMemcpy2DAsync(e.y, size_t(pitch) * 4, src, size_t(sl.b->cq[i].P) * 4, size_t(pitch) * 4, size_t(rows),
                             cudaMemcpyDeviceToDevice, sl.s) != cudaSuccess ||
           cudaEventCreateWithFlags(&e.ev, cudaEventDisableTiming) != cudaSuccess ||
           cudaEventRecord(e.ev, sl.s) != cudaSuccess) {

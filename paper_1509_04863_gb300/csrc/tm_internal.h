@@ -22,6 +22,14 @@ constexpr int64_t kMaxQueryBytes = (int64_t(1) << 31) - (int64_t(1) << 16);
 constexpr int kFoldWarps0 = 8;                       // consumer warps of modulus M1
 constexpr int kFoldWarps1 = 9;                       // consumer warps of modulus M2
 constexpr int kFoldConsumers = 32 * (kFoldWarps0 + kFoldWarps1);
+
+// Consumer warps of modulus j: with two moduli 8 and 9, with three 6, 6, 5.
+__host__ __device__ inline int fold_warp_first(int nmod, int j) {
+  return nmod == 3 ? 6 * j : (j == 0 ? 0 : kFoldWarps0);
+}
+__host__ __device__ inline int fold_warp_count(int nmod, int j) {
+  return nmod == 3 ? (j == 2 ? 5 : 6) : (j == 0 ? kFoldWarps0 : kFoldWarps1);
+}
 constexpr int kFoldThreads = kFoldConsumers + 32;    // + producer warp
 // The ring of shared-memory stages: 3 x 64 KiB by default; an autotuner
 // may pick 6 x 32 KiB or 12 x 16 KiB for a batch (same ring bytes).
@@ -63,8 +71,9 @@ struct FoldQ {
   const uint8_t* x;   // signal bytes, 16-byte aligned
   int64_t goff;       // first byte of this signal in the flattened space
   int32_t nbytes;     // bytes folded by the kernel (multiple of 16)
-  int32_t Mp[2];      // effective moduli R_j * M_j (>= fold_geom(dtype).min_mp)
-  int32_t moff[2];    // offset of modulus j inside a slot (int32 units)
+  int32_t nmod;       // moduli folded (2 or 3)
+  int32_t Mp[3];      // effective moduli R_j * M_j (>= fold_geom(dtype).min_mp)
+  int32_t moff[3];    // offset of modulus j inside a slot (int32 units)
   int32_t stride;     // slot length (int32 units)
   int32_t first_cta;  // CTA whose share holds goff
   int32_t nslots;
@@ -102,18 +111,20 @@ struct CorrQ {
   int64_t N;
   int32_t K;
   int32_t xdtype;
-  int32_t M[2];
-  int32_t R[2];       // fold multipliers: Mp = R * M
-  int64_t L[2];       // ceil(N / M_j)
+  int32_t nmod;       // 2 or 3 moduli
+  int32_t M[3];
+  int32_t R[3];       // fold multipliers: Mp = R * M
+  int64_t L[3];       // ceil(N / M_j)
   int32_t P, logP;
   int32_t inv;        // M1^{-1} mod M2
+  int32_t inv3;       // (M1 M2)^{-1} mod M3
   int32_t thm2;       // Thm. 2 sampling: no wrap-around term, periodic extension
   int32_t nelem16;    // elements covered by the fold kernel
   int32_t nslots;
-  int32_t moff[2];
+  int32_t moff[3];
   int32_t stride;
   int64_t part;       // first slot in the partial buffer (int32 units)
-  int64_t y_off;      // fold output [2][P] (int32 or float), element offset
+  int64_t y_off;      // fold output [nmod][P] (int32 or float), element offset
   int64_t spec_off;   // template spectrum scratch [P] float2, element offset
   int64_t r_off;      // correlation output [2][P] float, or -1
   const void* y_in;   // complete folds [2][P] supplied by the caller (the fold

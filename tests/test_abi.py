@@ -98,3 +98,32 @@ def test_crt_closed_form_equals_set_intersection(tm, N, M1, M2):
         for b in range(M2):
             want = sorted(O.candidate_set(a, M1, N) & O.candidate_set(b, M2, N))
             assert tm.tm_crt_candidates(N, M1, M2, a, b) == want, (N, M1, M2, a, b)
+
+
+@pytest.mark.parametrize("N,K,mode,M,ambig", [
+    (10 ** 6, 64, "paper", (0, 0, 0), True), (10 ** 6, 100, "auto", (0, 0, 0), False),
+    (10 ** 6, 63, "paper", (0, 0, 0), False), (5000, 7, "paper", (0, 0, 0), True),
+    (10 ** 6, 50, "explicit", (101, 103, 107), False), (10 ** 6, 50, "explicit", (102, 104, 105), False),
+    (10 ** 7, 50, "explicit", (51, 52, 53), False), (1 << 20, 16000, "paper", (0, 0, 0), False)])
+def test_planner_three_moduli_matches_oracle(tm, N, K, mode, M, ambig):
+    """TM_THREE_MODULI against the oracle's plan3 (reading R14): moduli,
+    rejection of shared factors and of products not above N, FFT length."""
+    try:
+        want = O.plan3(N, K, mode, *M, allow_ambig=ambig)
+    except ValueError:
+        want = None
+    if want is None:
+        with pytest.raises(tm.TMError) as e:
+            tm.Plan(N, K, "i8", mode, M[0], M[1], ambig, three=True, M3=M[2])
+        assert e.value.status == tm.TM_EINVAL
+        return
+    if max(want) + K - 1 > 16384:
+        with pytest.raises(tm.TMError) as e:
+            tm.Plan(N, K, "i8", mode, M[0], M[1], ambig, three=True, M3=M[2])
+        assert e.value.status == tm.TM_EUNSUPPORTED
+        return
+    p = tm.Plan(N, K, "i8", mode, M[0], M[1], ambig, three=True, M3=M[2])
+    assert (p.info["M1"], p.info["M2"], p.info["M3"]) == want
+    assert p.info["L3"] == -(-N // want[2])
+    P = p.info["P"]
+    assert P >= max(want) + K - 1 and P // 2 < max(want) + K - 1

@@ -29,7 +29,7 @@ def test_noalloc_rejects_what_does_not_fit(tm):
     clear error before any GPU work (no device needed)."""
     x = torch.zeros(16, dtype=torch.int8)   # never read: the size check comes first
     with pytest.raises(tm.TMError) as e:
-        tm.tm_match_noalloc(x, torch.zeros(4, dtype=torch.float32), torch.zeros(6, dtype=torch.int64),
+        tm.tm_match_noalloc(x, torch.zeros(4, dtype=torch.float32), torch.zeros(tm.RESULT_BYTES // 8, dtype=torch.int64),
                             N=(1 << 28) + 16, K=4096, mode="paper", allow_ambig=True)
     assert e.value.status == tm.TM_EUNSUPPORTED
     assert "no-allocation" in str(e.value)
