@@ -126,8 +126,8 @@ tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t 
     if (j >= nm) { pc.R[j] = 1; pc.Mp[j] = 0; continue; }
     pc.R[j] = int32_t(std::max<int64_t>(1, ceil_div(g.min_mp, pc.M[j])));
     pc.Mp[j] = pc.R[j] * pc.M[j];
-    if (fold_units_per_lane(pc.Mp[j], fold_warp_count(nm, j), g.E) > g.jmax)
-      return fail(TM_EUNSUPPORTED, "modulus too large for the fold kernel of this signal type");
+    // wider moduli: folded entry by entry (fold_direct.cu)
+    if (fold_units_per_lane(pc.Mp[j], fold_warp_count(nm, j), g.E) > g.jmax) pc.direct = 1;
   }
   const long double prod = (long double)m[0] * (long double)m[1] * (three ? (long double)m[2] : 1.0L);
   pc.max_cand = int64_t(std::ceil((long double)N / prod)) + 3;
@@ -236,6 +236,10 @@ void bind_pointers(tm_batch_t b) {
     b->fq[b->fold_of[i]].x = static_cast<const uint8_t*>(x);
     b->cq[i].x = x;
     b->cq[i].t = t;
+    // entry-by-entry folds land in the batch's fold buffer and are given to
+    // the correlation as complete folds
+    b->cq[i].y_in = b->cq[i].direct ? static_cast<const void*>(static_cast<const char*>(b->d_y) + b->cq[i].y_off * 4)
+                                    : nullptr;
   }
 }
 
@@ -296,7 +300,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
       if (p.xdtype != dt) continue;
       const int32_t pos = gr.first + gr.count++;
       b->fold_of[i] = pos;
-      const int64_t nb = (nofold && nofold[i]) ? 0 : fold_bytes(p.xdtype, p.N);
+      const int64_t nb = ((nofold && nofold[i]) || p.direct) ? 0 : fold_bytes(p.xdtype, p.N);
       FoldQ& f = b->fq[pos];
       f.goff = W;
       f.nbytes = int32_t(nb);
@@ -353,6 +357,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     c.nmod = p.nmod;
     for (int j = 0; j < 3; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
     c.P = p.P; c.logP = p.logP; c.inv = p.inv; c.inv3 = p.inv3;
+    c.direct = p.direct;
     c.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
     c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
     c.nslots = f.nslots; c.stride = f.stride; c.part = f.part;
@@ -365,6 +370,14 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     if (!blocked) b->maxP = std::max(b->maxP, p.P);
   }
   b->y_elems = yo; b->spec_elems = so; b->r_elems = ro;
+  b->direct.clear();
+  b->maxP_direct = b->maxmod_direct = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!b->pc[i].direct) continue;
+    b->direct.push_back(i);
+    b->maxP_direct = std::max(b->maxP_direct, b->pc[i].P);
+    b->maxmod_direct = std::max(b->maxmod_direct, b->pc[i].nmod);
+  }
   // processing order: shared-memory queries (largest P first), then blocked ones
   b->order.resize(n);
   for (int i = 0; i < n; ++i) b->order[i] = i;
@@ -388,7 +401,7 @@ tm_status batch_alloc(tm_batch_s* b) {
   };
   bool ok = alloc((void**)&b->d_fq, n * sizeof(FoldQ)) == cudaSuccess &&
             alloc((void**)&b->d_cq, n * sizeof(CorrQ)) == cudaSuccess &&
-            alloc((void**)&b->d_order, n * sizeof(int32_t)) == cudaSuccess &&
+            alloc((void**)&b->d_order, 2 * n * sizeof(int32_t)) == cudaSuccess &&
             alloc((void**)&b->d_partial, b->part_elems * sizeof(int32_t)) == cudaSuccess &&
             alloc(&b->d_y, b->y_elems * sizeof(int32_t)) == cudaSuccess &&
             alloc((void**)&b->d_spec, b->spec_elems * sizeof(float2)) == cudaSuccess &&
@@ -413,6 +426,9 @@ tm_status batch_alloc(tm_batch_s* b) {
   }
   TM_CUDA(cudaMemset(b->d_err, 0, 16));
   TM_CUDA(cudaMemcpy(b->d_order, b->order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (!b->direct.empty())   // the entry-by-entry folds' query list follows the order
+    TM_CUDA(cudaMemcpy(b->d_order + n, b->direct.data(), b->direct.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice));
   return TM_OK;
 }
 
@@ -448,6 +464,9 @@ tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
     a.partial = b->d_partial; a.err = b->d_err; a.tile = g.tile;
     TM_CUDA(launch_fold(a, g.jmax, s));
   }
+  if (!b->direct.empty())
+    TM_CUDA(launch_fold_direct(b->d_cq, b->d_order + b->n, int32_t(b->direct.size()), b->maxP_direct,
+                               b->maxmod_direct, b->d_y, s));
   return TM_OK;
 }
 
@@ -585,6 +604,7 @@ tm_status tm_fold_slice(tm_plan_t p, const void* x, int64_t n0, int64_t len, voi
   if (pc.P > kPMax) return fail(TM_EUNSUPPORTED, "slices need P <= 16384");
   if (pc.flags & TM_THM2_SAMPLING) return fail(TM_EUNSUPPORTED, "slices use the sampling of Eq. (3)");
   if (pc.nmod != 2) return fail(TM_EUNSUPPORTED, "slices use two moduli");
+  if (pc.direct) return fail(TM_EUNSUPPORTED, "slices need moduli the streaming fold holds");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0, sms = 0;
   TM_CUDA(cudaGetDevice(&dev));
@@ -890,6 +910,7 @@ tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, in
   if (launches) {
     int32_t l = (b->n > b->n_blocked ? 1 : 0) + (b->n_blocked > 0 ? 1 : 0);
     for (const auto& g : b->groups) l += g.W > 0 ? 1 : 0;
+    l += b->direct.empty() ? 0 : 1;
     *launches = l;
   }
   if (fold_ctas) *fold_ctas = b->nctas;

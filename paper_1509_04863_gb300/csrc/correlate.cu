@@ -1066,64 +1066,66 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
   // ------------------------------------------------ folds, straight to global memory
   int32_t* yi = static_cast<int32_t*>(a.y) + Q.y_off;
   float* yf = static_cast<float*>(a.y) + Q.y_off;
-  for (int j = 0; j < 2; ++j) {
-    const int M = Q.M[j], Rr = Q.R[j];
-    const int L = int(Q.L[j]);
-    const int Rw = int(N - int64_t(L - 1) * M);
-    const int32_t* part = a.partial + Q.part + Q.moff[j];
-    for (int k = tid; k < M; k += kCorrThreads) {
-      if (ints) {
-        int c = 0;
-        for (int s = 0; s < Q.nslots; ++s) {
-          const int32_t* ps = part + int64_t(s) * Q.stride;
-          for (int r = 0; r < Rr; ++r) c += ps[k + r * M];
+  if (Q.y_in == nullptr) {   // else the folds are given, complete, at y_off
+    for (int j = 0; j < 2; ++j) {
+      const int M = Q.M[j], Rr = Q.R[j];
+      const int L = int(Q.L[j]);
+      const int Rw = int(N - int64_t(L - 1) * M);
+      const int32_t* part = a.partial + Q.part + Q.moff[j];
+      for (int k = tid; k < M; k += kCorrThreads) {
+        if (ints) {
+          int c = 0;
+          for (int s = 0; s < Q.nslots; ++s) {
+            const int32_t* ps = part + int64_t(s) * Q.stride;
+            for (int r = 0; r < Rr; ++r) c += ps[k + r * M];
+          }
+          const int nk = L - 1 + (k < Rw ? 1 : 0);
+          int yk = Q.xdtype == TM_BITS_PM1 ? 2 * c - nk : nk - 2 * c;
+          if (k >= Rw && !Q.thm2) yk += sig.ival(k - Rw);
+          yi[int64_t(j) * P + k] = yk;
+        } else {
+          const float* pf = reinterpret_cast<const float*>(part);
+          float yk = 0.f;
+          for (int s = 0; s < Q.nslots; ++s) {
+            const float* ps = pf + int64_t(s) * Q.stride;
+            for (int r = 0; r < Rr; ++r) yk += ps[k + r * M];
+          }
+          if (k >= Rw && !Q.thm2) yk += sig.val(k - Rw);
+          yf[int64_t(j) * P + k] = yk;
         }
-        const int nk = L - 1 + (k < Rw ? 1 : 0);
-        int yk = Q.xdtype == TM_BITS_PM1 ? 2 * c - nk : nk - 2 * c;
-        if (k >= Rw && !Q.thm2) yk += sig.ival(k - Rw);
-        yi[int64_t(j) * P + k] = yk;
-      } else {
-        const float* pf = reinterpret_cast<const float*>(part);
-        float yk = 0.f;
-        for (int s = 0; s < Q.nslots; ++s) {
-          const float* ps = pf + int64_t(s) * Q.stride;
-          for (int r = 0; r < Rr; ++r) yk += ps[k + r * M];
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int64_t n = Q.nelem16; n < N; ++n) {
+        for (int j = 0; j < 2; ++j) {
+          const int64_t e = int64_t(j) * P + n % Q.M[j];
+          if (Q.xdtype == TM_I8_PM1) yi[e] -= sig.ival(n) < 0 ? 2 : 0;
+          else if (Q.xdtype == TM_BITS_PM1) yi[e] += sig.ival(n) > 0 ? 2 : 0;
+          else yf[e] += sig.val(n);
         }
-        if (k >= Rw && !Q.thm2) yk += sig.val(k - Rw);
-        yf[int64_t(j) * P + k] = yk;
       }
     }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int64_t n = Q.nelem16; n < N; ++n) {
-      for (int j = 0; j < 2; ++j) {
-        const int64_t e = int64_t(j) * P + n % Q.M[j];
-        if (Q.xdtype == TM_I8_PM1) yi[e] -= sig.ival(n) < 0 ? 2 : 0;
-        else if (Q.xdtype == TM_BITS_PM1) yi[e] += sig.ival(n) > 0 ? 2 : 0;
-        else yf[e] += sig.val(n);
+    __syncthreads();
+    for (int j = 0; j < 2; ++j) {
+      const int M = Q.M[j];
+      const int64_t LM = Q.L[j] * M;
+      for (int i = tid; i < K - 1; i += kCorrThreads) {
+        int64_t w = i + LM - N;
+        if (w >= N) w %= N;
+        const int64_t e = int64_t(j) * P + M + i, e0 = int64_t(j) * P + i;
+        if (Q.thm2) {   // periodic extension
+          if (ints) yi[e] = yi[e0];
+          else yf[e] = yf[e0];
+        } else if (ints) {
+          yi[e] = yi[e0] - sig.ival(i) + sig.ival(w);
+        } else {
+          yf[e] = yf[e0] - sig.val(i) + sig.val(w);
+        }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int j = 0; j < 2; ++j) {
-    const int M = Q.M[j];
-    const int64_t LM = Q.L[j] * M;
-    for (int i = tid; i < K - 1; i += kCorrThreads) {
-      int64_t w = i + LM - N;
-      if (w >= N) w %= N;
-      const int64_t e = int64_t(j) * P + M + i, e0 = int64_t(j) * P + i;
-      if (Q.thm2) {   // periodic extension
-        if (ints) yi[e] = yi[e0];
-        else yf[e] = yf[e0];
-      } else if (ints) {
-        yi[e] = yi[e0] - sig.ival(i) + sig.ival(w);
-      } else {
-        yf[e] = yf[e0] - sig.val(i) + sig.val(w);
-      }
-    }
-  }
-  __syncthreads();
   // norms of z = y_1 + i y_2
   auto yval = [&](int j, int64_t k) -> float {
     if (k >= Q.M[j] + K - 1) return 0.f;

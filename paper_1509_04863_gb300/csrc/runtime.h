@@ -37,6 +37,7 @@ struct PlanCore {
   int32_t R[3] = {1, 1, 1}, Mp[3] = {0, 0, 0};
   int64_t max_cand = 0;
   uint32_t flags = 0;   // TM_ALLOW_AMBIG, TM_THM2_SAMPLING, TM_THREE_MODULI
+  int32_t direct = 0;   // moduli too wide for the streaming fold: entry-by-entry fold
 };
 
 
@@ -75,6 +76,8 @@ struct tm_batch_s {
   int32_t nctas = 0;   // largest fold grid
   int64_t W = 0;       // bytes folded in total
   int32_t maxP = 0;        // largest FFT of the shared-memory correlation launch
+  std::vector<int32_t> direct;   // queries folded entry by entry (fold_direct)
+  int32_t maxP_direct = 0, maxmod_direct = 0;
   int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_blocked, n))
   int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
   ftm::FoldQ* d_fq = nullptr;

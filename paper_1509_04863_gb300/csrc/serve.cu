@@ -118,7 +118,7 @@ namespace {
 // Device bytes of a planned batch when carved from an arena.
 size_t batch_bytes(const tm_batch_s* b, int64_t t_floats) {
   const size_t n = size_t(b->n);
-  return align_up(n * sizeof(FoldQ)) + align_up(n * sizeof(CorrQ)) + align_up(n * sizeof(int32_t)) +
+  return align_up(n * sizeof(FoldQ)) + align_up(n * sizeof(CorrQ)) + align_up(2 * n * sizeof(int32_t)) +
          align_up(size_t(b->part_elems) * 4) + align_up(size_t(b->y_elems) * 4) +
          align_up(size_t(b->spec_elems) * sizeof(float2)) + align_up(size_t(b->r_elems) * 4) + align_up(16) +
          align_up(n * sizeof(tm_result)) + align_up(size_t(t_floats) * 4);
@@ -134,7 +134,7 @@ void carve(tm_batch_s* b, char* base, int64_t t_floats) {
   const size_t n = size_t(b->n);
   b->d_fq = reinterpret_cast<FoldQ*>(take(n * sizeof(FoldQ)));
   b->d_cq = reinterpret_cast<CorrQ*>(take(n * sizeof(CorrQ)));
-  b->d_order = reinterpret_cast<int32_t*>(take(n * sizeof(int32_t)));
+  b->d_order = reinterpret_cast<int32_t*>(take(2 * n * sizeof(int32_t)));
   b->d_partial = reinterpret_cast<int32_t*>(take(size_t(b->part_elems) * 4));
   b->d_y = take(size_t(b->y_elems) * 4);
   b->d_spec = reinterpret_cast<float2*>(take(size_t(b->spec_elems) * sizeof(float2)));
@@ -224,6 +224,8 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
     std::memcpy(sl.h_t + toff[i], reqs[i].t.data(), size_t(reqs[i].q.K) * sizeof(float));
   }
   std::memcpy(sl.h_order, sl.b->order.data(), size_t(n) * sizeof(int32_t));
+  if (!sl.b->direct.empty())   // the entry-by-entry folds' query list follows the order
+    std::memcpy(sl.h_order + n, sl.b->direct.data(), sl.b->direct.size() * sizeof(int32_t));
   bind_pointers(sl.b);
   for (int i = 0; i < n; ++i) {
     if (!hit[i]) continue;
@@ -232,7 +234,8 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
     TM_CUDA(cudaStreamWaitEvent(sl.s, hit[i]->ev, 0));
   }
   TM_CUDA(cudaMemcpyAsync(sl.b->d_t, sl.h_t, size_t(t_floats) * sizeof(float), cudaMemcpyHostToDevice, sl.s));
-  TM_CUDA(cudaMemcpyAsync(sl.b->d_order, sl.h_order, size_t(n) * sizeof(int32_t), cudaMemcpyHostToDevice, sl.s));
+  TM_CUDA(cudaMemcpyAsync(sl.b->d_order, sl.h_order, size_t(n + sl.b->direct.size()) * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, sl.s));
   st = upload_descriptors(sl.b, sl.s);
   if (st != TM_OK) return st;
   st = batch_fold(sl.b, sl.s);
@@ -481,7 +484,7 @@ tm_status tm_serve_create(const tm_serve_cfg* cfg_in, tm_server_t* out) {
               cudaMallocHost(&sl.h_t, size_t(t_cap) * sizeof(float)) == cudaSuccess &&
               cudaMallocHost(&sl.h_out, size_t(cfg.max_batch) * sizeof(tm_result)) == cudaSuccess &&
               cudaMallocHost(&sl.h_stage, stage_cap) == cudaSuccess &&
-              cudaMallocHost(&sl.h_order, size_t(cfg.max_batch) * sizeof(int32_t)) == cudaSuccess;
+              cudaMallocHost(&sl.h_order, 2 * size_t(cfg.max_batch) * sizeof(int32_t)) == cudaSuccess;
     sl.arena_bytes = cfg.arena_bytes;
     sl.h_t_cap = t_cap;
     sl.h_stage_cap = stage_cap;

@@ -129,6 +129,7 @@ struct CorrQ {
   int64_t r_off;      // correlation output [2][P] float, or -1
   const void* y_in;   // complete folds [2][P] supplied by the caller (the fold
                       // completion is skipped; x may then be null: no exact score)
+  int32_t direct;     // folded by fold_direct_kernel into y (then given as y_in)
   const void* y_core; // cached folds over k < M_j (wrap-around and last entries
                       // included), row j at y_core + j core_pitch; the fold
                       // kernel skips the signal, only the extension is added
@@ -157,7 +158,7 @@ cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s);
 // and an r buffer [2][P] (r_off >= 0).
 cudaError_t launch_correlate_blocked(const CorrArgs& a, cudaStream_t s);
 int blocked_spectra(int K, int maxM);
-constexpr int kLogPMaxBlocked = 16;   // largest FFT length the planner accepts: 65536
+constexpr int kLogPMaxBlocked = 18;   // largest FFT length the planner accepts: 262144
 // ---------------------------------------------------------------- slices of one signal
 // Completion of a slice's fold: the extended folds [2][P] of Eq. (2)
 // restricted to the entries x_n with n in [n0, n0 + len), from the fold
@@ -188,6 +189,11 @@ struct SliceScoreArgs {
   double* out;
 };
 cudaError_t launch_score_slice(const SliceScoreArgs& a, cudaStream_t s);
+
+// Step 3 entry by entry for the queries idx[0..n) of q (CorrQ::direct):
+// complete folds written to y + q.y_off.
+cudaError_t launch_fold_direct(const CorrQ* q, const int32_t* idx, int32_t n, int32_t maxP, int32_t maxmod, void* y,
+                               cudaStream_t s);
 
 cudaError_t fold_configure();   // one-time kernel attributes
 cudaError_t corr_configure();

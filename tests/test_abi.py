@@ -84,8 +84,11 @@ def test_planner_matches_oracle(tm, N, K, mode, M1, M2, ambig):
 
 
 def test_planner_unsupported_sizes(tm):
+    # Table 2's size (N = 2^26, K = 2^16): FFT length 2^17, within the
+    # overlap-save correlation's 2^18
+    assert tm.Plan(1 << 26, 1 << 16, "i8", "paper").info["P"] == 1 << 17
     with pytest.raises(tm.TMError) as e:
-        tm.Plan(1 << 26, 1 << 16, "i8", "paper")       # P = 2^17 > 16384
+        tm.Plan(1 << 27, 1 << 17 + 1, "i8", "paper")    # P = 2^19 > 2^18
     assert e.value.status == tm.TM_EUNSUPPORTED
 
 
