@@ -534,6 +534,193 @@ def run_sweep(args):
     return 0
 
 
+def _flush_l2(buf, i):
+    buf.fill_(i & 0xFF)   # writes 256 MiB > L2 between timed runs
+
+
+def _time_single(tm, spec, flush, reps):
+    """Median CUDA-event time (ms) of one query run alone (fold + steps
+    4-9), L2 flushed before each run; and its result."""
+    import torch
+    b = tm.Batch([spec])
+    out = tm.result_buffer(1)
+    b.run(out)
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(reps):
+        _flush_l2(flush, i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run(out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), tm.decode_results(out)[0]
+
+
+def _time_fulln(x, t, flush, reps):
+    """Median time (ms) of the full-length-N FFT correlation + argmax
+    (cuFFT through torch), L2 flushed before each run; and its argmax."""
+    import torch
+    N = x.shape[0]
+
+    def one():
+        X = torch.fft.rfft(x.float())
+        T = torch.fft.rfft(t, n=N)
+        return torch.argmax(torch.fft.irfft(torch.conj(T) * X, n=N))
+
+    one()
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(reps):
+        _flush_l2(flush, i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        m = one()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), int(m.item())
+
+
+def _success_batch(tm, N, K, n, seed, snr_db=None, chunk_bytes=4 << 30, allow_ambig=False):
+    """Success rate of the paper's protocol (Sec. 4): x uniform +-1, t the
+    window of x at a uniform random shift m, moduli K and K+1, success iff
+    the returned shift equals m; with snr_db, x_e = x + Gaussian noise
+    (float32 signal) is matched against the clean template. Runs n trials
+    in batches; returns (rate, ms per query, flagged results)."""
+    import torch
+    from workloads import device as WD
+    rng = W.rng_for(seed)
+    per = N * (4 if snr_db is not None else 1)
+    B = max(1, min(n, chunk_bytes // per))
+    ok = flagged = 0
+    ms = 0.0
+    for c0 in range(0, n, B):
+        nb = min(B, n - c0)
+        specs, kst = [], []
+        for i in range(nb):
+            s = seed * 1000003 + c0 + i
+            if snr_db is None:
+                x = WD.signal(N, "i8", s)
+                xs, dt = x, "i8"
+            else:
+                x, xs = WD.pm1_with_noise(N, snr_db, s)
+                dt = "f32"
+            k = int(rng.integers(0, N))
+            t = WD.template(x, K, k, 0.0, s)
+            specs.append(dict(x=xs, t=t, N=N, K=K, xdtype=dt, mode="paper", allow_ambig=allow_ambig))
+            kst.append(k)
+        b = tm.Batch(specs)
+        out = tm.result_buffer(nb)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run(out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        res = tm.decode_results(out)
+        ok += sum(r["shift"] == k for r, k in zip(res, kst))
+        flagged += sum(1 for r in res if r["status"] & ~0xFF)
+        assert b.device_error() == 0
+        del b, specs
+    torch.cuda.empty_cache()
+    return ok / n, ms / n, flagged
+
+
+TABLE1 = ((1 << 23, 0.05), (1 << 24, 0.21), (1 << 25, 0.85), (1 << 26, 1.0), (1 << 27, 1.0))
+TABLE2 = ((20, 1.0), (10, 1.0), (6, 0.95), (1, 0.72), (-2, 0.48), (-6, 0.06))
+
+
+def run_tables(args):
+    """The paper's experiments (Sec. 4) on synthetic +-1 signals.
+
+    table1: success rate at K = N/2^10, N = 2^23 .. 2^27, noiseless.
+    table2: success rate at N = 2^26, K = 2^16 under additive Gaussian noise
+            on x, SNR 20 .. -6 dB (float32 signals).
+    fig1a:  time of one query vs K at N = 2^26, next to the full-N FFT.
+    fig1b:  time of one query vs N at K = 2^16, and at the smallest K whose
+            trials all succeed ("best"), next to the full-N FFT.
+    One JSON line; each part holds the paper's value beside the measured one
+    where the paper prints one."""
+    import torch
+    import paper_1509_04863_gb300 as tm
+    parts = set(args.parts.split(","))
+    T = args.trials
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    line = {"metric": "success rate (Table 1-2) and time per query (Fig. 1)", "unit": "fraction / ms",
+            "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "data": "synthetic",
+            "dtype": "int32/f32 fold, f32 FFT, exact rescoring",
+            "config": {"workload": f"tables: Sec. 4 protocol, {T} trials per point (Tables 1-2), M1=K, M2=K+1, "
+                                   "L2 flushed before each timed single query"}}
+    if "table1" in parts:
+        rows = []
+        for N, paper in TABLE1:
+            rate, ms, fl = _success_batch(tm, N, N >> 10, T, seed=N >> 20)
+            rows.append({"N": N, "K": N >> 10, "success_rate": rate, "paper": paper, "ms_per_query_batched": ms,
+                         "flagged": fl})
+        line["table1"] = rows
+    if "table2" in parts:
+        rows = []
+        for snr, paper in TABLE2:
+            rate, ms, fl = _success_batch(tm, 1 << 26, 1 << 16, T, seed=5000 + snr, snr_db=snr)
+            rows.append({"snr_db": snr, "success_rate": rate, "paper": paper, "ms_per_query_batched": ms,
+                         "flagged": fl})
+        line["table2"] = rows
+    from workloads import device as WD
+    reps = 5
+    if "fig1a" in parts:
+        N = 1 << 26
+        rows = []
+        x = WD.signal(N, "i8", 77)
+        rng = W.rng_for(78)
+        ms_full = None
+        for lk in range(16, 26):
+            K = 1 << lk
+            k = int(rng.integers(0, N))
+            t = WD.template(x, K, k, 0.0, 79)
+            if ms_full is None:
+                ms_full, mf = _time_fulln(x, t, flush, reps)
+            row = {"K": K, "ms_fulln_fft": ms_full}
+            try:
+                ms, r = _time_single(tm, dict(x=x, t=t, N=N, K=K, xdtype="i8", mode="paper"), flush, reps)
+                row.update(ms_per_query=ms, found=r["shift"] == k)
+            except Exception as e:   # sizes the library does not plan
+                row["unsupported"] = str(e).splitlines()[0][:120]
+            rows.append(row)
+        line["fig1a"] = rows
+    if "fig1b" in parts:
+        rows = []
+        rng = W.rng_for(80)
+        for ln in range(16, 27):
+            N = 1 << ln
+            x = WD.signal(N, "i8", 81 + ln)
+            row = {"N": N}
+            K = 1 << 16
+            k = int(rng.integers(0, N))
+            t = WD.template(x, K, k, 0.0, 82)
+            row["ms_fulln_fft"], mf = _time_fulln(x, t, flush, reps)
+            ms, r = _time_single(tm, dict(x=x, t=t, N=N, K=K, xdtype="i8", mode="paper"), flush, reps)
+            row.update(ms_per_query=ms, found=r["shift"] == k)
+            # "best": the smallest K (powers of two and 1.5x between) whose
+            # args.best_trials trials all succeed
+            lo = ln // 2
+            for kb in sorted({3 << (j - 1) for j in range(lo, ln)} | {1 << j for j in range(lo, ln + 1)}):
+                rate, _, _ = _success_batch(tm, N, kb, args.best_trials, seed=90 + ln, allow_ambig=True)
+                if rate == 1.0:
+                    break
+            kk = int(rng.integers(0, N))
+            tb = WD.template(x, kb, kk, 0.0, 83)
+            msb, rb = _time_single(tm, dict(x=x, t=tb, N=N, K=kb, xdtype="i8", mode="paper", allow_ambig=True),
+                                   flush, reps)
+            row.update(best_K=kb, ms_per_query_best=msb, found_best=rb["shift"] == kk)
+            rows.append(row)
+        line["fig1b"] = rows
+    line["value"] = next((r["success_rate"] for r in line.get("table1", []) if r["N"] == 1 << 26), None)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -545,10 +732,13 @@ def main():
     ap.add_argument("--queries", type=int, default=64)
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--K", type=int, default=K_T)
-    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve", "sweep"],
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve", "sweep", "tables"],
                     help="batch64 (default line), uneven (4096-query mix as one CUDA graph), "
                          "serve (Poisson arrivals through the continuous-batching server)")
     ap.add_argument("--seeds", type=int, default=256)
+    ap.add_argument("--trials", type=int, default=1000, help="tables: trials per Table 1-2 point")
+    ap.add_argument("--best-trials", type=int, default=64, help="tables: trials per K in the Fig. 1(b) search")
+    ap.add_argument("--parts", default="table1,table2,fig1a,fig1b")
     ap.add_argument("--rate", type=float, default=20000.0)
     ap.add_argument("--duration", type=float, default=3.0)
     ap.add_argument("--signals", type=int, default=1024)
@@ -567,6 +757,8 @@ def main():
         return run_serve(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "tables":
+        return run_tables(args)
     return run_native(args)
 
 

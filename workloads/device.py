@@ -59,3 +59,15 @@ def uneven(seed: int = 5000, n: int = 4096, t_sigma: float = 0.3, logN=(14.0, 24
         t = template(x, K, k_star, t_sigma, seed * 7919 + i + (1 << 40))
         out.append(dict(x=x, t=t, N=N, K=K, xdtype=dt, k_star=k_star))
     return out
+
+
+def pm1_with_noise(N: int, snr_db: float, seed: int, device="cuda"):
+    """A +-1 int8 signal x and x_e = x + e, e ~ N(0, sigma^2) iid with
+    sigma^2 = 10^(-snr_db/10) (E[x^2] = 1, so the SNR is 1/sigma^2), as
+    float32. Returns (x, x_e)."""
+    import torch
+    x = signal(N, "i8", seed, device)
+    sigma = 10.0 ** (-float(snr_db) / 20.0)
+    xe = torch.randn(N, generator=_gen(device, seed + (1 << 41)), device=device, dtype=torch.float32)
+    xe.mul_(sigma).add_(x)
+    return x, xe
