@@ -90,6 +90,11 @@ typedef enum { TM_MODE_AUTO = 0, TM_MODE_PAPER = 1, TM_MODE_EXPLICIT = 2 } tm_mo
 #define TM_RF_SCORE_PENDING 0x400 /* tm_correlate_folds: no signal, so the member(s)
                                      of S1 ∩ S2 are unscored; shift = the first
                                      member, to be resolved by the caller */
+#define TM_RF_UNCERTIFIED 0x800   /* FFT lengths above 2^18 only: more than 4096
+                                     indices lay within the FFT rounding bound of
+                                     the maximum and M K > 2^36, so m_j is the
+                                     largest FFT value (smallest index among
+                                     equal ones), not proven the exact argmax */
 
 typedef struct {
   int64_t N;       /* signal length, 1 <= N */

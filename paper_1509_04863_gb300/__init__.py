@@ -28,6 +28,7 @@ TM_FOUND, TM_EMPTY, TM_RESOLVED = 0, 1, 2
 TM_RF_FULL_RESCORE = 0x100
 TM_RF_DEVICE_ERROR = 0x200
 TM_RF_SCORE_PENDING = 0x400
+TM_RF_UNCERTIFIED = 0x800
 TM_BATCH_KEEP_CORR = 0x1
 TM_BATCH_HOST_INPUTS = 0x2
 

@@ -108,7 +108,7 @@ tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t 
   const int64_t need = mmax + K - 1;
   int32_t logP = 0;
   while ((int64_t(1) << logP) < need) ++logP;
-  if (logP > kLogPMaxBlocked) return fail(TM_EUNSUPPORTED, "FFT length above 65536 (max(M)+K-1 > 65536)");
+  if (logP > kLogPMaxLarge) return fail(TM_EUNSUPPORTED, "FFT length above 2^26 (max(M)+K-1 > 67108864)");
   if (three && logP > kLogPMax) return fail(TM_EUNSUPPORTED, "three moduli: FFT lengths up to 16384");
   if (signal_bytes(xdtype, N) > kMaxQueryBytes) return fail(TM_EUNSUPPORTED, "signal larger than 2^31-2^16 bytes");
   pc.N = N; pc.K = K; pc.xdtype = xdtype; pc.nmod = nm;
@@ -132,6 +132,9 @@ tm_status make_plan(int64_t N, int32_t K, int32_t xdtype, int32_t mode, int32_t 
   const long double prod = (long double)m[0] * (long double)m[1] * (three ? (long double)m[2] : 1.0L);
   pc.max_cand = int64_t(std::ceil((long double)N / prod)) + 3;
   pc.flags = flags;
+  // FFTs longer than the blocked correlation's: passes over all SMs, on
+  // folds computed entry by entry
+  if (logP > kLogPMaxBlocked) pc.large = pc.direct = 1;
   return TM_OK;
 }
 
@@ -166,6 +169,7 @@ tm_status device_setup(int dev, float2** tw) {
   if (!g_configured[dev]) {
     TM_CUDA(fold_configure());
     TM_CUDA(corr_configure());
+    TM_CUDA(large_configure());
     std::vector<float2> h(kPMax);
     const double two_pi = 6.283185307179586476925286766559;
     for (int m = 0; m < kPMax; ++m) {
@@ -240,6 +244,18 @@ void bind_pointers(tm_batch_t b) {
     // the correlation as complete folds
     b->cq[i].y_in = b->cq[i].direct ? static_cast<const void*>(static_cast<const char*>(b->d_y) + b->cq[i].y_off * 4)
                                     : nullptr;
+    if (b->is_large.size() == size_t(b->n) && b->is_large[i]) {
+      LQ& l = b->lq[i];
+      const CorrQ& c = b->cq[i];
+      l.x = x;
+      l.t = t;
+      l.y = c.y_in;
+      l.r = b->d_r + c.r_off;
+      l.A = b->d_spec + c.spec_off;
+      l.B = l.A + c.P;
+      l.ws = l.B + c.P;
+      l.err = b->d_err;
+    }
   }
 }
 
@@ -275,6 +291,18 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
       if (reinterpret_cast<uintptr_t>(q[i].t) & 3) return fail(TM_EINVAL, "t must be 4-byte aligned");
     }
   }
+  // few queries with long FFTs: each on all SMs instead of one CTA
+  int nbig = 0;
+  for (int i = 0; i < n; ++i) nbig += b->pc[i].P > kPMax ? 1 : 0;
+  b->is_large.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    PlanCore& p = b->pc[i];
+    if (p.P > kPMax && (p.large || nbig <= kLargeMaxQueries) && !(nofold && nofold[i])) {
+      p.large = p.direct = 1;
+      b->is_large[i] = 1;
+    }
+    if (p.large && !b->is_large[i]) return fail(TM_EUNSUPPORTED, "FFT length above 2^18 with cached folds");
+  }
   TM_CUDA(cudaGetDevice(&b->device));
   int sms = 0;
   TM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
@@ -286,6 +314,9 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
   b->fq.resize(n);
   b->cq.resize(n);
   b->fold_of.assign(n, 0);
+  b->dh.assign(n, 0);
+  b->drows.assign(n, 0);
+  b->dpart.assign(n, 0);
   int64_t part = 0;
   for (int32_t dt = TM_I8_PM1; dt <= TM_F32; ++dt) {
     tm_batch_s::FoldGroup gr;
@@ -345,6 +376,20 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     b->nctas = std::max(b->nctas, gr.nctas);
     b->groups.push_back(gr);
   }
+  // partial sums of the entry-by-entry folds follow the streaming fold's slots
+  b->maxM_direct = b->maxHM_direct = 0;
+  for (int i = 0; i < n; ++i) {
+    const PlanCore& p = b->pc[i];
+    if (!p.direct) continue;
+    const int32_t dh = direct_row_groups(p.L[0]);
+    const int32_t mmax = *std::max_element(p.M, p.M + p.nmod);
+    b->dh[i] = dh;
+    b->drows[i] = dh > 0 ? int32_t(ceil_div(p.L[0], dh)) : 0;
+    b->dpart[i] = part;
+    part += int64_t(p.nmod) * dh * mmax;
+    b->maxM_direct = std::max(b->maxM_direct, mmax);
+    b->maxHM_direct = std::max(b->maxHM_direct, std::max(1, dh) * p.nmod);
+  }
   b->part_elems = std::max<int64_t>(part, 16);
 
   // ---- correlation descriptors and output layout
@@ -358,16 +403,22 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     for (int j = 0; j < 3; ++j) { c.M[j] = p.M[j]; c.R[j] = p.R[j]; c.L[j] = p.L[j]; c.moff[j] = f.moff[j]; }
     c.P = p.P; c.logP = p.logP; c.inv = p.inv; c.inv3 = p.inv3;
     c.direct = p.direct;
+    c.dh = b->dh[i];
+    c.drows = b->drows[i];
+    c.dpart = b->dpart[i];
     c.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
     c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
     c.nslots = f.nslots; c.stride = f.stride; c.part = f.part;
     c.y_off = yo; yo += int64_t(p.nmod) * p.P;
-    const bool blocked = p.P > kPMax;   // correlation in blocks (overlap-save), r kept in global memory
+    const bool large = b->is_large[i];
+    const bool blocked = p.P > kPMax && !large;   // correlation in blocks (overlap-save), r kept in global memory
+    if (large) so = (so + 31) & ~int64_t(31);   // 256-byte aligned spectra (vector loads)
     c.spec_off = so;
-    so += blocked ? int64_t(blocked_spectra(p.K, std::max(p.M[0], p.M[1]))) * kPMax : p.P;
-    c.r_off = ((flags & TM_BATCH_KEEP_CORR) || blocked) ? ro : -1;
+    if (large) so += (2 * int64_t(p.P) + int64_t(large_ws_bytes() / sizeof(float2)) + 31) & ~int64_t(31);
+    else so += blocked ? int64_t(blocked_spectra(p.K, std::max(p.M[0], p.M[1]))) * kPMax : p.P;
+    c.r_off = ((flags & TM_BATCH_KEEP_CORR) || blocked || large) ? ro : -1;
     if (c.r_off >= 0) ro += int64_t(p.nmod) * p.P;
-    if (!blocked) b->maxP = std::max(b->maxP, p.P);
+    if (!blocked && !large) b->maxP = std::max(b->maxP, p.P);
   }
   b->y_elems = yo; b->spec_elems = so; b->r_elems = ro;
   b->direct.clear();
@@ -378,16 +429,31 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     b->maxP_direct = std::max(b->maxP_direct, b->pc[i].P);
     b->maxmod_direct = std::max(b->maxmod_direct, b->pc[i].nmod);
   }
-  // processing order: shared-memory queries (largest P first), then blocked ones
+  // processing order: shared-memory queries (largest P first), then blocked
+  // ones, then those on the multi-CTA path
+  auto cls = [&](int i) { return b->is_large[i] ? 2 : (b->pc[i].P > kPMax ? 1 : 0); };
   b->order.resize(n);
   for (int i = 0; i < n; ++i) b->order[i] = i;
   std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) {
-    const bool ba = b->pc[a].P > kPMax, bc = b->pc[c].P > kPMax;
-    if (ba != bc) return bc;
+    if (cls(a) != cls(c)) return cls(a) < cls(c);
     return b->pc[a].P > b->pc[c].P;
   });
-  b->n_blocked = 0;
-  for (int i = 0; i < n; ++i) b->n_blocked += b->pc[i].P > kPMax ? 1 : 0;
+  b->n_blocked = b->n_large = 0;
+  for (int i = 0; i < n; ++i) {
+    b->n_blocked += cls(i) == 1 ? 1 : 0;
+    b->n_large += cls(i) == 2 ? 1 : 0;
+  }
+  b->lq.assign(n, LQ{});
+  for (int i = 0; i < n; ++i) {
+    if (!b->is_large[i]) continue;
+    const PlanCore& p = b->pc[i];
+    LQ& l = b->lq[i];
+    l.N = p.N; l.K = p.K; l.xdtype = p.xdtype;
+    l.M[0] = p.M[0]; l.M[1] = p.M[1];
+    l.inv = p.inv; l.P = p.P; l.logP = p.logP;
+    l.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
+    l.nsd = large_dims(p.logP, l.logL);
+  }
 
   return TM_OK;
 }
@@ -466,20 +532,26 @@ tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
   }
   if (!b->direct.empty())
     TM_CUDA(launch_fold_direct(b->d_cq, b->d_order + b->n, int32_t(b->direct.size()), b->maxP_direct,
-                               b->maxmod_direct, b->d_y, s));
+                               b->maxmod_direct, b->maxM_direct, b->maxHM_direct, b->d_partial, b->d_y, s));
   return TM_OK;
 }
 
 tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s) {
   CorrArgs a;
-  a.q = b->d_cq; a.order = b->d_order; a.nq = b->n - b->n_blocked;
+  a.q = b->d_cq; a.order = b->d_order; a.nq = b->n - b->n_blocked - b->n_large;
   a.partial = b->d_partial; a.y = b->d_y; a.spec = b->d_spec; a.r = b->d_r; a.tw = b->tw;
   a.out = out; a.err = b->d_err;
   if (a.nq > 0) TM_CUDA(launch_correlate(a, b->maxP, s));
   if (b->n_blocked > 0) {
-    a.order = b->d_order + (b->n - b->n_blocked);
+    a.order = b->d_order + (b->n - b->n_large - b->n_blocked);
     a.nq = b->n_blocked;
     TM_CUDA(launch_correlate_blocked(a, s));
+  }
+  for (int k = b->n - b->n_large; k < b->n; ++k) {
+    const int i = b->order[k];
+    LQ l = b->lq[i];
+    l.out = out + i;
+    TM_CUDA(launch_correlate_large(l, s));
   }
   return TM_OK;
 }
@@ -908,9 +980,11 @@ tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r) {
 tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, int64_t* ws) {
   if (!b) return fail(TM_EINVAL, "null batch");
   if (launches) {
-    int32_t l = (b->n > b->n_blocked ? 1 : 0) + (b->n_blocked > 0 ? 1 : 0);
+    int32_t l = (b->n > b->n_blocked + b->n_large ? 1 : 0) + (b->n_blocked > 0 ? 1 : 0);
     for (const auto& g : b->groups) l += g.W > 0 ? 1 : 0;
-    l += b->direct.empty() ? 0 : 1;
+    l += b->direct.empty() ? 0 : 2;
+    for (int i = 0; i < b->n; ++i)
+      if (b->is_large[i]) l += large_launches(b->lq[i].nsd);
     *launches = l;
   }
   if (fold_ctas) *fold_ctas = b->nctas;

@@ -38,6 +38,7 @@ struct PlanCore {
   int64_t max_cand = 0;
   uint32_t flags = 0;   // TM_ALLOW_AMBIG, TM_THM2_SAMPLING, TM_THREE_MODULI
   int32_t direct = 0;   // moduli too wide for the streaming fold: entry-by-entry fold
+  int32_t large = 0;    // FFT longer than the blocked correlation: multi-CTA passes
 };
 
 
@@ -77,8 +78,13 @@ struct tm_batch_s {
   int64_t W = 0;       // bytes folded in total
   int32_t maxP = 0;        // largest FFT of the shared-memory correlation launch
   std::vector<int32_t> direct;   // queries folded entry by entry (fold_direct)
-  int32_t maxP_direct = 0, maxmod_direct = 0;
-  int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_blocked, n))
+  int32_t maxP_direct = 0, maxmod_direct = 0, maxM_direct = 0, maxHM_direct = 0;
+  std::vector<int32_t> dh, drows;   // entry-by-entry folds: row groups, rows per group, partial offsets
+  std::vector<int64_t> dpart;
+  int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_large - n_blocked, n - n_large))
+  int32_t n_large = 0;     // queries on the multi-CTA path (order[n - n_large, n))
+  std::vector<uint8_t> is_large;
+  std::vector<ftm::LQ> lq;  // their launch descriptors (by query)
   int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
   ftm::FoldQ* d_fq = nullptr;
   ftm::CorrQ* d_cq = nullptr;

@@ -129,7 +129,10 @@ struct CorrQ {
   int64_t r_off;      // correlation output [2][P] float, or -1
   const void* y_in;   // complete folds [2][P] supplied by the caller (the fold
                       // completion is skipped; x may then be null: no exact score)
-  int32_t direct;     // folded by fold_direct_kernel into y (then given as y_in)
+  int32_t direct;     // folded entry by entry into y (then given as y_in)
+  int32_t dh;         // entry-by-entry fold: row groups of the first stage
+  int32_t drows;      // rows per group
+  int64_t dpart;      // its partial sums [nmod][dh][M_j] in the partial buffer (int32 units)
   const void* y_core; // cached folds over k < M_j (wrap-around and last entries
                       // included), row j at y_core + j core_pitch; the fold
                       // kernel skips the signal, only the extension is added
@@ -158,7 +161,7 @@ cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s);
 // and an r buffer [2][P] (r_off >= 0).
 cudaError_t launch_correlate_blocked(const CorrArgs& a, cudaStream_t s);
 int blocked_spectra(int K, int maxM);
-constexpr int kLogPMaxBlocked = 18;   // largest FFT length the planner accepts: 262144
+constexpr int kLogPMaxBlocked = 18;   // longest FFT of the blocked correlation: 262144
 // ---------------------------------------------------------------- slices of one signal
 // Completion of a slice's fold: the extended folds [2][P] of Eq. (2)
 // restricted to the entries x_n with n in [n0, n0 + len), from the fold
@@ -191,9 +194,65 @@ struct SliceScoreArgs {
 cudaError_t launch_score_slice(const SliceScoreArgs& a, cudaStream_t s);
 
 // Step 3 entry by entry for the queries idx[0..n) of q (CorrQ::direct):
-// complete folds written to y + q.y_off.
-cudaError_t launch_fold_direct(const CorrQ* q, const int32_t* idx, int32_t n, int32_t maxP, int32_t maxmod, void* y,
-                               cudaStream_t s);
+// partial sums over dh row groups into partial + q.dpart, then the complete
+// folds written to y + q.y_off. maxM, maxHM: the largest M_j and dh * nmod.
+cudaError_t launch_fold_direct(const CorrQ* q, const int32_t* idx, int32_t n, int32_t maxP, int32_t maxmod,
+                               int32_t maxM, int32_t maxHM, int32_t* partial, void* y, cudaStream_t s);
+// Row groups of the entry-by-entry fold for L rows: about 16 rows each.
+inline int32_t direct_row_groups(int64_t L) {
+  const int64_t h = (L + 15) / 16;
+  return int32_t(h < 1 ? 1 : (h > 64 ? 64 : h));
+}
+constexpr int kDirCols = 4;   // fold columns per thread of the first stage
+
+// ---------------------------------------------------------------- long FFTs on all SMs (steps 4-9)
+// One query whose FFT length P = 2^logP (2^14 <= P <= 2^26) runs as a
+// sequence of launches over global memory: the transforms are cut into
+// 8192-point contiguous row blocks and one or two strided column passes
+// (dims logL[0..nsd) outermost first, each <= 2^9 points), then candidate
+// collection, chunked exact rescoring, the intersection and the scores.
+constexpr int kLogPMinLarge = 14;
+constexpr int kLogPMaxLarge = 26;
+constexpr int kLargeCap = 4096;       // candidates per modulus rescored from a list
+constexpr int kLargePart = 1 << 18;   // partial dot products of all candidates
+constexpr int kLargeMembers = 256;    // members scored from a list
+constexpr int kLargeMPart = 1 << 16;  // partial dot products of all members
+constexpr int kLargeCtas = 1216;      // grid of the rescoring and scoring launches
+// A single query in a batch with at most this many queries of P > kPMax
+// takes this path also when P <= 2^kLogPMaxBlocked (all SMs instead of one).
+constexpr int kLargeMaxQueries = 8;
+
+struct LQ {
+  const void* x;
+  const float* t;
+  const void* y;        // complete folds [2][P] (int32 for +-1 signals, else float)
+  float* r;             // correlations [2][P]
+  float2* A;            // [P] signal spectrum, then the products
+  float2* B;            // [P] template spectrum
+  void* ws;             // large_ws_bytes() of statistics, candidates and partial sums
+  tm_result* out;       // result slot of this query
+  int32_t* err;
+  int64_t N;
+  int32_t K, xdtype;
+  int32_t M[2];
+  int32_t inv;
+  int32_t P, logP;
+  int32_t thm2;
+  int32_t nsd;          // strided dims (1 or 2)
+  int32_t logL[2];
+};
+size_t large_ws_bytes();
+// Strided dims of a length-2^logP transform (8192-point rows innermost).
+inline int large_dims(int logP, int32_t (&logL)[2]) {
+  const int q = logP - 13;
+  if (q <= 9) { logL[0] = q; logL[1] = 0; return 1; }
+  logL[0] = (q + 1) / 2; logL[1] = q / 2;
+  return 2;
+}
+// The launches of one query on stream s (fold given in q.y).
+cudaError_t launch_correlate_large(const LQ& q, cudaStream_t s);
+int large_launches(int nsd);
+cudaError_t large_configure();
 
 cudaError_t fold_configure();   // one-time kernel attributes
 cudaError_t corr_configure();

@@ -84,11 +84,12 @@ def test_planner_matches_oracle(tm, N, K, mode, M1, M2, ambig):
 
 
 def test_planner_unsupported_sizes(tm):
-    # Table 2's size (N = 2^26, K = 2^16): FFT length 2^17, within the
-    # overlap-save correlation's 2^18
+    # Table 2's size (N = 2^26, K = 2^16): FFT length 2^17; Fig. 1(a)'s
+    # largest template (K = 2^25): 2^26, the longest FFT planned
     assert tm.Plan(1 << 26, 1 << 16, "i8", "paper").info["P"] == 1 << 17
+    assert tm.Plan(1 << 26, 1 << 25, "i8", "paper").info["P"] == 1 << 26
     with pytest.raises(tm.TMError) as e:
-        tm.Plan(1 << 27, 1 << 17 + 1, "i8", "paper")    # P = 2^19 > 2^18
+        tm.Plan(1 << 27, (1 << 25) + 1, "i8", "paper")    # P = 2^27 > 2^26
     assert e.value.status == tm.TM_EUNSUPPORTED
 
 

@@ -2,7 +2,10 @@
 (K >= 2^14, up to FFT lengths of 2^17 here): the entry-by-entry fold and the
 overlap-save correlation against the oracle (FFT route in fp64, rounded for
 integer data): folds bit-exact for +-1 signals and within 1e-5 for reals,
-maxima, shift, status, score identical; also with the Thm. 2 sampling."""
+maxima, shift, status, score identical; also with the Thm. 2 sampling.
+The batches hold more than eight such queries (each pair five times), so
+they take the one-CTA-per-query overlap-save path; smaller batches take
+the multi-CTA path (test_gpu_large.py)."""
 import numpy as np
 import pytest
 import torch
@@ -37,13 +40,15 @@ def test_wide_moduli_vs_oracle(tm, N, K, mode, xdtype, thm2):
         q.meta["thm2"] = thm2
         specs.append(dict(x=torch.from_numpy(q.x).cuda(), t=torch.from_numpy(q.t).cuda(), N=q.N, K=q.K,
                           xdtype=xdtype, mode=mode, thm2=thm2))
-    b = tm.Batch(specs, keep_corr=True)
-    assert b.stats()["launches_per_run"] == 2      # entry-by-entry fold + overlap-save correlation
-    out = tm.result_buffer(len(qs))
+    b = tm.Batch(specs * 5, keep_corr=True)
+    assert b.stats()["launches_per_run"] == 3      # entry-by-entry fold (two) + overlap-save correlation
+    out = tm.result_buffer(5 * len(qs))
     b.run(out)
     torch.cuda.synchronize()
     assert b.device_error() == 0
     res = tm.decode_results(out)
+    for i in range(len(qs), 5 * len(qs)):
+        assert res[i] == res[i % len(qs)]
     for i, q in enumerate(qs):
         ref = O.match_query(q, corr="fft") if not thm2 else O.match_query(q)
         P = b.infos[i]["P"]
