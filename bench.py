@@ -281,7 +281,7 @@ def run_native(args):
     th = [torch.from_numpy(q.t).pin_memory() for q in qs]
     oh = torch.zeros(QUERIES * tm.RESULT_BYTES // 8, dtype=torch.int64).pin_memory()
     bh.run_host(xh, th, oh)
-    e2e_steps = max(3, min(20, K // 50))
+    e2e_steps = 20   # about 0.1 s: 1 GiB host-to-device per step at about 205 GB/s
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
