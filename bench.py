@@ -46,6 +46,32 @@ WORKLOAD = {"workload": "batch64: 64 queries x (N=2^24 +-1 int8, K=4096, 5% temp
 METRIC = "queries/s"
 
 
+def bind_local_numa(dev_index: int):
+    """Pins this process to the host cores of the GPU's NUMA node, so that
+    pinned host buffers (first touched by this thread) sit next to the GPU's
+    host link. Best effort: returns the node, or None."""
+    try:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        if vis:
+            dev_index = vis.split(",")[dev_index].strip()
+        out = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", str(dev_index)],
+                             capture_output=True, text=True, timeout=30).stdout.strip()
+        bus = out.lower()
+        if bus.count(":") == 2 and len(bus.split(":")[0]) == 8:
+            bus = bus[4:]
+        node = int(open(f"/sys/bus/pci/devices/{bus}/numa_node").read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        os.sched_setaffinity(0, cpus)
+        return node
+    except Exception:
+        return None
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -229,6 +255,7 @@ def run_native(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    numa = bind_local_numa(local)
     import paper_1509_04863_gb300 as tm
 
     qs = gen_queries(rank)
@@ -318,7 +345,8 @@ def run_native(args):
                          "fold_ms": float(fold_ms.mean()), "corr_ms": float((step_ms - fold_ms).mean())},
             "e2e": {"value": world * QUERIES * e2e_steps / e2e_s, "unit": "queries/s",
                     "h2d_bytes_per_step": in_bytes + QUERIES * K_T * 4, "d2h_bytes_per_step": QUERIES * tm.RESULT_BYTES,
-                    "api": "tm_batch_run_host (pinned host buffers)", "matches_device_run": e2e_ok},
+                    "api": "tm_batch_run_host (pinned host buffers)", "matches_device_run": e2e_ok,
+                    "host_numa_node": numa},
             "gpu_launches": K * launches,
             "clocks": clk,
             "success_rate": success,
@@ -632,6 +660,104 @@ TABLE1 = ((1 << 23, 0.05), (1 << 24, 0.21), (1 << 25, 0.85), (1 << 26, 1.0), (1 
 TABLE2 = ((20, 1.0), (10, 1.0), (6, 0.95), (1, 0.72), (-2, 0.48), (-6, 0.06))
 
 
+def run_single(args):
+    """Configuration 1: one query (N = 65536 +-1 int8, K = 1024, M1 = K,
+    M2 = K+1) matched 1000 times through tm_match with a reused plan:
+    device-time and host-wall latency percentiles (a latency-bound case),
+    the same through host buffers (copies inside the timed region), the
+    full-N cuFFT correlation's latency, and the success rate of the paper's
+    protocol over 256 seeds."""
+    import torch
+    import paper_1509_04863_gb300 as tm
+    import oracle.ftm as O
+    q = W.single_query(seed=1)
+    dev = torch.device("cuda", 0)
+    x, t = torch.from_numpy(q.x).to(dev), torch.from_numpy(q.t).to(dev)
+    plan = tm.Plan(q.N, q.K, "i8", "paper")
+    out = tm.result_buffer(1)
+    n = args.repeats
+    for _ in range(20):
+        plan.match(x, t, out)
+    torch.cuda.synchronize()
+    dev_us, host_us = [], []
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for e0, e1 in evs:
+        h0 = time.perf_counter()
+        e0.record()
+        plan.match(x, t, out)
+        e1.record()
+        e1.synchronize()
+        host_us.append((time.perf_counter() - h0) * 1e6)
+    dev_us = [e0.elapsed_time(e1) * 1e3 for e0, e1 in evs]
+    res = tm.decode_results(out)[0]
+    # end to end: host signal and template in pinned memory, result read back
+    xh = torch.from_numpy(q.x).pin_memory()
+    th = torch.from_numpy(q.t).pin_memory()
+    oh = torch.empty(tm.RESULT_BYTES // 8, dtype=torch.int64).pin_memory()
+    e2e_us = []
+    for i in range(n + 20):
+        h0 = time.perf_counter()
+        x.copy_(xh, non_blocking=True)
+        t.copy_(th, non_blocking=True)
+        plan.match(x, t, out)
+        oh.copy_(out.view(torch.int64).reshape(-1)[: tm.RESULT_BYTES // 8], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if i >= 20:
+            e2e_us.append((time.perf_counter() - h0) * 1e6)
+    # full-N FFT correlation of the same query
+    X = x.float()
+
+    def fulln():
+        r = torch.fft.irfft(torch.conj(torch.fft.rfft(t, n=q.N)) * torch.fft.rfft(X), n=q.N)
+        return torch.argmax(r)
+
+    for _ in range(20):
+        fulln()
+    torch.cuda.synchronize()
+    fu = []
+    for _ in range(200):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fulln()
+        e1.record()
+        e1.synchronize()
+        fu.append(e0.elapsed_time(e1) * 1e3)
+    # success of the protocol over 256 seeds (batched)
+    qs = [W.planted_query(1000 + s, q.N, q.K, "i8", mode="paper") for s in range(256)]
+    b = tm.Batch([dict(x=torch.from_numpy(v.x).to(dev), t=torch.from_numpy(v.t).to(dev), N=v.N, K=v.K, xdtype="i8",
+                       mode="paper") for v in qs])
+    ob = tm.result_buffer(len(qs))
+    b.run(ob)
+    torch.cuda.synchronize()
+    succ = sum(r["shift"] == v.k_star for r, v in zip(tm.decode_results(ob), qs)) / len(qs)
+    # tm_match runs a one-query batch: its kernels per call
+    per_call = tm.Batch([dict(x=x, t=t, N=q.N, K=q.K, xdtype="i8", mode="paper")]).stats()["launches_per_run"]
+    # the oracle on the host, same query
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 2.0:
+        O.match_query(q)
+        reps += 1
+    cpu_us = (time.perf_counter() - t0) / reps * 1e6
+    pct = lambda v, p: float(np.percentile(v, p))
+    line = {"metric": "single-query latency p50 (device)", "value": pct(dev_us, 50), "unit": "us", "n_gpus": 1,
+            "steps": n, "warmup": 20, "higher_is_better": False, "scaling": "none", "vs_baseline": None,
+            "dtype": "int32 (fold), f32 (FFT), int64 (rescoring)", "data": "synthetic",
+            "config": {"workload": "single: N=65536 +-1 int8, K=1024, M1=K, M2=K+1, plan reused, inputs resident "
+                                   "(64 KiB: in L2 after the first call)"},
+            "latency_us": {"device_p50": pct(dev_us, 50), "device_p99": pct(dev_us, 99),
+                           "host_p50": pct(host_us, 50), "host_p99": pct(host_us, 99)},
+            "e2e": {"value": pct(e2e_us, 50), "unit": "us (p50, host wall)", "p99": pct(e2e_us, 99),
+                    "h2d_bytes_per_step": q.N + q.K * 4, "d2h_bytes_per_step": tm.RESULT_BYTES},
+            "found_shift": res["shift"] == q.k_star, "success_rate_256_seeds": succ,
+            "fullN_fft_xcorr_us_p50": pct(fu, 50),
+            "cpu_baseline": {"value": cpu_us, "unit": "us per query", "cores": 1, "kind": "oracle",
+                             "sample": f"{reps} repeats of the same query, numpy oracle, 1 thread"},
+            "gpu_launches": n * per_call}
+    print(json.dumps(line))
+    return 0
+
+
 def run_tables(args):
     """The paper's experiments (Sec. 4) on synthetic +-1 signals.
 
@@ -668,18 +794,18 @@ def run_tables(args):
                          "flagged": fl})
         line["table2"] = rows
     from workloads import device as WD
-    reps = 5
+    reps = args.reps
     if "fig1a" in parts:
-        N = 1 << 26
+        N = 1 << args.fig_logn
         rows = []
         x = WD.signal(N, "i8", 77)
         rng = W.rng_for(78)
         ms_full = None
-        for lk in range(16, 26):
+        for lk in [int(v) for v in args.fig_ks.split(",")] if args.fig_ks else range(16, args.fig_logn):
             K = 1 << lk
             k = int(rng.integers(0, N))
             t = WD.template(x, K, k, 0.0, 79)
-            if ms_full is None:
+            if ms_full is None and not args.no_fulln:
                 ms_full, mf = _time_fulln(x, t, flush, reps)
             row = {"K": K, "ms_fulln_fft": ms_full}
             try:
@@ -732,13 +858,18 @@ def main():
     ap.add_argument("--queries", type=int, default=64)
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--K", type=int, default=K_T)
-    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve", "sweep", "tables"],
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve", "sweep", "tables", "single"],
                     help="batch64 (default line), uneven (4096-query mix as one CUDA graph), "
                          "serve (Poisson arrivals through the continuous-batching server)")
     ap.add_argument("--seeds", type=int, default=256)
     ap.add_argument("--trials", type=int, default=1000, help="tables: trials per Table 1-2 point")
+    ap.add_argument("--repeats", type=int, default=1000, help="single: timed tm_match calls")
     ap.add_argument("--best-trials", type=int, default=64, help="tables: trials per K in the Fig. 1(b) search")
     ap.add_argument("--parts", default="table1,table2,fig1a,fig1b")
+    ap.add_argument("--reps", type=int, default=5, help="tables: timed runs per Fig. 1 point")
+    ap.add_argument("--fig-logn", type=int, default=26, help="tables: log2 N of Fig. 1(a)")
+    ap.add_argument("--fig-ks", default="", help="tables: comma-separated log2 K of Fig. 1(a) (default 16 .. logn-1)")
+    ap.add_argument("--no-fulln", action="store_true", help="tables: skip the full-N FFT timing")
     ap.add_argument("--rate", type=float, default=20000.0)
     ap.add_argument("--duration", type=float, default=3.0)
     ap.add_argument("--signals", type=int, default=1024)
@@ -759,6 +890,8 @@ def main():
         return run_sweep(args)
     if args.workload == "tables":
         return run_tables(args)
+    if args.workload == "single":
+        return run_single(args)
     return run_native(args)
 
 

@@ -351,6 +351,20 @@ __device__ __forceinline__ void with_sig(int dtype, const void* x, F&& f) {
   }
 }
 
+// Asks L2 for the signal elements [e0, e1) (128-byte lines; no data comes
+// back to the SM). Loads of them later in the kernel then wait for L2
+// instead of HBM: the fold kernel streamed the signal with evict-first.
+__device__ __forceinline__ void prefetch_elems(const void* x, int dtype, int64_t e0, int64_t e1) {
+  if (e1 <= e0) return;
+  const int sh = dtype == TM_F32 ? 2 : (dtype == TM_F16 ? 1 : 0);
+  int64_t b0 = dtype == TM_BITS_PM1 ? e0 >> 3 : e0 << sh;
+  const int64_t b1 = dtype == TM_BITS_PM1 ? (e1 + 7) >> 3 : e1 << sh;
+  b0 &= ~int64_t(127);
+  const char* c = static_cast<const char*>(x);
+  for (int64_t o = b0 + int64_t(threadIdx.x) * 128; o < b1; o += int64_t(kCorrThreads) * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
 // Exact sum_{i<K} t_i * v(i) over one warp: integer terms in int32 when
 // `small` guarantees no partial sum reaches 2^31, else int64; reals in fp64.
 template <class F>
@@ -472,94 +486,110 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
   const bool small = exact_int && double(t1) * double(maxy) < 2.0e9;
   const void* yv = Q.y_in != nullptr ? Q.y_in : static_cast<const void*>(static_cast<const char*>(a.y) + Q.y_off * 4);
 
-  // exact rescoring of the candidates
-  for (int j = 0; j < Q.nmod; ++j) {
-    const int nc = cs.ncand[j];
-    const int32_t* yi = static_cast<const int32_t*>(yv) + int64_t(j) * P;
-    const float* yf = static_cast<const float*>(yv) + int64_t(j) * P;
-    if (nc <= kCandCap) {
-      // up to four candidates at a time, each summed by the whole block
-      double bv = -INFINITY;
-      int64_t bi = 0x7fffffffffffffffll;
-      for (int c0 = 0; c0 < nc; c0 += 4) {
-        const int nb = min(4, nc - c0);
-        int jj[4];
+  // exact rescoring: the listed candidates of every modulus together, four
+  // at a time, each summed by the whole block
+  int nlist[3] = {0, 0, 0};
+  for (int j = 0; j < Q.nmod; ++j) nlist[j] = cs.ncand[j] <= kCandCap ? cs.ncand[j] : 0;
+  const int b1 = nlist[0], b2 = nlist[0] + nlist[1], total = b2 + nlist[2];
+  double bvj[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int64_t bij[3] = {0x7fffffffffffffffll, 0x7fffffffffffffffll, 0x7fffffffffffffffll};
+  for (int c0 = 0; c0 < total; c0 += 4) {
+    const int nb = min(4, total - c0);
+    int jj[4], mj[4];
+    const int32_t* ypi[4];
+    const float* ypf[4];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) jj[b] = cs.cand[j][c0 + (b < nb ? b : 0)];
-        double v[4];
-        // loads for four indices i per thread go out before any is used
-        constexpr int kU = 4;
-        if (exact_int) {
-          long long acc[4] = {0, 0, 0, 0};
-          for (int i0 = tid; i0 < K; i0 += kU * kCorrThreads) {
-            float tv[kU];
-            int yv[kU][4];
+    for (int b = 0; b < 4; ++b) {
+      const int v = c0 + (b < nb ? b : 0);
+      mj[b] = v < b1 ? 0 : (v < b2 ? 1 : 2);
+      jj[b] = cs.cand[mj[b]][v - (mj[b] == 0 ? 0 : (mj[b] == 1 ? b1 : b2))];
+      ypi[b] = static_cast<const int32_t*>(yv) + int64_t(mj[b]) * P + jj[b];
+      ypf[b] = static_cast<const float*>(yv) + int64_t(mj[b]) * P + jj[b];
+    }
+    double v[4];
+    // loads for four indices i per thread go out before any is used
+    constexpr int kU = 4;
+    if (exact_int) {
+      long long acc[4] = {0, 0, 0, 0};
+      for (int i0 = tid; i0 < K; i0 += kU * kCorrThreads) {
+        float tv[kU];
+        int yw[kU][4];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-              const int i = i0 + u * kCorrThreads;
-              tv[u] = i < K ? __ldg(&t[i]) : 0.f;
+        for (int u = 0; u < kU; ++u) {
+          const int i = i0 + u * kCorrThreads;
+          tv[u] = i < K ? __ldg(&t[i]) : 0.f;
 #pragma unroll
-              for (int b = 0; b < 4; ++b) yv[u][b] = i < K ? yi[jj[b] + i] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-              const long long ti = __float2int_rn(tv[u]);
-#pragma unroll
-              for (int b = 0; b < 4; ++b) acc[b] += ti * yv[u][b];
-            }
-          }
-          block_sum4(acc, redl4);
-#pragma unroll
-          for (int b = 0; b < 4; ++b) v[b] = double(acc[b]);
-        } else {
-          double acc[4] = {0.0, 0.0, 0.0, 0.0};
-          for (int i0 = tid; i0 < K; i0 += kU * kCorrThreads) {
-            float tv[kU], yv[kU][4];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-              const int i = i0 + u * kCorrThreads;
-              tv[u] = i < K ? __ldg(&t[i]) : 0.f;
-#pragma unroll
-              for (int b = 0; b < 4; ++b) yv[u][b] = i < K ? (ints ? float(yi[jj[b] + i]) : yf[jj[b] + i]) : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-#pragma unroll
-              for (int b = 0; b < 4; ++b) acc[b] = fma(double(tv[u]), double(yv[u][b]), acc[b]);
-          }
-          block_sum4(acc, redd4);
-#pragma unroll
-          for (int b = 0; b < 4; ++b) v[b] = acc[b];
+          for (int b = 0; b < 4; ++b) yw[u][b] = i < K ? ypi[b][i] : 0;
         }
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (b < nb) betterd(bv, bi, v[b], jj[b]);
+        for (int u = 0; u < kU; ++u) {
+          const long long ti = __float2int_rn(tv[u]);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[b] += ti * yw[u][b];
+        }
       }
-      if (tid == 0) {
-        s_m[j] = int(bi);
-        s_r[j] = bv;
-      }
+      block_sum4(acc, redl4);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) v[b] = double(acc[b]);
     } else {
-      // more candidates than the list holds: every index, one per warp
-      const int M = Q.M[j];
-      double wv = -INFINITY;
-      int64_t wi = 0x7fffffffffffffffll;
-      for (int c = warp; c < M; c += kWarps) {
-        double v;
-        if (ints) v = warp_dot(t, K, exact_int, small, [&](int i) { return yi[c + i]; });
-        else v = warp_dot(t, K, false, false, [&](int i) { return yf[c + i]; });
-        betterd(wv, wi, v, c);
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i0 = tid; i0 < K; i0 += kU * kCorrThreads) {
+        float tv[kU], yw[kU][4];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int i = i0 + u * kCorrThreads;
+          tv[u] = i < K ? __ldg(&t[i]) : 0.f;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) yw[u][b] = i < K ? (ints ? float(ypi[b][i]) : ypf[b][i]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[b] = fma(double(tv[u]), double(yw[u][b]), acc[b]);
       }
-      if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
-      __syncthreads();
-      if (tid == 0) {
-        double v = wbest_v[0];
-        int64_t i = wbest_i[0];
-        for (int w = 1; w < kWarps; ++w) betterd(v, i, wbest_v[w], wbest_i[w]);
-        s_m[j] = int(i);
-        s_r[j] = v;
-        s_flags |= TM_RF_FULL_RESCORE;
-      }
+      block_sum4(acc, redd4);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) v[b] = acc[b];
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (b >= nb) continue;
+      if (mj[b] == 0) betterd(bvj[0], bij[0], v[b], jj[b]);
+      else if (mj[b] == 1) betterd(bvj[1], bij[1], v[b], jj[b]);
+      else betterd(bvj[2], bij[2], v[b], jj[b]);
+    }
+  }
+  if (tid == 0) {
+    for (int j = 0; j < Q.nmod; ++j) {
+      if (nlist[j] == 0) continue;
+      s_m[j] = int(j == 0 ? bij[0] : (j == 1 ? bij[1] : bij[2]));
+      s_r[j] = j == 0 ? bvj[0] : (j == 1 ? bvj[1] : bvj[2]);
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < Q.nmod; ++j) {
+    if (cs.ncand[j] <= kCandCap) continue;
+    // more candidates than the list holds: every index, one per warp
+    const int32_t* yi = static_cast<const int32_t*>(yv) + int64_t(j) * P;
+    const float* yf = static_cast<const float*>(yv) + int64_t(j) * P;
+    const int M = Q.M[j];
+    double wv = -INFINITY;
+    int64_t wi = 0x7fffffffffffffffll;
+    for (int c = warp; c < M; c += kWarps) {
+      double v;
+      if (ints) v = warp_dot(t, K, exact_int, small, [&](int i) { return yi[c + i]; });
+      else v = warp_dot(t, K, false, false, [&](int i) { return yf[c + i]; });
+      betterd(wv, wi, v, c);
+    }
+    if (lane == 0) { wbest_v[warp] = wv; wbest_i[warp] = wi; }
+    __syncthreads();
+    if (tid == 0) {
+      double v = wbest_v[0];
+      int64_t i = wbest_i[0];
+      for (int w = 1; w < kWarps; ++w) betterd(v, i, wbest_v[w], wbest_i[w]);
+      s_m[j] = int(i);
+      s_r[j] = v;
+      s_flags |= TM_RF_FULL_RESCORE;
     }
     __syncthreads();
   }
@@ -660,10 +690,27 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   __shared__ int redi[kWarps];
 
   const int tid = threadIdx.x;
-  const CorrQ Q = a.q[qi];
+  // the descriptor, once per CTA in shared memory (its moduli are indexed at
+  // run time: a per-thread copy would sit in local memory)
+  __shared__ CorrQ sQ;
+  __syncthreads();   // the previous query's readers are done
+  if (tid < int(sizeof(CorrQ) / 4)) reinterpret_cast<int*>(&sQ)[tid] = reinterpret_cast<const int*>(a.q + qi)[tid];
+  __syncthreads();
+  const CorrQ& Q = sQ;
   const int P = Q.P, logP = Q.logP, K = Q.K;
   const int64_t N = Q.N;
   const Sig sig{Q.x, Q.xdtype};
+  if (Q.y_in == nullptr && Q.y_core == nullptr && !Q.thm2 && Q.x != nullptr) {
+    // the signal entries of the wrap-around and extension terms (part b):
+    // x_n for n < max(K-1, w_j) and n in [w_j, w_j + K - 1), w_j = L_j M_j - N
+    int64_t lo = K - 1;
+    for (int j = 0; j < Q.nmod; ++j) {
+      const int64_t w = Q.L[j] * Q.M[j] - N;
+      lo = max(lo, w);
+      prefetch_elems(Q.x, Q.xdtype, w, min(N, w + K - 1));
+    }
+    prefetch_elems(Q.x, Q.xdtype, 0, min(N, lo));
+  }
   const bool ints = is_int_dtype(Q.xdtype);
   const float* __restrict__ t = Q.t;
   const int npad = P + (P >> 4);
@@ -888,24 +935,29 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       }
     }
     __syncthreads();
-    // extension y[M+i] = y[i] - x_i + x_{(i+LM) mod N}, i < K-1
-    for (int j = 0; j < 2; ++j) {
-      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
-      if (mj < 0) continue;
-      const int M = Q.M[mj];
-      const int64_t LM = Q.L[mj] * M;
+    // extension y[M+i] = y[i] - x_i + x_{(i+LM) mod N}, i < K-1, both
+    // complex slots at once (x_i is shared)
+    {
+      const int m0 = pass == 0 ? 0 : 2, m1 = pass == 0 ? 1 : -1;   // moduli in complex slots 0, 1
+      const int M0 = Q.M[m0], M1 = m1 >= 0 ? Q.M[m1] : 0;
+      const int64_t LM0 = Q.L[m0] * M0, LM1 = m1 >= 0 ? Q.L[m1] * M1 : 0;
       for (int i0 = tid; i0 < K - 1; i0 += kB * kCorrThreads) {
-        float xi[kB], xw[kB];
+        float xi[kB], xw0[kB], xw1[kB];
         with_sig(Q.xdtype, Q.x, [&](auto sx) {
 #pragma unroll
           for (int b = 0; b < kB; ++b) {
             const int i = i0 + b * kCorrThreads;
-            xi[b] = xw[b] = 0.f;
+            xi[b] = xw0[b] = xw1[b] = 0.f;
             if (i < K - 1 && !Q.thm2) {   // Thm. 2: periodic, y[M+i] = y[i]
-              int64_t w = i + LM - N;   // LM >= N and i + LM - N < 2M, so one reduction is rare
-              if (w >= N) w %= N;
+              int64_t w0 = i + LM0 - N;   // LM >= N and i + LM - N < 2M, so one reduction is rare
+              if (w0 >= N) w0 %= N;
               xi[b] = sx.val(i);
-              xw[b] = sx.val(w);
+              xw0[b] = sx.val(w0);
+              if (m1 >= 0) {
+                int64_t w1 = i + LM1 - N;
+                if (w1 >= N) w1 %= N;
+                xw1[b] = sx.val(w1);
+              }
             }
           }
         });
@@ -913,9 +965,14 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
         for (int b = 0; b < kB; ++b) {
           const int i = i0 + b * kCorrThreads;
           if (i < K - 1) {
-            const int e = 2 * pad_idx(M + i) + j, e0 = 2 * pad_idx(i) + j;
-            if (ints) ib[e] = ib[e0] - int(xi[b]) + int(xw[b]);
-            else fb[e] = fb[e0] - xi[b] + xw[b];
+            const int e = 2 * pad_idx(M0 + i), ee = 2 * pad_idx(i);
+            if (ints) ib[e] = ib[ee] - int(xi[b]) + int(xw0[b]);
+            else fb[e] = fb[ee] - xi[b] + xw0[b];
+            if (m1 >= 0) {
+              const int e1 = 2 * pad_idx(M1 + i) + 1;
+              if (ints) ib[e1] = ib[ee + 1] - int(xi[b]) + int(xw1[b]);
+              else fb[e1] = fb[ee + 1] - xi[b] + xw1[b];
+            }
           }
         }
       }
@@ -1029,7 +1086,10 @@ __global__ void __launch_bounds__(kCorrThreads, 1) corr_blocked_kernel(const Cor
 
   const int tid = threadIdx.x;
   const int qi = a.order[blockIdx.x];
-  const CorrQ Q = a.q[qi];
+  __shared__ CorrQ sQ;   // the descriptor, once per CTA
+  if (tid < int(sizeof(CorrQ) / 4)) reinterpret_cast<int*>(&sQ)[tid] = reinterpret_cast<const int*>(a.q + qi)[tid];
+  __syncthreads();
+  const CorrQ& Q = sQ;
   const int P = Q.P, K = Q.K;
   const int64_t N = Q.N;
   const Sig sig{Q.x, Q.xdtype};
