@@ -316,6 +316,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
   b->fold_of.assign(n, 0);
   b->dh.assign(n, 0);
   b->drows.assign(n, 0);
+  b->dpitch.assign(n, 0);
   b->dpart.assign(n, 0);
   int64_t part = 0;
   for (int32_t dt = TM_I8_PM1; dt <= TM_F32; ++dt) {
@@ -381,14 +382,18 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
   for (int i = 0; i < n; ++i) {
     const PlanCore& p = b->pc[i];
     if (!p.direct) continue;
-    const int32_t dh = direct_row_groups(p.L[0]);
+    // int8 with at most 16 rows: the completion sums the rows itself (dh = 0)
+    const int32_t dh = (p.xdtype == TM_I8_PM1 && p.L[0] <= 16) ? 0 : direct_row_groups(p.L[0]);
     const int32_t mmax = *std::max_element(p.M, p.M + p.nmod);
+    const int32_t pitch = (mmax + 3) & ~3;   // rows of 16-byte multiples: vector stores
+    part = (part + 3) & ~int64_t(3);
     b->dh[i] = dh;
     b->drows[i] = dh > 0 ? int32_t(ceil_div(p.L[0], dh)) : 0;
+    b->dpitch[i] = pitch;
     b->dpart[i] = part;
-    part += int64_t(p.nmod) * dh * mmax;
+    part += int64_t(p.nmod) * dh * pitch;
     b->maxM_direct = std::max(b->maxM_direct, mmax);
-    b->maxHM_direct = std::max(b->maxHM_direct, std::max(1, dh) * p.nmod);
+    b->maxHM_direct = std::max(b->maxHM_direct, dh * p.nmod);   // 0: no first-stage launch
   }
   b->part_elems = std::max<int64_t>(part, 16);
 
@@ -405,6 +410,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     c.direct = p.direct;
     c.dh = b->dh[i];
     c.drows = b->drows[i];
+    c.dpitch = b->dpitch[i];
     c.dpart = b->dpart[i];
     c.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
     c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
@@ -982,7 +988,7 @@ tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, in
   if (launches) {
     int32_t l = (b->n > b->n_blocked + b->n_large ? 1 : 0) + (b->n_blocked > 0 ? 1 : 0);
     for (const auto& g : b->groups) l += g.W > 0 ? 1 : 0;
-    l += b->direct.empty() ? 0 : 2;
+    l += b->direct.empty() ? 0 : (b->maxHM_direct > 0 ? 2 : 1);
     for (int i = 0; i < b->n; ++i)
       if (b->is_large[i]) l += large_launches(b->lq[i].nsd);
     *launches = l;

@@ -7,6 +7,7 @@
 //     group) sums its rows' natural entries (k + l M < N) with the loads of
 //     eight rows in flight at once. A warp's consecutive threads read
 //     consecutive entries of x, so every row is read with coalesced loads.
+//     int8 signals with at most 16 rows skip this stage (dh = 0).
 //  2. Completion, one thread per fold entry k < M+K-1: the group sums in
 //     group order, the wrap-around entry x_{k + (L-1) M - N} when the last
 //     row runs past N, and for k >= M the extension
@@ -101,13 +102,11 @@ __device__ __forceinline__ void part_cols(const CorrQ& Q, int j, int h, int64_t 
       else sf[u] += v;
     }
   }
-  int32_t* dst = partial + Q.dpart + (int64_t(j) * Q.dh + h) * M + k0;
-#pragma unroll
-  for (int u = 0; u < kDirCols; ++u) {
-    if (k0 + u >= M) break;
-    if constexpr (kInt) dst[u] = si[u];
-    else reinterpret_cast<float*>(dst)[u] = sf[u];
-  }
+  // the row pitch is a multiple of four columns: one 16-byte store (columns
+  // past M land in the row's padding)
+  int4* dst = reinterpret_cast<int4*>(partial + Q.dpart + (int64_t(j) * Q.dh + h) * Q.dpitch + k0);
+  if constexpr (kInt) *dst = make_int4(si[0], si[1], si[2], si[3]);
+  else *dst = make_int4(__float_as_int(sf[0]), __float_as_int(sf[1]), __float_as_int(sf[2]), __float_as_int(sf[3]));
 }
 
 __global__ void __launch_bounds__(kDirThreads) fold_direct_part_kernel(const CorrQ* q, const int32_t* idx,
@@ -129,7 +128,7 @@ __global__ void __launch_bounds__(kDirThreads) fold_direct_part_kernel(const Cor
 struct DirQ {
   const void* x;
   int64_t N, M, L, P, dpart;
-  int32_t K, dh, thm2;
+  int32_t K, dh, thm2, pitch;
 };
 
 // Value of fold entry k (int32 bits for +-1 signals, else fp32 bits).
@@ -141,12 +140,13 @@ __device__ __forceinline__ uint32_t complete_entry(const DirQ& Q, int j, int64_t
   int vi = 0;
   if (k < M + Q.K - 1) {
     const int64_t c = k < M ? k : k - M;
-    const int32_t* ps = partial + Q.dpart + int64_t(j) * Q.dh * M + c;
+    const int32_t* ps = partial + Q.dpart + int64_t(j) * Q.dh * Q.pitch + c;
     // group sums in group order, eight loads in flight
     for (int h0 = 0; h0 < Q.dh; h0 += 8) {
       uint32_t w[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) w[u] = h0 + u < Q.dh ? __ldg(reinterpret_cast<const uint32_t*>(ps) + int64_t(h0 + u) * M) : 0u;
+      for (int u = 0; u < 8; ++u)
+        w[u] = h0 + u < Q.dh ? __ldg(reinterpret_cast<const uint32_t*>(ps) + int64_t(h0 + u) * Q.pitch) : 0u;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         if constexpr (kInt) vi += int(w[u]);
@@ -175,6 +175,154 @@ __device__ __forceinline__ uint32_t complete_entry(const DirQ& Q, int j, int64_t
 
 // kDirCols entries per thread (a block's threads on consecutive k): all
 // loads first, then the stores.
+// int8 signals: four consecutive entries k0 .. k0+3 per thread, 32-bit
+// index arithmetic where it fits, the group loads of the four entries in
+// flight together.
+__device__ __forceinline__ int i8v(const uint8_t* x, int64_t n) { return (__ldg(x + n) & 2u) ? -1 : 1; }
+
+__device__ __forceinline__ void complete4_i8(const DirQ& D, int j, const int32_t* partial, int32_t* yj) {
+  const int M = int(D.M), P = int(D.P), kend = int(D.M) + D.K - 1, dh = D.dh, pitch = D.pitch;
+  const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (k0 >= P) return;
+  int c[4], s[4];
+  bool live[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int k = k0 + u;
+    live[u] = k < kend;
+    c[u] = k < M ? k : k - M;
+    s[u] = 0;
+  }
+  const int32_t* base = partial + D.dpart + int64_t(j) * dh * pitch;
+#pragma unroll 4
+  for (int h = 0; h < dh; ++h) {
+    const int32_t* ph = base + int64_t(h) * pitch;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] += live[u] ? __ldg(ph + c[u]) : 0;
+  }
+  if (!D.thm2) {
+    const uint8_t* x = static_cast<const uint8_t*>(D.x);
+    const int64_t wr = (D.L - 1) * D.M - D.N, ex = D.L * D.M - D.N;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!live[u]) continue;
+      const int64_t w = c[u] + wr;   // the last row's entry past N wraps around
+      if (w >= 0) s[u] += i8v(x, w);
+      if (k0 + u >= M) {              // extension: y[M+c] = y[c] - x_c + x_{(c + L M) mod N}
+        int64_t e = c[u] + ex;
+        if (e >= D.N) e %= D.N;
+        s[u] += i8v(x, e) - i8v(x, c[u]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) if (!live[u]) s[u] = 0;
+  int32_t* o = yj + k0;
+  if ((reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+    *reinterpret_cast<int4*>(o) = make_int4(s[0], s[1], s[2], s[3]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) o[u] = s[u];   // P is a multiple of 4: k0 + 3 < P
+  }
+}
+
+// int8 signals with at most 16 rows (no first stage, dh = 0): four
+// consecutive entries per thread summed from the definition,
+// y[k] = sum_{l<L} x_{(k + l M) mod N} (Thm. 2: terms below N of entry
+// k mod M). Each row's four bytes come from two aligned words and a funnel
+// shift and are added bytewise (at most 16 terms per byte lane); rows whose
+// words would leave the signal's 16-byte-aligned prefix, or that wrap
+// within the four bytes, go byte by byte.
+constexpr int kDirQuads = 2;   // quads of four entries per thread of the direct int8 path
+
+__device__ __forceinline__ void direct4_i8(const DirQ& D, int32_t* yj) {
+  const int M = int(D.M), P = int(D.P), kend = int(D.M) + D.K - 1, L = int(D.L);
+  const int64_t N = D.N, n16 = D.N & ~int64_t(15);
+  const int kq0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4 * kDirQuads;
+  if (kq0 >= P) return;
+  const uint8_t* x = static_cast<const uint8_t*>(D.x);
+  const uint32_t* X = static_cast<const uint32_t*>(D.x);
+  int s[kDirQuads][4];
+  uint32_t acc[kDirQuads];
+  int64_t cb[kDirQuads];
+  bool live[kDirQuads], split[kDirQuads];
+#pragma unroll
+  for (int g = 0; g < kDirQuads; ++g) {
+    const int k0 = kq0 + 4 * g;
+    live[g] = k0 < P && k0 < kend;
+    // Thm. 2 with the four entries on both sides of M: entry by entry below
+    split[g] = D.thm2 && k0 < M && k0 + 3 >= M;
+    cb[g] = D.thm2 && k0 >= M ? k0 - M : k0;   // consecutive columns cb .. cb+3
+    acc[g] = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[g][u] = 0;
+  }
+#pragma unroll 2
+  for (int l = 0; l < L; ++l) {
+    uint32_t w0[kDirQuads], w1[kDirQuads];
+    int64_t nr[kDirQuads];
+    bool fast[kDirQuads];
+#pragma unroll
+    for (int g = 0; g < kDirQuads; ++g) {
+      int64_t n = cb[g] + int64_t(l) * M;
+      if (n >= N && !D.thm2) {
+        n -= N;
+        if (n >= N) n %= N;
+      }
+      nr[g] = n;
+      fast[g] = live[g] && !split[g] && n + 8 <= n16;
+      w0[g] = fast[g] ? __ldg(&X[n >> 2]) : 0u;
+      w1[g] = fast[g] ? __ldg(&X[(n >> 2) + 1]) : 0u;
+    }
+#pragma unroll
+    for (int g = 0; g < kDirQuads; ++g) {
+      if (fast[g]) {
+        acc[g] = __vadd4(acc[g], __funnelshift_r(w0[g], w1[g], int(nr[g] & 3) * 8));
+      } else if (live[g] && !split[g]) {
+        // near the end of the signal: byte by byte
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int64_t nn = nr[g] + u;
+          if (nn >= N) {
+            if (D.thm2) continue;   // zero padding
+            nn -= N;
+          }
+          s[g][u] += i8v(x, nn);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < kDirQuads; ++g) {
+    const int k0 = kq0 + 4 * g;
+    if (k0 >= P) break;
+    if (split[g] && live[g]) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u;
+        const int64_t c = k >= M ? k - M : k;
+        for (int l = 0; l < L; ++l) {
+          const int64_t n = c + int64_t(l) * M;
+          if (n >= N) break;
+          s[g][u] += i8v(x, n);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      s[g][u] += int(int8_t(uint8_t(acc[g] >> (8 * u))));
+      if (k0 + u >= kend) s[g][u] = 0;
+    }
+    int32_t* o = yj + k0;
+    if ((reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+      *reinterpret_cast<int4*>(o) = make_int4(s[g][0], s[g][1], s[g][2], s[g][3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) o[u] = s[g][u];   // P is a multiple of 4
+    }
+  }
+}
+
 template <int DT>
 __device__ __forceinline__ void complete_cols(const DirQ& D, int j, const int32_t* partial, void* y) {
   uint32_t v[kDirCols];
@@ -191,19 +339,22 @@ __device__ __forceinline__ void complete_cols(const DirQ& D, int j, const int32_
   }
 }
 
-__global__ void __launch_bounds__(kDirThreads) fold_direct_complete_kernel(const CorrQ* q, const int32_t* idx,
+__global__ void __launch_bounds__(kDirThreads, 4) fold_direct_complete_kernel(const CorrQ* q, const int32_t* idx,
                                                                            const int32_t* partial, void* y_base) {
   const CorrQ& Q = q[idx[blockIdx.z]];
   const int j = blockIdx.y;
   if (j >= Q.nmod) return;
   DirQ D;
   D.x = Q.x; D.N = Q.N; D.M = Q.M[j]; D.L = Q.L[j]; D.P = Q.P; D.dpart = Q.dpart;
-  D.K = Q.K; D.dh = Q.dh; D.thm2 = Q.thm2;
+  D.K = Q.K; D.dh = Q.dh; D.thm2 = Q.thm2; D.pitch = Q.dpitch;
   const int dt = Q.xdtype;
   void* y = static_cast<char*>(y_base) + Q.y_off * 4;
   // kDirCols entries per thread, a block's threads on consecutive k
   switch (dt) {
-    case TM_I8_PM1: complete_cols<TM_I8_PM1>(D, j, partial, y); break;
+    case TM_I8_PM1:
+      if (D.dh == 0) direct4_i8(D, static_cast<int32_t*>(y) + int64_t(j) * D.P);
+      else complete4_i8(D, j, partial, static_cast<int32_t*>(y) + int64_t(j) * D.P);
+      break;
     case TM_BITS_PM1: complete_cols<TM_BITS_PM1>(D, j, partial, y); break;
     case TM_F16: complete_cols<TM_F16>(D, j, partial, y); break;
     default: complete_cols<TM_F32>(D, j, partial, y); break;
@@ -216,8 +367,10 @@ cudaError_t launch_fold_direct(const CorrQ* q, const int32_t* idx, int32_t n, in
                                int32_t maxM, int32_t maxHM, int32_t* partial, void* y, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t per = int64_t(kDirThreads) * kDirCols;
-  const dim3 g1(unsigned((maxM + per - 1) / per), unsigned(maxHM), unsigned(n));
-  fold_direct_part_kernel<<<g1, kDirThreads, 0, s>>>(q, idx, partial);
+  if (maxHM > 0) {   // some query has row groups (dh > 0)
+    const dim3 g1(unsigned((maxM + per - 1) / per), unsigned(maxHM), unsigned(n));
+    fold_direct_part_kernel<<<g1, kDirThreads, 0, s>>>(q, idx, partial);
+  }
   const dim3 g2(unsigned((maxP + per - 1) / per), unsigned(maxmod), unsigned(n));
   fold_direct_complete_kernel<<<g2, kDirThreads, 0, s>>>(q, idx, partial, y);
   return cudaGetLastError();

@@ -79,7 +79,7 @@ struct tm_batch_s {
   int32_t maxP = 0;        // largest FFT of the shared-memory correlation launch
   std::vector<int32_t> direct;   // queries folded entry by entry (fold_direct)
   int32_t maxP_direct = 0, maxmod_direct = 0, maxM_direct = 0, maxHM_direct = 0;
-  std::vector<int32_t> dh, drows;   // entry-by-entry folds: row groups, rows per group, partial offsets
+  std::vector<int32_t> dh, drows, dpitch;   // entry-by-entry folds: row groups, rows per group, row pitch, partial offsets
   std::vector<int64_t> dpart;
   int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_large - n_blocked, n - n_large))
   int32_t n_large = 0;     // queries on the multi-CTA path (order[n - n_large, n))

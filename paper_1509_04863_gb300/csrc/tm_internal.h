@@ -130,9 +130,10 @@ struct CorrQ {
   const void* y_in;   // complete folds [2][P] supplied by the caller (the fold
                       // completion is skipped; x may then be null: no exact score)
   int32_t direct;     // folded entry by entry into y (then given as y_in)
-  int32_t dh;         // entry-by-entry fold: row groups of the first stage
+  int32_t dh;         // entry-by-entry fold: row groups of the first stage (0: none)
   int32_t drows;      // rows per group
-  int64_t dpart;      // its partial sums [nmod][dh][M_j] in the partial buffer (int32 units)
+  int32_t dpitch;     // columns per group row of the partial sums (max M_j, rounded up to 4)
+  int64_t dpart;      // its partial sums [nmod][dh][dpitch] in the partial buffer (int32 units)
   const void* y_core; // cached folds over k < M_j (wrap-around and last entries
                       // included), row j at y_core + j core_pitch; the fold
                       // kernel skips the signal, only the extension is added
@@ -195,7 +196,8 @@ cudaError_t launch_score_slice(const SliceScoreArgs& a, cudaStream_t s);
 
 // Step 3 entry by entry for the queries idx[0..n) of q (CorrQ::direct):
 // partial sums over dh row groups into partial + q.dpart, then the complete
-// folds written to y + q.y_off. maxM, maxHM: the largest M_j and dh * nmod.
+// folds written to y + q.y_off. maxM, maxHM: the largest M_j and dh * nmod
+// (maxHM = 0: no query has a first stage, one launch).
 cudaError_t launch_fold_direct(const CorrQ* q, const int32_t* idx, int32_t n, int32_t maxP, int32_t maxmod,
                                int32_t maxM, int32_t maxHM, int32_t* partial, void* y, cudaStream_t s);
 // Row groups of the entry-by-entry fold for L rows: about 16 rows each.

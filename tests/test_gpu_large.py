@@ -57,7 +57,9 @@ def test_large_vs_oracle(tm, N, K, mode, xdtype):
     assert b.infos[0]["P"] > 16384
     P = b.infos[0]["P"]
     nsd = 1 if P <= 1 << 22 else 2
-    assert b.stats()["launches_per_run"] == 2 + 1 + 2 * (nsd + 1) + nsd + 5
+    L = -(-N // b.infos[0]["M1"])
+    fold_launches = 1 if (xdtype == "i8" and L <= 16) else 2   # int8 with few rows: no first stage
+    assert b.stats()["launches_per_run"] == fold_launches + 1 + 2 * (nsd + 1) + nsd + 5
     ref = O.match_query(q, corr="fft")
     r = res[0]
     assert r["status"] & ~0xFF == 0, r
