@@ -168,29 +168,54 @@ __device__ __forceinline__ float2 wsc(int a, int e) {
   return cmul(make_float2(c, -s), make_float2(c2, -s2));
 }
 
+// Twiddles along a thread's elements. A thread's elements of a tile share
+// the column c and step down the rows by s = kLT / C, so their twiddles
+// W^{(n0+c) i} form a geometric sequence in the element number u. TwSeq
+// gives them in order: exact values (sincospif) at u = 0, 4, 8, 12 and up
+// to three multiplications by the exact step W^{(n0+c) s} in between
+// (about 10 ulp at most, inside the rounding bound's margin).
+struct TwSeq {
+  int a;
+  uint32_t e0, d;
+  float2 step, w;
+  __device__ __forceinline__ TwSeq(int a_, uint32_t e0_, uint32_t d_) : a(a_), e0(e0_), d(d_) {
+    step = wsc(a, d & ((1u << a) - 1));
+  }
+  __device__ __forceinline__ float2 at(int u) {   // called for u = 0, 1, 2, ... in order
+    if ((u & 3) == 0) w = wsc(a, (e0 + uint32_t(u) * d) & ((1u << a) - 1));
+    else w = cmul(w, step);
+    return w;
+  }
+};
+
 // One Stockham pass of radix R over NC = 2^logNC independent DFTs of
-// length L = 2^logL held in buf at pad(i sI + col sC): butterfly j of a
-// column takes i = j + r L/R, twiddles by W_{Ns R}^{r (j mod Ns)} and
-// writes to (j - j mod Ns) R + j mod Ns + r Ns.
+// length L = 2^logL (NC L = 8192) held in buf at pad(i NC + col): butterfly
+// j of a column takes i = j + r L/R, twiddles by W_{Ns R}^{r (j mod Ns)} and
+// writes to (j - j mod Ns) R + j mod Ns + r Ns. With NC L = 8192 the read
+// index of leg r is bi + r 8192/R (bi = j NC + col, the butterfly number)
+// and the write index W0 + r Ns NC, both multiples of 16 apart, so the
+// padded addresses step by constants.
 template <int R>
-__device__ __forceinline__ void bpass(float2* buf, int logL, int logNs, int sI, int sC, int logNC) {
+__device__ __forceinline__ void bpass(float2* buf, int logL, int logNs, int logNC) {
   constexpr int NB = kLPPT / R;
   constexpr int LR = lg<R>();
+  constexpr int kRead = (kLPts / R) / 16 * 17;   // padded step between legs
   const int Ns = 1 << logNs;
-  const int legs = 1 << (logL - LR);
   const int twsh = kLRowLog - logNs - LR;
   const int cmask = (1 << logNC) - 1;
+  const int wstep = ((Ns << logNC) >> 4) * 17;    // padded step between outputs
   float2 v[NB][R];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int bi = threadIdx.x + b * kLT;
-    const int col = bi & cmask, jp = bi >> logNC;
-    const int k = jp & (Ns - 1);
+    const int k = (bi >> logNC) & (Ns - 1);
+    const int a0 = pad(bi);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b][r] = buf[pad((jp + r * legs) * sI + col * sC)];
+    for (int r = 0; r < R; ++r) v[b][r] = buf[a0 + r * kRead];
     if (Ns > 1) {
+      const int tk = k << twsh;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], __ldg(&g_tw13[(r * k) << twsh]));
+      for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], __ldg(&g_tw13[r * tk]));
     }
     dftr<R>(v[b]);
   }
@@ -200,21 +225,21 @@ __device__ __forceinline__ void bpass(float2* buf, int logL, int logNs, int sI, 
     const int bi = threadIdx.x + b * kLT;
     const int col = bi & cmask, jp = bi >> logNC;
     const int k = jp & (Ns - 1);
-    const int base = (jp - k) * R + k;
+    const int w0 = pad((((jp - k) * R + k) << logNC) + col);
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[pad((base + r * Ns) * sI + col * sC)] = v[b][brev<R>(r)];
+    for (int r = 0; r < R; ++r) buf[w0 + r * wstep] = v[b][brev<R>(r)];
   }
   __syncthreads();
 }
 
 // Forward DFTs of length 2^logL (natural order in and out) of 8192 >> logL
-// columns; caller synchronised before.
-__device__ void bfft(float2* buf, int logL, int sI, int sC, int logNC) {
+// columns at pad(i 2^logNC + col); caller synchronised before.
+__device__ void bfft(float2* buf, int logL, int logNC) {
   const int first = logL & 3;
-  if (first == 1) bpass<2>(buf, logL, 0, sI, sC, logNC);
-  else if (first == 2) bpass<4>(buf, logL, 0, sI, sC, logNC);
-  else if (first == 3) bpass<8>(buf, logL, 0, sI, sC, logNC);
-  for (int logNs = first; logNs < logL; logNs += 4) bpass<16>(buf, logL, logNs, sI, sC, logNC);
+  if (first == 1) bpass<2>(buf, logL, 0, logNC);
+  else if (first == 2) bpass<4>(buf, logL, 0, logNC);
+  else if (first == 3) bpass<8>(buf, logL, 0, logNC);
+  for (int logNs = first; logNs < logL; logNs += 4) bpass<16>(buf, logL, logNs, logNC);
 }
 
 // ---------------------------------------------------------------- reductions
@@ -378,12 +403,23 @@ __global__ void __launch_bounds__(kLT, 2) lfwd_kernel(const LQ q, int d, const f
     }
   }
   __syncthreads();
-  bfft(sm, tl.logL, 1 << tl.logC, 1, tl.logC);
+  bfft(sm, tl.logL, tl.logC);
   float2* d0 = dst + tl.base;
-  for (int u = 0; u < kLPPT; ++u) {
-    const int e = threadIdx.x + u * kLT;
-    const int i = e >> tl.logC, c = e & tl.cmask;
-    d0[tile_off(tl, e)] = cmul(sm[pad(e)], wsc(tl.logPd, (tl.n0 + c) * i));
+  if (tl.logC <= 9) {   // C <= kLT: the thread's elements share their column
+    const int c = threadIdx.x & tl.cmask;
+    const uint32_t nc = uint32_t(tl.n0 + c);
+    TwSeq tw(tl.logPd, nc * uint32_t(threadIdx.x >> tl.logC), nc * uint32_t(kLT >> tl.logC));
+#pragma unroll
+    for (int u = 0; u < kLPPT; ++u) {
+      const int e = threadIdx.x + u * kLT;
+      d0[tile_off(tl, e)] = cmul(sm[pad(e)], tw.at(u));
+    }
+  } else {
+    for (int u = 0; u < kLPPT; ++u) {
+      const int e = threadIdx.x + u * kLT;
+      const int i = e >> tl.logC, c = e & tl.cmask;
+      d0[tile_off(tl, e)] = cmul(sm[pad(e)], wsc(tl.logPd, (tl.n0 + c) * i));
+    }
   }
 }
 
@@ -398,19 +434,33 @@ __global__ void __launch_bounds__(kLT, 2) linv_kernel(const LQ q, int d) {
   float2* a0 = q.A + tl.base;
   // loads of eight elements in flight before their twiddles
   static_assert(kLPPT % 8 == 0, "load batches");
-  for (int u0 = 0; u0 < kLPPT; u0 += 8) {
-    float2 v[8];
+  if (tl.logC <= 9) {   // C <= kLT: the thread's elements share their column
+    const int c = threadIdx.x & tl.cmask;
+    const uint32_t nc = uint32_t(tl.n0 + c);
+    TwSeq tw(tl.logPd, nc * uint32_t(threadIdx.x >> tl.logC), nc * uint32_t(kLT >> tl.logC));
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = a0[tile_off(tl, threadIdx.x + (u0 + u) * kLT)];
+    for (int u0 = 0; u0 < kLPPT; u0 += 8) {
+      float2 v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = threadIdx.x + (u0 + u) * kLT;
-      const int i = e >> tl.logC, c = e & tl.cmask;
-      sm[pad(e)] = cmul(v[u], wsc(tl.logPd, (tl.n0 + c) * i));
+      for (int u = 0; u < 8; ++u) v[u] = a0[tile_off(tl, threadIdx.x + (u0 + u) * kLT)];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sm[pad(threadIdx.x + (u0 + u) * kLT)] = cmul(v[u], tw.at(u0 + u));
+    }
+  } else {
+    for (int u0 = 0; u0 < kLPPT; u0 += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = a0[tile_off(tl, threadIdx.x + (u0 + u) * kLT)];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = threadIdx.x + (u0 + u) * kLT;
+        const int i = e >> tl.logC, c = e & tl.cmask;
+        sm[pad(e)] = cmul(v[u], wsc(tl.logPd, (tl.n0 + c) * i));
+      }
     }
   }
   __syncthreads();
-  bfft(sm, tl.logL, 1 << tl.logC, 1, tl.logC);
+  bfft(sm, tl.logL, tl.logC);
   if constexpr (!OUT) {
     for (int u = 0; u < kLPPT; ++u) {
       const int e = threadIdx.x + u * kLT;
@@ -460,17 +510,23 @@ __global__ void __launch_bounds__(kLT, 2) lrow_kernel(const LQ q) {
     sm[pad(e)] = buf[base + e];
   }
   __syncthreads();
-  bfft(sm, 9, 16, 1, 4);
+  bfft(sm, 9, 4);
   float mx = 0.f;
   // each thread: rows k_i = tid + h kLT
 #pragma unroll
   for (int h = 0; h < 512 / kLT; ++h) {
     const int ki = threadIdx.x + h * kLT;
+    // W_8192^{c k_i}: the table's exact values at c = 4, 8, 12, steps by W^{k_i} between
+    const float2 wst = __ldg(&g_tw13[ki]);
+    float2 rw[16];
+    rw[0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int c = 1; c < 16; ++c) rw[c] = (c & 3) == 0 ? __ldg(&g_tw13[(c * ki) & 8191]) : cmul(rw[c - 1], wst);
     float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const float2 x = sm[pad(ki * 16 + c)];
-      v[c] = c == 0 ? x : cmul(x, wsc(kLRowLog, c * ki));
+      v[c] = c == 0 ? x : cmul(x, rw[c]);
     }
     dftr<16>(v);   // v[brev(k_c)] = spectrum at (k_i, k_c)
     if constexpr (TEMPLATE) {
@@ -497,12 +553,12 @@ __global__ void __launch_bounds__(kLT, 2) lrow_kernel(const LQ q) {
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const float2 x = g[brev<16>(c)];
-        sm[pad(ki * 16 + c)] = c == 0 ? x : cmul(x, wsc(kLRowLog, c * ki));
+        sm[pad(ki * 16 + c)] = c == 0 ? x : cmul(x, rw[c]);
       }
     }
   }
   __syncthreads();
-  if constexpr (!TEMPLATE) bfft(sm, 9, 16, 1, 4);
+  if constexpr (!TEMPLATE) bfft(sm, 9, 4);
   for (int u = 0; u < kLPPT; ++u) {
     const int e = threadIdx.x + u * kLT;
     buf[base + e] = sm[pad(e)];
