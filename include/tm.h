@@ -161,7 +161,11 @@ typedef struct tm_plan_s* tm_plan_t;
  * length P >= max(M)+K-1 (steps 4-5 zero-pad t and y to a common length).
  * Host only; needs no GPU. TM_EINVAL when K < 1, K > N, M_i < K, M_i > 2N,
  * gcd(M1, M2) != 1, or M1*M2 <= N without TM_ALLOW_AMBIG;
- * TM_EUNSUPPORTED when P > 16384 or the byte size of x exceeds 2^31-16. */
+ * TM_EUNSUPPORTED when P > 2^26 (2^14 with TM_THREE_MODULI) or the byte
+ * size of x exceeds 2^31-2^16. FFT lengths up to 16384 run in shared
+ * memory, one CTA per query; longer ones in overlap-save blocks (a CTA per
+ * query, batches of more than eight such queries) or as passes over global
+ * memory on all SMs (up to 2^26; every P above 2^18). */
 TM_API tm_status tm_plan_create(const tm_plan_desc* desc, tm_plan_t* out);
 TM_API tm_status tm_plan_get_info(tm_plan_t plan, tm_plan_info* info);
 /* Frees the plan and its device workspace. Safe on NULL. */
@@ -220,12 +224,15 @@ typedef struct tm_batch_s* tm_batch_t;
 TM_API tm_status tm_batch_create(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* out);
 /* Replace the x / t pointers of every query (same shapes as at creation). */
 TM_API tm_status tm_batch_set_inputs(tm_batch_t b, const tm_query* q, int32_t n);
-/* Step 3 for the whole batch: one launch that streams every signal once and
- * writes partial column sums of both folds. */
+/* Step 3 for the whole batch: one launch per signal storage type that
+ * streams every signal once and writes partial column sums of both folds;
+ * moduli too wide for its register-resident columns (about 2^14 and more)
+ * are folded entry by entry instead (one or two more launches). */
 TM_API tm_status tm_batch_fold(tm_batch_t b, tm_stream_t stream);
 /* Steps 3 (completion: wrap term, extension k >= M), 4-9 for every query:
  * one CTA per query, largest FFT first, in one launch (plus one launch for
- * queries whose FFT exceeds 16384 points); writes n tm_results to out_dev.
+ * the overlap-save queries, and a sequence of launches per query on the
+ * all-SM path, see tm_plan_create); writes n tm_results to out_dev.
  * Must follow tm_batch_fold on the same stream. */
 TM_API tm_status tm_batch_correlate(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
 /* tm_batch_fold + tm_batch_correlate. */

@@ -188,3 +188,30 @@ def test_fold_cache(tm):
                 {f: b[f] for f in ("shift", "status", "m1", "m2", "r1", "r2", "score", "n_cand")}, (i, a, b)
         else:
             assert (a["m1"], a["m2"]) == (b["m1"], b["m2"]) or abs(a["r1"] - b["r1"]) <= 1e-4 * max(1.0, abs(a["r1"]))
+
+
+def test_long_fft_requests(tm):
+    """Requests whose FFT exceeds the overlap-save range (P = 2^19, the
+    all-SM path) and others in the overlap-save range go through the server
+    among ordinary ones and equal the standalone runs (+-1 signals)."""
+    srv = tm.Server(n_streams=2, max_batch=16, arena_bytes=1 << 30)
+    long_q = W.planted_query(31, 1 << 20, 1 << 18, "i8", flip_p=0.05, mode="paper")
+    mid_q = W.planted_query(32, 1 << 21, 40000, "i8", flip_p=0.05, mode="paper")
+    small_q = W.planted_query(33, 1 << 20, 1024, "i8", flip_p=0.05, mode="paper")
+    xs, sids = [], []
+    for q in (long_q, mid_q, small_q):
+        xs.append(torch.from_numpy(q.x).cuda())
+        sids.append(srv.register_signal(q.x, q.N, "i8"))
+    order = [0, 2, 1, 2, 0, 1, 2, 2]
+    for tag, k in enumerate(order):
+        assert srv.submit(sids[k], (long_q, mid_q, small_q)[k].t, tag=tag, mode="paper") == tm.TM_OK
+    got = _collect(srv, len(order))
+    for tag, k in enumerate(order):
+        q = (long_q, mid_q, small_q)[k]
+        r = got[tag]
+        assert r["req_status"] == tm.TM_OK
+        ref = _standalone(tm, q, xs[k])
+        assert {f: r[f] for f in ref} == ref, (tag, r, ref)
+        if k < 2:   # K^2 / ln K well above N: the planted shift comes back
+            assert r["shift"] == q.k_star
+    srv.close()
