@@ -193,7 +193,20 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
     toff[i] = t_floats;
     t_floats += pad16(reqs[i].q.K);
   }
-  if (t_floats > sl.h_t_cap) return TM_ENOMEM;
+  if (t_floats > sl.h_t_cap) {
+    // a template longer than the staging holds (long FFTs): alone, the
+    // slot's staging grows (the slot is idle, nothing reads it); with
+    // others, the iteration is split
+    if (n > 1) return TM_ENOMEM;
+    float* h = nullptr;
+    if (cudaMallocHost(&h, size_t(t_floats) * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return TM_ENOMEM;
+    }
+    cudaFreeHost(sl.h_t);
+    sl.h_t = h;
+    sl.h_t_cap = t_floats;
+  }
   // the template pointers are only known after carving; plan with
   // placeholders (planning reads shapes only), then bind
   for (int i = 0; i < n; ++i) {
@@ -534,7 +547,7 @@ tm_status tm_serve_register_signal(tm_server_t sv, const void* x, int64_t N, int
 tm_status tm_serve_submit(tm_server_t sv, int32_t sig_id, const float* t_host, int32_t K, int32_t mode, int32_t M1,
                           int32_t M2, uint32_t plan_flags, uint64_t tag) {
   if (!sv || !t_host) return fail(TM_EINVAL, "null argument");
-  if (K > 65536) return fail(TM_EINVAL, "template longer than 65536");
+  if (K < 1) return fail(TM_EINVAL, "empty template");
   Req r;
   r.tag = tag;
   r.sig = sig_id;
