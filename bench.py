@@ -377,6 +377,55 @@ def run_native(args):
                     "h2d_bytes_per_step": bytes_b + QUERIES * K_T * 4, "d2h_bytes_per_step": QUERIES * tm.RESULT_BYTES,
                     "api": "tm_batch_run_host (pinned host buffers)", "matches_device_run": bits_e2e_ok}}
 
+    # ---- at equal success: the Table 1 point N = 2^26, K = 2^16 (K^2/ln K
+    # well above N: the method's success is 1 there, like the full-N FFT's)
+    equal = None
+    if rank == 0 and not args.no_equal:
+        from workloads import device as WD
+        Ne, Ke, ne = 1 << 26, 1 << 16, 32
+        rng_e = W.rng_for(424242)
+        xe, te, ke = [], [], []
+        for i in range(ne):
+            x = WD.signal(Ne, "i8", 5000 + i)
+            k = int(rng_e.integers(0, Ne))
+            xe.append(x)
+            te.append(WD.template(x, Ke, k, 0.0, 6000 + i))
+            ke.append(k)
+        be = tm.Batch([dict(x=x, t=t, N=Ne, K=Ke, xdtype="i8", mode="paper") for x, t in zip(xe, te)])
+        oute = tm.result_buffer(ne, device=dev)
+        be.run(oute)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            be.run(oute)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1) / 5
+        succ_e = sum(r["shift"] == k for r, k in zip(tm.decode_results(oute), ke)) / ne
+
+        def fulln_one(x, t):
+            X = torch.fft.rfft(x.float())
+            T = torch.fft.rfft(t, n=Ne)
+            return torch.argmax(torch.fft.irfft(torch.conj(T) * X, n=Ne))
+
+        fulln_one(xe[0], te[0])
+        torch.cuda.synchronize()
+        nf = 8
+        e0.record(stream)
+        picks = [fulln_one(xe[i], te[i]) for i in range(nf)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_f = e0.elapsed_time(e1) / nf
+        succ_f = sum(int(p.item()) == ke[i] for i, p in enumerate(picks)) / nf
+        equal = {"config": f"{ne} queries x (N=2^26 +-1 int8, K=2^16, noiseless planted window, M1=K, M2=K+1): "
+                           "the Table 1 point where the method's success is 1",
+                 "queries_per_s": ne / (ms_e / 1e3), "success_rate": succ_e,
+                 "fullN_fft_queries_per_s": 1e3 / ms_f, "fullN_fft_success_rate": succ_f,
+                 "ratio": (ne / (ms_e / 1e3)) / (1e3 / ms_f)}
+        del be, xe, te
+        torch.cuda.empty_cache()
+
     line = None
     if rank == 0:
         fulln_qps, fulln_succ = fulln_fft_qps(qs[:8], dev)
@@ -409,6 +458,7 @@ def run_native(args):
                                 "what": "torch.fft rfft/irfft over the full N per query + argmax (cuFFT)"},
             "cpu_baseline": cpu,
             "bits": bits,
+            "at_equal_success": equal,
         }
         print(json.dumps(line))
     if world > 1:
@@ -922,6 +972,7 @@ def main():
     ap.add_argument("--repeats", type=int, default=1000, help="single: timed tm_match calls")
     ap.add_argument("--best-trials", type=int, default=64, help="tables: trials per K in the Fig. 1(b) search")
     ap.add_argument("--parts", default="table1,table2,fig1a,fig1b")
+    ap.add_argument("--no-equal", action="store_true", help="batch64: skip the equal-success comparison")
     ap.add_argument("--reps", type=int, default=5, help="tables: timed runs per Fig. 1 point")
     ap.add_argument("--fig-logn", type=int, default=26, help="tables: log2 N of Fig. 1(a)")
     ap.add_argument("--fig-ks", default="", help="tables: comma-separated log2 K of Fig. 1(a) (default 16 .. logn-1)")
