@@ -383,7 +383,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     const PlanCore& p = b->pc[i];
     if (!p.direct) continue;
     // int8 with at most 16 rows: the completion sums the rows itself (dh = 0)
-    const int32_t dh = (p.xdtype == TM_I8_PM1 && p.L[0] <= 16) ? 0 : direct_row_groups(p.L[0]);
+    const int32_t dh = (p.xdtype == TM_I8_PM1 && p.L[0] <= 16) ? 0 : direct_row_groups(p.L[0], p.xdtype);
     const int32_t mmax = *std::max_element(p.M, p.M + p.nmod);
     const int32_t pitch = (mmax + 3) & ~3;   // rows of 16-byte multiples: vector stores
     part = (part + 3) & ~int64_t(3);
@@ -393,7 +393,8 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     b->dpart[i] = part;
     part += int64_t(p.nmod) * dh * pitch;
     b->maxM_direct = std::max(b->maxM_direct, mmax);
-    b->maxHM_direct = std::max(b->maxHM_direct, dh * p.nmod);   // 0: no first-stage launch
+    // first-stage grid rows: groups (int8: all moduli per thread) or groups x moduli
+    b->maxHM_direct = std::max(b->maxHM_direct, p.xdtype == TM_I8_PM1 ? dh : dh * p.nmod);   // 0: no launch
   }
   b->part_elems = std::max<int64_t>(part, 16);
 

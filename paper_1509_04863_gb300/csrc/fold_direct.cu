@@ -109,9 +109,111 @@ __device__ __forceinline__ void part_cols(const CorrQ& Q, int j, int h, int64_t 
   else *dst = make_int4(__float_as_int(sf[0]), __float_as_int(sf[1]), __float_as_int(sf[2]), __float_as_int(sf[3]));
 }
 
+__device__ __forceinline__ int i8b(const uint8_t* x, int64_t n) { return (__ldg(x + n) & 2u) ? -1 : 1; }
+
+// int8 signals: the first stage for every modulus at once. A thread folds
+// columns k0 .. k0+3 of each modulus over the group's rows; row l of
+// modulus j starts at k0 + l M_j, so the rows of the moduli (M, M+1, ...)
+// lie a few bytes apart and the second and third reads mostly hit L1.
+// Eight rows of every modulus are in flight at a time; the byte lanes are
+// unpacked every 64 rows.
+template <int NM>
+__device__ __forceinline__ void part_i8_all(const CorrQ& Q, int h, int64_t k0, int32_t* partial) {
+  const int64_t N = Q.N, n16 = Q.N & ~int64_t(15);
+  const uint32_t* X = static_cast<const uint32_t*>(Q.x);
+  const uint8_t* x8 = static_cast<const uint8_t*>(Q.x);
+  const int64_t l0 = int64_t(h) * Q.drows;
+  int64_t M[NM], lend[NM];
+  int64_t lmain = INT64_MAX;
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    M[j] = Q.M[j];
+    const int64_t L = Q.L[j];
+    lend[j] = min(L, l0 + Q.drows);
+    lmain = min(lmain, min(lend[j], L - 1));   // rows natural for every column
+  }
+  int s[NM][4];
+  uint32_t acc[NM];
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    acc[j] = 0u;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[j][c] = 0;
+  }
+  int64_t l = l0;
+  int rows = 0;
+  while (l < lmain) {
+    const int nb = int(min(int64_t(8), lmain - l));
+    uint32_t w0[NM][8], w1[NM][8];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t a = k0 + (l + u) * M[j];
+        const bool wok = u < nb && a + 8 <= n16;
+        w0[j][u] = wok ? __ldg(&X[a >> 2]) : 0u;
+        w1[j][u] = wok ? __ldg(&X[(a >> 2) + 1]) : 0u;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (u >= nb) continue;
+        const int64_t a = k0 + (l + u) * M[j];
+        if (a + 8 <= n16) {
+          acc[j] = __vadd4(acc[j], __funnelshift_r(w0[j][u], w1[j][u], int(a & 3) * 8));
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (a + c < N) s[j][c] += i8b(x8, a + c);
+        }
+      }
+    }
+    l += nb;
+    rows += nb;
+    if (rows >= 56 || l >= lmain) {   // at most 64 rows per byte lane
+#pragma unroll
+      for (int j = 0; j < NM; ++j) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s[j][c] += int(int8_t(uint8_t(acc[j] >> (8 * c))));
+        acc[j] = 0u;
+      }
+      rows = 0;
+    }
+  }
+  // the remaining rows of each modulus (its last row: natural entries only)
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    for (int64_t r = max(l0, lmain); r < lend[j]; ++r) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t n = k0 + c + r * M[j];
+        if (k0 + c < M[j] && n < N) s[j][c] += i8b(x8, n);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    if (k0 >= M[j]) continue;
+    int4* dst = reinterpret_cast<int4*>(partial + Q.dpart + (int64_t(j) * Q.dh + h) * Q.dpitch + k0);
+    *dst = make_int4(s[j][0], s[j][1], s[j][2], s[j][3]);
+  }
+}
+
 __global__ void __launch_bounds__(kDirThreads) fold_direct_part_kernel(const CorrQ* q, const int32_t* idx,
                                                                        int32_t* partial) {
   const CorrQ& Q = q[idx[blockIdx.z]];   // read in place: no per-thread copy
+  if (Q.xdtype == TM_I8_PM1) {          // every modulus in one thread: blockIdx.y is the group
+    const int h = blockIdx.y;
+    const int64_t k0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kDirCols;
+    int mmax = Q.M[0];
+    for (int j = 1; j < Q.nmod; ++j) mmax = max(mmax, Q.M[j]);
+    if (h >= Q.dh || k0 >= mmax) return;
+    if (Q.nmod == 3) part_i8_all<3>(Q, h, k0, partial);
+    else part_i8_all<2>(Q, h, k0, partial);
+    return;
+  }
   const int j = blockIdx.y % Q.nmod, h = blockIdx.y / Q.nmod;
   const int64_t k0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kDirCols;
   if (h >= Q.dh || k0 >= Q.M[j]) return;

@@ -200,9 +200,11 @@ cudaError_t launch_score_slice(const SliceScoreArgs& a, cudaStream_t s);
 // (maxHM = 0: no query has a first stage, one launch).
 cudaError_t launch_fold_direct(const CorrQ* q, const int32_t* idx, int32_t n, int32_t maxP, int32_t maxmod,
                                int32_t maxM, int32_t maxHM, int32_t* partial, void* y, cudaStream_t s);
-// Row groups of the entry-by-entry fold for L rows: about 16 rows each.
-inline int32_t direct_row_groups(int64_t L) {
-  const int64_t h = (L + 15) / 16;
+// Row groups of the entry-by-entry fold for L rows: about 64 rows each for
+// int8 signals (all moduli in one thread), 16 for the others.
+inline int32_t direct_row_groups(int64_t L, int32_t dtype) {
+  const int64_t per = dtype == TM_I8_PM1 ? 64 : 16;
+  const int64_t h = (L + per - 1) / per;
   return int32_t(h < 1 ? 1 : (h > 64 ? 64 : h));
 }
 constexpr int kDirCols = 4;   // fold columns per thread of the first stage
