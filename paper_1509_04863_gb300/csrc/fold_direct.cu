@@ -123,56 +123,54 @@ __device__ __forceinline__ void part_i8_all(const CorrQ& Q, int h, int64_t k0, i
   const uint32_t* X = static_cast<const uint32_t*>(Q.x);
   const uint8_t* x8 = static_cast<const uint8_t*>(Q.x);
   const int64_t l0 = int64_t(h) * Q.drows;
-  int64_t M[NM], lend[NM];
-  int64_t lmain = INT64_MAX;
+  int64_t lend[NM];
+  uint32_t M[NM];
+  int64_t lmain = INT64_MAX, Mmax = 0;
 #pragma unroll
   for (int j = 0; j < NM; ++j) {
-    M[j] = Q.M[j];
+    M[j] = uint32_t(Q.M[j]);
     const int64_t L = Q.L[j];
     lend[j] = min(L, l0 + Q.drows);
     lmain = min(lmain, min(lend[j], L - 1));   // rows natural for every column
+    Mmax = max(Mmax, int64_t(M[j]));
   }
+  // rows whose words stay inside the aligned prefix for every modulus:
+  // k0 + l M + 8 <= n16 (int8 signals are below 2^31 bytes: 32-bit offsets)
+  const int64_t lsafe = n16 >= k0 + 8 ? (n16 - 8 - k0) / Mmax + 1 : 0;
+  const int64_t lfast = max(l0, min(lmain, lsafe));
   int s[NM][4];
-  uint32_t acc[NM];
+  uint32_t acc[NM], a[NM];
 #pragma unroll
   for (int j = 0; j < NM; ++j) {
     acc[j] = 0u;
+    a[j] = uint32_t(k0 + l0 * int64_t(M[j]));
 #pragma unroll
     for (int c = 0; c < 4; ++c) s[j][c] = 0;
   }
   int64_t l = l0;
   int rows = 0;
-  while (l < lmain) {
-    const int nb = int(min(int64_t(8), lmain - l));
+  for (; l + 8 <= lfast; l += 8) {
     uint32_t w0[NM][8], w1[NM][8];
 #pragma unroll
     for (int j = 0; j < NM; ++j) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int64_t a = k0 + (l + u) * M[j];
-        const bool wok = u < nb && a + 8 <= n16;
-        w0[j][u] = wok ? __ldg(&X[a >> 2]) : 0u;
-        w1[j][u] = wok ? __ldg(&X[(a >> 2) + 1]) : 0u;
+        const uint32_t au = a[j] + uint32_t(u) * M[j];
+        w0[j][u] = __ldg(&X[au >> 2]);
+        w1[j][u] = __ldg(&X[(au >> 2) + 1]);
       }
     }
 #pragma unroll
     for (int j = 0; j < NM; ++j) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        if (u >= nb) continue;
-        const int64_t a = k0 + (l + u) * M[j];
-        if (a + 8 <= n16) {
-          acc[j] = __vadd4(acc[j], __funnelshift_r(w0[j][u], w1[j][u], int(a & 3) * 8));
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (a + c < N) s[j][c] += i8b(x8, a + c);
-        }
+        const uint32_t au = a[j] + uint32_t(u) * M[j];
+        acc[j] = __vadd4(acc[j], __funnelshift_r(w0[j][u], w1[j][u], (au & 3u) << 3));
       }
+      a[j] += 8u * M[j];
     }
-    l += nb;
-    rows += nb;
-    if (rows >= 56 || l >= lmain) {   // at most 64 rows per byte lane
+    rows += 8;
+    if (rows >= 56) {   // at most 64 rows per byte lane
 #pragma unroll
       for (int j = 0; j < NM; ++j) {
 #pragma unroll
@@ -182,13 +180,19 @@ __device__ __forceinline__ void part_i8_all(const CorrQ& Q, int h, int64_t k0, i
       rows = 0;
     }
   }
-  // the remaining rows of each modulus (its last row: natural entries only)
 #pragma unroll
   for (int j = 0; j < NM; ++j) {
-    for (int64_t r = max(l0, lmain); r < lend[j]; ++r) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[j][c] += int(int8_t(uint8_t(acc[j] >> (8 * c))));
+  }
+  // the other rows of each modulus byte by byte (a short remainder, rows near
+  // the end of the signal and the last row: natural entries only)
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    for (int64_t r = l; r < lend[j]; ++r) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int64_t n = k0 + c + r * M[j];
+        const int64_t n = k0 + c + r * int64_t(M[j]);
         if (k0 + c < M[j] && n < N) s[j][c] += i8b(x8, n);
       }
     }
