@@ -223,7 +223,7 @@ void batch_free(tm_batch_t b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->ev_stage) { cudaEventSynchronize(b->ev_stage); cudaEventDestroy(b->ev_stage); }
   if (b->owns_memory) {
-    cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_order); cudaFree(b->d_partial);
+    cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_lq); cudaFree(b->d_order); cudaFree(b->d_partial);
     cudaFree(b->d_y); cudaFree(b->d_spec); cudaFree(b->d_r); cudaFree(b->d_err); cudaFree(b->d_out);
     cudaFree(b->d_x); cudaFree(b->d_t);
     if (b->h_stage) cudaFreeHost(b->h_stage);
@@ -244,8 +244,8 @@ void bind_pointers(tm_batch_t b) {
     // the correlation as complete folds
     b->cq[i].y_in = b->cq[i].direct ? static_cast<const void*>(static_cast<const char*>(b->d_y) + b->cq[i].y_off * 4)
                                     : nullptr;
-    if (b->is_large.size() == size_t(b->n) && b->is_large[i]) {
-      LQ& l = b->lq[i];
+    if (b->lq_of.size() == size_t(b->n) && b->lq_of[i] >= 0) {
+      LQ& l = b->lq[b->lq_of[i]];
       const CorrQ& c = b->cq[i];
       l.x = x;
       l.t = t;
@@ -263,12 +263,15 @@ void bind_pointers(tm_batch_t b) {
 // previous upload to have been consumed by the copy engine).
 tm_status upload_descriptors(tm_batch_t b, cudaStream_t s) {
   const size_t nf = b->fq.size() * sizeof(FoldQ), nc = b->cq.size() * sizeof(CorrQ);
+  const size_t nl = b->lq.size() * sizeof(LQ);
   TM_CUDA(cudaEventSynchronize(b->ev_stage));
   char* h = static_cast<char*>(b->h_stage);
   std::memcpy(h, b->fq.data(), nf);
   std::memcpy(h + nf, b->cq.data(), nc);
+  if (nl > 0) std::memcpy(h + nf + nc, b->lq.data(), nl);
   TM_CUDA(cudaMemcpyAsync(b->d_fq, h, nf, cudaMemcpyHostToDevice, s));
   TM_CUDA(cudaMemcpyAsync(b->d_cq, h + nf, nc, cudaMemcpyHostToDevice, s));
+  if (nl > 0) TM_CUDA(cudaMemcpyAsync(b->d_lq, h + nf + nc, nl, cudaMemcpyHostToDevice, s));
   TM_CUDA(cudaEventRecord(b->ev_stage, s));
   return TM_OK;
 }
@@ -297,7 +300,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
   b->is_large.assign(n, 0);
   for (int i = 0; i < n; ++i) {
     PlanCore& p = b->pc[i];
-    if (p.P > kPMax && (p.large || nbig <= kLargeMaxQueries) && !(nofold && nofold[i])) {
+    if (p.P > kPMax && (p.large || p.logP >= kLogPLargeAlways || nbig <= kLargeMaxQueries) && !(nofold && nofold[i])) {
       p.large = p.direct = 1;
       b->is_large[i] = 1;
     }
@@ -450,16 +453,25 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     b->n_blocked += cls(i) == 1 ? 1 : 0;
     b->n_large += cls(i) == 2 ? 1 : 0;
   }
-  b->lq.assign(n, LQ{});
-  for (int i = 0; i < n; ++i) {
+  b->lq.clear();
+  b->lq_of.assign(n, -1);
+  b->lq_maxP = b->lq_maxM = b->lq_two = 0;
+  for (int k = 0; k < n; ++k) {
+    const int i = b->order[k];   // the order puts these queries last, largest P first
     if (!b->is_large[i]) continue;
     const PlanCore& p = b->pc[i];
-    LQ& l = b->lq[i];
+    b->lq_of[i] = int32_t(b->lq.size());
+    b->lq.push_back(LQ{});
+    LQ& l = b->lq.back();
+    l.qi = i;
     l.N = p.N; l.K = p.K; l.xdtype = p.xdtype;
     l.M[0] = p.M[0]; l.M[1] = p.M[1];
     l.inv = p.inv; l.P = p.P; l.logP = p.logP;
     l.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
     l.nsd = large_dims(p.logP, l.logL);
+    b->lq_maxP = std::max(b->lq_maxP, p.P);
+    b->lq_maxM = std::max(b->lq_maxM, std::max(p.M[0], p.M[1]));
+    b->lq_two = b->lq_two || l.nsd == 2;
   }
 
   return TM_OK;
@@ -474,6 +486,7 @@ tm_status batch_alloc(tm_batch_s* b) {
   };
   bool ok = alloc((void**)&b->d_fq, n * sizeof(FoldQ)) == cudaSuccess &&
             alloc((void**)&b->d_cq, n * sizeof(CorrQ)) == cudaSuccess &&
+            alloc((void**)&b->d_lq, std::max<size_t>(b->lq.size(), 1) * sizeof(LQ)) == cudaSuccess &&
             alloc((void**)&b->d_order, 2 * n * sizeof(int32_t)) == cudaSuccess &&
             alloc((void**)&b->d_partial, b->part_elems * sizeof(int32_t)) == cudaSuccess &&
             alloc(&b->d_y, b->y_elems * sizeof(int32_t)) == cudaSuccess &&
@@ -490,7 +503,7 @@ tm_status batch_alloc(tm_batch_s* b) {
     }
     ok = alloc((void**)&b->d_x, xb) == cudaSuccess && alloc((void**)&b->d_t, tb * sizeof(float)) == cudaSuccess;
   }
-  b->stage_bytes = n * (sizeof(FoldQ) + sizeof(CorrQ));
+  b->stage_bytes = n * (sizeof(FoldQ) + sizeof(CorrQ) + sizeof(LQ));
   if (ok) ok = cudaMallocHost(&b->h_stage, b->stage_bytes) == cudaSuccess;
   if (ok) ok = cudaEventCreateWithFlags(&b->ev_stage, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
@@ -554,12 +567,9 @@ tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s) {
     a.nq = b->n_blocked;
     TM_CUDA(launch_correlate_blocked(a, s));
   }
-  for (int k = b->n - b->n_large; k < b->n; ++k) {
-    const int i = b->order[k];
-    LQ l = b->lq[i];
-    l.out = out + i;
-    TM_CUDA(launch_correlate_large(l, s));
-  }
+  if (!b->lq.empty())
+    TM_CUDA(launch_correlate_large(b->d_lq, b->lq.data(), int(b->lq.size()), b->lq_maxP, b->lq_two != 0, b->lq_maxM,
+                                   out, s));
   return TM_OK;
 }
 
@@ -990,8 +1000,7 @@ tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, in
     int32_t l = (b->n > b->n_blocked + b->n_large ? 1 : 0) + (b->n_blocked > 0 ? 1 : 0);
     for (const auto& g : b->groups) l += g.W > 0 ? 1 : 0;
     l += b->direct.empty() ? 0 : (b->maxHM_direct > 0 ? 2 : 1);
-    for (int i = 0; i < b->n; ++i)
-      if (b->is_large[i]) l += large_launches(b->lq[i].nsd);
+    if (!b->lq.empty()) l += large_launches(b->lq_two ? 2 : 1);
     *launches = l;
   }
   if (fold_ctas) *fold_ctas = b->nctas;

@@ -63,6 +63,7 @@ struct LHdr {
   int flags;
   int nch;                  // chunks per listed candidate (set by the rescoring)
   int nchm;                 // chunks per listed member (set by the scoring)
+  int nbest;                // CTAs per query of the rescoring and scoring launches
   CrtSet crt;
   long long ncs;
 };
@@ -306,6 +307,21 @@ __device__ __forceinline__ float sval(const void* x, int64_t n) {
   else return __ldg(static_cast<const float*>(x) + n);
 }
 
+// The query of this block: a single query's descriptor is a kernel
+// parameter (q1); in a batch (B) the descriptor of query blockIdx.z is
+// copied to shared memory and every thread reads its fields there.
+#define TM_LQ(q)                       \
+  __shared__ LQ sq_;                   \
+  if constexpr (B) load_lq(lqs, sq_);  \
+  const LQ& q = B ? sq_ : q1;
+
+__device__ __forceinline__ void load_lq(const LQ* __restrict__ lqs, LQ& sq) {
+  static_assert(sizeof(LQ) % 4 == 0, "LQ words");
+  const int* src = reinterpret_cast<const int*>(lqs + blockIdx.z);
+  for (int i = threadIdx.x; i < int(sizeof(LQ) / 4); i += blockDim.x) reinterpret_cast<int*>(&sq)[i] = src[i];
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- strided passes
 // Tile of pass d: C = 8192 >> logL columns (inner indices n0 .. n0+C-1) of
 // one block, all L rows; element e = i C + c at global block + i S + n0 + c.
@@ -338,9 +354,15 @@ enum { kSrcBuf = 0, kSrcY = 1, kSrcT = 2 };
 
 // Forward pass over strided dim d: source buffer, the folds (first pass of
 // z) or the template (first pass of t); result to dst.
-template <int SRC>
-__global__ void __launch_bounds__(kLT, 2) lfwd_kernel(const LQ q, int d, const float2* src, float2* dst) {
+// src_b / dst_b: 0 for the signal buffer A, 1 for the template buffer B.
+template <int SRC, bool B>
+__global__ void __launch_bounds__(kLT, 2) lfwd_kernel(const LQ q1, const LQ* __restrict__ lqs, int d, int src_b,
+                                                      int dst_b) {
   extern __shared__ __align__(16) float2 sm[];
+  TM_LQ(q)
+  if (blockIdx.x >= unsigned(q.P >> kLRowLog) || d >= q.nsd) return;
+  const float2* src = src_b ? q.B : q.A;
+  float2* dst = dst_b ? q.B : q.A;
   __shared__ double redd[kLW];
   __shared__ unsigned long long redu[kLW];
   __shared__ int redi[kLW];
@@ -426,9 +448,11 @@ __global__ void __launch_bounds__(kLT, 2) lfwd_kernel(const LQ q, int d, const f
 // Inverse pass over strided dim d in conjugated form (twiddle, then DFT).
 // OUT: the outermost dim, results r_1 = Re/P (n < M1), r_2 = -Im/P (n < M2)
 // and their maxima.
-template <bool OUT>
-__global__ void __launch_bounds__(kLT, 2) linv_kernel(const LQ q, int d) {
+template <bool OUT, bool B>
+__global__ void __launch_bounds__(kLT, 2) linv_kernel(const LQ q1, const LQ* __restrict__ lqs, int d) {
   extern __shared__ __align__(16) float2 sm[];
+  TM_LQ(q)
+  if (blockIdx.x >= unsigned(q.P >> kLRowLog) || d >= q.nsd) return;
   __shared__ unsigned long long redu[kLW];
   const Tile tl = tile_of(q, d);
   float2* a0 = q.A + tl.base;
@@ -499,9 +523,11 @@ __global__ void __launch_bounds__(kLT, 2) linv_kernel(const LQ q, int d) {
 // block: forward, maximum of |Z~|, product with the template spectrum in
 // conjugated form g = T~ conj(Z~), then the inverse of the row (DFT over c,
 // twiddle, DFT over i).
-template <bool TEMPLATE>
-__global__ void __launch_bounds__(kLT, 2) lrow_kernel(const LQ q) {
+template <bool TEMPLATE, bool B>
+__global__ void __launch_bounds__(kLT, 2) lrow_kernel(const LQ q1, const LQ* __restrict__ lqs) {
   extern __shared__ __align__(16) float2 sm[];
+  TM_LQ(q)
+  if (blockIdx.x >= unsigned(q.P >> kLRowLog)) return;
   __shared__ float redf[kLW];
   const int64_t base = int64_t(blockIdx.x) << kLRowLog;
   float2* buf = TEMPLATE ? q.B : q.A;
@@ -589,7 +615,9 @@ __device__ __forceinline__ float large_delta(const LHdr& h, int logP, bool ints)
 // Every index with r~_j >= max_j - 2 delta joins the candidate list of j
 // (grid: kCandPer entries per CTA, modulus j = blockIdx.y).
 constexpr int kCandPer = 8 * kLT;
-__global__ void __launch_bounds__(kLT) lcand_kernel(const LQ q) {
+template <bool B>
+__global__ void __launch_bounds__(kLT) lcand_kernel(const LQ q1, const LQ* __restrict__ lqs) {
+  TM_LQ(q)
   const Ws w = ws_of(q.ws);
   const LHdr& h = *w.h;
   const int j = blockIdx.y;
@@ -650,11 +678,11 @@ __device__ __forceinline__ long long block_dot(const float* t, int i0, int i1, b
   return __double_as_longlong(block_red(ad, rd, OpAdd()));
 }
 
-// Chunks per listed item: enough items for two waves of the grid, chunks of
-// at least 2048 terms, at most cap partial sums in all.
+// Chunks per listed item: enough items for two waves of the launch's CTAs
+// of this query, chunks of at least 2048 terms, at most cap partial sums.
 __device__ __forceinline__ int chunks_for(int items, int K, int cap) {
   if (items <= 0) return 1;
-  int n = (2 * kLargeCtas + items - 1) / items;
+  int n = (2 * int(gridDim.x) + items - 1) / items;
   n = min(n, (K + 2047) / 2048);
   n = min(n, cap / items);
   return max(n, 1);
@@ -682,7 +710,9 @@ constexpr int64_t kFullRescoreWork = int64_t(1) << 36;
 // Exact rescoring: the candidates of each modulus in chunks (partial sums),
 // or, above kLargeCap candidates, every index (a warp per index, the best
 // per CTA) when M K <= 2^36.
-__global__ void __launch_bounds__(kLT) lrescore_kernel(const LQ q) {
+template <bool B>
+__global__ void __launch_bounds__(kLT) lrescore_kernel(const LQ q1, const LQ* __restrict__ lqs) {
+  TM_LQ(q)
   __shared__ double rd[kLW];
   __shared__ long long rl[kLW];
   __shared__ double bv_s[kLW];
@@ -693,7 +723,10 @@ __global__ void __launch_bounds__(kLT) lrescore_kernel(const LQ q) {
   const int nc0 = w.h->ncand[0], nc1 = w.h->ncand[1];
   const int n0 = nc0 <= kLargeCap ? nc0 : 0, n1 = nc1 <= kLargeCap ? nc1 : 0;   // listed
   const int nch = chunks_for(n0 + n1, q.K, kLargePart);
-  if (blockIdx.x == 0 && threadIdx.x == 0) w.h->nch = nch;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    w.h->nch = nch;
+    w.h->nbest = int(gridDim.x);
+  }
   for (int it = blockIdx.x; it < (n0 + n1) * nch; it += gridDim.x) {
     const int cg = it / nch, hh = it - cg * nch;
     const int j = cg < n0 ? 0 : 1;
@@ -740,7 +773,9 @@ __device__ __forceinline__ double sum_chunks(const long long* p, int n, bool exa
 }
 
 // Step 7 decisions and steps 8 (one CTA).
-__global__ void __launch_bounds__(kLT) lselect_kernel(const LQ q) {
+template <bool B>
+__global__ void __launch_bounds__(kLT) lselect_kernel(const LQ q1, const LQ* __restrict__ lqs) {
+  TM_LQ(q)
   __shared__ double bv_s[kLW];
   __shared__ long long bi_s[kLW];
   const Ws w = ws_of(q.ws);
@@ -763,7 +798,7 @@ __global__ void __launch_bounds__(kLT) lselect_kernel(const LQ q) {
       }
     } else if (int64_t(Mj) * q.K <= kFullRescoreWork) {
       mode = 1;
-      for (int b = threadIdx.x; b < kLargeCtas; b += blockDim.x)
+      for (int b = threadIdx.x; b < h.nbest; b += blockDim.x)
         better(bv, bi, __longlong_as_double(w.best[(int64_t(j) * kLargeCtas + b) * 2]),
                w.best[(int64_t(j) * kLargeCtas + b) * 2 + 1]);
     } else {
@@ -840,7 +875,9 @@ __device__ void lscore_impl(const LQ& q) {
     }
   }
 }
-__global__ void __launch_bounds__(kLT) lscore_kernel(const LQ q) {
+template <bool B>
+__global__ void __launch_bounds__(kLT) lscore_kernel(const LQ q1, const LQ* __restrict__ lqs) {
+  TM_LQ(q)
   switch (q.xdtype) {
     case TM_I8_PM1: lscore_impl<TM_I8_PM1>(q); break;
     case TM_BITS_PM1: lscore_impl<TM_BITS_PM1>(q); break;
@@ -850,7 +887,9 @@ __global__ void __launch_bounds__(kLT) lscore_kernel(const LQ q) {
 }
 
 // The result record (one CTA).
-__global__ void __launch_bounds__(kLT) lfinish_kernel(const LQ q) {
+template <bool B>
+__global__ void __launch_bounds__(kLT) lfinish_kernel(const LQ q1, const LQ* __restrict__ lqs, tm_result* out) {
+  TM_LQ(q)
   __shared__ double bv_s[kLW];
   __shared__ long long bi_s[kLW];
   const Ws w = ws_of(q.ws);
@@ -867,7 +906,7 @@ __global__ void __launch_bounds__(kLT) lfinish_kernel(const LQ q) {
       if ((threadIdx.x & 31) == 0) better(bv, bi, v, member(h.crt, mi));
     }
   } else {
-    for (int b = threadIdx.x; b < kLargeCtas; b += blockDim.x)
+    for (int b = threadIdx.x; b < h.nbest; b += blockDim.x)
       better(bv, bi, __longlong_as_double(w.mbest[2 * b]), w.mbest[2 * b + 1]);
   }
   block_best(bv, bi, bv_s, bi_s);
@@ -885,36 +924,72 @@ __global__ void __launch_bounds__(kLT) lfinish_kernel(const LQ q) {
     res.m3 = 0;
     res.reserved = 0;
     res.r3 = 0.0;
-    *q.out = res;
+    out[q.qi] = res;
   }
 }
 
-__global__ void linit_kernel(const LQ q) {
-  LHdr* h = ws_of(q.ws).h;
+__global__ void linit_kernel(const LQ* __restrict__ lqs, void* ws1) {
+  void* ws = lqs != nullptr ? lqs[blockIdx.z].ws : ws1;
+  LHdr* h = ws_of(ws).h;
   unsigned* p = reinterpret_cast<unsigned*>(h);
   for (int i = threadIdx.x; i < int(sizeof(LHdr) / 4); i += blockDim.x) p[i] = 0u;
 }
 
 constexpr int kSmemBytes = kSmemPts * int(sizeof(float2));
 
+template <bool B>
+cudaError_t launch_large(const LQ& q1, const LQ* d_lq, int n, int maxP, bool two_dims, int maxM, tm_result* out,
+                         cudaStream_t s) {
+  const dim3 g(unsigned(maxP / kLPts), 1, unsigned(n));
+  // rescoring and scoring: about kLargeCtas CTAs in all, at least 64 per query
+  const unsigned per = unsigned(std::max(64, kLargeCtas / n));
+  const LQ* lq = B ? d_lq : nullptr;
+  linit_kernel<<<dim3(1, 1, unsigned(n)), 128, 0, s>>>(lq, q1.ws);
+  // template spectrum
+  lfwd_kernel<kSrcT, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 0, 1, 1);
+  if (two_dims) lfwd_kernel<kSrcBuf, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 1, 1, 1);
+  lrow_kernel<true, B><<<g, kLT, kSmemBytes, s>>>(q1, lq);
+  // signal spectrum, product and the row inverse
+  lfwd_kernel<kSrcY, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 0, 0, 0);
+  if (two_dims) lfwd_kernel<kSrcBuf, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 1, 0, 0);
+  lrow_kernel<false, B><<<g, kLT, kSmemBytes, s>>>(q1, lq);
+  // the rest of the inverse, outermost dim last
+  if (two_dims) linv_kernel<false, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 1);
+  linv_kernel<true, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 0);
+  // steps 7-9
+  lcand_kernel<B><<<dim3(unsigned((maxM + kCandPer - 1) / kCandPer), 2, unsigned(n)), kLT, 0, s>>>(q1, lq);
+  lrescore_kernel<B><<<dim3(per, 1, unsigned(n)), kLT, 0, s>>>(q1, lq);
+  lselect_kernel<B><<<dim3(1, 1, unsigned(n)), kLT, 0, s>>>(q1, lq);
+  lscore_kernel<B><<<dim3(per, 1, unsigned(n)), kLT, 0, s>>>(q1, lq);
+  lfinish_kernel<B><<<dim3(1, 1, unsigned(n)), kLT, 0, s>>>(q1, lq, out);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t large_ws_bytes() { return kWsBytes; }
 
-int large_launches(int nsd) { return 1 + 2 * (nsd + 1) + nsd + 5; }
+int large_launches(int nsd) { return 1 + 2 * (nsd + 1) + nsd + 5; }   // per batch (nsd: most strided dims)
 
 cudaError_t large_configure() {
   cudaError_t e;
 #define TM_SMEM(k)                                                                          \
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);    \
   if (e != cudaSuccess) return e;
-  TM_SMEM(lfwd_kernel<kSrcBuf>);
-  TM_SMEM(lfwd_kernel<kSrcY>);
-  TM_SMEM(lfwd_kernel<kSrcT>);
-  TM_SMEM(linv_kernel<false>);
-  TM_SMEM(linv_kernel<true>);
-  TM_SMEM(lrow_kernel<false>);
-  TM_SMEM(lrow_kernel<true>);
+  TM_SMEM((lfwd_kernel<kSrcBuf, false>));
+  TM_SMEM((lfwd_kernel<kSrcY, false>));
+  TM_SMEM((lfwd_kernel<kSrcT, false>));
+  TM_SMEM((linv_kernel<false, false>));
+  TM_SMEM((linv_kernel<true, false>));
+  TM_SMEM((lrow_kernel<false, false>));
+  TM_SMEM((lrow_kernel<true, false>));
+  TM_SMEM((lfwd_kernel<kSrcBuf, true>));
+  TM_SMEM((lfwd_kernel<kSrcY, true>));
+  TM_SMEM((lfwd_kernel<kSrcT, true>));
+  TM_SMEM((linv_kernel<false, true>));
+  TM_SMEM((linv_kernel<true, true>));
+  TM_SMEM((lrow_kernel<false, true>));
+  TM_SMEM((lrow_kernel<true, true>));
 #undef TM_SMEM
   float2 h[8192];
   const double two_pi = 6.283185307179586476925286766559;
@@ -925,29 +1000,12 @@ cudaError_t large_configure() {
   return cudaMemcpyToSymbol(g_tw13, h, sizeof(h));
 }
 
-cudaError_t launch_correlate_large(const LQ& q, cudaStream_t s) {
-  if (q.logP < kLogPMinLarge || q.logP > kLogPMaxLarge || q.nsd < 1 || q.nsd > 2) return cudaErrorInvalidValue;
-  const unsigned ctas = unsigned(q.P / kLPts);
-  linit_kernel<<<1, 128, 0, s>>>(q);
-  // template spectrum
-  lfwd_kernel<kSrcT><<<ctas, kLT, kSmemBytes, s>>>(q, 0, nullptr, q.B);
-  if (q.nsd == 2) lfwd_kernel<kSrcBuf><<<ctas, kLT, kSmemBytes, s>>>(q, 1, q.B, q.B);
-  lrow_kernel<true><<<ctas, kLT, kSmemBytes, s>>>(q);
-  // signal spectrum, product and the row inverse
-  lfwd_kernel<kSrcY><<<ctas, kLT, kSmemBytes, s>>>(q, 0, nullptr, q.A);
-  if (q.nsd == 2) lfwd_kernel<kSrcBuf><<<ctas, kLT, kSmemBytes, s>>>(q, 1, q.A, q.A);
-  lrow_kernel<false><<<ctas, kLT, kSmemBytes, s>>>(q);
-  // the rest of the inverse, outermost dim last
-  if (q.nsd == 2) linv_kernel<false><<<ctas, kLT, kSmemBytes, s>>>(q, 1);
-  linv_kernel<true><<<ctas, kLT, kSmemBytes, s>>>(q, 0);
-  // steps 7-9
-  const int mmax = std::max(q.M[0], q.M[1]);
-  lcand_kernel<<<dim3(unsigned((mmax + kCandPer - 1) / kCandPer), 2), kLT, 0, s>>>(q);
-  lrescore_kernel<<<kLargeCtas, kLT, 0, s>>>(q);
-  lselect_kernel<<<1, kLT, 0, s>>>(q);
-  lscore_kernel<<<kLargeCtas, kLT, 0, s>>>(q);
-  lfinish_kernel<<<1, kLT, 0, s>>>(q);
-  return cudaGetLastError();
+cudaError_t launch_correlate_large(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, int maxM,
+                                   tm_result* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (maxP < (1 << kLogPMinLarge) || maxP > (1 << kLogPMaxLarge)) return cudaErrorInvalidValue;
+  if (n == 1) return launch_large<false>(h_lq[0], d_lq, 1, maxP, two_dims, maxM, out, s);
+  return launch_large<true>(h_lq[0], d_lq, n, maxP, two_dims, maxM, out, s);
 }
 
 }  // namespace ftm

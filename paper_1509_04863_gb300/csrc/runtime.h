@@ -84,7 +84,10 @@ struct tm_batch_s {
   int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_large - n_blocked, n - n_large))
   int32_t n_large = 0;     // queries on the multi-CTA path (order[n - n_large, n))
   std::vector<uint8_t> is_large;
-  std::vector<ftm::LQ> lq;  // their launch descriptors (by query)
+  std::vector<ftm::LQ> lq;  // their launch descriptors, in the order of the all-SM launches
+  std::vector<int32_t> lq_of;   // query -> position in lq (-1: not on that path)
+  int32_t lq_maxP = 0, lq_maxM = 0, lq_two = 0;
+  ftm::LQ* d_lq = nullptr;
   int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
   ftm::FoldQ* d_fq = nullptr;
   ftm::CorrQ* d_cq = nullptr;

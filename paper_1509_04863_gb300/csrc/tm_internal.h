@@ -222,9 +222,12 @@ constexpr int kLargePart = 1 << 18;   // partial dot products of all candidates
 constexpr int kLargeMembers = 256;    // members scored from a list
 constexpr int kLargeMPart = 1 << 16;  // partial dot products of all members
 constexpr int kLargeCtas = 1216;      // grid of the rescoring and scoring launches
-// A single query in a batch with at most this many queries of P > kPMax
-// takes this path also when P <= 2^kLogPMaxBlocked (all SMs instead of one).
+// Queries with P > kPMax take this path (all SMs, the batch's queries in
+// the same launches) when P >= 2^kLogPLargeAlways, or when the batch holds
+// at most kLargeMaxQueries queries of P > kPMax; the others (many queries of
+// 2^15 or 2^16 points) take the overlap-save blocks, one CTA per query.
 constexpr int kLargeMaxQueries = 8;
+constexpr int kLogPLargeAlways = 17;
 
 struct LQ {
   const void* x;
@@ -234,7 +237,6 @@ struct LQ {
   float2* A;            // [P] signal spectrum, then the products
   float2* B;            // [P] template spectrum
   void* ws;             // large_ws_bytes() of statistics, candidates and partial sums
-  tm_result* out;       // result slot of this query
   int32_t* err;
   int64_t N;
   int32_t K, xdtype;
@@ -244,6 +246,8 @@ struct LQ {
   int32_t thm2;
   int32_t nsd;          // strided dims (1 or 2)
   int32_t logL[2];
+  int32_t qi;           // index of the query in the batch (its result slot)
+  int32_t pad_;
 };
 size_t large_ws_bytes();
 // Strided dims of a length-2^logP transform (8192-point rows innermost).
@@ -253,8 +257,13 @@ inline int large_dims(int logP, int32_t (&logL)[2]) {
   logL[0] = (q + 1) / 2; logL[1] = q / 2;
   return 2;
 }
-// The launches of one query on stream s (fold given in q.y).
-cudaError_t launch_correlate_large(const LQ& q, cudaStream_t s);
+// The launches for the n queries d_lq[0..n) on stream s (folds given in
+// each q.y; h_lq: the same descriptors on the host): maxP, the longest FFT;
+// two_dims, whether any has two strided dims; maxM, the largest modulus;
+// results to out[q.qi]. A single query's descriptor goes by value (no
+// load from memory ahead of each CTA's work).
+cudaError_t launch_correlate_large(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, int maxM,
+                                   tm_result* out, cudaStream_t s);
 int large_launches(int nsd);
 cudaError_t large_configure();
 

@@ -73,9 +73,10 @@ def test_large_vs_oracle(tm, N, K, mode, xdtype):
 @pytest.mark.parametrize("N,K,xdtype", [((1 << 18) + 11, 20000, "i8"), ((1 << 19) + 1, 70000, "f32"),
                                         (1 << 20, 1 << 17, "bits")])
 def test_large_equals_blocked(tm, N, K, xdtype):
-    """One query alone (multi-CTA path) and the same query among nine
-    (overlap-save path, one CTA per query): the same folds and maxima; for
-    +-1 signals every result field identical."""
+    """One query alone (all-SM launches for one query) and the same query
+    among nine (overlap-save blocks, one CTA per query, for 2^16 points; the
+    all-SM launches over the whole batch for 2^18): the same folds and
+    maxima; for +-1 signals every result field identical."""
     ints = xdtype != "f32"
     qs = [W.planted_query(2200 + s, N, K, xdtype, flip_p=0.05 if ints else 0.0, t_sigma=0.0 if ints else 0.3,
                           mode="paper") for s in range(9)]

@@ -4,8 +4,9 @@ overlap-save correlation against the oracle (FFT route in fp64, rounded for
 integer data): folds bit-exact for +-1 signals and within 1e-5 for reals,
 maxima, shift, status, score identical; also with the Thm. 2 sampling.
 The batches hold more than eight such queries (each pair five times), so
-they take the one-CTA-per-query overlap-save path; smaller batches take
-the multi-CTA path (test_gpu_large.py)."""
+FFTs of 2^15 and 2^16 points take the one-CTA-per-query overlap-save
+path; 2^17 points and more, and smaller batches, take the all-SM launches
+(test_gpu_large.py)."""
 import numpy as np
 import pytest
 import torch
@@ -41,7 +42,8 @@ def test_wide_moduli_vs_oracle(tm, N, K, mode, xdtype, thm2):
         specs.append(dict(x=torch.from_numpy(q.x).cuda(), t=torch.from_numpy(q.t).cuda(), N=q.N, K=q.K,
                           xdtype=xdtype, mode=mode, thm2=thm2))
     b = tm.Batch(specs * 5, keep_corr=True)
-    assert b.stats()["launches_per_run"] == 3      # entry-by-entry fold (two) + overlap-save correlation
+    if b.infos[0]["P"] < 1 << 17:   # ten queries of 2^15 or 2^16 points: overlap-save, one CTA per query
+        assert b.stats()["launches_per_run"] in (2, 3)   # entry-by-entry fold (one or two) + overlap-save
     out = tm.result_buffer(5 * len(qs))
     b.run(out)
     torch.cuda.synchronize()
