@@ -121,3 +121,28 @@ def test_large_thm2(tm, N, K):
     assert (r["m1"], r["m2"], r["shift"], r["status"] & 0xFF, r["n_cand"]) == \
         (ref["m1"], ref["m2"], ref["shift"], ref["status"], ref["n_cand"])
     assert r["score"] == float(ref["score"])
+
+
+def test_large_graph_and_repeat(tm):
+    """The long-FFT launches captured as a CUDA graph replay to the same
+    results as plain runs, run after run, alone and in a batch of three."""
+    qs = [W.planted_query(2400 + s, 1 << 20, 1 << 18, "i8", flip_p=0.05, mode="paper") for s in range(3)]
+    for specs in ([_spec(qs[0])], [_spec(q) for q in qs]):
+        b = tm.Batch(specs)
+        plain = tm.result_buffer(len(specs))
+        b.run(plain)
+        torch.cuda.synchronize()
+        want = tm.decode_results(plain)
+        assert all(r["shift"] == q.k_star for r, q in zip(want, qs))
+        for _ in range(2):
+            b.run(plain)
+            torch.cuda.synchronize()
+            assert tm.decode_results(plain) == want
+        out = tm.result_buffer(len(specs))
+        b.capture_graph(out)
+        for _ in range(3):
+            out.zero_()
+            b.launch_graph()
+            torch.cuda.synchronize()
+            assert tm.decode_results(out) == want
+        assert b.device_error() == 0
