@@ -1,4 +1,4 @@
-"""One signal cut into slices (the multi-GPU split of SURVEY §8e), on one
+"""One signal cut into slices (the multi-GPU split of one long signal), on one
 GPU: the library's slice folds equal the oracle's restricted folds and add
 up to the whole signal's folds (bit-exact for +-1 signals); steps 4-8 on
 the summed folds give the oracle's maxima; the slices' partial scores add
