@@ -222,6 +222,9 @@ void batch_free(tm_batch_t b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->ev_stage) { cudaEventSynchronize(b->ev_stage); cudaEventDestroy(b->ev_stage); }
+  if (b->aux) cudaStreamDestroy(b->aux);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->owns_memory) {
     cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_lq); cudaFree(b->d_order); cudaFree(b->d_partial);
     cudaFree(b->d_y); cudaFree(b->d_spec); cudaFree(b->d_r); cudaFree(b->d_err); cudaFree(b->d_out);
@@ -506,6 +509,10 @@ tm_status batch_alloc(tm_batch_s* b) {
   b->stage_bytes = n * (sizeof(FoldQ) + sizeof(CorrQ) + sizeof(LQ));
   if (ok) ok = cudaMallocHost(&b->h_stage, b->stage_bytes) == cudaSuccess;
   if (ok) ok = cudaEventCreateWithFlags(&b->ev_stage, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && !b->lq.empty())   // the side stream of the long-FFT queries' template spectra
+    ok = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return fail(TM_ENOMEM, "device workspace allocation failed");
@@ -543,6 +550,15 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
 
 tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
   TM_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int32_t), s));
+  if (!b->lq.empty() && b->aux) {
+    // the long-FFT queries' template spectra need only t: they run on a
+    // side stream while the fold streams x (joined in batch_correlate)
+    TM_CUDA(cudaEventRecord(b->ev_fork, s));
+    TM_CUDA(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
+    TM_CUDA(launch_large_template(b->d_lq, b->lq.data(), int(b->lq.size()), b->lq_maxP, b->lq_two != 0, b->aux));
+    TM_CUDA(cudaEventRecord(b->ev_join, b->aux));
+    b->tpl_pending = true;
+  }
   for (const auto& g : b->groups) {
     if (g.W == 0) continue;
     FoldArgs a;
@@ -567,9 +583,17 @@ tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s) {
     a.nq = b->n_blocked;
     TM_CUDA(launch_correlate_blocked(a, s));
   }
-  if (!b->lq.empty())
-    TM_CUDA(launch_correlate_large(b->d_lq, b->lq.data(), int(b->lq.size()), b->lq_maxP, b->lq_two != 0, b->lq_maxM,
-                                   out, s));
+  if (!b->lq.empty()) {
+    if (b->tpl_pending) {   // template spectra launched beside the fold
+      TM_CUDA(cudaStreamWaitEvent(s, b->ev_join, 0));
+      b->tpl_pending = false;
+      TM_CUDA(launch_large_signal(b->d_lq, b->lq.data(), int(b->lq.size()), b->lq_maxP, b->lq_two != 0,
+                                  b->lq_maxM, out, s));
+    } else {
+      TM_CUDA(launch_correlate_large(b->d_lq, b->lq.data(), int(b->lq.size()), b->lq_maxP, b->lq_two != 0,
+                                     b->lq_maxM, out, s));
+    }
+  }
   return TM_OK;
 }
 

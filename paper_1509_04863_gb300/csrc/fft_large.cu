@@ -937,18 +937,28 @@ __global__ void linit_kernel(const LQ* __restrict__ lqs, void* ws1) {
 
 constexpr int kSmemBytes = kSmemPts * int(sizeof(float2));
 
+// The template spectra (the workspace headers first): they read only t and
+// may run beside the fold.
 template <bool B>
-cudaError_t launch_large(const LQ& q1, const LQ* d_lq, int n, int maxP, bool two_dims, int maxM, tm_result* out,
-                         cudaStream_t s) {
+cudaError_t launch_large_tpl(const LQ& q1, const LQ* d_lq, int n, int maxP, bool two_dims, cudaStream_t s) {
+  const dim3 g(unsigned(maxP / kLPts), 1, unsigned(n));
+  const LQ* lq = B ? d_lq : nullptr;
+  linit_kernel<<<dim3(1, 1, unsigned(n)), 128, 0, s>>>(lq, q1.ws);
+  lfwd_kernel<kSrcT, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 0, 1, 1);
+  if (two_dims) lfwd_kernel<kSrcBuf, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 1, 1, 1);
+  lrow_kernel<true, B><<<g, kLT, kSmemBytes, s>>>(q1, lq);
+  return cudaGetLastError();
+}
+
+// The signal spectra, product and inverse, then steps 7-9 (after the folds
+// and the template spectra).
+template <bool B>
+cudaError_t launch_large_sig(const LQ& q1, const LQ* d_lq, int n, int maxP, bool two_dims, int maxM, tm_result* out,
+                             cudaStream_t s) {
   const dim3 g(unsigned(maxP / kLPts), 1, unsigned(n));
   // rescoring and scoring: about kLargeCtas CTAs in all, at least 64 per query
   const unsigned per = unsigned(std::max(64, kLargeCtas / n));
   const LQ* lq = B ? d_lq : nullptr;
-  linit_kernel<<<dim3(1, 1, unsigned(n)), 128, 0, s>>>(lq, q1.ws);
-  // template spectrum
-  lfwd_kernel<kSrcT, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 0, 1, 1);
-  if (two_dims) lfwd_kernel<kSrcBuf, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 1, 1, 1);
-  lrow_kernel<true, B><<<g, kLT, kSmemBytes, s>>>(q1, lq);
   // signal spectrum, product and the row inverse
   lfwd_kernel<kSrcY, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 0, 0, 0);
   if (two_dims) lfwd_kernel<kSrcBuf, B><<<g, kLT, kSmemBytes, s>>>(q1, lq, 1, 0, 0);
@@ -1000,12 +1010,26 @@ cudaError_t large_configure() {
   return cudaMemcpyToSymbol(g_tw13, h, sizeof(h));
 }
 
-cudaError_t launch_correlate_large(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, int maxM,
-                                   tm_result* out, cudaStream_t s) {
+cudaError_t launch_large_template(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (maxP < (1 << kLogPMinLarge) || maxP > (1 << kLogPMaxLarge)) return cudaErrorInvalidValue;
-  if (n == 1) return launch_large<false>(h_lq[0], d_lq, 1, maxP, two_dims, maxM, out, s);
-  return launch_large<true>(h_lq[0], d_lq, n, maxP, two_dims, maxM, out, s);
+  if (n == 1) return launch_large_tpl<false>(h_lq[0], d_lq, 1, maxP, two_dims, s);
+  return launch_large_tpl<true>(h_lq[0], d_lq, n, maxP, two_dims, s);
+}
+
+cudaError_t launch_large_signal(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, int maxM,
+                                tm_result* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (maxP < (1 << kLogPMinLarge) || maxP > (1 << kLogPMaxLarge)) return cudaErrorInvalidValue;
+  if (n == 1) return launch_large_sig<false>(h_lq[0], d_lq, 1, maxP, two_dims, maxM, out, s);
+  return launch_large_sig<true>(h_lq[0], d_lq, n, maxP, two_dims, maxM, out, s);
+}
+
+cudaError_t launch_correlate_large(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, int maxM,
+                                   tm_result* out, cudaStream_t s) {
+  const cudaError_t e = launch_large_template(d_lq, h_lq, n, maxP, two_dims, s);
+  if (e != cudaSuccess) return e;
+  return launch_large_signal(d_lq, h_lq, n, maxP, two_dims, maxM, out, s);
 }
 
 }  // namespace ftm

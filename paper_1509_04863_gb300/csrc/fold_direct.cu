@@ -332,100 +332,102 @@ __device__ __forceinline__ void complete4_i8(const DirQ& D, int j, const int32_t
   }
 }
 
-// int8 signals with at most 16 rows (no first stage, dh = 0): four
+// int8 signals with at most 16 rows (no first stage, dh = 0): sixteen
 // consecutive entries per thread summed from the definition,
 // y[k] = sum_{l<L} x_{(k + l M) mod N} (Thm. 2: terms below N of entry
-// k mod M). Each row's four bytes come from two aligned words and a funnel
-// shift and are added bytewise (at most 16 terms per byte lane); rows whose
-// words would leave the signal's 16-byte-aligned prefix, or that wrap
-// within the four bytes, go byte by byte.
-constexpr int kDirQuads = 2;   // quads of four entries per thread of the direct int8 path
+// k mod M). Each row's sixteen bytes come from five aligned words and four
+// funnel shifts and are added bytewise (at most 16 terms per byte lane), so
+// the index arithmetic of a row is shared by sixteen entries; rows whose
+// words would leave the signal's 16-byte-aligned prefix, or that wrap within
+// the sixteen bytes, go byte by byte.
+constexpr int kDirRun = 16;   // consecutive entries per thread of the direct int8 path
 
-__device__ __forceinline__ void direct4_i8(const DirQ& D, int32_t* yj) {
+__device__ __forceinline__ void direct16_i8(const DirQ& D, int32_t* yj) {
   const int M = int(D.M), P = int(D.P), kend = int(D.M) + D.K - 1, L = int(D.L);
   const int64_t N = D.N, n16 = D.N & ~int64_t(15);
-  const int kq0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4 * kDirQuads;
-  if (kq0 >= P) return;
-  const uint8_t* x = static_cast<const uint8_t*>(D.x);
-  const uint32_t* X = static_cast<const uint32_t*>(D.x);
-  int s[kDirQuads][4];
-  uint32_t acc[kDirQuads];
-  int64_t cb[kDirQuads];
-  bool live[kDirQuads], split[kDirQuads];
+  const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * kDirRun;
+  if (k0 >= P) return;
+  int s[kDirRun];
 #pragma unroll
-  for (int g = 0; g < kDirQuads; ++g) {
-    const int k0 = kq0 + 4 * g;
-    live[g] = k0 < P && k0 < kend;
-    // Thm. 2 with the four entries on both sides of M: entry by entry below
-    split[g] = D.thm2 && k0 < M && k0 + 3 >= M;
-    cb[g] = D.thm2 && k0 >= M ? k0 - M : k0;   // consecutive columns cb .. cb+3
-    acc[g] = 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) s[g][u] = 0;
-  }
-#pragma unroll 2
-  for (int l = 0; l < L; ++l) {
-    uint32_t w0[kDirQuads], w1[kDirQuads];
-    int64_t nr[kDirQuads];
-    bool fast[kDirQuads];
-#pragma unroll
-    for (int g = 0; g < kDirQuads; ++g) {
-      int64_t n = cb[g] + int64_t(l) * M;
-      if (n >= N && !D.thm2) {
-        n -= N;
-        if (n >= N) n %= N;
-      }
-      nr[g] = n;
-      fast[g] = live[g] && !split[g] && n + 8 <= n16;
-      w0[g] = fast[g] ? __ldg(&X[n >> 2]) : 0u;
-      w1[g] = fast[g] ? __ldg(&X[(n >> 2) + 1]) : 0u;
-    }
-#pragma unroll
-    for (int g = 0; g < kDirQuads; ++g) {
-      if (fast[g]) {
-        acc[g] = __vadd4(acc[g], __funnelshift_r(w0[g], w1[g], int(nr[g] & 3) * 8));
-      } else if (live[g] && !split[g]) {
-        // near the end of the signal: byte by byte
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          int64_t nn = nr[g] + u;
-          if (nn >= N) {
-            if (D.thm2) continue;   // zero padding
-            nn -= N;
-          }
-          s[g][u] += i8v(x, nn);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int g = 0; g < kDirQuads; ++g) {
-    const int k0 = kq0 + 4 * g;
-    if (k0 >= P) break;
-    if (split[g] && live[g]) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < kDirRun; ++u) s[u] = 0;
+  if (k0 < kend) {
+    const uint8_t* x = static_cast<const uint8_t*>(D.x);
+    const uint32_t* X = static_cast<const uint32_t*>(D.x);
+    if (D.thm2 && k0 < M && k0 + kDirRun > M) {
+      // Thm. 2 with the sixteen entries on both sides of M: entry by entry
+      for (int u = 0; u < kDirRun; ++u) {
         const int k = k0 + u;
         const int64_t c = k >= M ? k - M : k;
         for (int l = 0; l < L; ++l) {
           const int64_t n = c + int64_t(l) * M;
           if (n >= N) break;
-          s[g][u] += i8v(x, n);
+          s[u] += i8v(x, n);
         }
       }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      s[g][u] += int(int8_t(uint8_t(acc[g] >> (8 * u))));
-      if (k0 + u >= kend) s[g][u] = 0;
-    }
-    int32_t* o = yj + k0;
-    if ((reinterpret_cast<uintptr_t>(o) & 15) == 0) {
-      *reinterpret_cast<int4*>(o) = make_int4(s[g][0], s[g][1], s[g][2], s[g][3]);
     } else {
+      const int64_t cb = D.thm2 && k0 >= M ? k0 - M : k0;   // consecutive columns cb .. cb+15
+      uint32_t acc[kDirRun / 4] = {0u, 0u, 0u, 0u};
+#pragma unroll 2
+      for (int l = 0; l < L; ++l) {
+        int64_t n = cb + int64_t(l) * M;
+        if (n >= N && !D.thm2) {
+          n -= N;
+          if (n >= N) n %= N;
+        }
+        if (n + kDirRun + 4 <= n16) {
+          const uint32_t* w = X + (n >> 2);
+          uint32_t v[kDirRun / 4 + 1];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) o[u] = s[g][u];   // P is a multiple of 4
+          for (int b = 0; b <= kDirRun / 4; ++b) v[b] = __ldg(w + b);
+          const int sh = int(n & 3) * 8;
+#pragma unroll
+          for (int b = 0; b < kDirRun / 4; ++b) acc[b] = __vadd4(acc[b], __funnelshift_r(v[b], v[b + 1], sh));
+        } else {
+          // near the end of the signal: byte by byte
+#pragma unroll
+          for (int u = 0; u < kDirRun; ++u) {
+            int64_t nn = n + u;
+            if (nn >= N) {
+              if (D.thm2) continue;   // zero padding
+              nn -= N;
+            }
+            s[u] += i8v(x, nn);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kDirRun; ++u) s[u] += int(int8_t(uint8_t(acc[u >> 2] >> (8 * (u & 3)))));
     }
+#pragma unroll
+    for (int u = 0; u < kDirRun; ++u)
+      if (k0 + u >= kend) s[u] = 0;
+  }
+  // The warp's 512 entries are contiguous (P is a multiple of 512, so whole
+  // warps return above): they go out through shared memory as 16-byte
+  // stores of consecutive lanes. Slot s of the staging area sits at
+  // s ^ ((s >> 3) & 7), so both the writes (lane stride four slots) and the
+  // reads (consecutive slots) hit eight distinct 16-byte bank groups per
+  // quarter warp.
+  __shared__ int4 stage[kDirThreads / 32][32 * kDirRun / 4];
+  int4* st = stage[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  int32_t* o = yj + (k0 - lane * kDirRun);   // the warp's first entry
+  if ((reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+#pragma unroll
+    for (int b = 0; b < kDirRun / 4; ++b) {
+      const int sl = lane * (kDirRun / 4) + b;
+      st[sl ^ ((sl >> 3) & 7)] = make_int4(s[4 * b], s[4 * b + 1], s[4 * b + 2], s[4 * b + 3]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < kDirRun / 4; ++b) {
+      const int sl = b * 32 + lane;
+      reinterpret_cast<int4*>(o)[sl] = st[sl ^ ((sl >> 3) & 7)];
+    }
+  } else {
+    int32_t* ot = yj + k0;
+#pragma unroll
+    for (int u = 0; u < kDirRun; ++u) ot[u] = s[u];   // P is a multiple of 16: k0 + 15 < P
   }
 }
 
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(kDirThreads, 4) fold_direct_complete_kernel(co
   // kDirCols entries per thread, a block's threads on consecutive k
   switch (dt) {
     case TM_I8_PM1:
-      if (D.dh == 0) direct4_i8(D, static_cast<int32_t*>(y) + int64_t(j) * D.P);
+      if (D.dh == 0) direct16_i8(D, static_cast<int32_t*>(y) + int64_t(j) * D.P);
       else complete4_i8(D, j, partial, static_cast<int32_t*>(y) + int64_t(j) * D.P);
       break;
     case TM_BITS_PM1: complete_cols<TM_BITS_PM1>(D, j, partial, y); break;
@@ -477,7 +479,9 @@ cudaError_t launch_fold_direct(const CorrQ* q, const int32_t* idx, int32_t n, in
     const dim3 g1(unsigned((maxM + per - 1) / per), unsigned(maxHM), unsigned(n));
     fold_direct_part_kernel<<<g1, kDirThreads, 0, s>>>(q, idx, partial);
   }
-  const dim3 g2(unsigned((maxP + per - 1) / per), unsigned(maxmod), unsigned(n));
+  // every query int8 with at most 16 rows: sixteen entries per thread
+  const int64_t per2 = maxHM > 0 ? per : int64_t(kDirThreads) * kDirRun;
+  const dim3 g2(unsigned((maxP + per2 - 1) / per2), unsigned(maxmod), unsigned(n));
   fold_direct_complete_kernel<<<g2, kDirThreads, 0, s>>>(q, idx, partial, y);
   return cudaGetLastError();
 }

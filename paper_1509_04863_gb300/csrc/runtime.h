@@ -105,6 +105,12 @@ struct tm_batch_s {
   void* h_stage = nullptr;
   size_t stage_bytes = 0;
   cudaEvent_t ev_stage = nullptr;
+  // long-FFT queries: their template spectra run on aux beside the fold
+  // (fork on the caller's stream before the fold launches, join before
+  // the signal spectra); only batches that own their memory have aux
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool tpl_pending = false;
   int64_t ws_bytes = 0;
   // tm_batch_graph_capture: the captured run and the stream it was captured on
   cudaStream_t cap_stream = nullptr;

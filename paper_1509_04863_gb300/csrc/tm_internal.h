@@ -264,6 +264,12 @@ inline int large_dims(int logP, int32_t (&logL)[2]) {
 // load from memory ahead of each CTA's work).
 cudaError_t launch_correlate_large(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, int maxM,
                                    tm_result* out, cudaStream_t s);
+// The same launches in two parts: the template spectra (read t only, so
+// they may run on another stream beside the fold) and, once they and the
+// folds are done, the signal spectra with steps 7-9.
+cudaError_t launch_large_template(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, cudaStream_t s);
+cudaError_t launch_large_signal(const LQ* d_lq, const LQ* h_lq, int n, int maxP, bool two_dims, int maxM,
+                                tm_result* out, cudaStream_t s);
 int large_launches(int nsd);
 cudaError_t large_configure();
 
