@@ -269,6 +269,17 @@ __device__ __forceinline__ T block_red(T v, T* red, Op op) {
     for (int w = 1; w < int(blockDim.x >> 5); ++w) v = op(v, red[w]);
   return v;
 }
+// Two block reductions with one pair of barriers (valid in thread 0).
+template <class T1, class Op1, class T2, class Op2>
+__device__ __forceinline__ void block_red2(T1& a, T1* ra, Op1 op1, T2& b, T2* rb, Op2 op2) {
+  a = warp_red(a, op1);
+  b = warp_red(b, op2);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { ra[threadIdx.x >> 5] = a; rb[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) { a = op1(a, ra[w]); b = op2(b, rb[w]); }
+}
 struct OpAdd {
   template <class T>
   __device__ T operator()(T a, T b) const { return a + b; }
@@ -363,59 +374,87 @@ __global__ void __launch_bounds__(kLT, 2) lfwd_kernel(const LQ q1, const LQ* __r
   if (blockIdx.x >= unsigned(q.P >> kLRowLog) || d >= q.nsd) return;
   const float2* src = src_b ? q.B : q.A;
   float2* dst = dst_b ? q.B : q.A;
-  __shared__ double redd[kLW];
+  __shared__ float redf[kLW], redf2[kLW];
   __shared__ unsigned long long redu[kLW];
   __shared__ int redi[kLW];
   const Tile tl = tile_of(q, d);
   const Ws w = ws_of(q.ws);
+  // loads of eight elements in flight before their first use
   if constexpr (SRC == kSrcY) {
     const bool ints = int_dtype(q.xdtype);
     const int32_t* yi = static_cast<const int32_t*>(q.y);
     const float* yf = static_cast<const float*>(q.y);
     unsigned long long s2 = 0;
-    float f2 = 0.f;   // 32 terms per thread in fp32 (relative error < 2e-6), then fp64
+    float f2 = 0.f;   // fp32 sums within the CTA (see below), then fp64
     int my = 0;
-    for (int u = 0; u < kLPPT; ++u) {
-      const int e = threadIdx.x + u * kLT;
-      const int64_t n = tile_gidx(tl, e);
-      float2 v;
+#pragma unroll
+    for (int u0 = 0; u0 < kLPPT; u0 += 8) {
+      float2 v[8];
       if (ints) {
-        const int a = yi[n], b = yi[int64_t(q.P) + n];
-        s2 += (unsigned long long)((long long)a * a + (long long)b * b);
-        my = max(my, max(abs(a), abs(b)));
-        v = make_float2(float(a), float(b));
+        int a[8], b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t n = tile_gidx(tl, threadIdx.x + (u0 + u) * kLT);
+          a[u] = yi[n];
+          b[u] = yi[int64_t(q.P) + n];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          s2 += (unsigned long long)((long long)a[u] * a[u] + (long long)b[u] * b[u]);
+          my = max(my, max(abs(a[u]), abs(b[u])));
+          v[u] = make_float2(float(a[u]), float(b[u]));
+        }
       } else {
-        v = make_float2(yf[n], yf[int64_t(q.P) + n]);
-        f2 = fmaf(v.x, v.x, fmaf(v.y, v.y, f2));
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t n = tile_gidx(tl, threadIdx.x + (u0 + u) * kLT);
+          v[u] = make_float2(yf[n], yf[int64_t(q.P) + n]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) f2 = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, f2));
       }
-      sm[pad(e)] = v;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sm[pad(threadIdx.x + (u0 + u) * kLT)] = v[u];
     }
     if (ints) {
-      s2 = block_red(s2, redu, OpAdd());
-      my = block_red(my, redi, OpMax());
+      block_red2(s2, redu, OpAdd(), my, redi, OpMax());
       if (threadIdx.x == 0) { atomicAdd(&w.h->z2i, s2); atomicMax(&w.h->maxy, my); }
     } else {
-      const double d2 = block_red(double(f2) * (1.0 + 4e-6), redd, OpAdd());
-      if (threadIdx.x == 0) atomicAdd(&w.h->z2f, d2);
+      // nonnegative terms, each through at most 32 + 5 + 15 fp32 additions
+      // (thread, warp tree, warps in turn): relative error < 52 u < 4e-6,
+      // so the scaled sum bounds the exact one from above; FP64 only in
+      // thread 0 (this part has few FP64 units)
+      f2 = block_red(f2, redf, OpAdd());
+      if (threadIdx.x == 0) atomicAdd(&w.h->z2f, double(f2) * (1.0 + 4e-6));
     }
   } else if constexpr (SRC == kSrcT) {
-    float a1 = 0.f, a2 = 0.f;   // fp32 per thread (32 terms), fp64 across threads
+    float a1 = 0.f, a2 = 0.f;   // fp32 within the CTA, fp64 across CTAs
     int bad = 0;
-    for (int u = 0; u < kLPPT; ++u) {
-      const int e = threadIdx.x + u * kLT;
-      const int64_t n = tile_gidx(tl, e);
-      const float v = n < q.K ? __ldg(&q.t[n]) : 0.f;
-      a1 += fabsf(v);
-      a2 = fmaf(v, v, a2);
-      bad |= (v == rintf(v) && fabsf(v) <= 1048576.f) ? 0 : 1;
-      sm[pad(e)] = make_float2(v, 0.f);
+#pragma unroll
+    for (int u0 = 0; u0 < kLPPT; u0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t n = tile_gidx(tl, threadIdx.x + (u0 + u) * kLT);
+        v[u] = n < q.K ? __ldg(&q.t[n]) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a1 += fabsf(v[u]);
+        a2 = fmaf(v[u], v[u], a2);
+        bad |= (v[u] == rintf(v[u]) && fabsf(v[u]) <= 1048576.f) ? 0 : 1;
+        sm[pad(threadIdx.x + (u0 + u) * kLT)] = make_float2(v[u], 0.f);
+      }
     }
-    const double d1 = block_red(double(a1) * (1.0 + 4e-6), redd, OpAdd());
-    if (threadIdx.x == 0) atomicAdd(&w.h->t1, d1);
-    const double d2 = block_red(double(a2) * (1.0 + 4e-6), redd, OpAdd());
-    if (threadIdx.x == 0) atomicAdd(&w.h->t2sq, d2);
-    bad = block_red(bad, redi, OpMax());
-    if (threadIdx.x == 0 && bad) atomicOr(&w.h->tbad, 1);
+    // nonnegative terms, each through at most 16 + 5 + 15 fp32 additions:
+    // relative error < 36 u < 4e-6 (the scaled sums are upper bounds)
+    bad = __syncthreads_or(bad);
+    block_red2(a1, redf, OpAdd(), a2, redf2, OpAdd());
+    if (threadIdx.x == 0) {
+      atomicAdd(&w.h->t1, double(a1) * (1.0 + 4e-6));
+      atomicAdd(&w.h->t2sq, double(a2) * (1.0 + 4e-6));
+      if (bad) atomicOr(&w.h->tbad, 1);
+    }
   } else {
     const float2* s0 = src + tl.base;
 #pragma unroll 8
@@ -453,7 +492,7 @@ __global__ void __launch_bounds__(kLT, 2) linv_kernel(const LQ q1, const LQ* __r
   extern __shared__ __align__(16) float2 sm[];
   TM_LQ(q)
   if (blockIdx.x >= unsigned(q.P >> kLRowLog) || d >= q.nsd) return;
-  __shared__ unsigned long long redu[kLW];
+  __shared__ unsigned long long redu[kLW], redu2[kLW];
   const Tile tl = tile_of(q, d);
   float2* a0 = q.A + tl.base;
   // loads of eight elements in flight before their twiddles
@@ -509,9 +548,8 @@ __global__ void __launch_bounds__(kLT, 2) linv_kernel(const LQ q1, const LQ* __r
       }
     }
     const Ws w = ws_of(q.ws);
-    k1 = block_red(k1, redu, OpMax());
+    block_red2(k1, redu, OpMax(), k2, redu2, OpMax());
     if (threadIdx.x == 0 && k1) atomicMax(&w.h->rkey[0], k1);
-    k2 = block_red(k2, redu, OpMax());
     if (threadIdx.x == 0 && k2) atomicMax(&w.h->rkey[1], k2);
   }
 }
