@@ -564,6 +564,7 @@ tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
     FoldArgs a;
     a.q = b->d_fq + g.first; a.nq = g.count; a.dtype = g.dtype; a.nctas = g.nctas; a.W = g.W;
     a.partial = b->d_partial; a.err = b->d_err; a.tile = g.tile;
+    fold_args_first_queries(a, b->fq.data() + g.first);
     TM_CUDA(launch_fold(a, g.jmax, s));
   }
   if (!b->direct.empty())
@@ -915,6 +916,7 @@ tm_status tm_batch_autotune(tm_batch_t b, tm_stream_t stream, uint32_t flags, in
     FoldArgs a;
     a.q = b->d_fq + g.first; a.nq = g.count; a.dtype = g.dtype; a.nctas = g.nctas; a.W = g.W;
     a.partial = b->d_partial; a.err = b->d_err;
+    fold_args_first_queries(a, b->fq.data() + g.first);
     float best = 0.f;
     int32_t best_tile = kFoldTile;
     for (int32_t tile : {65536, 32768, 16384}) {

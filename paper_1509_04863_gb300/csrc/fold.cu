@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
   }
   __syncthreads();
   if (cb >= ce) return;
-  const int q0 = first_query(a.q, a.nq, cb);
+  const int q0 = a.has_q0 ? a.q0[blockIdx.x] : first_query(a.q, a.nq, cb);
 
   // ---------------------------------------------------------------- producer
   if (tid >= kFoldConsumers) {

@@ -41,6 +41,7 @@ constexpr int kFoldMaxStages = kFoldRingBytes / kFoldMinTile;
 // A consumer's 16-bit lane counters hold twice the number of -1 entries;
 // the host caps a CTA's share so that no column sees more rows than this.
 constexpr int kFoldMaxRowsPerSlot = 32000;
+constexpr int kFoldMaxCtas = 256;   // CTAs whose first signal a launch can carry as a parameter
 
 // Per signal storage type: columns per consumer unit (a unit is 16 bytes of
 // a row, 4 bytes for bit-packed signals), bits per element, the floor of the
@@ -92,6 +93,11 @@ struct FoldArgs {
                       // +1 (bits) entries, or fp32 sums (real signals)
   int32_t* err;       // device error word
   int32_t tile = kFoldTile;   // bytes per stage: 16384, 32768 or 65536
+  // q0[c]: the first signal whose bytes reach CTA c's share (has_q0 set by
+  // fold_args_first_queries); otherwise each CTA searches the descriptors,
+  // a chain of dependent global loads ahead of its first copy
+  int32_t has_q0 = 0;
+  int32_t q0[kFoldMaxCtas];
 };
 
 // Start of CTA c's share of W bytes (multiple of 16). Shared by the host
@@ -99,6 +105,20 @@ struct FoldArgs {
 __host__ __device__ inline int64_t fold_cta_begin(int64_t W, int32_t nctas, int32_t c) {
   const int64_t units = W >> 4;
   return ((units * c) / nctas) << 4;
+}
+
+// Fills a.q0 from the host copy hq[0..a.nq) of the descriptors a.q points
+// to (same order), when a.nctas fits.
+inline void fold_args_first_queries(FoldArgs& a, const FoldQ* hq) {
+  a.has_q0 = 0;
+  if (a.nctas <= 0 || a.nctas > kFoldMaxCtas) return;
+  int i = 0;
+  for (int32_t c = 0; c < a.nctas; ++c) {
+    const int64_t cb = fold_cta_begin(a.W, a.nctas, c);
+    while (i < a.nq && hq[i].goff + hq[i].nbytes <= cb) ++i;   // shares ascend with c
+    a.q0[c] = i;
+  }
+  a.has_q0 = 1;
 }
 
 // ---------------------------------------------------------------- correlation kernel (steps 3-9)
