@@ -14,7 +14,7 @@ bounded sample, and a plain full-length FFT correlation (cuFFT via torch)
 on the same GPU for comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-  python bench.py --workload uneven|serve|sweep   (other workloads, one line each)
+  python bench.py --workload uneven|serve|sweep|tables|single|foldscale   (other workloads, one line each)
   N > 1: torchrun --nproc-per-node N bench.py --gpus N ... (queries sharded by
   rank, no collective on the data path: weak scaling).
 """
@@ -864,6 +864,48 @@ def run_single(args):
     return 0
 
 
+def run_foldscale(args):
+    """The streaming fold alone on Q = 8 .. 128 int8 +-1 signals of 2^24
+    bytes (K = 4096, M1 = K, M2 = K+1): median CUDA-event time of the fold
+    call per Q, and a least-squares line through them. The slope is the
+    streaming rate, the intercept the fixed cost of a launch."""
+    import torch
+    import paper_1509_04863_gb300 as tm
+    torch.manual_seed(0)
+    N, K = N_SIG, K_T
+    pts = []
+    for Q in (8, 16, 32, 64, 128):
+        xs = [torch.randint(0, 2, (N,), device="cuda", dtype=torch.int8) * 2 - 1 for _ in range(Q)]
+        ts = [torch.randint(0, 2, (K,), device="cuda").float() * 2 - 1 for _ in range(Q)]
+        b = tm.Batch([dict(x=x, t=t, N=N, K=K, xdtype="i8", mode="paper") for x, t in zip(xs, ts)])
+        out = tm.result_buffer(Q)
+        for _ in range(args.warmup):
+            b.run(out)
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(40)]
+        for e0, e1 in ev:
+            e0.record(s)
+            b.fold()
+            e1.record(s)
+            b.correlate(out)
+        torch.cuda.synchronize()
+        ms = sorted(e0.elapsed_time(e1) for e0, e1 in ev)
+        pts.append((Q, ms[len(ms) // 2]))
+        del b, xs, ts, out
+        torch.cuda.empty_cache()
+    q = np.array([p[0] for p in pts], dtype=np.float64)
+    t = np.array([p[1] for p in pts], dtype=np.float64)
+    slope, icpt = np.polyfit(q, t, 1)
+    peak, kind = measured_peaks()
+    gbps = N / (slope / 1e3) / 1e9
+    print(json.dumps({"workload": "foldscale: the int8 fold of Q x 2^24-byte signals, Q = 8 .. 128",
+                      "points": [{"Q": int(a), "fold_ms_median": b_} for a, b_ in pts],
+                      "slope_us_per_signal": slope * 1e3, "intercept_us": icpt * 1e3,
+                      "slope_GBps": gbps, "slope_frac_of_" + kind + "_copy_peak": gbps / peak}))
+    return 0
+
+
 def run_tables(args):
     """The paper's experiments (Sec. 4) on synthetic +-1 signals.
 
@@ -964,7 +1006,7 @@ def main():
     ap.add_argument("--queries", type=int, default=64)
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--K", type=int, default=K_T)
-    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve", "sweep", "tables", "single"],
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve", "sweep", "tables", "single", "foldscale"],
                     help="batch64 (default line), uneven (4096-query mix as one CUDA graph), "
                          "serve (Poisson arrivals through the continuous-batching server)")
     ap.add_argument("--seeds", type=int, default=256)
@@ -999,6 +1041,8 @@ def main():
         return run_tables(args)
     if args.workload == "single":
         return run_single(args)
+    if args.workload == "foldscale":
+        return run_foldscale(args)
     return run_native(args)
 
 
