@@ -227,13 +227,19 @@ TM_API tm_status tm_batch_set_inputs(tm_batch_t b, const tm_query* q, int32_t n)
 /* Step 3 for the whole batch: one launch per signal storage type that
  * streams every signal once and writes partial column sums of both folds;
  * moduli too wide for its register-resident columns (about 2^14 and more)
- * are folded entry by entry instead (one or two more launches). */
+ * are folded entry by entry instead (one or two more launches). Queries on
+ * the all-SM path also get their template spectra (steps 4-5, which read
+ * only t) here, launched on a stream private to the batch that waits for
+ * `stream`'s earlier work and runs beside the fold; tm_batch_correlate
+ * joins it into its own stream, so t and the descriptors must stay as they
+ * are until tm_batch_correlate is enqueued. */
 TM_API tm_status tm_batch_fold(tm_batch_t b, tm_stream_t stream);
 /* Steps 3 (completion: wrap term, extension k >= M), 4-9 for every query:
  * one CTA per query, largest FFT first, in one launch (plus one launch for
  * the overlap-save queries, and a sequence of launches per query on the
  * all-SM path, see tm_plan_create); writes n tm_results to out_dev.
- * Must follow tm_batch_fold on the same stream. */
+ * Must follow tm_batch_fold on the same stream (it first waits for the
+ * template spectra tm_batch_fold launched on the batch's private stream). */
 TM_API tm_status tm_batch_correlate(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
 /* tm_batch_fold + tm_batch_correlate. */
 TM_API tm_status tm_batch_run(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
