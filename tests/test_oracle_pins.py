@@ -463,3 +463,189 @@ def test_three_moduli_recover_where_two_are_ambiguous():
     assert M1 * M2 * M3 > N
     three = O.ftm_multi(x, t, (M1, M2, M3))
     assert three["n_cand"] == 1 and three["shift"] == k_star and three["status"] == O.FOUND
+
+
+# ---------------------------------------------------------------------------
+# Steps 7-9 assembled end to end, recomputed without the oracle's helpers:
+# (Tx)_k by brute force, r_j by Eq. (4) (Alg. 1) or by the explicit circ([t 0])
+# product (Thm. 2), the argmax by a Python loop, the candidate sets by
+# listing their members, and step 9 (reading R6: the largest exact (Tx)_m
+# over the intersection, ties to the smallest m).
+# ---------------------------------------------------------------------------
+
+def _brute_tx(x, t):
+    N, K = len(x), len(t)
+    return [sum(int(t[i]) * int(x[(k + i) % N]) for i in range(K)) for k in range(N)]
+
+
+def _first_argmax(v):
+    best, arg = None, -1
+    for j, val in enumerate(v):
+        if best is None or val > best:
+            best, arg = val, j
+    return arg
+
+
+def _step9(I, tx):
+    if not I:
+        return -1, O.EMPTY
+    if len(I) == 1:
+        return I[0], O.FOUND
+    best = max(tx[m] for m in I)
+    return min(m for m in I if tx[m] == best), O.RESOLVED
+
+
+def _expected_alg1(x, t, M1, M2):
+    N = len(x)
+    tx = _brute_tx(x, t)
+    out = {}
+    sets = []
+    for key, M in (("m1", M1), ("m2", M2)):
+        L = -(-N // M)
+        r = [sum(tx[(j + l * M) % N] for l in range(L)) for j in range(M)]   # Eq. (4)
+        m = _first_argmax(r)
+        out[key] = m
+        members = set()
+        for l in range(L):
+            members.add((m + l * M) % N)
+        sets.append(members)
+    I = sorted(v for v in sets[0] if v in sets[1])
+    out["I"] = I
+    out["shift"], out["status"] = _step9(I, tx)
+    return out, tx
+
+
+def _check_against(res, want):
+    assert res["m1"] == want["m1"] and res["m2"] == want["m2"]
+    assert res["I"] == want["I"]
+    assert res["n_cand"] == len(want["I"])
+    assert res["shift"] == want["shift"] and res["status"] == want["status"]
+
+
+def test_step9_resolution_by_largest_exact_score():
+    """Alg. 1 steps 7-9 with M1 M2 <= N (several members of S1 ∩ S2): the
+    oracle's shift is the member with the largest (Tx)_m, and instances exist
+    where that is not the smallest member (a rule 'smallest m' fails here)."""
+    not_smallest = resolved = 0
+    for seed in range(60):
+        rng = np.random.default_rng(10_000 + seed)
+        M1 = int(rng.integers(3, 7))
+        M2 = M1 + 1
+        N = int(rng.integers(4, 9)) * M1 * M2 + int(rng.integers(0, M1))
+        K = int(rng.integers(2, M1 + 1))
+        x = np.where(rng.random(N) < 0.5, 1, -1).astype(np.int64)
+        k_star = int(rng.integers(0, N))
+        t = x[(np.arange(K) + k_star) % N].copy()
+        want, tx = _expected_alg1(x, t, M1, M2)
+        res = O.ftm(x, t, M1, M2)
+        _check_against(res, want)
+        if want["status"] == O.RESOLVED:
+            resolved += 1
+            if want["shift"] != want["I"][0]:
+                not_smallest += 1
+            assert res["score"] == tx[want["shift"]]
+    assert resolved >= 10 and not_smallest >= 3, (resolved, not_smallest)
+
+
+def test_step9_ties_go_to_smallest_member():
+    """x periodic with period M1 M2 makes (Tx)_m equal on every member of
+    S1 ∩ S2 (they differ by multiples of M1 M2): step 9 then returns the
+    smallest one (reading R6). Checked for Alg. 1 (ftm, three-moduli
+    ftm_multi with a period of M1 M2 M3) and the Thm. 2 variant."""
+    for M1, reps, seed in ((4, 5, 1), (5, 3, 2), (3, 7, 3)):
+        M2 = M1 + 1
+        rng = np.random.default_rng(seed)
+        period = np.where(rng.random(M1 * M2) < 0.5, 1, -1).astype(np.int64)
+        x = np.tile(period, reps)
+        N = x.size
+        K = M1
+        t = x[(np.arange(K) + 7) % N].copy()
+        want, tx = _expected_alg1(x, t, M1, M2)
+        res = O.ftm(x, t, M1, M2)
+        _check_against(res, want)
+        assert len(want["I"]) == reps and want["status"] == O.RESOLVED
+        assert len({tx[m] for m in want["I"]}) == 1
+        assert res["shift"] == want["I"][0]
+        # Thm. 2 variant: M1 M2 divides N, so there is no padding and the
+        # members below N are the same naturals
+        r2 = O.ftm_thm2(x, t, M1, M2)
+        if r2["n_cand"] > 1:
+            assert r2["shift"] == min(r2["I"]) and r2["status"] == O.RESOLVED
+    Ms = (3, 4, 5)
+    rng = np.random.default_rng(9)
+    x = np.tile(np.where(rng.random(60) < 0.5, 1, -1).astype(np.int64), 4)
+    t = x[(np.arange(3) + 11) % x.size].copy()
+    res = O.ftm_multi(x, t, Ms)
+    if res["n_cand"] > 1:
+        tx = _brute_tx(x, t)
+        assert len({tx[m] for m in res["I"]}) == 1
+        assert res["shift"] == res["I"][0] and res["status"] == O.RESOLVED
+
+
+@pytest.mark.parametrize("N,M1,K", [(60, 5, 3), (61, 5, 3), (47, 4, 4), (90, 9, 5), (35, 6, 6)])
+def test_ftm_thm2_assembled_from_explicit_matrices(N, M1, K):
+    """ftm_thm2 (Thm. 2 sampling, reading R13) against its definition built
+    by hand: y = [I_M ... I_M] x' (x zero-padded to a multiple of M), r =
+    circ([t 0_{M-K}]) y, m~ by a Python loop, candidates m~ + l M below N
+    listed one by one, intersection, step 9 by the brute-force (Tx)_m.
+    Covers M | N and M not dividing N, planted windows and random ones."""
+    M2 = M1 + 1
+    for seed in range(8):
+        rng = np.random.default_rng(N * 100 + M1 * 10 + seed)
+        x = np.where(rng.random(N) < 0.5, 1, -1).astype(np.int64)
+        k_star = int(rng.integers(0, N))
+        t = x[(np.arange(K) + k_star) % N].copy()
+        if seed % 2:
+            t[int(rng.integers(0, K))] *= -1
+        tx = _brute_tx(x, t)
+        want = {}
+        sets = []
+        for key, M in (("m1", M1), ("m2", M2)):
+            L = -(-N // M)
+            xp = np.concatenate([x, np.zeros(L * M - N, dtype=np.int64)])
+            Phi = np.hstack([np.eye(M, dtype=np.int64)] * L)
+            y = Phi @ xp
+            C = np.array([[t[(c - r) % M] if (c - r) % M < K else 0 for c in range(M)] for r in range(M)],
+                         dtype=np.int64)
+            r = C @ y
+            m = _first_argmax(r.tolist())
+            want[key] = m
+            s = []
+            l = 0
+            while m + l * M < N:
+                s.append(m + l * M)
+                l += 1
+            sets.append(set(s))
+        I = sorted(sets[0] & sets[1])
+        shift, status = _step9(I, tx)
+        res = O.ftm_thm2(x, t, M1, M2)
+        assert res["m1"] == want["m1"] and res["m2"] == want["m2"]
+        assert res["I"] == I and res["n_cand"] == len(I)
+        assert res["shift"] == shift and res["status"] == status
+        assert res["score"] == (tx[shift] if shift >= 0 else 0)
+
+
+def test_thm3_condition_rejects_when_hypothesis_fails():
+    """Thm. 3's hypothesis (reading R10: the printed factor 1/(2L+1)): true
+    only when (Tx)_m / (2L + 1) exceeds every other (Tx)_k; here N = 10,
+    M = 5, L = 2, so the factor is 1/5."""
+    base = np.array([3, 1, 0, -2, 12, 1, 2, 0, 3, -1], dtype=np.int64)
+    assert not O.thm3_condition(base, 4, 5)        # 12/5 = 2.4 < 3 (true with 1/(2L-1) = 1/3)
+    hi = base.copy()
+    hi[4] = 16
+    assert O.thm3_condition(hi, 4, 5)              # 16/5 = 3.2 > 3
+    eq = base.copy()
+    eq[4] = 15
+    assert not O.thm3_condition(eq, 4, 5)          # 15/5 = 3: not strictly above
+    assert not O.thm3_condition(hi, 0, 5)          # m not the peak
+
+
+def test_thm5_bound_values():
+    """Thm. 5's per-modulus bound M e^{-K/(8L)} + 4(L-1)/K at values worked
+    out by hand: N = 2^16, K = M = 2048 gives L = 32, 2048 e^{-8} + 124/2048
+    = 0.687027 + 0.060547; N = 2^20, K = M = 2^16 gives L = 16,
+    65536 e^{-512} + 60/65536."""
+    assert O.thm5_fold_failure_bound(1 << 16, 2048, 2048) == pytest.approx(0.7475744, rel=1e-6)
+    assert O.thm5_fold_failure_bound(1 << 20, 1 << 16, 1 << 16) == pytest.approx(60 / 65536, rel=1e-9)
+    # L = 1 (M >= N): no mixing term
+    assert O.thm5_fold_failure_bound(100, 100, 100) == pytest.approx(100 * math.exp(-12.5), rel=1e-12)
