@@ -391,12 +391,15 @@ TM_API int32_t tm_crt_candidates(int64_t N, int32_t M1, int32_t M2, int32_t m1, 
  *
  * The first call on a device sets that device up (finds the array's device
  * address, configures the kernels, uploads the FFT twiddles with a
- * synchronous copy); make that first call before any stream capture.
- * Every call reuses the same array, which keeps the previous call's
- * contents: calls that overlap on the GPU (different streams, or other
- * threads) race and corrupt each other's results. Calls on one stream are
- * ordered: each call's small descriptor upload waits for the stream's
- * earlier work. */
+ * synchronous copy); make that first call before any stream capture. The
+ * address and the twiddles are kept for the life of the process: do not
+ * reset the device (cudaDeviceReset) while the process still calls this
+ * entry point. Every call reuses the same array, which keeps the previous
+ * call's contents: calls that overlap on the GPU (different streams, or
+ * other threads) race and corrupt each other's results. Calls on one stream
+ * are ordered: each call's descriptors reach the array as the arguments of
+ * a small kernel launched on that stream, so no host buffer is read after
+ * the call returns. */
 #define TM_NOALLOC_SCRATCH_BYTES (4u << 20)
 #define TM_NOALLOC_MAX_SIGNAL_BYTES (1ll << 28)
 TM_API tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x_dev, const float* t_dev,

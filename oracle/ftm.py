@@ -213,6 +213,34 @@ def tx_slice(xs: np.ndarray, n0: int, N: int, t: np.ndarray, m: int):
     return float(np.dot(t[inside].astype(np.float64), xs[idx[inside] - n0].astype(np.float64)))
 
 
+def intersect_and_resolve(x: np.ndarray, t: np.ndarray, sets: List[Set[int]]) -> Dict:
+    """Alg. 1 step 9 on the candidate sets of step 8 (R6): their
+    intersection I; |I| = 1 gives the shift (FOUND), |I| = 0 gives -1
+    (EMPTY), |I| > 1 the member with the largest exact (Tx)_m, ties to the
+    smallest m (RESOLVED); score = (Tx)_shift (0 without a shift)."""
+    I = sorted(set.intersection(*sets))
+    if len(I) == 0:
+        shift, status = -1, EMPTY
+    elif len(I) == 1:
+        shift, status = I[0], FOUND
+    else:
+        scores = [tx_at(x, t, m) for m in I]
+        shift, status = I[scores.index(max(scores))], RESOLVED
+    score = tx_at(x, t, shift) if shift >= 0 else 0
+    return dict(I=I, shift=int(shift), status=status, n_cand=len(I), score=score)
+
+
+def steps_8_9(x: np.ndarray, t: np.ndarray, picks, moduli, thm2: bool = False) -> Dict:
+    """Steps 8-9 for given step-7 maxima m~_j of the moduli M_j: candidate
+    sets (candidate_set, or candidate_set_thm2 for the Thm. 2 sampling) and
+    their resolution (intersect_and_resolve). Lets a caller check a result
+    whose step-7 picks came from elsewhere."""
+    N = x.shape[0]
+    t = template_values(t) if t.dtype.kind == "f" else t
+    cs = candidate_set_thm2 if thm2 else candidate_set
+    return intersect_and_resolve(x, t, [cs(int(m), int(M), N) for m, M in zip(picks, moduli)])
+
+
 def ftm(x: np.ndarray, t: np.ndarray, M1: int, M2: int, corr: str = "direct") -> Dict:
     """Algorithm 1 steps 3-9 for decoded x (int64/float64) and template t.
 
@@ -233,20 +261,8 @@ def ftm(x: np.ndarray, t: np.ndarray, M1: int, M2: int, corr: str = "direct") ->
             r1, r2 = np.rint(r1).astype(np.int64), np.rint(r2).astype(np.int64)
     m1, m2 = argmax_first(r1), argmax_first(r2)               # step 7
     S1, S2 = candidate_set(m1, M1, N), candidate_set(m2, M2, N)  # step 8
-    I = sorted(S1 & S2)                                       # step 9
-    if len(I) == 0:
-        shift, status = -1, EMPTY
-    elif len(I) == 1:
-        shift, status = I[0], FOUND
-    else:
-        scores = [tx_at(x, t, m) for m in I]
-        best = max(scores)
-        shift = I[scores.index(best)]
-        status = RESOLVED
-    score = tx_at(x, t, shift) if shift >= 0 else 0
-    return dict(M1=M1, M2=M2, y1=y1, y2=y2, r1=r1, r2=r2, m1=m1, m2=m2,
-                S1=S1, S2=S2, I=I, shift=int(shift), status=status,
-                n_cand=len(I), score=score)
+    res = intersect_and_resolve(x, t, [S1, S2])               # step 9
+    return dict(M1=M1, M2=M2, y1=y1, y2=y2, r1=r1, r2=r2, m1=m1, m2=m2, S1=S1, S2=S2, **res)
 
 
 # ---------------------------------------------------------------------------
@@ -291,17 +307,8 @@ def ftm_thm2(x: np.ndarray, t: np.ndarray, M1: int, M2: int) -> Dict:
     r1, r2 = correlate_circular(y1, t, M1), correlate_circular(y2, t, M2)
     m1, m2 = argmax_first(r1), argmax_first(r2)
     S1, S2 = candidate_set_thm2(m1, M1, N), candidate_set_thm2(m2, M2, N)
-    I = sorted(S1 & S2)
-    if len(I) == 0:
-        shift, status = -1, EMPTY
-    elif len(I) == 1:
-        shift, status = I[0], FOUND
-    else:
-        scores = [tx_at(x, t, m) for m in I]
-        shift, status = I[scores.index(max(scores))], RESOLVED
-    score = tx_at(x, t, shift) if shift >= 0 else 0
-    return dict(M1=M1, M2=M2, y1=y1, y2=y2, r1=r1, r2=r2, m1=m1, m2=m2, S1=S1, S2=S2, I=I,
-                shift=int(shift), status=status, n_cand=len(I), score=score)
+    res = intersect_and_resolve(x, t, [S1, S2])
+    return dict(M1=M1, M2=M2, y1=y1, y2=y2, r1=r1, r2=r2, m1=m1, m2=m2, S1=S1, S2=S2, **res)
 
 
 # ---------------------------------------------------------------------------
@@ -360,17 +367,8 @@ def ftm_multi(x: np.ndarray, t: np.ndarray, moduli, corr: str = "direct") -> Dic
         rs.append(r)
         ms.append(m)
         Ss.append(candidate_set(m, M, N))
-    I = sorted(set.intersection(*Ss))
-    if len(I) == 0:
-        shift, status = -1, EMPTY
-    elif len(I) == 1:
-        shift, status = I[0], FOUND
-    else:
-        scores = [tx_at(x, t, m) for m in I]
-        shift, status = I[scores.index(max(scores))], RESOLVED
-    score = tx_at(x, t, shift) if shift >= 0 else 0
-    return dict(moduli=tuple(moduli), ys=ys, rs=rs, ms=ms, Ss=Ss, I=I, shift=int(shift), status=status,
-                n_cand=len(I), score=score)
+    res = intersect_and_resolve(x, t, Ss)
+    return dict(moduli=tuple(moduli), ys=ys, rs=rs, ms=ms, Ss=Ss, **res)
 
 
 def match_query(q, corr: str = "direct") -> Dict:

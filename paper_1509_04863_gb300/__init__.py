@@ -109,12 +109,12 @@ TM_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
 def tm_match_noalloc(x, t, out, N: int, K: int, xdtype: str = "i8", mode: str = "paper", M1: int = 0, M2: int = 0,
-                     allow_ambig: bool = False, stream=None):
+                     allow_ambig: bool = False, thm2: bool = False, stream=None):
     """One query through the entry point that allocates no device memory
     (its scratch is a fixed array inside the library; calls must not
     overlap on the GPU). x, t, out: CUDA tensors as for Plan.match."""
     import torch
-    d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2, TM_ALLOW_AMBIG if allow_ambig else 0, 0, 0)
+    d = tm_plan_desc(N, K, DTYPE_CODES[xdtype], MODE_CODES[mode], M1, M2, _plan_flags(allow_ambig, thm2), 0, 0)
     sp = _stream_ptr(stream) if (stream is not None or torch.cuda.is_available()) else None
     _check(lib().tm_match_noalloc(C.byref(d), x.data_ptr(), t.data_ptr(), out.data_ptr(), sp), "tm_match_noalloc")
 

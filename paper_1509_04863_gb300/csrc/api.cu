@@ -1094,6 +1094,24 @@ constexpr size_t kNaPart = kNaSpec + size_t(kPMax) * sizeof(float2);    // parti
 constexpr size_t kNaPartBytes = TM_NOALLOC_SCRATCH_BYTES - kNaPart;
 static_assert(sizeof(FoldQ) <= 256 && sizeof(CorrQ) <= 512, "descriptor slots");
 
+}  // namespace
+
+namespace ftm_noalloc {
+// Writes one call's descriptors into the scratch array. They travel as
+// kernel parameters (copied by the launch itself), so no host buffer has to
+// outlive the call.
+__global__ void noalloc_write_descriptors(const FoldQ f, const CorrQ c, unsigned char* base) {
+  const int tid = threadIdx.x;
+  if (tid < int(sizeof(FoldQ) / 4)) reinterpret_cast<int*>(base + kNaFoldQ)[tid] = reinterpret_cast<const int*>(&f)[tid];
+  if (tid < int(sizeof(CorrQ) / 4)) reinterpret_cast<int*>(base + kNaCorrQ)[tid] = reinterpret_cast<const int*>(&c)[tid];
+  if (tid < 4) reinterpret_cast<int*>(base + kNaOrder)[tid] = 0;   // processing order of the one query
+  if (tid == 0) *reinterpret_cast<int*>(base + kNaErr) = 0;          // the previous call's error word is stale
+}
+static_assert(sizeof(FoldQ) % 4 == 0 && sizeof(CorrQ) % 4 == 0 && sizeof(CorrQ) / 4 <= 256, "descriptor words");
+}  // namespace ftm_noalloc
+
+namespace {
+
 std::mutex g_na_mu;
 unsigned char* g_na_base[128] = {};   // device address of the array, per device
 float2 g_na_tw_host[kPMax];           // host copy of the twiddles (static storage)
@@ -1139,6 +1157,8 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   if (p.nmod != 2) return fail(TM_EUNSUPPORTED, "the no-allocation entry point uses two moduli (use tm_match)");
   if (p.P > kPMax)
     return fail(TM_EUNSUPPORTED, "the no-allocation entry point handles FFT lengths up to 16384 (use tm_match)");
+  if (p.direct)
+    return fail(TM_EUNSUPPORTED, "the no-allocation entry point needs moduli the streaming fold holds (use tm_match)");
   if (signal_bytes(p.xdtype, p.N) > TM_NOALLOC_MAX_SIGNAL_BYTES)
     return fail(TM_EUNSUPPORTED, "signal larger than the " + std::to_string(TM_NOALLOC_MAX_SIGNAL_BYTES) +
                                      " bytes the no-allocation entry point accepts (use tm_match)");
@@ -1187,15 +1207,11 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
   c.nslots = f.nslots; c.stride = f.stride; c.part = 0;
   c.y_off = 0; c.spec_off = 0; c.r_off = -1;
-  const int32_t order0 = 0;
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int32_t* err = reinterpret_cast<int32_t*>(base + kNaErr);
-  TM_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));   // the previous call's error word is stale
-  // pageable-source copies: each returns once the source has been staged
-  TM_CUDA(cudaMemcpyAsync(base + kNaOrder, &order0, sizeof(order0), cudaMemcpyHostToDevice, s));
-  TM_CUDA(cudaMemcpyAsync(base + kNaFoldQ, &f, sizeof(f), cudaMemcpyHostToDevice, s));
-  TM_CUDA(cudaMemcpyAsync(base + kNaCorrQ, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+  ftm_noalloc::noalloc_write_descriptors<<<1, 256, 0, s>>>(f, c, base);
+  TM_CUDA(cudaGetLastError());
   if (W > 0) {
     FoldArgs fa;
     fa.q = reinterpret_cast<const FoldQ*>(base + kNaFoldQ);

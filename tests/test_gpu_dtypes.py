@@ -19,7 +19,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-5
+from parity import check_int, check_real, TOL  # noqa: F401
 
 
 @pytest.fixture(scope="module")
@@ -43,47 +43,6 @@ def _run(tm, qs):
     torch.cuda.synchronize()
     assert b.device_error() == 0
     return b, tm.decode_results(out)
-
-
-def _normwise(got, want):
-    scale = max(1e-30, float(np.abs(want).max()))
-    return float(np.abs(got - want).max()) / scale
-
-
-def check_int(b, i, q, res, ref):
-    P = b.infos[i]["P"]
-    M1, M2, K = ref["M1"], ref["M2"], q.K
-    y = b.folds(i).cpu().numpy().astype(np.int64)
-    assert np.array_equal(y[:M1 + K - 1], ref["y1"]) and np.array_equal(y[P:P + M2 + K - 1], ref["y2"])
-    r = b.corr(i).cpu().numpy().astype(np.float64)
-    assert _normwise(r[:M1], ref["r1"]) <= TOL and _normwise(r[P:P + M2], ref["r2"]) <= TOL
-    assert (res["m1"], res["m2"], res["shift"], res["n_cand"]) == (ref["m1"], ref["m2"], ref["shift"], ref["n_cand"])
-    assert res["score"] == float(ref["score"])
-
-
-def check_real(b, i, q, res, ref):
-    P = b.infos[i]["P"]
-    M1, M2, K = ref["M1"], ref["M2"], q.K
-    y = b.folds(i).cpu().numpy().astype(np.float64)
-    assert _normwise(y[:M1 + K - 1], ref["y1"]) <= TOL, _normwise(y[:M1 + K - 1], ref["y1"])
-    assert _normwise(y[P:P + M2 + K - 1], ref["y2"]) <= TOL
-    r = b.corr(i).cpu().numpy().astype(np.float64)
-    assert _normwise(r[:M1], ref["r1"]) <= TOL and _normwise(r[P:P + M2], ref["r2"]) <= TOL
-    # exactness of step 7 holds for the GPU's own fp32 folds; against the
-    # fp64 folds a pick may differ only between entries the fold error
-    # cannot order: |r_gpu - r| <= ||t||_1 max|dy|
-    t1 = float(np.abs(q.t.astype(np.float64)).sum())
-    for key, mk, rr, yy, yref in (("r1", "m1", ref["r1"], y[:M1 + K - 1], ref["y1"]),
-                                  ("r2", "m2", ref["r2"], y[P:P + M2 + K - 1], ref["y2"])):
-        slack = 2.0 * t1 * float(np.abs(yy - yref).max()) + 1e-9 * float(np.abs(rr).max())
-        m_gpu, m_ref = res[mk], ref[mk]
-        if m_gpu != m_ref:
-            assert rr[m_gpu] >= rr.max() - slack, (key, m_gpu, m_ref, rr[m_gpu], rr.max(), slack)
-            return False
-        assert abs(res[key] - rr[m_ref]) <= slack
-    assert res["shift"] == ref["shift"] and res["n_cand"] == ref["n_cand"]
-    assert abs(res["score"] - ref["score"]) <= 1e-9 * max(1.0, abs(ref["score"]))
-    return True
 
 
 @pytest.mark.parametrize("N,K", [(1 << 20, 2048), ((1 << 18) + 77, 1024), (5000, 300), (100, 20), (1 << 22, 4096)])

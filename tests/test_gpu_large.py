@@ -13,7 +13,7 @@ import torch
 
 import oracle.ftm as O
 import workloads as W
-from test_gpu_dtypes import check_int, check_real
+from parity import check_int, check_real
 
 pytestmark = pytest.mark.gpu
 
