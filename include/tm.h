@@ -216,6 +216,8 @@ typedef struct tm_batch_s* tm_batch_t;
 #define TM_BATCH_KEEP_CORR 0x1u   /* keep r_{M1}, r_{M2} for tm_batch_corr */
 #define TM_BATCH_HOST_INPUTS 0x2u /* allocate device copies of x and t so that
                                      tm_batch_run_host can take host buffers */
+#define TM_BATCH_PIPELINED 0x4u   /* allocate a second partial-fold buffer, a
+                                     stream and events for tm_batch_run_pipelined */
 
 /* Plan n queries (each as tm_plan_create does) and allocate one device
  * workspace for them: partial folds, folds, template spectra. The pointers
@@ -270,6 +272,37 @@ TM_API tm_status tm_batch_graph_capture(tm_batch_t b, tm_result* out_dev);
 /* Launch the captured graph on a stream: the same work as tm_batch_run in
  * one graph launch. TM_EINVAL without a capture. */
 TM_API tm_status tm_batch_graph_launch(tm_batch_t b, tm_stream_t stream);
+/* Launch geometry: the fold runs on at most fold_ctas CTAs (one per SM
+ * when 0 or above the SM count; the batch's signals are re-split into that
+ * many equal shares, which needs no new memory when fold_ctas does not
+ * exceed the SM count), and the shared-memory correlation keeps at most
+ * corr_ctas CTAs running at a time (0: one CTA per query, all launched at
+ * once; otherwise waves of launches of corr_ctas CTAs each). With
+ * fold_ctas + corr_ctas <= the SM count, the two kernels of
+ * tm_batch_run_pipelined run side by side on disjoint SMs (each of their
+ * CTAs takes a whole SM's shared memory). Results do not change for +-1
+ * signals; for real signals the fold's fp32 sums follow the new shares.
+ * Replaces a graph captured before (capture again). Not while a pipelined
+ * run is pending (TM_EBUSY: flush first). */
+TM_API tm_status tm_batch_set_grid(tm_batch_t b, int32_t fold_ctas, int32_t corr_ctas);
+/* Pipelined runs (needs TM_BATCH_PIPELINED): call i folds the batch's
+ * current inputs (step 3, on `stream`) while the correlation of call i-1's
+ * folds (steps 3-9) runs beside it on a stream of the batch, into the
+ * out_dev that call i-1 was given; `stream` then waits for both, so each
+ * call costs about the longer of the two rather than their sum when
+ * tm_batch_set_grid has split the SMs between them. Call i-1's results are
+ * therefore complete once call i (or tm_batch_pipeline_flush) has finished
+ * on `stream`, and the inputs (x, t) of call i-1 must stay unchanged until
+ * then (its correlation reads them for the wrap-around, extension and
+ * exact scores). Batches whose queries all use the shared-memory
+ * correlation (P <= 16384) and the streaming fold only (TM_EUNSUPPORTED
+ * otherwise). The fold alternates between two partial buffers and error
+ * words, so call i's fold never overwrites what call i-1's correlation
+ * reads. */
+TM_API tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
+/* Runs the pending correlation of the last pipelined call on `stream`
+ * (nothing when none is pending). */
+TM_API tm_status tm_batch_pipeline_flush(tm_batch_t b, tm_stream_t stream);
 /* Device pointers to query i's folds from the last run: y[0..P) for M1,
  * y[P..2P) for M2 (and y[2P..3P) for M3 with TM_THREE_MODULI), entries
  * k < M_j+K-1 valid. int32 for +-1 signals, float32 for real signals

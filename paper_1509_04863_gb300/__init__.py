@@ -31,6 +31,7 @@ TM_RF_SCORE_PENDING = 0x400
 TM_RF_UNCERTIFIED = 0x800
 TM_BATCH_KEEP_CORR = 0x1
 TM_BATCH_HOST_INPUTS = 0x2
+TM_BATCH_PIPELINED = 0x4
 
 DTYPE_CODES = {"i8": TM_I8_PM1, "bits": TM_BITS_PM1, "f16": TM_F16, "f32": TM_F32}
 MODE_CODES = {"auto": TM_MODE_AUTO, "paper": TM_MODE_PAPER, "explicit": TM_MODE_EXPLICIT}
@@ -79,6 +80,9 @@ _SIGS = {
     "tm_batch_run_host": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p,
                                     C.c_void_p]),
     "tm_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
+    "tm_batch_set_grid": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "tm_batch_run_pipelined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tm_batch_pipeline_flush": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_graph_capture": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_folds": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]),
@@ -239,7 +243,8 @@ class Batch:
     batches), t (CUDA tensor or None), N, K, xdtype, mode, and optionally M1,
     M2, allow_ambig."""
 
-    def __init__(self, specs: Sequence[dict], keep_corr: bool = False, host_inputs: bool = False):
+    def __init__(self, specs: Sequence[dict], keep_corr: bool = False, host_inputs: bool = False,
+                 pipelined: bool = False):
         self.n = len(specs)
         self.specs = list(specs)
         arr = (tm_query * self.n)()
@@ -250,7 +255,8 @@ class Batch:
                                    s.get("M1", 0), s.get("M2", 0), s.get("allow_ambig", False), s.get("thm2", False),
                                    s.get("three", False), s.get("M3", 0))
         self._arr = arr
-        flags = (TM_BATCH_KEEP_CORR if keep_corr else 0) | (TM_BATCH_HOST_INPUTS if host_inputs else 0)
+        flags = (TM_BATCH_KEEP_CORR if keep_corr else 0) | (TM_BATCH_HOST_INPUTS if host_inputs else 0) | \
+            (TM_BATCH_PIPELINED if pipelined else 0)
         h = C.c_void_p()
         _check(lib().tm_batch_create(arr, self.n, flags, C.byref(h)), "tm_batch_create")
         self._h = h
@@ -267,6 +273,20 @@ class Batch:
 
     def run(self, out, stream=None):
         _check(lib().tm_batch_run(self._h, out.data_ptr(), _stream_ptr(stream)), "tm_batch_run")
+
+    def set_grid(self, fold_ctas: int = 0, corr_ctas: int = 0):
+        """tm_batch_set_grid: at most fold_ctas fold CTAs (0: one per SM) and
+        corr_ctas correlation CTAs at a time (0: one per query)."""
+        _check(lib().tm_batch_set_grid(self._h, int(fold_ctas), int(corr_ctas)), "tm_batch_set_grid")
+
+    def run_pipelined(self, out, stream=None):
+        """tm_batch_run_pipelined: fold now, correlate the previous call's
+        folds beside it (into the previous call's `out`)."""
+        _check(lib().tm_batch_run_pipelined(self._h, out.data_ptr(), _stream_ptr(stream)), "tm_batch_run_pipelined")
+
+    def flush(self, stream=None):
+        """tm_batch_pipeline_flush: the last pipelined call's correlation."""
+        _check(lib().tm_batch_pipeline_flush(self._h, _stream_ptr(stream)), "tm_batch_pipeline_flush")
 
     def fold(self, stream=None):
         _check(lib().tm_batch_fold(self._h, _stream_ptr(stream)), "tm_batch_fold")
@@ -340,8 +360,8 @@ class Batch:
             pass
 
 
-def tm_batch_create(specs, keep_corr=False, host_inputs=False) -> Batch:
-    return Batch(specs, keep_corr, host_inputs)
+def tm_batch_create(specs, keep_corr=False, host_inputs=False, pipelined=False) -> Batch:
+    return Batch(specs, keep_corr, host_inputs, pipelined)
 
 
 def tm_match_batch(specs, out, stream=None):

@@ -225,7 +225,11 @@ void batch_free(tm_batch_t b) {
   if (b->aux) cudaStreamDestroy(b->aux);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->cstream) { cudaStreamSynchronize(b->cstream); cudaStreamDestroy(b->cstream); }
+  if (b->ev_pfork) cudaEventDestroy(b->ev_pfork);
+  if (b->ev_pjoin) cudaEventDestroy(b->ev_pjoin);
   if (b->owns_memory) {
+    cudaFree(b->d_partial2);
     cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_lq); cudaFree(b->d_order); cudaFree(b->d_partial);
     cudaFree(b->d_y); cudaFree(b->d_spec); cudaFree(b->d_r); cudaFree(b->d_err); cudaFree(b->d_out);
     cudaFree(b->d_x); cudaFree(b->d_t);
@@ -283,6 +287,10 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
   if (n < 1 || !q) return fail(TM_EINVAL, "empty batch");
   b->flags = flags;
   b->n = n;
+  b->groups.clear();   // planning again (tm_batch_set_grid) starts afresh
+  b->W = 0;
+  b->nctas = 0;
+  b->maxP = 0;
   b->q.assign(q, q + n);
   b->pc.resize(n);
   for (int i = 0; i < n; ++i) {
@@ -340,6 +348,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
       b->fold_of[i] = pos;
       const int64_t nb = ((nofold && nofold[i]) || p.direct) ? 0 : fold_bytes(p.xdtype, p.N);
       FoldQ& f = b->fq[pos];
+      f = FoldQ{};
       f.goff = W;
       f.nbytes = int32_t(nb);
       f.nmod = p.nmod;
@@ -360,7 +369,8 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     }
     if (gr.count == 0) continue;
     gr.W = W;
-    int64_t nctas = std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(W, 65536)));
+    const int64_t cap = b->fold_cap > 0 ? std::min<int64_t>(sms, b->fold_cap) : sms;
+    int64_t nctas = std::min<int64_t>(cap, std::max<int64_t>(1, ceil_div(W, 65536)));
     if (W > 0) nctas = std::max<int64_t>(nctas, ceil_div(W, max_share));
     gr.nctas = int32_t(nctas);
     auto cta_of = [&](int64_t pos) {   // CTA whose share holds byte pos
@@ -371,11 +381,40 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
       }
       return lo;
     };
+    const bool real = dt == TM_F16 || dt == TM_F32;
+    gr.cb.clear();
+    if (real && W > 0 && gr.nctas <= kFoldMaxCtas) {
+      // real signals: fixed pieces per signal, one slot each, and shares
+      // that start on piece boundaries (the nearest to the equal split), so
+      // every fp32 column sum is the same whatever else the batch holds
+      std::vector<int64_t> bounds;
+      for (int32_t k = gr.first; k < gr.first + gr.count; ++k) {
+        FoldQ& f = b->fq[k];
+        if (f.nbytes == 0) continue;
+        f.piece = fold_piece_bytes(f.nbytes);
+        for (int64_t o = 0; o < f.nbytes; o += f.piece) bounds.push_back(f.goff + o);
+      }
+      bounds.push_back(W);
+      gr.cb.assign(size_t(gr.nctas) + 1, 0);
+      gr.cb[gr.nctas] = W;
+      for (int32_t c = 1; c < gr.nctas; ++c) {
+        const int64_t want = fold_cta_begin(W, gr.nctas, c);
+        auto it = std::lower_bound(bounds.begin(), bounds.end(), want);
+        int64_t v = it == bounds.end() ? W : *it;
+        if (it != bounds.begin() && want - *(it - 1) < v - want) v = *(it - 1);
+        gr.cb[c] = std::max(gr.cb[c - 1], v);
+      }
+    }
+    auto share_of = [&](int64_t pos) {   // CTA whose share holds byte pos
+      if (gr.cb.empty()) return cta_of(pos);
+      return int32_t(std::upper_bound(gr.cb.begin(), gr.cb.end() - 1, pos) - gr.cb.begin()) - 1;
+    };
     for (int32_t k = gr.first; k < gr.first + gr.count; ++k) {
       FoldQ& f = b->fq[k];
       if (f.nbytes == 0) { f.first_cta = 0; f.nslots = 0; f.part = part; continue; }
-      f.first_cta = cta_of(f.goff);
-      f.nslots = cta_of(f.goff + f.nbytes - 1) - f.first_cta + 1;
+      f.first_cta = share_of(f.goff);
+      f.nslots = f.piece > 0 ? int32_t(ceil_div(f.nbytes, f.piece))
+                             : share_of(f.goff + f.nbytes - 1) - f.first_cta + 1;
       f.part = part;
       part += int64_t(f.nslots) * f.stride;
     }
@@ -497,6 +536,13 @@ tm_status batch_alloc(tm_batch_s* b) {
             alloc((void**)&b->d_err, 16) == cudaSuccess &&
             alloc((void**)&b->d_out, n * sizeof(tm_result)) == cudaSuccess;
   if (ok && b->r_elems > 0) ok = alloc((void**)&b->d_r, b->r_elems * sizeof(float)) == cudaSuccess;
+  b->part_alloc = b->part_elems;
+  if (ok && (flags & TM_BATCH_PIPELINED)) {
+    ok = alloc((void**)&b->d_partial2, b->part_elems * sizeof(int32_t)) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_pfork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_pjoin, cudaEventDisableTiming) == cudaSuccess;
+  }
   if (ok && (flags & TM_BATCH_HOST_INPUTS)) {
     int64_t xb = 0, tb = 0;
     b->xoff.resize(n); b->toff.resize(n);
@@ -548,8 +594,16 @@ tm_status batch_build(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* 
   return TM_OK;
 }
 
-tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
-  TM_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int32_t), s));
+// The share starts of a fold group whose shares follow piece boundaries.
+void fold_args_shares(FoldArgs& a, const tm_batch_s::FoldGroup& g) {
+  a.has_cb = g.cb.empty() ? 0 : 1;
+  for (size_t c = 0; c < g.cb.size(); ++c) a.cb[c] = g.cb[c];
+}
+
+tm_status batch_fold(tm_batch_t b, cudaStream_t s, int parity) {
+  int32_t* partial = parity ? b->d_partial2 : b->d_partial;
+  int32_t* err = b->d_err + parity;
+  TM_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
   if (!b->lq.empty() && b->aux) {
     // the long-FFT queries' template spectra need only t: they run on a
     // side stream while the fold streams x (joined in batch_correlate)
@@ -563,22 +617,27 @@ tm_status batch_fold(tm_batch_t b, cudaStream_t s) {
     if (g.W == 0) continue;
     FoldArgs a;
     a.q = b->d_fq + g.first; a.nq = g.count; a.dtype = g.dtype; a.nctas = g.nctas; a.W = g.W;
-    a.partial = b->d_partial; a.err = b->d_err; a.tile = g.tile;
+    a.partial = partial; a.err = err; a.tile = g.tile;
+    fold_args_shares(a, g);
     fold_args_first_queries(a, b->fq.data() + g.first);
     TM_CUDA(launch_fold(a, g.jmax, s));
   }
   if (!b->direct.empty())
     TM_CUDA(launch_fold_direct(b->d_cq, b->d_order + b->n, int32_t(b->direct.size()), b->maxP_direct,
-                               b->maxmod_direct, b->maxM_direct, b->maxHM_direct, b->d_partial, b->d_y, s));
+                               b->maxmod_direct, b->maxM_direct, b->maxHM_direct, partial, b->d_y, s));
   return TM_OK;
 }
 
-tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s) {
+tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s, int parity) {
   CorrArgs a;
   a.q = b->d_cq; a.order = b->d_order; a.nq = b->n - b->n_blocked - b->n_large;
-  a.partial = b->d_partial; a.y = b->d_y; a.spec = b->d_spec; a.r = b->d_r; a.tw = b->tw;
-  a.out = out; a.err = b->d_err;
+  a.partial = parity ? b->d_partial2 : b->d_partial;
+  a.y = b->d_y; a.spec = b->d_spec; a.r = b->d_r; a.tw = b->tw;
+  a.out = out; a.err = b->d_err + parity;
+  a.ctas = b->corr_ctas;
   if (a.nq > 0) TM_CUDA(launch_correlate(a, b->maxP, s));
+  a.ctas = 0;
+  a.first = 0;
   if (b->n_blocked > 0) {
     a.order = b->d_order + (b->n - b->n_large - b->n_blocked);
     a.nq = b->n_blocked;
@@ -861,6 +920,81 @@ tm_status tm_batch_run(tm_batch_t b, tm_result* out, tm_stream_t stream) {
   return tm_batch_correlate(b, out, stream);
 }
 
+tm_status tm_batch_set_grid(tm_batch_t b, int32_t fold_ctas, int32_t corr_ctas) {
+  if (!b) return fail(TM_EINVAL, "null batch");
+  if (!b->owns_memory) return fail(TM_EINVAL, "the batch's memory belongs to a server");
+  if (fold_ctas < 0 || corr_ctas < 0) return fail(TM_EINVAL, "negative CTA count");
+  if (b->pending) return fail(TM_EBUSY, "a pipelined run is pending (tm_batch_pipeline_flush first)");
+  TM_CUDA(cudaSetDevice(b->device));
+  int32_t tiles[4] = {kFoldTile, kFoldTile, kFoldTile, kFoldTile};
+  for (const auto& g : b->groups) tiles[g.dtype] = g.tile;
+  const std::vector<tm_query> q = b->q;
+  b->fold_cap = fold_ctas;
+  b->corr_ctas = corr_ctas;
+  tm_status st = batch_plan(b, q.data(), b->n, b->flags);
+  if (st != TM_OK) return st;
+  for (auto& g : b->groups) g.tile = tiles[g.dtype];
+  if (b->part_elems > b->part_alloc) {
+    // more shares than the buffers were sized for: grow them
+    TM_CUDA(cudaDeviceSynchronize());
+    cudaFree(b->d_partial);
+    b->d_partial = nullptr;
+    if (b->d_partial2) { cudaFree(b->d_partial2); b->d_partial2 = nullptr; }
+    bool ok = cudaMalloc((void**)&b->d_partial, b->part_elems * sizeof(int32_t)) == cudaSuccess;
+    if (ok && (b->flags & TM_BATCH_PIPELINED))
+      ok = cudaMalloc((void**)&b->d_partial2, b->part_elems * sizeof(int32_t)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return fail(TM_ENOMEM, "partial fold buffers");
+    }
+    b->ws_bytes += (b->part_elems - b->part_alloc) * int64_t(sizeof(int32_t)) * ((b->flags & TM_BATCH_PIPELINED) ? 2 : 1);
+    b->part_alloc = b->part_elems;
+  }
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  bind_pointers(b);
+  st = upload_descriptors(b, nullptr);
+  if (st != TM_OK) return st;
+  TM_CUDA(cudaStreamSynchronize(nullptr));
+  return TM_OK;
+}
+
+tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out, tm_stream_t stream) {
+  if (!b || !out) return fail(TM_EINVAL, "null argument");
+  if (!(b->flags & TM_BATCH_PIPELINED)) return fail(TM_EINVAL, "batch was created without TM_BATCH_PIPELINED");
+  if (b->n_large > 0 || b->n_blocked > 0 || !b->direct.empty())
+    return fail(TM_EUNSUPPORTED, "pipelined runs need every query on the streaming fold and FFT lengths up to 16384");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int par = b->pp;
+  // the correlation stream starts after the caller's earlier work
+  TM_CUDA(cudaEventRecord(b->ev_pfork, s));
+  TM_CUDA(cudaStreamWaitEvent(b->cstream, b->ev_pfork, 0));
+  tm_status st = batch_fold(b, s, par);
+  if (st != TM_OK) return st;
+  if (b->pending) {
+    st = batch_correlate(b, b->pending_out, b->cstream, par ^ 1);
+    if (st != TM_OK) return st;
+  }
+  TM_CUDA(cudaEventRecord(b->ev_pjoin, b->cstream));
+  TM_CUDA(cudaStreamWaitEvent(s, b->ev_pjoin, 0));
+  b->pending = true;
+  b->pending_out = out;
+  b->pp = par ^ 1;
+  return TM_OK;
+}
+
+tm_status tm_batch_pipeline_flush(tm_batch_t b, tm_stream_t stream) {
+  if (!b) return fail(TM_EINVAL, "null batch");
+  if (!b->pending) return TM_OK;
+  tm_status st = batch_correlate(b, b->pending_out, reinterpret_cast<cudaStream_t>(stream), b->pp ^ 1);
+  if (st != TM_OK) return st;
+  b->pending = false;
+  b->pending_out = nullptr;
+  return TM_OK;
+}
+
 tm_status tm_selftest_wait_timeout(int64_t limit_ns, int32_t* gave_up) {
   if (!gave_up) return fail(TM_EINVAL, "tm_selftest_wait_timeout: null argument");
   const int64_t lim = limit_ns < 1000 ? 1000 : limit_ns > 100000000 ? 100000000 : limit_ns;
@@ -916,6 +1050,7 @@ tm_status tm_batch_autotune(tm_batch_t b, tm_stream_t stream, uint32_t flags, in
     FoldArgs a;
     a.q = b->d_fq + g.first; a.nq = g.count; a.dtype = g.dtype; a.nctas = g.nctas; a.W = g.W;
     a.partial = b->d_partial; a.err = b->d_err;
+    fold_args_shares(a, g);
     fold_args_first_queries(a, b->fq.data() + g.first);
     float best = 0.f;
     int32_t best_tile = kFoldTile;
@@ -1023,7 +1158,9 @@ tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r) {
 tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, int64_t* ws) {
   if (!b) return fail(TM_EINVAL, "null batch");
   if (launches) {
-    int32_t l = (b->n > b->n_blocked + b->n_large ? 1 : 0) + (b->n_blocked > 0 ? 1 : 0);
+    const int32_t nsm = b->n - b->n_blocked - b->n_large;   // queries of the shared-memory correlation
+    const int32_t waves = nsm == 0 ? 0 : (b->corr_ctas > 0 ? int32_t(ceil_div(nsm, b->corr_ctas)) : 1);
+    int32_t l = waves + (b->n_blocked > 0 ? 1 : 0);
     for (const auto& g : b->groups) l += g.W > 0 ? 1 : 0;
     l += b->direct.empty() ? 0 : (b->maxHM_direct > 0 ? 2 : 1);
     if (!b->lq.empty()) l += large_launches(b->lq_two ? 2 : 1);
@@ -1037,7 +1174,9 @@ tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, in
 tm_status tm_batch_device_error(tm_batch_t b, tm_stream_t stream, int32_t* err) {
   if (!b || !err) return fail(TM_EINVAL, "null argument");
   TM_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
-  TM_CUDA(cudaMemcpy(err, b->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  int32_t w[2] = {0, 0};   // pipelined batches alternate between two error words
+  TM_CUDA(cudaMemcpy(w, b->d_err, sizeof(w), cudaMemcpyDeviceToHost));
+  *err = w[0] | ((b->flags & TM_BATCH_PIPELINED) ? w[1] : 0);
   return TM_OK;
 }
 

@@ -1055,15 +1055,16 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   resolve(a, Q, qi, t_integral, t1, maxy_all, cands);
 }
 
-// One CTA per query, in a.order (largest FFT first); the hardware hands the
-// next query to whichever SM frees up. (A persistent loop over queries with
-// twiddles reused across them was tried: carrying state across iterations
-// pushes this kernel past its 128 registers and into local memory.)
+// One CTA per query, in a.order (largest FFT first) from a.first on; the
+// hardware hands the next query to whichever SM frees up. (A loop over
+// queries inside a CTA was tried: the state it carries across iterations
+// pushes this kernel past its 128 registers and into local memory. A
+// launch limited to fewer CTAs is therefore cut into waves of launches.)
 template <int NBMAX>
 __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a) {
   extern __shared__ __align__(16) float2 sbuf[];
   int loaded_logP = -1;
-  corr_query<NBMAX>(a, a.order[blockIdx.x], sbuf, loaded_logP);
+  corr_query<NBMAX>(a, a.order[a.first + blockIdx.x], sbuf, loaded_logP);
 }
 
 // ---------------------------------------------------------------- blocked correlation
@@ -1300,10 +1301,19 @@ cudaError_t corr_configure() {
 cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s) {
   CorrArgs b = a;
   b.smem_bytes = corr_smem_bytes(maxP);
-  // one butterfly of radix 16 per thread and pass up to P = 8192, two above
-  if (maxP <= kPMax / 2) corr_kernel<1><<<a.nq, kCorrThreads, b.smem_bytes, s>>>(b);
-  else corr_kernel<2><<<a.nq, kCorrThreads, b.smem_bytes, s>>>(b);
-  return cudaGetLastError();
+  // at most a.ctas CTAs at a time (so that a concurrent fold keeps its
+  // SMs): waves of launches over the order
+  const int wave = (a.ctas > 0 && a.ctas < a.nq) ? a.ctas : a.nq;
+  for (int f = 0; f < a.nq; f += wave) {
+    b.first = a.first + f;
+    const int grid = min(wave, a.nq - f);
+    // one butterfly of radix 16 per thread and pass up to P = 8192, two above
+    if (maxP <= kPMax / 2) corr_kernel<1><<<grid, kCorrThreads, b.smem_bytes, s>>>(b);
+    else corr_kernel<2><<<grid, kCorrThreads, b.smem_bytes, s>>>(b);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_correlate_blocked(const CorrArgs& a, cudaStream_t s) {

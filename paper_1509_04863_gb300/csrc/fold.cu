@@ -573,8 +573,8 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
   uint64_t* empty = full + kFoldMaxStages;
 
   const int tid = threadIdx.x;
-  const int64_t cb = fold_cta_begin(a.W, a.nctas, blockIdx.x);
-  const int64_t ce = fold_cta_begin(a.W, a.nctas, blockIdx.x + 1);
+  const int64_t cb = fold_share_begin(a, blockIdx.x);
+  const int64_t ce = fold_share_begin(a, blockIdx.x + 1);
 
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -662,15 +662,25 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
     const int Mp = a.q[qi].Mp[m];
     // rows are counted from element e0 of the signal (0 unless x is a slice)
     const int ph = int(a.q[qi].e0 % Mp);
-    int32_t* dst = a.partial + a.q[qi].part + int64_t(blockIdx.x - a.q[qi].first_cta) * a.q[qi].stride +
-                   a.q[qi].moff[m];
     const int J = fold_units_per_lane(Mp, W, U::kE);
     if constexpr (U::kWalk) {
-      if (J <= 1) ok = consume_share_walk<U, 1>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
-      else if (J == 2 || JMAX == 2) ok = consume_share_walk<U, 2>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
-      else if (J <= 3 || JMAX <= 3) ok = consume_share_walk<U, (JMAX < 3 ? JMAX : 3)>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
-      else ok = consume_share_walk<U, JMAX>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
+      // one slot per CTA share, or (piece > 0) one per fixed piece of the
+      // signal, the share then holding whole pieces
+      const int64_t piece = a.q[qi].piece;
+      const int64_t step = piece > 0 ? piece : int64_t(hi - lo);
+      for (int64_t plo = lo; plo < hi && ok; plo += step) {
+        const int phi = int(min(int64_t(hi), plo + step));
+        const int64_t slot = piece > 0 ? plo / piece : int64_t(blockIdx.x - a.q[qi].first_cta);
+        int32_t* dst = a.partial + a.q[qi].part + slot * a.q[qi].stride + a.q[qi].moff[m];
+        const int pl = int(plo);
+        if (J <= 1) ok = consume_share_walk<U, 1>(smem, full, empty, tile, stages, pl, phi, Mp, ph, W, wig, dst, rp);
+        else if (J == 2 || JMAX == 2) ok = consume_share_walk<U, 2>(smem, full, empty, tile, stages, pl, phi, Mp, ph, W, wig, dst, rp);
+        else if (J <= 3 || JMAX <= 3) ok = consume_share_walk<U, (JMAX < 3 ? JMAX : 3)>(smem, full, empty, tile, stages, pl, phi, Mp, ph, W, wig, dst, rp);
+        else ok = consume_share_walk<U, JMAX>(smem, full, empty, tile, stages, pl, phi, Mp, ph, W, wig, dst, rp);
+      }
     } else {
+      int32_t* dst = a.partial + a.q[qi].part + int64_t(blockIdx.x - a.q[qi].first_cta) * a.q[qi].stride +
+                     a.q[qi].moff[m];
       if (J <= 1) ok = consume_share<U, 1>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
       else if (J == 2 || JMAX == 2) ok = consume_share<U, 2>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);
       else if (J <= 4 || JMAX <= 4) ok = consume_share<U, (JMAX < 4 ? JMAX : 4)>(smem, full, empty, tile, stages, lo, hi, Mp, ph, W, wig, dst, rp);

@@ -71,6 +71,7 @@ struct tm_batch_s {
     int32_t dtype, first, count, nctas, jmax;
     int64_t W;
     int32_t tile = ftm::kFoldTile;   // stage bytes (tm_batch_autotune may change it)
+    std::vector<int64_t> cb;         // share starts on piece boundaries (real signals), else empty
   };
   std::vector<FoldGroup> groups;
   std::vector<int32_t> fold_of;
@@ -115,6 +116,19 @@ struct tm_batch_s {
   // tm_batch_graph_capture: the captured run and the stream it was captured on
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // launch geometry (tm_batch_set_grid): most fold CTAs (0: one per SM) and
+  // most correlation CTAs at a time (0: one per query)
+  int32_t fold_cap = 0, corr_ctas = 0;
+  int64_t part_alloc = 0;   // int32 entries allocated for each partial buffer
+  // pipelined runs (TM_BATCH_PIPELINED): a second partial buffer, the
+  // correlation's stream, the fork/join events, and the run whose
+  // correlation is still to come
+  int32_t* d_partial2 = nullptr;
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t ev_pfork = nullptr, ev_pjoin = nullptr;
+  int32_t pp = 0;                 // partial buffer of the next fold
+  bool pending = false;
+  tm_result* pending_out = nullptr;
 };
 
 
@@ -131,7 +145,8 @@ tm_status batch_alloc(tm_batch_s* b);
 void batch_free(tm_batch_s* b);
 void bind_pointers(tm_batch_s* b);
 tm_status upload_descriptors(tm_batch_s* b, cudaStream_t s);
-tm_status batch_fold(tm_batch_s* b, cudaStream_t s);
-tm_status batch_correlate(tm_batch_s* b, tm_result* out, cudaStream_t s);
+// parity: which partial buffer and error word (pipelined batches alternate)
+tm_status batch_fold(tm_batch_s* b, cudaStream_t s, int parity = 0);
+tm_status batch_correlate(tm_batch_s* b, tm_result* out, cudaStream_t s, int parity = 0);
 
 }  // namespace ftm

@@ -81,6 +81,11 @@ struct FoldQ {
   int64_t part;       // offset of this query's first slot in the partial buffer
   int64_t e0;         // element index of x[0] within its signal (a slice), else 0;
                       // the byte offset e0 * bits / 8 is a multiple of 16
+  int64_t piece;      // 0: one slot per CTA share holding bytes of this signal;
+                      // > 0: the signal is cut into pieces of this many bytes
+                      // (a multiple of 64 KiB, fixed by the signal alone) that
+                      // no CTA share splits, one slot per piece in piece order,
+                      // so fp32 sums do not depend on the rest of the batch
 };
 
 struct FoldArgs {
@@ -98,6 +103,10 @@ struct FoldArgs {
   // a chain of dependent global loads ahead of its first copy
   int32_t has_q0 = 0;
   int32_t q0[kFoldMaxCtas];
+  // cb[c]: start of CTA c's share (cb[nctas] = W) when the shares follow
+  // piece boundaries (has_cb); otherwise equal shares (fold_cta_begin)
+  int32_t has_cb = 0;
+  int64_t cb[kFoldMaxCtas + 1];
 };
 
 // Start of CTA c's share of W bytes (multiple of 16). Shared by the host
@@ -107,18 +116,32 @@ __host__ __device__ inline int64_t fold_cta_begin(int64_t W, int32_t nctas, int3
   return ((units * c) / nctas) << 4;
 }
 
+// Start of CTA c's share of a launch.
+__host__ __device__ inline int64_t fold_share_begin(const FoldArgs& a, int32_t c) {
+  return a.has_cb ? a.cb[c] : fold_cta_begin(a.W, a.nctas, c);
+}
+
 // Fills a.q0 from the host copy hq[0..a.nq) of the descriptors a.q points
-// to (same order), when a.nctas fits.
+// to (same order), when a.nctas fits; a.cb (has_cb) must be set before.
 inline void fold_args_first_queries(FoldArgs& a, const FoldQ* hq) {
   a.has_q0 = 0;
   if (a.nctas <= 0 || a.nctas > kFoldMaxCtas) return;
   int i = 0;
   for (int32_t c = 0; c < a.nctas; ++c) {
-    const int64_t cb = fold_cta_begin(a.W, a.nctas, c);
+    const int64_t cb = fold_share_begin(a, c);
     while (i < a.nq && hq[i].goff + hq[i].nbytes <= cb) ++i;   // shares ascend with c
     a.q0[c] = i;
   }
   a.has_q0 = 1;
+}
+
+// Piece size of a real signal of `bytes` bytes: at least 2 MiB, at most 64
+// pieces, a multiple of 64 KiB (so that every stage of the fold's ring lies
+// inside one piece). Depends on the signal alone.
+inline int64_t fold_piece_bytes(int64_t bytes) {
+  const int64_t unit = 65536;
+  const int64_t per = ((bytes + 63) / 64 + unit - 1) / unit * unit;
+  return per > (int64_t(2) << 20) ? per : (int64_t(2) << 20);
 }
 
 // ---------------------------------------------------------------- correlation kernel (steps 3-9)
@@ -172,6 +195,9 @@ struct CorrArgs {
   tm_result* out;
   int32_t* err;
   int32_t smem_bytes;     // dynamic shared memory of the launch (set by the launcher)
+  int32_t ctas = 0;       // most CTAs running at a time (0: one CTA per query,
+                          // all at once); more queries run as waves of launches
+  int32_t first = 0;      // first position in the order (set per wave by the launcher)
 };
 
 // ---------------------------------------------------------------- kernels' host launchers

@@ -108,17 +108,22 @@ def test_alone_and_in_the_mix(tm):
     sid = srv.register_signal(qa.x, qa.N, "i8")
     qb = W.planted_query(78, 1 << 19, 2048, "bits", flip_p=0.05, mode="auto")
     sid2 = srv.register_signal(qb.x, qb.N, "bits")
+    qc = W.planted_query(79, (1 << 21) + 5, 1500, "f32", t_sigma=0.3, mode="auto")
+    sid3 = srv.register_signal(qc.x, qc.N, "f32")
     srv.submit(sid, qa.t, tag=1, mode="paper")
-    alone = _collect(srv, 1)[1]
-    rng = np.random.default_rng(5)
+    srv.submit(sid3, qc.t, tag=3, mode="auto")
+    alone = _collect(srv, 2)
     for i in range(40):
         srv.submit(sid2, qb.t, tag=100 + i, mode="auto")
         if i == 20:
             srv.submit(sid, qa.t, tag=2, mode="paper")
-    mixed = _collect(srv, 41)
-    a = {k: v for k, v in alone.items() if k not in ("tag", "latency_us")}
-    m = {k: v for k, v in mixed[2].items() if k not in ("tag", "latency_us")}
-    assert a == m
+            srv.submit(sid3, qc.t, tag=4, mode="auto")
+    mixed = _collect(srv, 42)
+    for ta, tb in ((1, 2), (3, 4)):
+        a = {k: v for k, v in alone[ta].items() if k not in ("tag", "latency_us")}
+        m = {k: v for k, v in mixed[tb].items() if k not in ("tag", "latency_us")}
+        assert a == m, (ta, a, m)   # real signals too: their folds follow fixed pieces
+    check_result(qc, mixed[4], O.match_query(qc))
     srv.close()
 
 
@@ -157,8 +162,8 @@ def test_submit_validation(tm):
 
 def test_fold_cache(tm):
     """Requests on resident signals whose moduli repeat are served from the
-    fold cache (no O(N) fold): the same results as a server without it
-    (bit-equal for +-1 signals, near for real ones), and the cache reports
+    fold cache (no O(N) fold): both servers meet the oracle bar and agree
+    bit for bit (real folds follow fixed pieces), and the cache reports
     hits after the first fold of each (signal, M1, M2)."""
     # N = 2^20 + 3: automatic moduli M1 = max(K, 1024), so every K <= 1024
     # shares one pair
@@ -196,8 +201,8 @@ def test_fold_cache(tm):
         ref = O.match_query(q)
         check_result(q, a, ref)
         check_result(q, b, ref)
-        if base[k].xdtype in ("i8", "bits"):
-            assert {f: a[f] for f in fields} == {f: b[f] for f in fields}, (i, a, b)
+        # real folds follow fixed pieces: cached and uncached alike, bit for bit
+        assert {f: a[f] for f in fields} == {f: b[f] for f in fields}, (i, a, b)
 
 
 def test_long_fft_requests(tm):
