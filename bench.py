@@ -326,46 +326,93 @@ def run_native(args):
     qs = gen_queries(rank)
     specs = [dict(x=torch.from_numpy(q.x).to(dev), t=torch.from_numpy(q.t).to(dev), N=q.N, K=q.K,
                   xdtype="i8", mode="paper") for q in qs]
-    b = tm.Batch(specs)
-    launches = b.stats()["launches_per_run"]
+    b = tm.Batch(specs, pipelined=True)
     out = tm.result_buffer(QUERIES, device=dev)
+    outs = [tm.result_buffer(QUERIES, device=dev) for _ in range(2)]
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         b.run(out)
     torch.cuda.synchronize()
     res = tm.decode_results(out)
     success = sum(r["shift"] == q.k_star for r, q in zip(res, qs)) / len(qs)
-
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        dist.barrier()
+
+    # ---- sequential steps (fold on every SM, then the correlation): the
+    # latency of one step and the split between the two kernels
+    Ks = min(K, 500)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(Ks)]
     torch.cuda.synchronize()
-    for i in range(K):
+    for i in range(Ks):
         ev[i][0].record(stream)
         b.fold()
         ev[i][1].record(stream)
         b.correlate(out)
         ev[i][2].record(stream)
     torch.cuda.synchronize()
+    step_ms = np.array([ev[i][0].elapsed_time(ev[i][2]) for i in range(Ks)])
+    fold_ms_seq = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(Ks)])
+    seq_ms_per_step = ev[0][0].elapsed_time(ev[Ks - 1][2]) / Ks
+    seq_ok = tm.decode_results(out) == res
+
+    # ---- pipelined steps: each step's fold beside the previous step's
+    # correlation on disjoint SMs (tm_batch_set_grid + tm_batch_run_pipelined);
+    # the split is chosen by timing a few candidates
+    def pipe_ms(F, C, n):
+        b.set_grid(F, C)
+        for i in range(3):
+            b.run_pipelined(outs[i % 2])
+        b.flush()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(n):
+            b.run_pipelined(outs[i % 2])
+        b.flush()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+    cands = [(sms - c, c) for c in (16, 20, 22, 24, 28, 32)] + [(0, 0)]
+    tried = {f"{F}+{C}": pipe_ms(F, C, 40) for F, C in cands}
+    best = min(cands, key=lambda fc: tried[f"{fc[0]}+{fc[1]}"])
+    b.set_grid(*best)
+    for i in range(3):
+        b.run_pipelined(outs[i % 2])
+    b.flush()
+
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    for i in range(K):
+        b.run_pipelined(outs[i % 2], fold_events=pev[i])
+    b.flush()
+    e_end.record(stream)
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = np.array([ev[i][0].elapsed_time(ev[i][2]) for i in range(K)])
-    fold_ms = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(K)])
-    total_ms = ev[0][0].elapsed_time(ev[K - 1][2])
+    pipe_ok = tm.decode_results(outs[0]) == res and tm.decode_results(outs[1]) == res
+    assert b.device_error() == 0
+    fold_ms = np.array([pev[i][0].elapsed_time(pev[i][1]) for i in range(K)])
+    total_ms = e_start.elapsed_time(e_end)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     ms_per_step = total_ms / K
     value = world * QUERIES / (ms_per_step / 1e3)
+    launches = b.stats()["launches_per_run"]
     in_bytes = QUERIES * N_SIG   # int8: one byte per element, read once for both folds
     fold_s = float(fold_ms.mean()) / 1e3
     hbm_peak, peak_kind = measured_peaks()
     achieved = in_bytes / fold_s / 1e9
+    achieved_seq = in_bytes / (float(fold_ms_seq.mean()) / 1e3) / 1e9
+    b.set_grid(0, 0)
 
     # ---- end to end through the C ABI from pinned host buffers
     bh = tm.Batch([dict(x=None, t=None, N=q.N, K=q.K, xdtype="i8", mode="paper") for q in qs], host_inputs=True)
@@ -511,12 +558,24 @@ def run_native(args):
             "vs_baseline": None, "dtype": "int32 (fold), f32 (FFT), int64 (rescoring)", "data": "synthetic",
             "config": dict(WORKLOAD, parallelism=f"queries sharded over {world} GPU(s), no collective"),
             "input_GBps": world * in_bytes / (ms_per_step / 1e3) / 1e9,
+            "pipelined": {"fold_ctas": best[0], "corr_ctas": best[1], "sms": sms,
+                          "what": "each step's fold (fold_ctas CTAs) runs beside the previous step's correlation "
+                                  "(waves of corr_ctas CTAs) on disjoint SMs; K steps + the last correlation "
+                                  "are timed; results identical to the sequential run",
+                          "results_equal_sequential": pipe_ok, "tried_ms_per_step": tried},
+            "sequential": {"ms_per_step": seq_ms_per_step, "queries_per_s": world * QUERIES / (seq_ms_per_step / 1e3),
+                           "steps": Ks, "fold_ms": float(fold_ms_seq.mean()),
+                           "corr_ms": float((step_ms - fold_ms_seq).mean()),
+                           "fold_frac_of_peak": achieved_seq / hbm_peak, "results_equal": seq_ok,
+                           "what": "fold on every SM, then the correlation, one step at a time"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                           "what": "one batch64 step (64 queries), device time"},
+                           "what": "one sequential batch64 step (64 queries), device time"},
             "roofline": {"bound": "hbm", "kernel": "fold_kernel<UnitI8,3>", "achieved": achieved, "peak": hbm_peak,
                          "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": in_bytes,
-                         "fold_ms": float(fold_ms.mean()), "corr_ms": float((step_ms - fold_ms).mean())},
+                         "fold_ms": float(fold_ms.mean()), "fold_ctas": best[0] or sms,
+                         "what": "the fold launch of each pipelined step, timed on its stream while the "
+                                 "previous step's correlation runs beside it"},
             "e2e": {"value": world * QUERIES * e2e_steps / e2e_s, "unit": "queries/s",
                     "h2d_bytes_per_step": in_bytes + QUERIES * K_T * 4, "d2h_bytes_per_step": QUERIES * tm.RESULT_BYTES,
                     "api": "tm_batch_run_host (pinned host buffers)", "matches_device_run": e2e_ok,

@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct CUstream_st* tm_stream_t;
+typedef struct CUevent_st* tm_event_t;   /* the same type as cudaEvent_t */
 
 typedef enum {
   TM_OK = 0,
@@ -298,8 +299,11 @@ TM_API tm_status tm_batch_set_grid(tm_batch_t b, int32_t fold_ctas, int32_t corr
  * correlation (P <= 16384) and the streaming fold only (TM_EUNSUPPORTED
  * otherwise). The fold alternates between two partial buffers and error
  * words, so call i's fold never overwrites what call i-1's correlation
- * reads. */
-TM_API tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out_dev, tm_stream_t stream);
+ * reads. fold_begin / fold_end (optional, NULL to skip): events recorded on
+ * `stream` just before and after this call's fold launches, so that a
+ * caller can time the fold while the correlation runs beside it. */
+TM_API tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out_dev, tm_stream_t stream, tm_event_t fold_begin,
+                                        tm_event_t fold_end);
 /* Runs the pending correlation of the last pipelined call on `stream`
  * (nothing when none is pending). */
 TM_API tm_status tm_batch_pipeline_flush(tm_batch_t b, tm_stream_t stream);

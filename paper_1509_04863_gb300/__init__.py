@@ -81,7 +81,7 @@ _SIGS = {
                                     C.c_void_p]),
     "tm_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
     "tm_batch_set_grid": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
-    "tm_batch_run_pipelined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tm_batch_run_pipelined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tm_batch_pipeline_flush": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_graph_capture": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -236,6 +236,13 @@ def _query_struct(x_ptr, t_ptr, N, K, xdtype, mode, M1=0, M2=0, allow_ambig=Fals
                     _plan_flags(allow_ambig, thm2, three), int(M3), 0)
 
 
+def _event_ptr(ev):
+    """The cudaEvent_t of a torch.cuda.Event (created on first use)."""
+    if ev.cuda_event == 0:   # torch creates the event lazily at its first record
+        ev.record()
+    return ev.cuda_event
+
+
 class Batch:
     """tm_batch_create / tm_batch_run / tm_batch_fold / tm_batch_correlate / ...
 
@@ -279,10 +286,15 @@ class Batch:
         corr_ctas correlation CTAs at a time (0: one per query)."""
         _check(lib().tm_batch_set_grid(self._h, int(fold_ctas), int(corr_ctas)), "tm_batch_set_grid")
 
-    def run_pipelined(self, out, stream=None):
+    def run_pipelined(self, out, stream=None, fold_events=None):
         """tm_batch_run_pipelined: fold now, correlate the previous call's
-        folds beside it (into the previous call's `out`)."""
-        _check(lib().tm_batch_run_pipelined(self._h, out.data_ptr(), _stream_ptr(stream)), "tm_batch_run_pipelined")
+        folds beside it (into the previous call's `out`). fold_events: an
+        optional pair of torch.cuda.Event recorded around the fold."""
+        e0 = e1 = None
+        if fold_events is not None:
+            e0, e1 = (_event_ptr(e) for e in fold_events)
+        _check(lib().tm_batch_run_pipelined(self._h, out.data_ptr(), _stream_ptr(stream), e0, e1),
+               "tm_batch_run_pipelined")
 
     def flush(self, stream=None):
         """tm_batch_pipeline_flush: the last pipelined call's correlation."""

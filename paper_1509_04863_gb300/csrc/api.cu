@@ -961,7 +961,8 @@ tm_status tm_batch_set_grid(tm_batch_t b, int32_t fold_ctas, int32_t corr_ctas) 
   return TM_OK;
 }
 
-tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out, tm_stream_t stream) {
+tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out, tm_stream_t stream, tm_event_t fold_begin,
+                                 tm_event_t fold_end) {
   if (!b || !out) return fail(TM_EINVAL, "null argument");
   if (!(b->flags & TM_BATCH_PIPELINED)) return fail(TM_EINVAL, "batch was created without TM_BATCH_PIPELINED");
   if (b->n_large > 0 || b->n_blocked > 0 || !b->direct.empty())
@@ -971,8 +972,10 @@ tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out, tm_stream_t strea
   // the correlation stream starts after the caller's earlier work
   TM_CUDA(cudaEventRecord(b->ev_pfork, s));
   TM_CUDA(cudaStreamWaitEvent(b->cstream, b->ev_pfork, 0));
+  if (fold_begin) TM_CUDA(cudaEventRecord(reinterpret_cast<cudaEvent_t>(fold_begin), s));
   tm_status st = batch_fold(b, s, par);
   if (st != TM_OK) return st;
+  if (fold_end) TM_CUDA(cudaEventRecord(reinterpret_cast<cudaEvent_t>(fold_end), s));
   if (b->pending) {
     st = batch_correlate(b, b->pending_out, b->cstream, par ^ 1);
     if (st != TM_OK) return st;

@@ -104,6 +104,25 @@ __device__ __forceinline__ void load16p(const uint8_t* buf, int o, uint32_t (&w)
   }
 }
 
+// The two aligned 16-byte words around byte o of a stage (-16 < o < valid
+// + 16), and the 16 bytes [o, o+16) extracted from them (r = o & 15 warp-
+// uniform). Split so that a batch of rows issues all its loads first.
+__device__ __forceinline__ void load32raw(const uint8_t* buf, int o, uint4& a, uint4& b) {
+  const uint4* p = reinterpret_cast<const uint4*>(buf + (o & ~15));
+  a = p[0];
+  b = p[1];
+}
+__device__ __forceinline__ void extract16(const uint4& a, const uint4& b, int o, uint32_t (&w)[4]) {
+  const int r = o & 15;
+  const uint32_t sh = uint32_t(r & 3) * 8u;
+  switch (r >> 2) {
+    case 0: w[0] = fsr(a.x, a.y, sh); w[1] = fsr(a.y, a.z, sh); w[2] = fsr(a.z, a.w, sh); w[3] = fsr(a.w, b.x, sh); break;
+    case 1: w[0] = fsr(a.y, a.z, sh); w[1] = fsr(a.z, a.w, sh); w[2] = fsr(a.w, b.x, sh); w[3] = fsr(b.x, b.y, sh); break;
+    case 2: w[0] = fsr(a.z, a.w, sh); w[1] = fsr(a.w, b.x, sh); w[2] = fsr(b.x, b.y, sh); w[3] = fsr(b.y, b.z, sh); break;
+    default: w[0] = fsr(a.w, b.x, sh); w[1] = fsr(b.x, b.y, sh); w[2] = fsr(b.y, b.z, sh); w[3] = fsr(b.z, b.w, sh); break;
+  }
+}
+
 // ---------------------------------------------------------------- int8 +-1
 // An entry is 0x01 (+1) or 0xFF (-1), i.e. 1 + 254 [entry = -1]. Whole
 // 32-bit words are added, carries between byte lanes included, so after R
@@ -156,6 +175,11 @@ struct UnitI8 {
     s[3] += a.w + b.w;
     rows += 2u;
   }
+  __device__ __forceinline__ void add_words(const uint32_t (&w)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s[i] += w[i];
+    ++rows;
+  }
   __device__ __forceinline__ void widen() {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -193,8 +217,14 @@ struct UnitI8 {
 // Row walkers for units that read past stage edges without masks: read
 // the rows o, o + Mp, ... with o < el and return the first offset >= el.
 // Offsets and Mp multiples of 16: aligned loads, two rows per step.
-template <class U>
+template <class U, int G>
 __device__ __forceinline__ int walk_aligned(U& u, const uint8_t* buf, int o, int el, int Mp) {
+  if constexpr (G == 4) {
+    for (; o + 3 * Mp < el; o += 4 * Mp) {
+      u.add2_aligned(buf, o, o + Mp);
+      u.add2_aligned(buf, o + 2 * Mp, o + 3 * Mp);
+    }
+  }
   for (; o + Mp < el; o += 2 * Mp) u.add2_aligned(buf, o, o + Mp);
   if (o < el) {
     u.template addp<0>(buf, o);
@@ -203,11 +233,42 @@ __device__ __forceinline__ int walk_aligned(U& u, const uint8_t* buf, int o, int
   return o;
 }
 
+// Four rows o + k Mp (k < 4) with Mp = 1 (mod 16), the first at phase P:
+// all eight loads are issued before any sum, so the rows' shared-memory
+// round trips overlap.
+template <int P, class U>
+__device__ __forceinline__ void add4_step1(U& u, const uint8_t* buf, int o, int Mp) {
+  uint32_t w0[4], w1[4], w2[4], w3[4];
+  load16p<P>(buf, o, w0);
+  load16p<(P + 1) & 15>(buf, o + Mp, w1);
+  load16p<(P + 2) & 15>(buf, o + 2 * Mp, w2);
+  load16p<(P + 3) & 15>(buf, o + 3 * Mp, w3);
+  u.add_words(w0);
+  u.add_words(w1);
+  u.add_words(w2);
+  u.add_words(w3);
+}
+
 // Mp = 1 (mod 16), as for the modulus K+1 with K a multiple of 16: the
-// phase o & 15 advances by one per row, so the rows are visited through a
-// cycle of 16 compile-time phases entered at the first row's phase.
-template <class U>
+// phase o & 15 advances by one per row. Rows go four at a time (the phase
+// of the group's first row taken at run time, the others following at
+// compile time), the last ones through a cycle of 16 compile-time phases
+// entered at the first remaining row's phase.
+template <class U, int G>
 __device__ __forceinline__ int walk_step1(U& u, const uint8_t* buf, int o, int el, int Mp) {
+#define FTM_GROUP(P)                       \
+  case P:                                  \
+    add4_step1<P>(u, buf, o, Mp);          \
+    break;
+  if constexpr (G == 4) {
+    for (; o + 3 * Mp < el; o += 4 * Mp) {
+      switch (o & 15) {
+        FTM_GROUP(0) FTM_GROUP(1) FTM_GROUP(2) FTM_GROUP(3) FTM_GROUP(4) FTM_GROUP(5) FTM_GROUP(6) FTM_GROUP(7)
+        FTM_GROUP(8) FTM_GROUP(9) FTM_GROUP(10) FTM_GROUP(11) FTM_GROUP(12) FTM_GROUP(13) FTM_GROUP(14) FTM_GROUP(15)
+      }
+    }
+  }
+#undef FTM_GROUP
 #define FTM_ROW(P)            \
   case P:                     \
     if (o >= el) return o;    \
@@ -223,9 +284,21 @@ __device__ __forceinline__ int walk_step1(U& u, const uint8_t* buf, int o, int e
   return o;
 }
 
-// Any other Mp: the phase is taken at run time.
-template <class U>
+// Any other Mp: the phase is taken at run time; rows go four at a time,
+// their loads first.
+template <class U, int G>
 __device__ __forceinline__ int walk_any(U& u, const uint8_t* buf, int o, int el, int Mp) {
+  for (; o + (G - 1) * Mp < el; o += G * Mp) {
+    uint4 a[G], b[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) load32raw(buf, o + k * Mp, a[k], b[k]);
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      uint32_t w[4];
+      extract16(a[k], b[k], o + k * Mp, w);
+      u.add_words(w);
+    }
+  }
   for (; o < el; o += Mp) u.add(buf, o);
   return o;
 }
@@ -361,6 +434,10 @@ struct UnitF32 {
   }
   template <int P>
   __device__ __forceinline__ void addp(const uint8_t* buf, int ob) { add(buf, ob); }
+  __device__ __forceinline__ void add_words(const uint32_t (&w)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] += __uint_as_float(w[i]);
+  }
   __device__ __forceinline__ void add2_aligned(const uint8_t* buf, int o, int o2) {
     const float4 a = *reinterpret_cast<const float4*>(buf + o);
     const float4 b = *reinterpret_cast<const float4*>(buf + o2);
@@ -541,9 +618,12 @@ __device__ __forceinline__ bool consume_share_walk(const uint8_t* smem, uint64_t
     for (int j = 0; j < J; ++j) {
       if (colb(j) >= Mb) continue;
       int e;
-      if (step == 0) e = walk_aligned(u[j], buf, o[j], el, Mb);
-      else if constexpr (kEB == 1) e = step == 1 ? walk_step1(u[j], buf, o[j], el, Mb) : walk_any(u[j], buf, o[j], el, Mb);
-      else e = walk_any(u[j], buf, o[j], el, Mb);
+      // rows in groups of G (loads first): four for one unit per lane, two
+      // for more (register pressure)
+      constexpr int G = J == 1 ? 4 : 2;
+      if (step == 0) e = walk_aligned<U, G>(u[j], buf, o[j], el, Mb);
+      else if constexpr (kEB == 1) e = step == 1 ? walk_step1<U, G>(u[j], buf, o[j], el, Mb) : walk_any<U, G>(u[j], buf, o[j], el, Mb);
+      else e = walk_any<U, G>(u[j], buf, o[j], el, Mb);
       // a last row that started within 16 bytes of the end continues in
       // the next stage (its first bytes there fall at negative offsets)
       o[j] = e - Mb > el - 16 ? e - Mb - el : e - el;
