@@ -263,7 +263,17 @@ TM_API tm_status tm_batch_run_host(tm_batch_t b, const void* const* x_host,
  * tm_dtype) receives the chosen stage bytes, 0 for types not in the batch.
  * Partial folds are overwritten: run the batch again before reading them. */
 #define TM_TUNE_FORCE 0x1u
+/* With TM_TUNE_GRID (batches created with TM_BATCH_PIPELINED only), the
+ * autotuner also times pipelined calls (tm_batch_run_pipelined into the
+ * batch's own result buffer, flushed) for splits of the SMs between the fold
+ * and the correlation: corr_ctas C from a fixed list of counts (16 to half
+ * the SM count), fold_ctas = SMs - C, and the unsplit launch; it keeps the
+ * fastest with tm_batch_set_grid (cached per process by the batch's query
+ * count, bytes and largest FFT length). tm_batch_get_grid reads the choice. */
+#define TM_TUNE_GRID 0x2u
 TM_API tm_status tm_batch_autotune(tm_batch_t b, tm_stream_t stream, uint32_t flags, int32_t* tiles);
+/* The launch geometry set by tm_batch_set_grid or the autotuner. */
+TM_API tm_status tm_batch_get_grid(tm_batch_t b, int32_t* fold_ctas, int32_t* corr_ctas);
 /* Record one tm_batch_run(b, out_dev) - the fold launches and the
  * correlation launches with the memsets before them - as a CUDA graph held
  * by the batch (captured on a private stream; nothing runs). Replaces an

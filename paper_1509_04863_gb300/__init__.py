@@ -81,6 +81,7 @@ _SIGS = {
                                     C.c_void_p]),
     "tm_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
     "tm_batch_set_grid": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "tm_batch_get_grid": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "tm_batch_run_pipelined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tm_batch_pipeline_flush": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tm_batch_graph_capture": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -286,6 +287,12 @@ class Batch:
         corr_ctas correlation CTAs at a time (0: one per query)."""
         _check(lib().tm_batch_set_grid(self._h, int(fold_ctas), int(corr_ctas)), "tm_batch_set_grid")
 
+    def get_grid(self):
+        """(fold_ctas, corr_ctas) set by set_grid or the autotuner (0: default)."""
+        f, c = C.c_int32(), C.c_int32()
+        _check(lib().tm_batch_get_grid(self._h, C.byref(f), C.byref(c)), "tm_batch_get_grid")
+        return f.value, c.value
+
     def run_pipelined(self, out, stream=None, fold_events=None):
         """tm_batch_run_pipelined: fold now, correlate the previous call's
         folds beside it (into the previous call's `out`). fold_events: an
@@ -306,10 +313,13 @@ class Batch:
     def correlate(self, out, stream=None):
         _check(lib().tm_batch_correlate(self._h, out.data_ptr(), _stream_ptr(stream)), "tm_batch_correlate")
 
-    def autotune(self, stream=None, force: bool = False) -> dict:
-        """tm_batch_autotune: pick the fold's stage ring per storage type; returns {dtype: stage bytes}."""
+    def autotune(self, stream=None, force: bool = False, grid: bool = False) -> dict:
+        """tm_batch_autotune: pick the fold's stage ring per storage type
+        (and, with grid=True on a pipelined batch, the split of the SMs
+        between fold and correlation); returns {dtype: stage bytes}."""
         tiles = (C.c_int32 * 4)()
-        _check(lib().tm_batch_autotune(self._h, _stream_ptr(stream), 1 if force else 0, tiles), "tm_batch_autotune")
+        flags = (1 if force else 0) | (2 if grid else 0)
+        _check(lib().tm_batch_autotune(self._h, _stream_ptr(stream), flags, tiles), "tm_batch_autotune")
         names = {v: k for k, v in DTYPE_CODES.items()}
         return {names[d]: tiles[d] for d in range(4) if tiles[d]}
 

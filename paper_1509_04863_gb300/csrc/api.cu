@@ -1029,6 +1029,66 @@ int ilog2(int64_t v) {
 
 }  // namespace
 
+namespace {
+
+std::map<std::tuple<int32_t, int64_t, int32_t>, std::pair<int32_t, int32_t>> g_tune_grid;
+
+// Pipelined calls per candidate split of the SMs; keeps the fastest.
+tm_status tune_grid(tm_batch_t b, cudaStream_t s, uint32_t flags, cudaEvent_t e0, cudaEvent_t e1) {
+  if (!(b->flags & TM_BATCH_PIPELINED)) return fail(TM_EINVAL, "TM_TUNE_GRID needs a TM_BATCH_PIPELINED batch");
+  if (b->pending) return fail(TM_EBUSY, "a pipelined run is pending (tm_batch_pipeline_flush first)");
+  const auto key = std::make_tuple(b->n, b->W, b->maxP);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_grid.find(key);
+    if (it != g_tune_grid.end() && !(flags & TM_TUNE_FORCE))
+      return tm_batch_set_grid(b, it->second.first, it->second.second);
+  }
+  int sms = 0;
+  TM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  std::vector<std::pair<int32_t, int32_t>> cand = {{0, 0}};
+  for (int c : {16, 20, 22, 24, 28, 32, sms / 5, sms / 4, sms / 3, sms / 2}) {
+    if (c < 1 || c >= sms || c > b->n) continue;
+    const std::pair<int32_t, int32_t> fc(sms - c, c);
+    if (std::find(cand.begin(), cand.end(), fc) == cand.end()) cand.push_back(fc);
+  }
+  float best = -1.f;
+  std::pair<int32_t, int32_t> pick(0, 0);
+  for (const auto& fc : cand) {
+    tm_status st = tm_batch_set_grid(b, fc.first, fc.second);
+    if (st != TM_OK) return st;
+    const int reps = 6;
+    for (int r = 0; r < 2 && st == TM_OK; ++r) st = tm_batch_run_pipelined(b, b->d_out, s, nullptr, nullptr);
+    if (st == TM_OK) st = tm_batch_pipeline_flush(b, s);
+    TM_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps && st == TM_OK; ++r) st = tm_batch_run_pipelined(b, b->d_out, s, nullptr, nullptr);
+    if (st == TM_OK) st = tm_batch_pipeline_flush(b, s);
+    if (st != TM_OK) return st;
+    TM_CUDA(cudaEventRecord(e1, s));
+    TM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    TM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (best < 0.f || ms < best) {
+      best = ms;
+      pick = fc;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_grid[key] = pick;
+  }
+  return tm_batch_set_grid(b, pick.first, pick.second);
+}
+
+}  // namespace
+
+tm_status tm_batch_get_grid(tm_batch_t b, int32_t* fold_ctas, int32_t* corr_ctas) {
+  if (!b) return fail(TM_EINVAL, "null batch");
+  if (fold_ctas) *fold_ctas = b->fold_cap;
+  if (corr_ctas) *corr_ctas = b->corr_ctas;
+  return TM_OK;
+}
+
 tm_status tm_batch_autotune(tm_batch_t b, tm_stream_t stream, uint32_t flags, int32_t* tiles) {
   if (!b) return fail(TM_EINVAL, "null batch");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1080,6 +1140,7 @@ tm_status tm_batch_autotune(tm_batch_t b, tm_stream_t stream, uint32_t flags, in
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = best_tile;
   }
+  if (st == TM_OK && (flags & TM_TUNE_GRID)) st = tune_grid(b, s, flags, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != TM_OK) return st;
