@@ -103,6 +103,23 @@ def profile_traffic(kernel_src: str, summary: str):
     return float(m_bytes.group(1))
 
 
+def profile_value(kernel_src: str, summary: str, key: str):
+    """A per-unit figure (`key: value`) from a committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, kernel_src)
+    if not os.path.exists(path) or not os.path.exists(src):
+        return None
+    import re
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha:\s*`?([0-9a-f]+)", text)
+    m_v = re.search(key + r":\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_v or m_sha.group(1) != sha:
+        return None
+    return float(m_v.group(1))
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -155,20 +172,37 @@ def gen_queries(rank: int):
 
 def run_kernels_only(args):
     """Small-workload driver for profiler captures: builds one batch of
-    --queries signals of 2^--log2n bytes and runs --steps full steps."""
+    --queries signals of 2^--log2n elements (--xdtype i8, bits or f32; f32
+    signals are N(0,1) with automatic moduli) and runs --steps full steps,
+    sequential or (--pipelined F,C) pipelined on F fold and C correlation
+    CTAs."""
     import torch
     import paper_1509_04863_gb300 as tm
-    qs = W.batch64(seed=100, n=args.queries, N=1 << args.log2n, K=args.K, flip_p=FLIP)
+    N = 1 << args.log2n
+    if args.xdtype == "f32":
+        qs = [W.planted_query(100 + i, N, args.K, "f32", t_sigma=0.3, mode="auto") for i in range(args.queries)]
+        mode = "auto"
+    else:
+        qs = W.batch64(seed=100, n=args.queries, N=N, K=args.K, flip_p=FLIP, xdtype=args.xdtype)
+        mode = "paper"
     specs = [dict(x=torch.from_numpy(q.x).cuda(), t=torch.from_numpy(q.t).cuda(), N=q.N, K=q.K,
-                  xdtype="i8", mode="paper") for q in qs]
-    b = tm.Batch(specs)
-    out = tm.result_buffer(len(qs))
-    for _ in range(args.warmup + args.steps):
-        b.run(out)
+                  xdtype=args.xdtype, mode=mode) for q in qs]
+    b = tm.Batch(specs, pipelined=bool(args.pipelined))
+    outs = [tm.result_buffer(len(qs)) for _ in range(2)]
+    if args.pipelined:
+        F, C = (int(v) for v in args.pipelined.split(","))
+        b.set_grid(F, C)
+        for i in range(args.warmup + args.steps):
+            b.run_pipelined(outs[i % 2])
+        b.flush()
+    else:
+        for _ in range(args.warmup + args.steps):
+            b.run(outs[0])
     torch.cuda.synchronize()
     assert b.device_error() == 0
     print(json.dumps({"kernels_only": True, "queries": args.queries, "log2n": args.log2n, "K": args.K,
-                      "steps": args.steps, "warmup": args.warmup}))
+                      "xdtype": args.xdtype, "pipelined": args.pipelined, "steps": args.steps,
+                      "warmup": args.warmup}))
     return 0
 
 
@@ -477,14 +511,26 @@ def run_native(args):
     bits_e2e_ok = tm.decode_results(ohb) == res
     bhb.close()
     bb.close()
+    # instruction roofline of the bit-sliced fold: warp instructions per
+    # element from the committed ncu capture, one warp instruction per SM
+    # sub-partition per clock as the peak
+    ipe = profile_value("paper_1509_04863_gb300/csrc/fold.cu", "fold_kernel_bits_batch64.md",
+                        "warp_instructions_per_element")
+    sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6 if isinstance(clk, dict) else 2070e6
+    issue_peak = sms * 4 * sm_hz
+    bits_fold = {"bound": "alu", "kernel": "fold_kernel<UnitBits,2>", "unit": "warp instructions/s",
+                 "achieved": None if ipe is None else ipe * QUERIES * N_SIG / (fold_b / 1e3),
+                 "peak": issue_peak, "frac": None if ipe is None else ipe * QUERIES * N_SIG / (fold_b / 1e3) / issue_peak,
+                 "warp_instructions_per_element": ipe,
+                 "input_GBps": bytes_b / (fold_b / 1e3) / 1e9, "hbm_frac": bytes_b / (fold_b / 1e3) / 1e9 / hbm_peak,
+                 "elements_per_s": QUERIES * N_SIG / (fold_b / 1e3),
+                 "note": "bit-sliced counters bound by integer issue (ncu: ALU pipe 65%, issue 62%, DRAM 25%); "
+                         "peak = SMs x 4 sub-partitions x SM clock, one warp instruction each per clock"}
     bits = {"what": "the same 64 signals bit-packed (LSB first, 1 = +1): 1/8 of the bytes, identical results",
             "value": world * QUERIES / (ms_b / 1e3), "unit": "queries/s", "ms_per_step": ms_b, "steps": Kb,
             "results_equal_int8": bits_same,
             "fold_ms": fold_b, "corr_ms": ms_b - fold_b,
-            "fold": {"bound": "alu", "kernel": "fold_kernel<UnitBits>", "input_GBps": bytes_b / (fold_b / 1e3) / 1e9,
-                     "elements_per_s": QUERIES * N_SIG / (fold_b / 1e3),
-                     "note": "bit-sliced vertical counters: 1/8 of the int8 bytes, limited by integer ALU "
-                             "work rather than HBM (no HBM roofline fraction)"},
+            "fold": bits_fold,
             "e2e": {"value": world * QUERIES * e2e_steps / e2e_b, "unit": "queries/s",
                     "h2d_bytes_per_step": bytes_b + QUERIES * K_T * 4, "d2h_bytes_per_step": QUERIES * tm.RESULT_BYTES,
                     "api": "tm_batch_run_host (pinned host buffers)", "matches_device_run": bits_e2e_ok}}
@@ -1278,6 +1324,9 @@ def main():
     ap.add_argument("--queries", type=int, default=64)
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--K", type=int, default=K_T)
+    ap.add_argument("--xdtype", default="i8", choices=["i8", "bits", "f32"], help="kernels-only: signal storage")
+    ap.add_argument("--pipelined", default="", help="kernels-only: F,C for pipelined steps on F fold and C "
+                                                    "correlation CTAs")
     ap.add_argument("--workload", default="batch64", choices=["batch64", "uneven", "serve", "sweep", "tables", "single", "foldscale"],
                     help="batch64 (default line), uneven (4096-query mix as one CUDA graph), "
                          "serve (Poisson arrivals through the continuous-batching server)")
