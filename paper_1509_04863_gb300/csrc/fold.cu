@@ -309,23 +309,30 @@ __device__ __forceinline__ int walk_any(U& u, const uint8_t* buf, int o, int el,
 }
 
 // ---------------------------------------------------------------- bit-packed +-1
+// A unit is one 32-bit word of a row: 32 columns, bit i = column i, 1 = +1.
+// Rows are added bit-sliced. A carry-save state (planes of weight 1, 2, 4)
+// takes eight rows at a time through a tree of seven 3-input full adders
+// (each a bitwise sum and majority); the tree's weight-8 output feeds a
+// vertical counter (planes of weight 8 .. 256). Single rows (the masked
+// first and last rows of a stage, leftovers) ripple through the same
+// planes. Before the vertical counter can overflow (63 weight-8 steps) all
+// planes are flushed into 16-bit lane counts. Output: count of +1 entries
+// per column.
 struct UnitBits {
   static constexpr int kE = 32, kBits = 1;
   static constexpr bool kWalk = false;
-  static constexpr int kPlanes = 5;       // vertical counter: up to 31 rows
-  uint32_t p[kPlanes];
-  uint32_t c8[8];                         // byte lanes: word k holds columns k, k+8, k+16, k+24
-  uint32_t c16[16];                       // 16-bit lanes: word 2k (cols k, k+16), 2k+1 (k+8, k+24)
-  int rows, flushes;
+  static constexpr int kV = 6;            // vertical counter planes, weights 8 .. 256
+  uint32_t ones, twos, fours;
+  uint32_t v[kV];
+  uint32_t c16[16];                       // 16-bit lanes: word k holds columns k (low) and k+16 (high)
+  int steps;                              // weight-8 steps into v since the last flush
   __device__ __forceinline__ void clear() {
+    ones = twos = fours = 0u;
 #pragma unroll
-    for (int i = 0; i < kPlanes; ++i) p[i] = 0u;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) c8[i] = 0u;
+    for (int i = 0; i < kV; ++i) v[i] = 0u;
 #pragma unroll
     for (int i = 0; i < 16; ++i) c16[i] = 0u;
-    rows = 0;
-    flushes = 0;
+    steps = 0;
   }
   static __device__ __forceinline__ int widen_every(int, int) { return 1 << 30; }   // planes flush themselves
   // 32 bits starting at bit o of the stage (o > -32; the word before the
@@ -335,80 +342,81 @@ struct UnitBits {
     const int q = o >> 5;
     return fsr(w[q], w[q + 1], uint32_t(o & 31));
   }
-  // add a value v (0/1 per column) of weight 1 to the planes
-  __device__ __forceinline__ void plane_add(uint32_t v) {
-#pragma unroll
-    for (int b = 0; b < kPlanes; ++b) {
-      const uint32_t c = p[b] & v;
-      p[b] ^= v;
-      v = c;
-    }
+  // full adder on bit planes: a + b + c = l + 2 h
+  static __device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
   }
-  // add s (weight 1) and c (weight 2): one full-adder step per plane
-  __device__ __forceinline__ void plane_add2(uint32_t s, uint32_t c) {
-    const uint32_t k0 = p[0] & s;
-    p[0] ^= s;
-    // plane 1 gets c + k0 (both weight 2)
-    uint32_t carry = (p[1] & c) | (p[1] & k0) | (c & k0);
-    p[1] ^= c ^ k0;
+  // all planes into the 16-bit lanes, weight by weight
+  __device__ __forceinline__ void flush() {
+    const uint32_t pl[3 + kV] = {ones, twos, fours, v[0], v[1], v[2], v[3], v[4], v[5]};
 #pragma unroll
-    for (int b = 2; b < kPlanes; ++b) {
-      const uint32_t nc = p[b] & carry;
-      p[b] ^= carry;
-      carry = nc;
+    for (int b = 0; b < 3 + kV; ++b) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) c16[k] += ((pl[b] >> k) & 0x00010001u) << b;
     }
+    ones = twos = fours = 0u;
+#pragma unroll
+    for (int i = 0; i < kV; ++i) v[i] = 0u;
+    steps = 0;
   }
-  __device__ __forceinline__ void flush_planes() {
+  // one weight-8 step: e (0/1 per column) into the vertical counter
+  __device__ __forceinline__ void step8(uint32_t e) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      uint32_t v = 0u;
-#pragma unroll
-      for (int b = 0; b < kPlanes; ++b) v |= ((p[b] >> k) & 0x01010101u) << b;
-      c8[k] += v;
+    for (int b = 0; b < kV; ++b) {
+      const uint32_t c = v[b] & e;
+      v[b] ^= e;
+      e = c;
     }
-#pragma unroll
-    for (int b = 0; b < kPlanes; ++b) p[b] = 0u;
-    rows = 0;
-    if (++flushes == 8) {   // 8 x 31 rows fit a byte lane
-      flushes = 0;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        c16[2 * k] += c8[k] & 0x00FF00FFu;
-        c16[2 * k + 1] += (c8[k] >> 8) & 0x00FF00FFu;
-        c8[k] = 0u;
-      }
-    }
+    if (++steps == 63) flush();
   }
-  __device__ __forceinline__ void add(const uint8_t* buf, int o) {
-    plane_add(load32(buf, o));
-    if (++rows >= 30) flush_planes();
+  // one row (0/1 per column, weight 1)
+  __device__ __forceinline__ void add1(uint32_t w) {
+    const uint32_t c1 = ones & w;
+    ones ^= w;
+    const uint32_t c2 = twos & c1;
+    twos ^= c1;
+    const uint32_t c4 = fours & c2;
+    fours ^= c2;
+    step8(c4);
   }
+  __device__ __forceinline__ void add(const uint8_t* buf, int o) { add1(load32(buf, o)); }
   __device__ __forceinline__ void add2(const uint8_t* buf, int o, int o2) {
     const uint32_t a = load32(buf, o), b = load32(buf, o2);
-    plane_add2(a ^ b, a & b);
-    rows += 2;
-    if (rows >= 30) flush_planes();
+    add1(a);
+    add1(b);
+  }
+  // eight rows o + i Mp, i < 8, all inside the stage: loads first, then the
+  // adder tree
+  __device__ __forceinline__ void add8(const uint8_t* buf, int o, int Mp) {
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = load32(buf, o + i * Mp);
+    uint32_t twosA, twosB, foursA, foursB, e;
+    csa(twosA, ones, ones, w[0], w[1]);
+    csa(twosB, ones, ones, w[2], w[3]);
+    csa(foursA, twos, twos, twosA, twosB);
+    csa(twosA, ones, ones, w[4], w[5]);
+    csa(twosB, ones, ones, w[6], w[7]);
+    csa(foursB, twos, twos, twosA, twosB);
+    csa(e, fours, fours, foursA, foursB);
+    step8(e);
   }
   __device__ __forceinline__ void add_masked(const uint8_t* buf, int o, int len) {
-    uint32_t v = load32(buf, o);
+    uint32_t w = load32(buf, o);
     // keep bits i with 0 <= o + i < len
-    if (o < 0) v &= 0xFFFFFFFFu << (-o);
-    if (len - o < 32) v &= (len - o) <= 0 ? 0u : (0xFFFFFFFFu >> (32 - (len - o)));
-    plane_add(v);
-    if (++rows >= 30) flush_planes();
+    if (o < 0) w &= 0xFFFFFFFFu << (-o);
+    if (len - o < 32) w &= (len - o) <= 0 ? 0u : (0xFFFFFFFFu >> (32 - (len - o)));
+    add1(w);
   }
   __device__ __forceinline__ void widen() {}
   __device__ __forceinline__ void write(int32_t* dst, int col, int width) {
-    flush_planes();
+    flush();
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t e0 = c16[2 * k] + (c8[k] & 0x00FF00FFu);
-      const uint32_t e1 = c16[2 * k + 1] + ((c8[k] >> 8) & 0x00FF00FFu);
-      const int cols[4] = {k, k + 16, k + 8, k + 24};
-      const int32_t v[4] = {int32_t(e0 & 0xFFFFu), int32_t(e0 >> 16), int32_t(e1 & 0xFFFFu), int32_t(e1 >> 16)};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (cols[i] < width) dst[col + cols[i]] = v[i];
+    for (int k = 0; k < 16; ++k) {
+      if (k < width) dst[col + k] = int32_t(c16[k] & 0xFFFFu);
+      if (k + 16 < width) dst[col + k + 16] = int32_t(c16[k] >> 16);
     }
   }
 };
@@ -561,6 +569,9 @@ __device__ __forceinline__ bool consume_share(const uint8_t* smem, uint64_t* ful
         // narrow last unit reads past its width into the next row or the
         // slack, in columns that are never written)
         int l = l0 + 1;
+        if constexpr (U::kBits == 1) {
+          for (; l + 7 < l1; l += 8) u[j].add8(buf, l * Mp + cj - es, Mp);
+        }
         for (; l + 1 < l1; l += 2) {
           const int o = l * Mp + cj - es;
           u[j].add2(buf, o, o + Mp);
