@@ -329,7 +329,9 @@ TM_API tm_status tm_batch_corr(tm_batch_t b, int32_t i, float** r_dev);
 TM_API tm_status tm_batch_stats(tm_batch_t b, int32_t* launches_per_run, int32_t* fold_ctas,
                          int64_t* workspace_bytes);
 /* Device error word of the last run (0 = none; bit 0: a bounded device-side
- * wait ran out). Synchronises the stream. */
+ * wait ran out). Synchronises the stream. Pipelined runs reset each error
+ * word once the correlation that reads it has flagged its results
+ * (TM_RF_DEVICE_ERROR), so for them the results carry the report. */
 TM_API tm_status tm_batch_device_error(tm_batch_t b, tm_stream_t stream, int32_t* err);
 TM_API tm_status tm_batch_destroy(tm_batch_t b);
 

@@ -600,10 +600,10 @@ void fold_args_shares(FoldArgs& a, const tm_batch_s::FoldGroup& g) {
   for (size_t c = 0; c < g.cb.size(); ++c) a.cb[c] = g.cb[c];
 }
 
-tm_status batch_fold(tm_batch_t b, cudaStream_t s, int parity) {
+tm_status batch_fold(tm_batch_t b, cudaStream_t s, int parity, bool clear_err) {
   int32_t* partial = parity ? b->d_partial2 : b->d_partial;
   int32_t* err = b->d_err + parity;
-  TM_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+  if (clear_err) TM_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
   if (!b->lq.empty() && b->aux) {
     // the long-FFT queries' template spectra need only t: they run on a
     // side stream while the fold streams x (joined in batch_correlate)
@@ -972,13 +972,20 @@ tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out, tm_stream_t strea
   // the correlation stream starts after the caller's earlier work
   TM_CUDA(cudaEventRecord(b->ev_pfork, s));
   TM_CUDA(cudaStreamWaitEvent(b->cstream, b->ev_pfork, 0));
+  // the fold's error word was reset on the correlation stream after its
+  // last reader (the previous call's); the first call after a flush or a
+  // plain run resets it here
+  const bool clear_here = !b->pending;
+  if (clear_here) TM_CUDA(cudaMemsetAsync(b->d_err + par, 0, sizeof(int32_t), s));
   if (fold_begin) TM_CUDA(cudaEventRecord(reinterpret_cast<cudaEvent_t>(fold_begin), s));
-  tm_status st = batch_fold(b, s, par);
+  tm_status st = batch_fold(b, s, par, false);
   if (st != TM_OK) return st;
   if (fold_end) TM_CUDA(cudaEventRecord(reinterpret_cast<cudaEvent_t>(fold_end), s));
   if (b->pending) {
     st = batch_correlate(b, b->pending_out, b->cstream, par ^ 1);
     if (st != TM_OK) return st;
+    // the next call folds into parity par ^ 1: its error word is free now
+    TM_CUDA(cudaMemsetAsync(b->d_err + (par ^ 1), 0, sizeof(int32_t), b->cstream));
   }
   TM_CUDA(cudaEventRecord(b->ev_pjoin, b->cstream));
   TM_CUDA(cudaStreamWaitEvent(s, b->ev_pjoin, 0));
@@ -991,8 +998,11 @@ tm_status tm_batch_run_pipelined(tm_batch_t b, tm_result* out, tm_stream_t strea
 tm_status tm_batch_pipeline_flush(tm_batch_t b, tm_stream_t stream) {
   if (!b) return fail(TM_EINVAL, "null batch");
   if (!b->pending) return TM_OK;
-  tm_status st = batch_correlate(b, b->pending_out, reinterpret_cast<cudaStream_t>(stream), b->pp ^ 1);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  tm_status st = batch_correlate(b, b->pending_out, s, b->pp ^ 1);
   if (st != TM_OK) return st;
+  // after its last reader: the error word is clean for the next fold of this parity
+  TM_CUDA(cudaMemsetAsync(b->d_err + (b->pp ^ 1), 0, sizeof(int32_t), s));
   b->pending = false;
   b->pending_out = nullptr;
   return TM_OK;

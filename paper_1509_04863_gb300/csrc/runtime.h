@@ -146,7 +146,9 @@ void batch_free(tm_batch_s* b);
 void bind_pointers(tm_batch_s* b);
 tm_status upload_descriptors(tm_batch_s* b, cudaStream_t s);
 // parity: which partial buffer and error word (pipelined batches alternate)
-tm_status batch_fold(tm_batch_s* b, cudaStream_t s, int parity = 0);
+// clear_err: reset the parity's error word on `s` first (pipelined runs
+// reset it on the correlation stream instead, after its last reader)
+tm_status batch_fold(tm_batch_s* b, cudaStream_t s, int parity = 0, bool clear_err = true);
 tm_status batch_correlate(tm_batch_s* b, tm_result* out, cudaStream_t s, int parity = 0);
 
 }  // namespace ftm
