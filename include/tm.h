@@ -403,6 +403,17 @@ TM_API tm_status tm_serve_register_signal(tm_server_t s, const void* x, int64_t 
  * the request alone exceeds the arena. mode/M1/M2/plan_flags as tm_plan_desc. */
 TM_API tm_status tm_serve_submit(tm_server_t s, int32_t sig_id, const float* t_host, int32_t K, int32_t mode,
                                  int32_t M1, int32_t M2, uint32_t plan_flags, uint64_t tag);
+/* n requests in one call (for clients that submit at high rates: one lock
+ * and one wake-up for all of them): request i is (sig_ids[i], t_host[i],
+ * K[i] floats, tags[i]) with the common mode (TM_MODE_AUTO or
+ * TM_MODE_PAPER) and plan_flags. Requests are queued in order while the
+ * queue has room; returns how many were queued (0..n; fewer than n when the
+ * queue filled: submit the rest later), or -tm_status when request 0 is
+ * invalid (a later invalid request stops the call after the valid prefix,
+ * which is queued and counted). Templates are copied before the call
+ * returns. */
+TM_API int32_t tm_serve_submit_many(tm_server_t s, int32_t n, const int32_t* sig_ids, const float* const* t_host,
+                                    const int32_t* K, int32_t mode, uint32_t plan_flags, const uint64_t* tags);
 /* Up to max finished results; waits up to timeout_us for the first one.
  * Returns the number written (0 on timeout) or -tm_status on error. */
 TM_API int32_t tm_serve_poll(tm_server_t s, tm_result_tagged* out, int32_t max, int64_t timeout_us);

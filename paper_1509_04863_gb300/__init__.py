@@ -446,6 +446,8 @@ _SIGS.update({
     "tm_serve_create": (C.c_int, [C.POINTER(tm_serve_cfg), C.POINTER(C.c_void_p)]),
     "tm_serve_register_signal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_uint32,
                                            C.POINTER(C.c_int32)]),
+    "tm_serve_submit_many": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                         C.c_uint32, C.c_void_p]),
     "tm_serve_submit": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                   C.c_uint32, C.c_uint64]),
     "tm_serve_poll": (C.c_int32, [C.c_void_p, C.POINTER(tm_result_tagged), C.c_int32, C.c_int64]),
@@ -490,6 +492,23 @@ class Server:
         if st not in (TM_OK, TM_EAGAIN):
             raise TMError(st, "tm_serve_submit")
         return st
+
+    def submit_many(self, sig_ids, ts, tags, mode: str = "paper", allow_ambig: bool = False) -> int:
+        """tm_serve_submit_many: queue len(sig_ids) requests in one call
+        (ts: float32 numpy arrays, kept alive by the caller until the call
+        returns); returns how many were queued."""
+        import numpy as np
+        n = len(sig_ids)
+        ids = (C.c_int32 * n)(*[int(v) for v in sig_ids])
+        tps = (C.c_void_p * n)(*[t.ctypes.data for t in ts])
+        ks = (C.c_int32 * n)(*[int(t.shape[0]) for t in ts])
+        tg = (C.c_uint64 * n)(*[int(v) for v in tags])
+        for t in ts:
+            assert t.dtype == np.float32 and t.flags["C_CONTIGUOUS"]
+        k = lib().tm_serve_submit_many(self._h, n, ids, tps, ks, MODE_CODES[mode], _plan_flags(allow_ambig), tg)
+        if k < 0:
+            raise TMError(-k, "tm_serve_submit_many")
+        return k
 
     def poll(self, max_results: int = 1024, timeout_us: int = 0):
         buf = (tm_result_tagged * max_results)()

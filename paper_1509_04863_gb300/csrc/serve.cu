@@ -546,11 +546,13 @@ tm_status tm_serve_register_signal(tm_server_t sv, const void* x, int64_t N, int
   return TM_OK;
 }
 
-tm_status tm_serve_submit(tm_server_t sv, int32_t sig_id, const float* t_host, int32_t K, int32_t mode, int32_t M1,
-                          int32_t M2, uint32_t plan_flags, uint64_t tag) {
-  if (!sv || !t_host) return fail(TM_EINVAL, "null argument");
+namespace {
+
+// A request record: plan, query shape, a copy of the template.
+tm_status build_request(tm_server_t sv, int32_t sig_id, const float* t_host, int32_t K, int32_t mode, int32_t M1,
+                        int32_t M2, uint32_t plan_flags, uint64_t tag, Req& r) {
+  if (!t_host) return fail(TM_EINVAL, "null template");
   if (K < 1) return fail(TM_EINVAL, "empty template");
-  Req r;
   r.tag = tag;
   r.sig = sig_id;
   Signal sg;
@@ -572,17 +574,52 @@ tm_status tm_serve_submit(tm_server_t sv, int32_t sig_id, const float* t_host, i
   r.q.flags = plan_flags;
   r.t.assign(t_host, t_host + K);
   r.t_submit = now_us();
+  return TM_OK;
+}
+
+// Queues reqs[0..n) in order while the queue has room; returns how many.
+int32_t enqueue_requests(tm_server_t sv, std::vector<Req>& reqs, int32_t n) {
+  int32_t k = 0;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
-    if (int64_t(sv->pending.size()) >= sv->cfg.queue_capacity) return fail(TM_EAGAIN, "queue full");
-    sv->pending.push_back(std::move(r));
+    while (k < n && int64_t(sv->pending.size()) < sv->cfg.queue_capacity) sv->pending.push_back(std::move(reqs[k++]));
   }
-  {
-    std::lock_guard<std::mutex> lk(sv->cmu);
-    ++sv->submitted;
+  if (k > 0) {
+    {
+      std::lock_guard<std::mutex> lk(sv->cmu);
+      sv->submitted += k;
+    }
+    sv->cv.notify_one();
   }
-  sv->cv.notify_one();
+  return k;
+}
+
+}  // namespace
+
+tm_status tm_serve_submit(tm_server_t sv, int32_t sig_id, const float* t_host, int32_t K, int32_t mode, int32_t M1,
+                          int32_t M2, uint32_t plan_flags, uint64_t tag) {
+  if (!sv || !t_host) return fail(TM_EINVAL, "null argument");
+  std::vector<Req> r(1);
+  tm_status st = build_request(sv, sig_id, t_host, K, mode, M1, M2, plan_flags, tag, r[0]);
+  if (st != TM_OK) return st;
+  if (enqueue_requests(sv, r, 1) == 0) return fail(TM_EAGAIN, "queue full");
   return TM_OK;
+}
+
+int32_t tm_serve_submit_many(tm_server_t sv, int32_t n, const int32_t* sig_ids, const float* const* t_host,
+                             const int32_t* K, int32_t mode, uint32_t plan_flags, const uint64_t* tags) {
+  if (!sv || n < 0 || (n > 0 && (!sig_ids || !t_host || !K || !tags)))
+    return -int32_t(fail(TM_EINVAL, "null argument"));
+  std::vector<Req> reqs(size_t(n > 0 ? n : 0));
+  for (int32_t i = 0; i < n; ++i) {
+    const tm_status st = build_request(sv, sig_ids[i], t_host[i], K[i], mode, 0, 0, plan_flags, tags[i], reqs[i]);
+    if (st != TM_OK) {
+      // the valid prefix still goes in; the caller learns where it stopped
+      const int32_t k = enqueue_requests(sv, reqs, i);
+      return k > 0 ? k : -int32_t(st);
+    }
+  }
+  return enqueue_requests(sv, reqs, n);
 }
 
 int32_t tm_serve_poll(tm_server_t sv, tm_result_tagged* out, int32_t max, int64_t timeout_us) {

@@ -230,3 +230,33 @@ def test_long_fft_requests(tm):
         if k < 2:   # K^2 / ln K well above N: the planted shift comes back
             assert r["shift"] == q.k_star
     srv.close()
+
+
+def test_submit_many(tm):
+    """tm_serve_submit_many queues a burst in one call; every result equals
+    the oracle's, and an unknown signal id stops the burst after the valid
+    prefix."""
+    srv = tm.Server(n_streams=2, max_batch=64, arena_bytes=1 << 28)
+    base = [W.planted_query(8100 + k, (1 << 19) + 11 * k, 512, dt, mode="auto")
+            for k, dt in enumerate(["i8", "f32", "bits"])]
+    ids = [srv.register_signal(q.x, q.N, q.xdtype) for q in base]
+    rng = np.random.default_rng(21)
+    qs, sig, ts = [], [], []
+    for i in range(30):
+        k = i % 3
+        K = int(rng.choice([300, 512, 700]))
+        t = W.flip_entries(rng, W.cyclic_window(_values(base[k]), int(rng.integers(0, base[k].N)), K), 0.03)
+        qs.append(W.Query(x=base[k].x, xdtype=base[k].xdtype, N=base[k].N, K=K, t=t, k_star=0, mode="auto"))
+        sig.append(ids[k])
+        ts.append(np.ascontiguousarray(t, dtype=np.float32))
+    assert srv.submit_many(sig, ts, list(range(30)), mode="auto") == 30
+    got = _collect(srv, 30)
+    for i, q in enumerate(qs):
+        assert got[i]["req_status"] == tm.TM_OK
+        check_result(q, got[i], O.match_query(q))
+    assert srv.submit_many([ids[0], 99, ids[1]], ts[:3], [100, 101, 102], mode="auto") == 1
+    got = _collect(srv, 1)
+    assert got[100]["req_status"] == tm.TM_OK
+    with pytest.raises(tm.TMError):
+        srv.submit_many([99], ts[:1], [200], mode="auto")
+    srv.close()

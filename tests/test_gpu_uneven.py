@@ -148,3 +148,28 @@ def test_pipelined_and_other_grids_equal_plain_run(tm, uneven):
         assert tm.decode_results(plain) == want, (F, C)
     assert b.device_error() == 0
     b.close()
+
+
+def test_full_range_sample_vs_oracle(tm):
+    """Sixteen queries of the uneven mix over its whole length range (N up
+    to 2^24, the range the 4096-query benchmark draws on the device), drawn
+    on the host and checked against the oracle in one batch."""
+    qs = W.uneven(seed=6100, n=16, logN=(20.0, 24.0))
+    specs = [dict(x=torch.from_numpy(q.x).cuda(), t=torch.from_numpy(q.t).cuda(), N=q.N, K=q.K,
+                  xdtype=q.xdtype, mode=q.mode) for q in qs]
+    b = tm.Batch(specs, keep_corr=True)
+    out = tm.result_buffer(len(qs))
+    b.run(out)
+    torch.cuda.synchronize()
+    assert b.device_error() == 0
+    res = tm.decode_results(out)
+    assert max(q.N for q in qs) > (1 << 23)
+    exact = n_real = 0
+    for i, q in enumerate(qs):
+        ref = O.match_query(q, corr="fft")
+        if q.xdtype == "i8":
+            check_int(b, i, q, res[i], ref)
+        else:
+            n_real += 1
+            exact += check_real(b, i, q, res[i], ref)
+    assert exact >= n_real - 1   # near-ties are rare
