@@ -901,13 +901,27 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
           float yk[kB];
 #pragma unroll
           for (int b = 0; b < kB; ++b) yk[b] = 0.f;
-          for (int sl = 0; sl < Q.nslots; ++sl) {
-            const float* ps = pf + int64_t(sl) * Q.stride;
-            for (int r = 0; r < Rr; ++r) {
+          // the terms (slot sl, replica r) in the order t = sl Rr + r,
+          // loaded four at a time before they are added in that order
+          const int nsr = Q.nslots * Rr;
+          int sl = 0, r = 0;
+          for (int t0 = 0; t0 < nsr; t0 += 4) {
+            float v[4][kB];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float* ps = pf + int64_t(sl) * Q.stride + r * M;
 #pragma unroll
               for (int b = 0; b < kB; ++b) {
                 const int k = k0 + b * kCorrThreads;
-                if (k < M) yk[b] += __ldg(&ps[k + r * M]);
+                v[u][b] = (t0 + u < nsr && k < M) ? __ldg(&ps[k]) : 0.f;
+              }
+              if (++r == Rr) { r = 0; ++sl; }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (t0 + u < nsr) {
+#pragma unroll
+                for (int b = 0; b < kB; ++b) yk[b] += v[u][b];
               }
             }
           }
