@@ -366,7 +366,8 @@ __device__ __forceinline__ void prefetch_elems(const void* x, int dtype, int64_t
 }
 
 // Exact sum_{i<K} t_i * v(i) over one warp: integer terms in int32 when
-// `small` guarantees no partial sum reaches 2^31, else int64; reals in fp64.
+// `small` guarantees no partial sum reaches 2^31, else int64; reals in
+// double-float pairs (DF), the lanes' pairs added in fp64.
 template <class F>
 __device__ __forceinline__ double warp_dot(const float* __restrict__ t, int K, bool integral, bool small, F v) {
   const int lane = threadIdx.x & 31;
@@ -386,9 +387,10 @@ __device__ __forceinline__ double warp_dot(const float* __restrict__ t, int K, b
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return double(acc);
   }
-  double acc = 0.0;
+  DF df;
 #pragma unroll 4
-  for (int i = lane; i < K; i += 32) acc = fma(double(t[i]), double(v(i)), acc);
+  for (int i = lane; i < K; i += 32) df.add_prod(t[i], float(v(i)));
+  double acc = df.value();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
@@ -532,7 +534,7 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
 #pragma unroll
       for (int b = 0; b < 4; ++b) v[b] = double(acc[b]);
     } else {
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      DF df[4];
       for (int i0 = tid; i0 < K; i0 += kU * kCorrThreads) {
         float tv[kU], yw[kU][4];
 #pragma unroll
@@ -545,8 +547,11 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
 #pragma unroll
         for (int u = 0; u < kU; ++u)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[b] = fma(double(tv[u]), double(yw[u][b]), acc[b]);
+          for (int b = 0; b < 4; ++b) df[b].add_prod(tv[u], yw[u][b]);
       }
+      double acc[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[b] = df[b].value();
       block_sum4(acc, redd4);
 #pragma unroll
       for (int b = 0; b < 4; ++b) v[b] = acc[b];
@@ -623,13 +628,13 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
       }
       best_v = double(block_sum(acc, redl));
     } else {
-      double acc = 0.0;
+      DF df;
       for (int i = tid; i < K; i += kCorrThreads) {
         int64_t n = mm + i;
         if (n >= N) n -= N;
-        acc = fma(double(t[i]), double(sig.val(n)), acc);
+        df.add_prod(t[i], sig.val(n));
       }
-      best_v = block_sum(acc, redd);
+      best_v = block_sum(df.value(), redd);
     }
     best_m = mm;
   } else if (ncs > 1) {

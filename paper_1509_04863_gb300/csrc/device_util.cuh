@@ -62,6 +62,25 @@ __device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, ui
   return true;
 }
 
+// Double-float accumulation on the FP32 pipes (GB300 has few FP64 units):
+// a times b is exactly p + e with p = a b rounded and e = fma(a, b, -p); p
+// goes into the running pair (hi, lo) through an error-free two-sum
+// (Knuth), e and the sum's error into lo. With n terms the pair's error
+// stays below about n 2^-47 sum |a_i b_i|, far below what fp32 folds carry.
+struct DF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += e + pe;
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return mbar_wait_for(bar, parity, kWaitTimeoutNs);
 }

@@ -35,6 +35,7 @@
 #include <cmath>
 
 #include "crt.h"
+#include "device_util.cuh"
 #include "tm_internal.h"
 
 namespace ftm {
@@ -688,14 +689,15 @@ __device__ __forceinline__ void chunk_range(int K, int nch, int h, int& i0, int&
 }
 
 // Exact partial dot sum_{i0<=i<i1} t_i v(i) over the block: int64 for
-// integer data (t integral), else fp64 in a fixed order. Thread 0 gets it.
+// integer data (t integral), else double-float pairs (DF) in a fixed order,
+// added across the block in fp64. Thread 0 gets it.
 // The loads of eight terms per thread are in flight before any is used.
 template <class F>
 __device__ __forceinline__ long long block_dot(const float* t, int i0, int i1, bool exact, F v, double* rd,
                                                long long* rl) {
   constexpr int U = 8;
   long long ai = 0;
-  double ad = 0.0;
+  DF ad;
   for (int i = i0 + threadIdx.x; i < i1; i += U * kLT) {
     float tv[U], xv[U];
 #pragma unroll
@@ -709,11 +711,11 @@ __device__ __forceinline__ long long block_dot(const float* t, int i0, int i1, b
       for (int u = 0; u < U; ++u) ai += (long long)__float2int_rn(tv[u]) * (long long)__float2int_rn(xv[u]);
     } else {
 #pragma unroll
-      for (int u = 0; u < U; ++u) ad = fma(double(tv[u]), double(xv[u]), ad);
+      for (int u = 0; u < U; ++u) ad.add_prod(tv[u], xv[u]);
     }
   }
   if (exact) return block_red(ai, rl, OpAdd());
-  return __double_as_longlong(block_red(ad, rd, OpAdd()));
+  return __double_as_longlong(block_red(ad.value(), rd, OpAdd()));
 }
 
 // Chunks per listed item: enough items for two waves of the launch's CTAs
@@ -733,9 +735,9 @@ __device__ __forceinline__ double warp_dot(const float* t, int K, bool exact, F 
     for (int i = lane; i < K; i += 32) a += (long long)__float2int_rn(__ldg(&t[i])) * (long long)v(i);
     return double(warp_red(a, OpAdd()));
   }
-  double a = 0.0;
-  for (int i = lane; i < K; i += 32) a = fma(double(__ldg(&t[i])), double(v(i)), a);
-  return warp_red(a, OpAdd());
+  DF a;
+  for (int i = lane; i < K; i += 32) a.add_prod(__ldg(&t[i]), float(v(i)));
+  return warp_red(a.value(), OpAdd());
 }
 
 __device__ __forceinline__ float yval(const LQ& q, int j, int64_t k) {
