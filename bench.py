@@ -671,6 +671,19 @@ def run_uneven(args):
     assert b.device_error() == 0
     res = tm.decode_results(out)
     success = sum(r["shift"] == q["k_star"] for r, q in zip(res, qs)) / n
+    # the device-drawn inputs against the oracle: queries of N <= 2^21 (so
+    # the oracle finishes in seconds), every 32nd of them, copied to the host
+    from oracle import ftm as O
+    small = [i for i in range(n) if qs[i]["N"] <= (1 << 21)][::32]
+    agree = {"i8": [0, 0], "f32": [0, 0]}
+    for i in small:
+        g = qs[i]
+        hq = W.Query(x=g["x"].cpu().numpy(), xdtype=g["xdtype"], N=g["N"], K=g["K"], t=g["t"].cpu().numpy(),
+                     k_star=g["k_star"], mode="auto")
+        ref = O.match_query(hq, corr="fft")
+        a = agree[g["xdtype"]]
+        a[0] += int((res[i]["shift"], res[i]["m1"], res[i]["m2"]) == (ref["shift"], ref["m1"], ref["m2"]))
+        a[1] += 1
     K = args.steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(torch.cuda.current_device())
@@ -745,6 +758,11 @@ def run_uneven(args):
                      "fold_ms": fold_ms, "what": "the fold launches on every SM, timed alone"},
         "gpu_launches": K * (pipe_launches if use_pipe else st["launches_per_run"]), "fold_ctas": st["fold_ctas"],
         "clocks": clk, "success_rate": success, "generation_s": gen_s,
+        "oracle_agreement": {"int8_equal_shift_and_picks": "{}/{}".format(*agree["i8"]),
+                             "fp32_equal_shift_and_picks": "{}/{}".format(*agree["f32"]),
+                             "sample": "every 32nd query of N <= 2^21 of the device-drawn batch, copied to the "
+                                       "host, oracle in fp64 (FFT route); real signals may differ at near-ties "
+                                       "of their noise-level maxima (the tests' near-tie rule)"},
     }
     print(json.dumps(line))
     return 0
