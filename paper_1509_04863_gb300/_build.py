@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 BUILD_DIR = os.path.join(OUT_DIR, "obj")
 LIB = os.path.join(OUT_DIR, "libtm.so")
 
-SOURCES = ["api.cu", "serve.cu", "fold.cu", "fold_direct.cu", "fft_large.cu", "correlate.cu", "slice.cu"]
+SOURCES = ["api.cu", "serve.cu", "fold.cu", "fold_direct.cu", "fft_large.cu", "correlate.cu", "slice.cu", "slot_sum.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE, "-I" + CSRC]

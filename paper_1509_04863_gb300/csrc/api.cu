@@ -230,7 +230,7 @@ void batch_free(tm_batch_t b) {
   if (b->ev_pjoin) cudaEventDestroy(b->ev_pjoin);
   if (b->owns_memory) {
     cudaFree(b->d_partial2);
-    cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_lq); cudaFree(b->d_order); cudaFree(b->d_partial);
+    cudaFree(b->d_fq); cudaFree(b->d_cq); cudaFree(b->d_lq); cudaFree(b->d_ssum); cudaFree(b->d_order); cudaFree(b->d_partial);
     cudaFree(b->d_y); cudaFree(b->d_spec); cudaFree(b->d_r); cudaFree(b->d_err); cudaFree(b->d_out);
     cudaFree(b->d_x); cudaFree(b->d_t);
     if (b->h_stage) cudaFreeHost(b->h_stage);
@@ -271,14 +271,17 @@ void bind_pointers(tm_batch_t b) {
 tm_status upload_descriptors(tm_batch_t b, cudaStream_t s) {
   const size_t nf = b->fq.size() * sizeof(FoldQ), nc = b->cq.size() * sizeof(CorrQ);
   const size_t nl = b->lq.size() * sizeof(LQ);
+  const size_t nj = b->ssum.size() * sizeof(SlotSumJob);
   TM_CUDA(cudaEventSynchronize(b->ev_stage));
   char* h = static_cast<char*>(b->h_stage);
   std::memcpy(h, b->fq.data(), nf);
   std::memcpy(h + nf, b->cq.data(), nc);
   if (nl > 0) std::memcpy(h + nf + nc, b->lq.data(), nl);
+  if (nj > 0) std::memcpy(h + nf + nc + nl, b->ssum.data(), nj);
   TM_CUDA(cudaMemcpyAsync(b->d_fq, h, nf, cudaMemcpyHostToDevice, s));
   TM_CUDA(cudaMemcpyAsync(b->d_cq, h + nf, nc, cudaMemcpyHostToDevice, s));
   if (nl > 0) TM_CUDA(cudaMemcpyAsync(b->d_lq, h + nf + nc, nl, cudaMemcpyHostToDevice, s));
+  if (nj > 0) TM_CUDA(cudaMemcpyAsync(b->d_ssum, h + nf + nc + nl, nj, cudaMemcpyHostToDevice, s));
   TM_CUDA(cudaEventRecord(b->ev_stage, s));
   return TM_OK;
 }
@@ -332,6 +335,9 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
   b->drows.assign(n, 0);
   b->dpitch.assign(n, 0);
   b->dpart.assign(n, 0);
+  b->ssum.clear();
+  b->ssum_of.assign(n, -1);
+  b->ssum_cols = 0;
   int64_t part = 0;
   for (int32_t dt = TM_I8_PM1; dt <= TM_F32; ++dt) {
     tm_batch_s::FoldGroup gr;
@@ -417,6 +423,15 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
                              : share_of(f.goff + f.nbytes - 1) - f.first_cta + 1;
       f.part = part;
       part += int64_t(f.nslots) * f.stride;
+      if (f.nslots >= kSlotSumMin) {
+        // many rows: summed into a row of their own ahead of the correlation
+        SlotSumJob j;
+        j.src = f.part; j.dst = part; j.nslots = f.nslots; j.cols = f.stride; j.real = real ? 1 : 0;
+        b->ssum_of[k] = int32_t(b->ssum.size());
+        b->ssum.push_back(j);
+        b->ssum_cols = std::max(b->ssum_cols, f.stride);
+        part += f.stride;
+      }
     }
     b->W += W;
     b->nctas = std::max(b->nctas, gr.nctas);
@@ -461,6 +476,10 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
     c.thm2 = (p.flags & TM_THM2_SAMPLING) ? 1 : 0;
     c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
     c.nslots = f.nslots; c.stride = f.stride; c.part = f.part;
+    if (b->ssum_of[b->fold_of[i]] >= 0) {   // the slot sums' row
+      c.nslots = 1;
+      c.part = b->ssum[b->ssum_of[b->fold_of[i]]].dst;
+    }
     c.y_off = yo; yo += int64_t(p.nmod) * p.P;
     const bool large = b->is_large[i];
     const bool blocked = p.P > kPMax && !large;   // correlation in blocks (overlap-save), r kept in global memory
@@ -529,6 +548,7 @@ tm_status batch_alloc(tm_batch_s* b) {
   bool ok = alloc((void**)&b->d_fq, n * sizeof(FoldQ)) == cudaSuccess &&
             alloc((void**)&b->d_cq, n * sizeof(CorrQ)) == cudaSuccess &&
             alloc((void**)&b->d_lq, std::max<size_t>(b->lq.size(), 1) * sizeof(LQ)) == cudaSuccess &&
+            alloc((void**)&b->d_ssum, n * sizeof(SlotSumJob)) == cudaSuccess &&
             alloc((void**)&b->d_order, 2 * n * sizeof(int32_t)) == cudaSuccess &&
             alloc((void**)&b->d_partial, b->part_elems * sizeof(int32_t)) == cudaSuccess &&
             alloc(&b->d_y, b->y_elems * sizeof(int32_t)) == cudaSuccess &&
@@ -552,7 +572,7 @@ tm_status batch_alloc(tm_batch_s* b) {
     }
     ok = alloc((void**)&b->d_x, xb) == cudaSuccess && alloc((void**)&b->d_t, tb * sizeof(float)) == cudaSuccess;
   }
-  b->stage_bytes = n * (sizeof(FoldQ) + sizeof(CorrQ) + sizeof(LQ));
+  b->stage_bytes = n * (sizeof(FoldQ) + sizeof(CorrQ) + sizeof(LQ) + sizeof(SlotSumJob));
   if (ok) ok = cudaMallocHost(&b->h_stage, b->stage_bytes) == cudaSuccess;
   if (ok) ok = cudaEventCreateWithFlags(&b->ev_stage, cudaEventDisableTiming) == cudaSuccess;
   if (ok && !b->lq.empty())   // the side stream of the long-FFT queries' template spectra
@@ -635,6 +655,14 @@ tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s, int pari
   a.y = b->d_y; a.spec = b->d_spec; a.r = b->d_r; a.tw = b->tw;
   a.out = out; a.err = b->d_err + parity;
   a.ctas = b->corr_ctas;
+  if (!b->ssum.empty()) {
+    SlotSumArgs sa;
+    sa.partial = parity ? b->d_partial2 : b->d_partial;
+    sa.job = b->d_ssum;
+    sa.njobs = int32_t(b->ssum.size());
+    sa.max_cols = b->ssum_cols;
+    TM_CUDA(launch_slot_sums(sa, s));
+  }
   if (a.nq > 0) TM_CUDA(launch_correlate(a, b->maxP, s));
   a.ctas = 0;
   a.first = 0;
@@ -1234,7 +1262,7 @@ tm_status tm_batch_stats(tm_batch_t b, int32_t* launches, int32_t* fold_ctas, in
   if (launches) {
     const int32_t nsm = b->n - b->n_blocked - b->n_large;   // queries of the shared-memory correlation
     const int32_t waves = nsm == 0 ? 0 : (b->corr_ctas > 0 ? int32_t(ceil_div(nsm, b->corr_ctas)) : 1);
-    int32_t l = waves + (b->n_blocked > 0 ? 1 : 0);
+    int32_t l = waves + (b->n_blocked > 0 ? 1 : 0) + (b->ssum.empty() ? 0 : 1);
     for (const auto& g : b->groups) l += g.W > 0 ? 1 : 0;
     l += b->direct.empty() ? 0 : (b->maxHM_direct > 0 ? 2 : 1);
     if (!b->lq.empty()) l += large_launches(b->lq_two ? 2 : 1);
@@ -1298,6 +1326,7 @@ namespace {
 // Layout of the scratch array (byte offsets, 256-aligned).
 constexpr size_t kNaErr = 0;                 // int32 error word (cleared by every call)
 constexpr size_t kNaOrder = 16;              // int32 processing order (one query: 0)
+constexpr size_t kNaJob = 64;                // slot-sum job (used when the fold has many rows)
 constexpr size_t kNaFoldQ = 256;             // FoldQ descriptor
 constexpr size_t kNaCorrQ = 512;             // CorrQ descriptor
 constexpr size_t kNaTw = 1024;               // twiddles W_16384^m, written once per device
@@ -1305,7 +1334,8 @@ constexpr size_t kNaY = kNaTw + size_t(kPMax) * sizeof(float2);      // folds [2
 constexpr size_t kNaSpec = kNaY + 2 * size_t(kPMax) * sizeof(int32_t);  // template spectrum
 constexpr size_t kNaPart = kNaSpec + size_t(kPMax) * sizeof(float2);    // partial fold counts
 constexpr size_t kNaPartBytes = TM_NOALLOC_SCRATCH_BYTES - kNaPart;
-static_assert(sizeof(FoldQ) <= 256 && sizeof(CorrQ) <= 512, "descriptor slots");
+static_assert(sizeof(FoldQ) <= 256 && sizeof(CorrQ) <= 512 && kNaJob + sizeof(SlotSumJob) <= kNaFoldQ,
+              "descriptor slots");
 
 }  // namespace
 
@@ -1313,14 +1343,17 @@ namespace ftm_noalloc {
 // Writes one call's descriptors into the scratch array. They travel as
 // kernel parameters (copied by the launch itself), so no host buffer has to
 // outlive the call.
-__global__ void noalloc_write_descriptors(const FoldQ f, const CorrQ c, unsigned char* base) {
+__global__ void noalloc_write_descriptors(const FoldQ f, const CorrQ c, const SlotSumJob j, unsigned char* base) {
   const int tid = threadIdx.x;
+  if (tid < int(sizeof(SlotSumJob) / 4))
+    reinterpret_cast<int*>(base + kNaJob)[tid] = reinterpret_cast<const int*>(&j)[tid];
   if (tid < int(sizeof(FoldQ) / 4)) reinterpret_cast<int*>(base + kNaFoldQ)[tid] = reinterpret_cast<const int*>(&f)[tid];
   if (tid < int(sizeof(CorrQ) / 4)) reinterpret_cast<int*>(base + kNaCorrQ)[tid] = reinterpret_cast<const int*>(&c)[tid];
   if (tid < 4) reinterpret_cast<int*>(base + kNaOrder)[tid] = 0;   // processing order of the one query
   if (tid == 0) *reinterpret_cast<int*>(base + kNaErr) = 0;          // the previous call's error word is stale
 }
-static_assert(sizeof(FoldQ) % 4 == 0 && sizeof(CorrQ) % 4 == 0 && sizeof(CorrQ) / 4 <= 256, "descriptor words");
+static_assert(sizeof(FoldQ) % 4 == 0 && sizeof(CorrQ) % 4 == 0 && sizeof(SlotSumJob) % 4 == 0 &&
+              sizeof(CorrQ) / 4 <= 256, "descriptor words");
 }  // namespace ftm_noalloc
 
 namespace {
@@ -1420,10 +1453,19 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   c.nelem16 = int32_t(fold_elems(p.xdtype, p.N));
   c.nslots = f.nslots; c.stride = f.stride; c.part = 0;
   c.y_off = 0; c.spec_off = 0; c.r_off = -1;
+  SlotSumJob job{};
+  const bool ssum = f.nslots >= kSlotSumMin && f.nslots < max_slots;
+  if (ssum) {   // the rows' sum in the row after them
+    job.src = 0; job.dst = int64_t(f.nslots) * stride;
+    job.nslots = f.nslots; job.cols = f.stride;
+    job.real = (p.xdtype == TM_F16 || p.xdtype == TM_F32) ? 1 : 0;
+    c.nslots = 1;
+    c.part = job.dst;
+  }
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int32_t* err = reinterpret_cast<int32_t*>(base + kNaErr);
-  ftm_noalloc::noalloc_write_descriptors<<<1, 256, 0, s>>>(f, c, base);
+  ftm_noalloc::noalloc_write_descriptors<<<1, 256, 0, s>>>(f, c, job, base);
   TM_CUDA(cudaGetLastError());
   if (W > 0) {
     FoldArgs fa;
@@ -1434,6 +1476,14 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
     const int E = fold_geom(p.xdtype).E;
     const int jmax = std::max(fold_units_per_lane(p.Mp[0], kFoldWarps0, E), fold_units_per_lane(p.Mp[1], kFoldWarps1, E));
     TM_CUDA(launch_fold(fa, jmax, s));
+  }
+  if (ssum) {
+    SlotSumArgs sa;
+    sa.partial = reinterpret_cast<int32_t*>(base + kNaPart);
+    sa.job = reinterpret_cast<const SlotSumJob*>(base + kNaJob);
+    sa.njobs = 1;
+    sa.max_cols = job.cols;
+    TM_CUDA(launch_slot_sums(sa, s));
   }
   CorrArgs ca;
   ca.q = reinterpret_cast<const CorrQ*>(base + kNaCorrQ);

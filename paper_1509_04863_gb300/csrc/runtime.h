@@ -82,6 +82,9 @@ struct tm_batch_s {
   int32_t maxP_direct = 0, maxmod_direct = 0, maxM_direct = 0, maxHM_direct = 0;
   std::vector<int32_t> dh, drows, dpitch;   // entry-by-entry folds: row groups, rows per group, row pitch, partial offsets
   std::vector<int64_t> dpart;
+  std::vector<ftm::SlotSumJob> ssum;   // folds whose rows are summed ahead of the correlation
+  std::vector<int32_t> ssum_of;        // fold descriptor -> job (-1: none)
+  int32_t ssum_cols = 0;               // longest row among them
   int32_t n_blocked = 0;   // queries correlated in blocks (order[n - n_large - n_blocked, n - n_large))
   int32_t n_large = 0;     // queries on the multi-CTA path (order[n - n_large, n))
   std::vector<uint8_t> is_large;
@@ -89,6 +92,7 @@ struct tm_batch_s {
   std::vector<int32_t> lq_of;   // query -> position in lq (-1: not on that path)
   int32_t lq_maxP = 0, lq_maxM = 0, lq_two = 0;
   ftm::LQ* d_lq = nullptr;
+  ftm::SlotSumJob* d_ssum = nullptr;   // the slot-sum jobs (device copy of ssum)
   int64_t y_elems = 0, spec_elems = 0, r_elems = 0, part_elems = 0;
   ftm::FoldQ* d_fq = nullptr;
   ftm::CorrQ* d_cq = nullptr;

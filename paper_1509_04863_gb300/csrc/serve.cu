@@ -119,6 +119,7 @@ namespace {
 size_t batch_bytes(const tm_batch_s* b, int64_t t_floats) {
   const size_t n = size_t(b->n);
   return align_up(n * sizeof(FoldQ)) + align_up(n * sizeof(CorrQ)) + align_up(n * sizeof(LQ)) +
+         align_up(n * sizeof(SlotSumJob)) +
          align_up(2 * n * sizeof(int32_t)) +
          align_up(size_t(b->part_elems) * 4) + align_up(size_t(b->y_elems) * 4) +
          align_up(size_t(b->spec_elems) * sizeof(float2)) + align_up(size_t(b->r_elems) * 4) + align_up(16) +
@@ -136,6 +137,7 @@ void carve(tm_batch_s* b, char* base, int64_t t_floats) {
   b->d_fq = reinterpret_cast<FoldQ*>(take(n * sizeof(FoldQ)));
   b->d_cq = reinterpret_cast<CorrQ*>(take(n * sizeof(CorrQ)));
   b->d_lq = reinterpret_cast<LQ*>(take(n * sizeof(LQ)));
+  b->d_ssum = reinterpret_cast<SlotSumJob*>(take(n * sizeof(SlotSumJob)));
   b->d_order = reinterpret_cast<int32_t*>(take(2 * n * sizeof(int32_t)));
   b->d_partial = reinterpret_cast<int32_t*>(take(size_t(b->part_elems) * 4));
   b->d_y = take(size_t(b->y_elems) * 4);
@@ -488,7 +490,7 @@ tm_status tm_serve_create(const tm_serve_cfg* cfg_in, tm_server_t* out) {
   }
   sv->cfg = cfg;
   sv->slots.resize(cfg.n_streams);
-  const size_t stage_cap = size_t(cfg.max_batch) * (sizeof(FoldQ) + sizeof(CorrQ) + sizeof(LQ));
+  const size_t stage_cap = size_t(cfg.max_batch) * (sizeof(FoldQ) + sizeof(CorrQ) + sizeof(LQ) + sizeof(SlotSumJob));
   // template staging: max_batch templates of 8192 entries on average; a
   // larger iteration is split
   const int64_t t_cap = std::max<int64_t>(int64_t(cfg.max_batch) * 8192, 65536);

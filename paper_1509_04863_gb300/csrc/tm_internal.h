@@ -209,6 +209,30 @@ cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s);
 cudaError_t launch_correlate_blocked(const CorrArgs& a, cudaStream_t s);
 int blocked_spectra(int K, int maxM);
 constexpr int kLogPMaxBlocked = 18;   // longest FFT of the blocked correlation: 262144
+// ---------------------------------------------------------------- slot sums (end of step 1)
+// A signal that many fold CTAs share leaves one partial row per share (or
+// per piece); a lone correlation CTA reading dozens of rows is bound by its
+// own load latency. The slot-sum kernel first adds the rows of such folds
+// into one row, spread over many CTAs; the correlation then reads that row.
+// The sum goes to a row of its own (not row 0), so correlating the same
+// fold twice sums the same rows again.
+constexpr int kSlotSumMin = 8;        // folds of at least this many rows are summed ahead
+constexpr int kSlotSumThreads = 512;  // 16 warps share a row's slots; 32 column quads per CTA
+struct SlotSumJob {
+  int64_t src;      // first row (int32 units in the partial buffer)
+  int64_t dst;      // the sum row
+  int32_t nslots;   // rows to add
+  int32_t cols;     // row length (int32 units, multiple of 16): the slot stride
+  int32_t real;     // rows hold fp32 sums (else int32 counts)
+};
+struct SlotSumArgs {
+  int32_t* partial;
+  const SlotSumJob* job;   // device array of njobs jobs
+  int32_t njobs;
+  int32_t max_cols;        // longest row among them
+};
+cudaError_t launch_slot_sums(const SlotSumArgs& a, cudaStream_t s);
+
 // ---------------------------------------------------------------- slices of one signal
 // Completion of a slice's fold: the extended folds [2][P] of Eq. (2)
 // restricted to the entries x_n with n in [n0, n0 + len), from the fold

@@ -85,7 +85,7 @@ def test_mixed_types_uneven_batch(tm):
         qs.append(W.planted_query(700 + s, N, K, dt, flip_p=0.05 if dt in ("i8", "bits") else 0.0,
                                   t_sigma=0.3 if dt in ("f16", "f32") else 0.0, mode="auto"))
     b, res = _run(tm, qs)
-    assert b.stats()["launches_per_run"] == 5
+    assert b.stats()["launches_per_run"] in (5, 6)   # 4 fold groups, correlation (+ slot sums of folds with >= 8 rows)
     for i, q in enumerate(qs):
         ref = O.match_query(q)
         if q.xdtype in ("i8", "bits"):
