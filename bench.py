@@ -832,6 +832,10 @@ def run_serve(args):
                         "p99_us": float(np.percentile(lat, 99)) if len(lat) else None,
                         "max_us": float(lat.max()) if len(lat) else None,
                         "mean_batch": st["mean_batch"], "iterations": st["iterations"],
+                        "mean_latency_parts_us": {"queue": st["queue_us"], "host": st["host_us"],
+                                                  "device": st["device_us"],
+                                                  "what": "submission -> taken by the worker -> last launch "
+                                                          "returned -> completion seen (host clock)"},
                         "fold_cache_hits": st["fold_cache_hits"], "fold_cache_misses": st["fold_cache_misses"],
                         "success_rate": float(np.mean([shift_by_storage[storage][i] == shifts[i]
                                                        for i in range(nreq)]))}
@@ -936,6 +940,8 @@ def run_serve(args):
                       "p50_us": float(np.percentile(lat, 50)) if len(lat) else None,
                       "p99_us": float(np.percentile(lat, 99)) if len(lat) else None,
                       "mean_batch": st["mean_batch"], "iterations": st["iterations"],
+                      "mean_latency_parts_us": {"queue": st["queue_us"], "host": st["host_us"],
+                                                "device": st["device_us"]},
                       "client_behind_ms": 1e3 * late})
         srv.close()
         del srv

@@ -388,6 +388,12 @@ typedef struct {
   double mean_batch;   /* requests per iteration */
   double p50_us, p99_us, max_us;   /* latency over the completed requests */
   int64_t fold_cache_hits, fold_cache_misses;   /* requests served from / missing the fold cache */
+  /* Mean over the completed requests of their latency's parts, host clock:
+   * queue_us from submission until the worker takes the request, host_us
+   * from then until its iteration's last launch has returned (planning,
+   * staging, launches), device_us from then until the worker sees the
+   * iteration's completion event. */
+  double queue_us, host_us, device_us;
 } tm_serve_stats;
 
 /* Signal registration flag: x is device memory to use in place (the caller

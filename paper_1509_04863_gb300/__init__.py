@@ -438,7 +438,8 @@ class tm_serve_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("iterations", C.c_int64), ("pending", C.c_int64), ("in_flight", C.c_int64),
                 ("mean_batch", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
-                ("fold_cache_hits", C.c_int64), ("fold_cache_misses", C.c_int64)]
+                ("fold_cache_hits", C.c_int64), ("fold_cache_misses", C.c_int64),
+                ("queue_us", C.c_double), ("host_us", C.c_double), ("device_us", C.c_double)]
 
 
 TM_SERVE_SIGNAL_DEVICE = 0x1

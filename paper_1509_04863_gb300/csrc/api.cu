@@ -648,22 +648,28 @@ tm_status batch_fold(tm_batch_t b, cudaStream_t s, int parity, bool clear_err) {
   return TM_OK;
 }
 
-tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s, int parity) {
+tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s, int parity, bool after_fold) {
   CorrArgs a;
   a.q = b->d_cq; a.order = b->d_order; a.nq = b->n - b->n_blocked - b->n_large;
   a.partial = parity ? b->d_partial2 : b->d_partial;
   a.y = b->d_y; a.spec = b->d_spec; a.r = b->d_r; a.tw = b->tw;
   a.out = out; a.err = b->d_err + parity;
   a.ctas = b->corr_ctas;
+  // a fold kernel (not a copy) ran last on s: the slot sums and the
+  // correlation may start before it ends (their template work overlaps it)
+  const bool pdl = after_fold && (b->W > 0 || !b->direct.empty());
   if (!b->ssum.empty()) {
     SlotSumArgs sa;
     sa.partial = parity ? b->d_partial2 : b->d_partial;
     sa.job = b->d_ssum;
     sa.njobs = int32_t(b->ssum.size());
     sa.max_cols = b->ssum_cols;
+    sa.pdl = pdl ? 1 : 0;
     TM_CUDA(launch_slot_sums(sa, s));
   }
+  a.pdl = pdl ? 1 : 0;
   if (a.nq > 0) TM_CUDA(launch_correlate(a, b->maxP, s));
+  a.pdl = 0;
   a.ctas = 0;
   a.first = 0;
   if (b->n_blocked > 0) {
@@ -913,7 +919,7 @@ tm_status tm_match(tm_plan_t p, const void* x, const float* t, tm_result* out, t
   }
   tm_status st = batch_fold(p->b, s);
   if (st != TM_OK) return st;
-  return batch_correlate(p->b, out, s);
+  return batch_correlate(p->b, out, s, 0, true);
 }
 
 tm_status tm_batch_create(const tm_query* q, int32_t n, uint32_t flags, tm_batch_t* out) {
@@ -943,9 +949,11 @@ tm_status tm_batch_correlate(tm_batch_t b, tm_result* out, tm_stream_t stream) {
 }
 
 tm_status tm_batch_run(tm_batch_t b, tm_result* out, tm_stream_t stream) {
-  tm_status st = tm_batch_fold(b, stream);
+  if (!b || !out) return fail(TM_EINVAL, "null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  tm_status st = batch_fold(b, s);
   if (st != TM_OK) return st;
-  return tm_batch_correlate(b, out, stream);
+  return batch_correlate(b, out, s, 0, true);
 }
 
 tm_status tm_batch_set_grid(tm_batch_t b, int32_t fold_ctas, int32_t corr_ctas) {
@@ -1200,7 +1208,7 @@ tm_status tm_batch_graph_capture(tm_batch_t b, tm_result* out) {
   }
   TM_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   tm_status st = batch_fold(b, b->cap_stream);
-  if (st == TM_OK) st = batch_correlate(b, out, b->cap_stream);
+  if (st == TM_OK) st = batch_correlate(b, out, b->cap_stream, 0, true);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
   if (st != TM_OK) {
@@ -1236,7 +1244,7 @@ tm_status tm_batch_run_host(tm_batch_t b, const void* const* x_host, const float
   }
   tm_status st = batch_fold(b, s);
   if (st != TM_OK) return st;
-  st = batch_correlate(b, b->d_out, s);
+  st = batch_correlate(b, b->d_out, s, 0, true);
   if (st != TM_OK) return st;
   TM_CUDA(cudaMemcpyAsync(out_host, b->d_out, size_t(b->n) * sizeof(tm_result), cudaMemcpyDeviceToHost, s));
   TM_CUDA(cudaStreamSynchronize(s));
@@ -1483,6 +1491,7 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
     sa.job = reinterpret_cast<const SlotSumJob*>(base + kNaJob);
     sa.njobs = 1;
     sa.max_cols = job.cols;
+    sa.pdl = 1;   // after the fold kernel
     TM_CUDA(launch_slot_sums(sa, s));
   }
   CorrArgs ca;
@@ -1496,6 +1505,7 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   ca.tw = reinterpret_cast<const float2*>(base + kNaTw);
   ca.out = out;
   ca.err = err;
+  ca.pdl = 1;   // after a kernel of this call (descriptors, fold or slot sums)
   TM_CUDA(launch_correlate(ca, p.P, s));
   return TM_OK;
 }

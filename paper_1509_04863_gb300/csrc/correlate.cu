@@ -777,6 +777,9 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
     tc2 = fmaxf(tc2, fmaf(T.x, T.x, T.y * T.y));
   }
   const float Tp = spectrum_max_bound(sqrtf(block_maxf(tc2, redf)), logP, t2);
+  // everything above reads only the template; the folds come from the
+  // kernel before this one (a programmatic dependent launch starts early)
+  pdl_acquire();
 
   // ------------------------------------------------ b-d, per pass: the first
   // pass carries M1 (real part) and M2 (imaginary part) through one complex
@@ -1327,9 +1330,11 @@ cudaError_t launch_correlate(const CorrArgs& a, int32_t maxP, cudaStream_t s) {
     b.first = a.first + f;
     const int grid = min(wave, a.nq - f);
     // one butterfly of radix 16 per thread and pass up to P = 8192, two above
-    if (maxP <= kPMax / 2) corr_kernel<1><<<grid, kCorrThreads, b.smem_bytes, s>>>(b);
-    else corr_kernel<2><<<grid, kCorrThreads, b.smem_bytes, s>>>(b);
-    const cudaError_t e = cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t c = launch_config(dim3(grid), dim3(kCorrThreads), size_t(b.smem_bytes), s,
+                                               a.pdl != 0 && wave == a.nq, attr);
+    const cudaError_t e = maxP <= kPMax / 2 ? cudaLaunchKernelEx(&c, corr_kernel<1>, b)
+                                            : cudaLaunchKernelEx(&c, corr_kernel<2>, b);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -20,6 +20,15 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   return t;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may start once every CTA of the kernel
+// before it in the stream has signalled (pdl_release) or exited; it must
+// call pdl_acquire before it reads what that kernel writes, which returns
+// once that kernel has completed and its writes are visible. Without the
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_acquire() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }

@@ -671,6 +671,9 @@ __global__ void __launch_bounds__(kFoldThreads, 1) fold_kernel(const FoldArgs a)
   const int tid = threadIdx.x;
   const int64_t cb = fold_share_begin(a, blockIdx.x);
   const int64_t ce = fold_share_begin(a, blockIdx.x + 1);
+  // a correlation launched as a dependent may start its template work now
+  // (it waits for this grid before reading the partial sums)
+  pdl_release();
 
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) {

@@ -153,6 +153,8 @@ tm_status upload_descriptors(tm_batch_s* b, cudaStream_t s);
 // clear_err: reset the parity's error word on `s` first (pipelined runs
 // reset it on the correlation stream instead, after its last reader)
 tm_status batch_fold(tm_batch_s* b, cudaStream_t s, int parity = 0, bool clear_err = true);
-tm_status batch_correlate(tm_batch_s* b, tm_result* out, cudaStream_t s, int parity = 0);
+// after_fold: the last operation on s is this batch's batch_fold, so the
+// first correlation launch may be a programmatic dependent of its kernels
+tm_status batch_correlate(tm_batch_s* b, tm_result* out, cudaStream_t s, int parity = 0, bool after_fold = false);
 
 }  // namespace ftm

@@ -45,6 +45,7 @@ struct Req {
   PlanCore plan;
   std::vector<float> t;
   double t_submit;
+  double t_admit = 0.0;   // taken from the queue by the worker
 };
 
 struct Signal {
@@ -87,6 +88,7 @@ struct Slot {
   std::vector<Req> reqs;
   std::vector<CacheKey> hits, made;   // fold-cache entries read / written by the iteration
   bool busy = false;
+  double t_launched = 0.0;   // the iteration's last launch returned
 };
 
 }  // namespace
@@ -104,6 +106,7 @@ struct tm_server_s {
   std::deque<tm_result_tagged> done;
   std::vector<double> lat;             // completed latencies (bounded)
   int64_t submitted = 0, completed = 0, failed = 0, iterations = 0, batched = 0;
+  double sum_queue = 0.0, sum_host = 0.0, sum_device = 0.0;   // over completed requests
   std::map<CacheKey, CacheEntry> fcache;   // worker thread only
   int64_t fcache_bytes = 0;
   uint64_t fclock = 0;
@@ -257,7 +260,7 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
   if (st != TM_OK) return st;
   st = batch_fold(sl.b, sl.s);
   if (st != TM_OK) return st;
-  st = batch_correlate(sl.b, sl.b->d_out, sl.s);
+  st = batch_correlate(sl.b, sl.b->d_out, sl.s, 0, true);
   if (st != TM_OK) return st;
   TM_CUDA(cudaMemcpyAsync(sl.h_out, sl.b->d_out, size_t(n) * sizeof(tm_result), cudaMemcpyDeviceToHost, sl.s));
   TM_CUDA(cudaEventRecord(sl.ev, sl.s));
@@ -336,11 +339,14 @@ void admit(tm_server_t sv, Slot& sl) {
       sv->pending.pop_front();
     }
   }
+  const double t_admit = now_us();
+  for (auto& r : take) r.t_admit = t_admit;
   while (!take.empty()) {
     sl.reqs = std::move(take);
     take.clear();
     const tm_status st = launch_iteration(sv, sl);
     if (st == TM_OK) {
+      sl.t_launched = now_us();
       sl.busy = true;
       sv->busy.fetch_add(1);
       std::lock_guard<std::mutex> lk(sv->cmu);
@@ -380,11 +386,20 @@ void retire(tm_server_t sv, Slot& sl) {
   release_cache(sv, sl);
   const double t = now_us();
   std::vector<tm_result_tagged> out(sl.reqs.size());
+  double q = 0.0, h = 0.0;
   for (size_t i = 0; i < sl.reqs.size(); ++i) {
     out[i].tag = sl.reqs[i].tag;
     out[i].status = TM_OK;
     out[i].latency_us = t - sl.reqs[i].t_submit;
     out[i].r = sl.h_out[i];
+    q += sl.reqs[i].t_admit - sl.reqs[i].t_submit;
+    h += sl.t_launched - sl.reqs[i].t_admit;
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->cmu);
+    sv->sum_queue += q;
+    sv->sum_host += h;
+    sv->sum_device += double(sl.reqs.size()) * (t - sl.t_launched);
   }
   sl.reqs.clear();
   sl.busy = false;
@@ -649,6 +664,10 @@ tm_status tm_serve_stats_get(tm_server_t sv, tm_serve_stats* st) {
     st->mean_batch = sv->iterations ? double(sv->batched) / double(sv->iterations) : 0.0;
     st->fold_cache_hits = sv->fc_hits;
     st->fold_cache_misses = sv->fc_misses;
+    const double nc = sv->completed > 0 ? double(sv->completed) : 1.0;
+    st->queue_us = sv->sum_queue / nc;
+    st->host_us = sv->sum_host / nc;
+    st->device_us = sv->sum_device / nc;
     lat = sv->lat;
   }
   {

@@ -7,6 +7,7 @@
 // columns, and warp 0 adds the 16 partial sums in warp order. The order
 // depends on the number of rows alone, so fp32 sums are the same whatever
 // else the batch holds; int32 counts are exact in any order.
+#include "device_util.cuh"
 #include "tm_internal.h"
 
 namespace ftm {
@@ -51,6 +52,8 @@ __device__ __forceinline__ void sum_quads(int32_t* partial, const SlotSumJob& j,
 
 __global__ void __launch_bounds__(kSlotSumThreads) slot_sum_kernel(const SlotSumArgs a) {
   __shared__ int4 part[kWarps][32];
+  pdl_release();   // the correlation after it may start its template work
+  pdl_acquire();   // the fold's rows are complete
   for (int jb = blockIdx.y; jb < a.njobs; jb += gridDim.y) {
     const SlotSumJob j = a.job[jb];
     if (int(blockIdx.x) * 128 >= j.cols) continue;   // the whole CTA is past this job's row
@@ -65,8 +68,9 @@ __global__ void __launch_bounds__(kSlotSumThreads) slot_sum_kernel(const SlotSum
 cudaError_t launch_slot_sums(const SlotSumArgs& a, cudaStream_t s) {
   if (a.njobs <= 0) return cudaSuccess;
   const dim3 grid(unsigned((a.max_cols + 127) / 128), unsigned(a.njobs < 65535 ? a.njobs : 65535));
-  slot_sum_kernel<<<grid, kSlotSumThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t c = launch_config(grid, dim3(kSlotSumThreads), 0, s, a.pdl != 0, attr);
+  return cudaLaunchKernelEx(&c, slot_sum_kernel, a);
 }
 
 }  // namespace ftm

@@ -198,7 +198,27 @@ struct CorrArgs {
   int32_t ctas = 0;       // most CTAs running at a time (0: one CTA per query,
                           // all at once); more queries run as waves of launches
   int32_t first = 0;      // first position in the order (set per wave by the launcher)
+  int32_t pdl = 0;        // programmatic dependent of the kernel before it in the stream
+                          // (a fold or the slot sums): the template spectrum runs
+                          // before that kernel has finished (one wave only)
 };
+
+// Launch configuration with the programmatic stream-serialisation attribute
+// when pdl is set (the kernel then calls pdl_acquire before reading what
+// the kernel before it writes).
+inline cudaLaunchConfig_t launch_config(dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                                        cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t c = {};
+  c.gridDim = grid;
+  c.blockDim = block;
+  c.dynamicSmemBytes = smem;
+  c.stream = s;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  c.attrs = attr;
+  c.numAttrs = pdl ? 1 : 0;
+  return c;
+}
 
 // ---------------------------------------------------------------- kernels' host launchers
 cudaError_t launch_fold(const FoldArgs& a, int jmax, cudaStream_t s);
@@ -230,6 +250,7 @@ struct SlotSumArgs {
   const SlotSumJob* job;   // device array of njobs jobs
   int32_t njobs;
   int32_t max_cols;        // longest row among them
+  int32_t pdl = 0;         // launched as a programmatic dependent of the fold before it
 };
 cudaError_t launch_slot_sums(const SlotSumArgs& a, cudaStream_t s);
 
