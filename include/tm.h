@@ -373,6 +373,11 @@ typedef struct {
                                  many templates). Least recently used pairs are
                                  dropped beyond this many device bytes. Requests with
                                  FFT lengths above 16384 are not cached. */
+  int64_t idle_spin_us;       /* with nothing pending or in flight, the worker keeps
+                                 polling the queue this long before it sleeps on a
+                                 condition variable (0: it sleeps at once): a request
+                                 arriving meanwhile is taken without a thread wake-up,
+                                 at the cost of a busy host core */
 } tm_serve_cfg;
 
 typedef struct {

@@ -426,7 +426,7 @@ def result_buffer(n: int, device="cuda"):
 class tm_serve_cfg(C.Structure):
     _fields_ = [("n_streams", C.c_int32), ("max_batch", C.c_int32), ("queue_capacity", C.c_int32),
                 ("flags", C.c_uint32), ("arena_bytes", C.c_int64), ("hbm_reserve_bytes", C.c_int64),
-                ("fold_cache_bytes", C.c_int64)]
+                ("fold_cache_bytes", C.c_int64), ("idle_spin_us", C.c_int64)]
 
 
 class tm_result_tagged(C.Structure):
@@ -461,9 +461,11 @@ class Server:
     """tm_serve_create / register_signal / submit / poll / stats / destroy."""
 
     def __init__(self, n_streams: int = 2, max_batch: int = 512, queue_capacity: int = 65536,
-                 arena_bytes: int = 0, hbm_reserve_bytes: int = 0, fold_cache_bytes: int = 0):
+                 arena_bytes: int = 0, hbm_reserve_bytes: int = 0, fold_cache_bytes: int = 0,
+                 idle_spin_us: int = 0):
         L = lib()
-        cfg = tm_serve_cfg(n_streams, max_batch, queue_capacity, 0, arena_bytes, hbm_reserve_bytes, fold_cache_bytes)
+        cfg = tm_serve_cfg(n_streams, max_batch, queue_capacity, 0, arena_bytes, hbm_reserve_bytes, fold_cache_bytes,
+                           idle_spin_us)
         h = C.c_void_p()
         _check(L.tm_serve_create(C.byref(cfg), C.byref(h)), "tm_serve_create")
         self._h = h

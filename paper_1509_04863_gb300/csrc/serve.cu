@@ -78,12 +78,9 @@ struct Slot {
   cudaEvent_t ev = nullptr;
   char* arena = nullptr;
   int64_t arena_bytes = 0;
-  float* h_t = nullptr;         // pinned template staging
-  int64_t h_t_cap = 0;          // floats
+  char* h_up = nullptr;         // pinned image of the arena's uploaded head (descriptors,
+  size_t h_up_cap = 0;          // order, error word, templates): one copy per iteration
   tm_result* h_out = nullptr;   // pinned results
-  void* h_stage = nullptr;      // pinned descriptor staging
-  size_t h_stage_cap = 0;
-  int32_t* h_order = nullptr;   // pinned processing order
   tm_batch_s* b = nullptr;
   std::vector<Req> reqs;
   std::vector<CacheKey> hits, made;   // fold-cache entries read / written by the iteration
@@ -118,15 +115,21 @@ struct tm_server_s {
 
 namespace {
 
-// Device bytes of a planned batch when carved from an arena.
-size_t batch_bytes(const tm_batch_s* b, int64_t t_floats) {
+// Arena layout of a planned batch: first the part written from the host
+// every iteration (descriptors, processing order, error word, templates),
+// then the device-only buffers.
+size_t upload_bytes(const tm_batch_s* b, int64_t t_floats) {
   const size_t n = size_t(b->n);
   return align_up(n * sizeof(FoldQ)) + align_up(n * sizeof(CorrQ)) + align_up(n * sizeof(LQ)) +
-         align_up(n * sizeof(SlotSumJob)) +
-         align_up(2 * n * sizeof(int32_t)) +
-         align_up(size_t(b->part_elems) * 4) + align_up(size_t(b->y_elems) * 4) +
-         align_up(size_t(b->spec_elems) * sizeof(float2)) + align_up(size_t(b->r_elems) * 4) + align_up(16) +
-         align_up(n * sizeof(tm_result)) + align_up(size_t(t_floats) * 4);
+         align_up(n * sizeof(SlotSumJob)) + align_up(2 * n * sizeof(int32_t)) + align_up(16) +
+         align_up(size_t(t_floats) * 4);
+}
+
+size_t batch_bytes(const tm_batch_s* b, int64_t t_floats) {
+  const size_t n = size_t(b->n);
+  return upload_bytes(b, t_floats) + align_up(size_t(b->part_elems) * 4) + align_up(size_t(b->y_elems) * 4) +
+         align_up(size_t(b->spec_elems) * sizeof(float2)) + align_up(size_t(b->r_elems) * 4) +
+         align_up(n * sizeof(tm_result));
 }
 
 void carve(tm_batch_s* b, char* base, int64_t t_floats) {
@@ -142,13 +145,14 @@ void carve(tm_batch_s* b, char* base, int64_t t_floats) {
   b->d_lq = reinterpret_cast<LQ*>(take(n * sizeof(LQ)));
   b->d_ssum = reinterpret_cast<SlotSumJob*>(take(n * sizeof(SlotSumJob)));
   b->d_order = reinterpret_cast<int32_t*>(take(2 * n * sizeof(int32_t)));
+  b->d_err = reinterpret_cast<int32_t*>(take(16));
+  b->d_t = reinterpret_cast<float*>(take(size_t(t_floats) * 4));
+  // o == upload_bytes(b, t_floats)
   b->d_partial = reinterpret_cast<int32_t*>(take(size_t(b->part_elems) * 4));
   b->d_y = take(size_t(b->y_elems) * 4);
   b->d_spec = reinterpret_cast<float2*>(take(size_t(b->spec_elems) * sizeof(float2)));
   b->d_r = b->r_elems > 0 ? reinterpret_cast<float*>(take(size_t(b->r_elems) * 4)) : nullptr;
-  b->d_err = reinterpret_cast<int32_t*>(take(16));
   b->d_out = reinterpret_cast<tm_result*>(take(n * sizeof(tm_result)));
-  b->d_t = reinterpret_cast<float*>(take(size_t(t_floats) * 4));
 }
 
 void reset_batch(tm_batch_s* b) {
@@ -200,20 +204,6 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
     toff[i] = t_floats;
     t_floats += pad16(reqs[i].q.K);
   }
-  if (t_floats > sl.h_t_cap) {
-    // a template longer than the staging holds (long FFTs): alone, the
-    // slot's staging grows (the slot is idle, nothing reads it); with
-    // others, the iteration is split
-    if (n > 1) return TM_ENOMEM;
-    float* h = nullptr;
-    if (cudaMallocHost(&h, size_t(t_floats) * sizeof(float)) != cudaSuccess) {
-      cudaGetLastError();
-      return TM_ENOMEM;
-    }
-    cudaFreeHost(sl.h_t);
-    sl.h_t = h;
-    sl.h_t_cap = t_floats;
-  }
   // the template pointers are only known after carving; plan with
   // placeholders (planning reads shapes only), then bind
   for (int i = 0; i < n; ++i) {
@@ -238,14 +228,33 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
   tm_status st = batch_plan(sl.b, qs.data(), n, 0, nofold.data());
   if (st != TM_OK) return st;
   if (batch_bytes(sl.b, t_floats) > size_t(sl.arena_bytes)) return TM_ENOMEM;
+  const size_t up = upload_bytes(sl.b, t_floats);
+  if (up > sl.h_up_cap) {
+    // templates longer than the staging holds (long FFTs): alone, the
+    // slot's staging grows (the slot is idle, nothing reads it); with
+    // others, the iteration is split
+    if (n > 1) return TM_ENOMEM;
+    char* h = nullptr;
+    if (cudaMallocHost(&h, up) != cudaSuccess) {
+      cudaGetLastError();
+      return TM_ENOMEM;
+    }
+    cudaFreeHost(sl.h_up);
+    sl.h_up = h;
+    sl.h_up_cap = up;
+  }
   carve(sl.b, sl.arena, t_floats);
+  // the host image of the arena's head, at the same offsets
+  char* h = sl.h_up;
+  auto at = [&](const void* d) { return h + (static_cast<const char*>(d) - sl.arena); };
   for (int i = 0; i < n; ++i) {
     sl.b->q[i].t = sl.b->d_t + toff[i];
-    std::memcpy(sl.h_t + toff[i], reqs[i].t.data(), size_t(reqs[i].q.K) * sizeof(float));
+    std::memcpy(at(sl.b->d_t + toff[i]), reqs[i].t.data(), size_t(reqs[i].q.K) * sizeof(float));
   }
-  std::memcpy(sl.h_order, sl.b->order.data(), size_t(n) * sizeof(int32_t));
+  std::memcpy(at(sl.b->d_order), sl.b->order.data(), size_t(n) * sizeof(int32_t));
   if (!sl.b->direct.empty())   // the entry-by-entry folds' query list follows the order
-    std::memcpy(sl.h_order + n, sl.b->direct.data(), sl.b->direct.size() * sizeof(int32_t));
+    std::memcpy(at(sl.b->d_order + n), sl.b->direct.data(), sl.b->direct.size() * sizeof(int32_t));
+  std::memset(at(sl.b->d_err), 0, 16);   // the error words start clear
   bind_pointers(sl.b);
   for (int i = 0; i < n; ++i) {
     if (!hit[i]) continue;
@@ -253,12 +262,13 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
     sl.b->cq[i].core_pitch = hit[i]->pitch;
     TM_CUDA(cudaStreamWaitEvent(sl.s, hit[i]->ev, 0));
   }
-  TM_CUDA(cudaMemcpyAsync(sl.b->d_t, sl.h_t, size_t(t_floats) * sizeof(float), cudaMemcpyHostToDevice, sl.s));
-  TM_CUDA(cudaMemcpyAsync(sl.b->d_order, sl.h_order, size_t(n + sl.b->direct.size()) * sizeof(int32_t),
-                          cudaMemcpyHostToDevice, sl.s));
-  st = upload_descriptors(sl.b, sl.s);
-  if (st != TM_OK) return st;
-  st = batch_fold(sl.b, sl.s);
+  std::memcpy(at(sl.b->d_fq), sl.b->fq.data(), sl.b->fq.size() * sizeof(FoldQ));
+  std::memcpy(at(sl.b->d_cq), sl.b->cq.data(), sl.b->cq.size() * sizeof(CorrQ));
+  if (!sl.b->lq.empty()) std::memcpy(at(sl.b->d_lq), sl.b->lq.data(), sl.b->lq.size() * sizeof(LQ));
+  if (!sl.b->ssum.empty())
+    std::memcpy(at(sl.b->d_ssum), sl.b->ssum.data(), sl.b->ssum.size() * sizeof(SlotSumJob));
+  TM_CUDA(cudaMemcpyAsync(sl.arena, h, up, cudaMemcpyHostToDevice, sl.s));
+  st = batch_fold(sl.b, sl.s, 0, false);   // the copy cleared the error word
   if (st != TM_OK) return st;
   st = batch_correlate(sl.b, sl.b->d_out, sl.s, 0, true);
   if (st != TM_OK) return st;
@@ -409,6 +419,7 @@ void retire(tm_server_t sv, Slot& sl) {
 
 void worker_main(tm_server_t sv) {
   cudaSetDevice(sv->device);
+  double t_last = now_us();   // last time the worker had something to do
   while (true) {
     bool progressed = false, any_busy = false;
     for (auto& sl : sv->slots) {
@@ -442,8 +453,9 @@ void worker_main(tm_server_t sv) {
       }
     }
     if (sv->stop.load() && !have_pending && !any_busy) break;
+    if (progressed || any_busy) t_last = now_us();
     if (!progressed) {
-      if (any_busy) {
+      if (any_busy || now_us() - t_last < double(sv->cfg.idle_spin_us)) {
         std::this_thread::yield();
       } else {
         std::unique_lock<std::mutex> lk(sv->mu);
@@ -461,10 +473,8 @@ void server_free(tm_server_t sv) {
     if (sl.ev) cudaEventDestroy(sl.ev);
     if (sl.s) cudaStreamDestroy(sl.s);
     cudaFree(sl.arena);
-    if (sl.h_t) cudaFreeHost(sl.h_t);
+    if (sl.h_up) cudaFreeHost(sl.h_up);
     if (sl.h_out) cudaFreeHost(sl.h_out);
-    if (sl.h_stage) cudaFreeHost(sl.h_stage);
-    if (sl.h_order) cudaFreeHost(sl.h_order);
   }
   for (auto& kv : sv->fcache) {
     cudaFree(kv.second.y);
@@ -487,6 +497,7 @@ tm_status tm_serve_create(const tm_serve_cfg* cfg_in, tm_server_t* out) {
   if (cfg.n_streams > 4) return fail(TM_EINVAL, "n_streams must be 1..4");
   if (cfg.max_batch <= 0) cfg.max_batch = 512;
   if (cfg.queue_capacity <= 0) cfg.queue_capacity = 65536;
+  if (cfg.idle_spin_us < 0) return fail(TM_EINVAL, "idle_spin_us must be >= 0");
   if (cfg.hbm_reserve_bytes <= 0) cfg.hbm_reserve_bytes = int64_t(4) << 30;
   tm_server_t sv = new (std::nothrow) tm_server_s();
   if (!sv) return fail(TM_ENOMEM, "host allocation");
@@ -505,29 +516,24 @@ tm_status tm_serve_create(const tm_serve_cfg* cfg_in, tm_server_t* out) {
   }
   sv->cfg = cfg;
   sv->slots.resize(cfg.n_streams);
-  const size_t stage_cap = size_t(cfg.max_batch) * (sizeof(FoldQ) + sizeof(CorrQ) + sizeof(LQ) + sizeof(SlotSumJob));
-  // template staging: max_batch templates of 8192 entries on average; a
-  // larger iteration is split
-  const int64_t t_cap = std::max<int64_t>(int64_t(cfg.max_batch) * 8192, 65536);
+  // upload staging: descriptors and order for max_batch requests and
+  // templates of 8192 entries on average; a larger iteration is split
+  const size_t nb = size_t(cfg.max_batch);
+  const size_t up_cap = align_up(nb * sizeof(FoldQ)) + align_up(nb * sizeof(CorrQ)) + align_up(nb * sizeof(LQ)) +
+                        align_up(nb * sizeof(SlotSumJob)) + align_up(2 * nb * sizeof(int32_t)) + align_up(16) +
+                        align_up(std::max<size_t>(nb * 8192, 65536) * sizeof(float));
   for (auto& sl : sv->slots) {
     bool ok = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaMalloc(&sl.arena, size_t(cfg.arena_bytes)) == cudaSuccess &&
-              cudaMallocHost(&sl.h_t, size_t(t_cap) * sizeof(float)) == cudaSuccess &&
-              cudaMallocHost(&sl.h_out, size_t(cfg.max_batch) * sizeof(tm_result)) == cudaSuccess &&
-              cudaMallocHost(&sl.h_stage, stage_cap) == cudaSuccess &&
-              cudaMallocHost(&sl.h_order, 2 * size_t(cfg.max_batch) * sizeof(int32_t)) == cudaSuccess;
+              cudaMallocHost(&sl.h_up, up_cap) == cudaSuccess &&
+              cudaMallocHost(&sl.h_out, size_t(cfg.max_batch) * sizeof(tm_result)) == cudaSuccess;
     sl.arena_bytes = cfg.arena_bytes;
-    sl.h_t_cap = t_cap;
-    sl.h_stage_cap = stage_cap;
+    sl.h_up_cap = up_cap;
     if (ok) {
       sl.b = new (std::nothrow) tm_batch_s();
       ok = sl.b != nullptr && cudaEventCreateWithFlags(&sl.b->ev_stage, cudaEventDisableTiming) == cudaSuccess;
-      if (ok) {
-        sl.b->owns_memory = false;
-        sl.b->h_stage = sl.h_stage;
-        sl.b->stage_bytes = stage_cap;
-      }
+      if (ok) sl.b->owns_memory = false;
     }
     if (!ok) {
       cudaGetLastError();
