@@ -390,10 +390,7 @@ __device__ __forceinline__ double warp_dot(const float* __restrict__ t, int K, b
   DF df;
 #pragma unroll 4
   for (int i = lane; i < K; i += 32) df.add_prod(t[i], float(v(i)));
-  double acc = df.value();
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  return acc;
+  return warp_sum_df(df).value();
 }
 
 // Bound on max_j |r~_j - r_j| for a correlation computed through length-P
@@ -462,9 +459,9 @@ __device__ void collect_candidates(Cands& cs, int mj, int M, float delta, RFn rv
 // (crt.h), the exact (Tx)_m of its member(s) and the result record.
 __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integral, float t1, int maxy, Cands& cs) {
   __shared__ long long redl[kWarps];
-  __shared__ double redd[kWarps];
+  __shared__ float2 redf2[kWarps];
   __shared__ long long redl4[4 * kWarps];
-  __shared__ double redd4[4 * kWarps];
+  __shared__ float2 redf4[4 * kWarps];
   __shared__ double wbest_v[kWarps];
   __shared__ int64_t wbest_i[kWarps];
   __shared__ int s_m[3];
@@ -508,7 +505,7 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
       ypi[b] = static_cast<const int32_t*>(yv) + int64_t(mj[b]) * P + jj[b];
       ypf[b] = static_cast<const float*>(yv) + int64_t(mj[b]) * P + jj[b];
     }
-    double v[4];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};   // thread 0's: the sums it compares
     // loads for four indices i per thread go out before any is used
     constexpr int kU = 4;
     if (exact_int) {
@@ -531,8 +528,9 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
         }
       }
       block_sum4(acc, redl4);
+      if (tid == 0)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) v[b] = double(acc[b]);
+        for (int b = 0; b < 4; ++b) v[b] = double(acc[b]);
     } else {
       DF df[4];
       for (int i0 = tid; i0 < K; i0 += kU * kCorrThreads) {
@@ -549,19 +547,19 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
 #pragma unroll
           for (int b = 0; b < 4; ++b) df[b].add_prod(tv[u], yw[u][b]);
       }
-      double acc[4];
+      block_sum_df<kWarps>(df, redf4);
+      if (tid == 0)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[b] = df[b].value();
-      block_sum4(acc, redd4);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) v[b] = acc[b];
+        for (int b = 0; b < 4; ++b) v[b] = df[b].value();
     }
+    if (tid == 0) {
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      if (b >= nb) continue;
-      if (mj[b] == 0) betterd(bvj[0], bij[0], v[b], jj[b]);
-      else if (mj[b] == 1) betterd(bvj[1], bij[1], v[b], jj[b]);
-      else betterd(bvj[2], bij[2], v[b], jj[b]);
+      for (int b = 0; b < 4; ++b) {
+        if (b >= nb) continue;
+        if (mj[b] == 0) betterd(bvj[0], bij[0], v[b], jj[b]);
+        else if (mj[b] == 1) betterd(bvj[1], bij[1], v[b], jj[b]);
+        else betterd(bvj[2], bij[2], v[b], jj[b]);
+      }
     }
   }
   if (tid == 0) {
@@ -634,7 +632,9 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
         if (n >= N) n -= N;
         df.add_prod(t[i], sig.val(n));
       }
-      best_v = block_sum(df.value(), redd);
+      DF s[1] = {df};
+      block_sum_df<kWarps>(s, redf2);
+      best_v = tid == 0 ? s[0].value() : 0.0;   // thread 0 writes the result
     }
     best_m = mm;
   } else if (ncs > 1) {

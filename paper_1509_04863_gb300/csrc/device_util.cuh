@@ -90,6 +90,59 @@ struct DF {
   __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
+// Sum of two pairs: the high parts by an error-free two-sum, the low parts
+// and its error added in fp32. Symmetric in its arguments (the two-sum's
+// error is unique), so both lanes of a butterfly exchange get the same pair.
+__device__ __forceinline__ DF df_sum(const DF& a, const DF& b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  DF r;
+  r.hi = s;
+  r.lo = (a.lo + b.lo) + e;
+  return r;
+}
+
+// Pair sum over a warp (butterfly; every lane ends with the same pair).
+__device__ __forceinline__ DF warp_sum_df(DF a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF b;
+    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    a = df_sum(a, b);
+  }
+  return a;
+}
+
+// Pair sums over a block of NW warps, n at a time (red: n NW entries),
+// warps added in index order; the same in every thread. GB300's FP64 rate
+// is a small fraction of its FP32 rate: the reductions stay in fp32 pairs
+// and the caller converts the one result it needs to double.
+template <int NW, int n>
+__device__ __forceinline__ void block_sum_df(DF (&v)[n], float2* red) {
+#pragma unroll
+  for (int i = 0; i < n; ++i) v[i] = warp_sum_df(v[i]);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < n; ++i) red[n * (threadIdx.x >> 5) + i] = make_float2(v[i].hi, v[i].lo);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    DF s;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      DF p;
+      const float2 q = red[n * w + i];
+      p.hi = q.x;
+      p.lo = q.y;
+      s = df_sum(s, p);
+    }
+    v[i] = s;
+  }
+}
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return mbar_wait_for(bar, parity, kWaitTimeoutNs);
 }

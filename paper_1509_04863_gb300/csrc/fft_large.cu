@@ -690,7 +690,8 @@ __device__ __forceinline__ void chunk_range(int K, int nch, int h, int& i0, int&
 
 // Exact partial dot sum_{i0<=i<i1} t_i v(i) over the block: int64 for
 // integer data (t integral), else double-float pairs (DF) in a fixed order,
-// added across the block in fp64. Thread 0 gets it.
+// added across the block as pairs (warps in index order) and converted to
+// fp64 once. Thread 0 gets it.
 // The loads of eight terms per thread are in flight before any is used.
 template <class F>
 __device__ __forceinline__ long long block_dot(const float* t, int i0, int i1, bool exact, F v, double* rd,
@@ -715,7 +716,9 @@ __device__ __forceinline__ long long block_dot(const float* t, int i0, int i1, b
     }
   }
   if (exact) return block_red(ai, rl, OpAdd());
-  return __double_as_longlong(block_red(ad.value(), rd, OpAdd()));
+  DF s[1] = {ad};
+  block_sum_df<kLW>(s, reinterpret_cast<float2*>(rd));   // a double per warp holds a float2
+  return __double_as_longlong(s[0].value());
 }
 
 // Chunks per listed item: enough items for two waves of the launch's CTAs
@@ -737,7 +740,7 @@ __device__ __forceinline__ double warp_dot(const float* t, int K, bool exact, F 
   }
   DF a;
   for (int i = lane; i < K; i += 32) a.add_prod(__ldg(&t[i]), float(v(i)));
-  return warp_red(a.value(), OpAdd());
+  return warp_sum_df(a).value();
 }
 
 __device__ __forceinline__ float yval(const LQ& q, int j, int64_t k) {
