@@ -81,6 +81,15 @@ typedef enum { TM_MODE_AUTO = 0, TM_MODE_PAPER = 1, TM_MODE_EXPLICIT = 2 } tm_mo
  * intersects the three candidate sets. FFT lengths up to 16384; no
  * slices, no Thm. 2 sampling with it. */
 #define TM_THREE_MODULI 0x4u
+/* Plan flag (no counterpart in the paper; real signals only): the fold of
+ * step 3 cuts an fp16/fp32 signal into pieces of at least 256 KiB (at most
+ * 128 per signal) instead of at least 2 MiB (at most 64), one partial row
+ * of R1 M1 + R2 M2 fp32 sums per piece. A signal folded alone then spreads
+ * over up to 8x more CTAs (lower latency) at the price of more partial-sum
+ * traffic in large batches. The fp32 sums are added in another order, so
+ * results depend on the flag; with a given flag they do not depend on the
+ * rest of the batch. */
+#define TM_FINE_PIECES 0x8u
 
 /* tm_result.status values (low byte) and flag bits. */
 #define TM_FOUND 0      /* |S1 ∩ S2| = 1 */
@@ -363,7 +372,7 @@ typedef struct {
   int32_t n_streams;          /* iterations in flight, 1..4 (0: 2) */
   int32_t max_batch;          /* requests per iteration (0: 512) */
   int32_t queue_capacity;     /* pending requests before TM_EAGAIN (0: 65536) */
-  uint32_t flags;             /* reserved, 0 */
+  uint32_t flags;             /* TM_SERVE_FINE_PIECES or 0 */
   int64_t arena_bytes;        /* device workspace per stream (0: share of free memory) */
   int64_t hbm_reserve_bytes;  /* left free when arena_bytes is 0 (0: 4 GiB) */
   int64_t fold_cache_bytes;   /* fold cache (0: off): the folds of a resident signal
@@ -400,6 +409,10 @@ typedef struct {
    * iteration's completion event. */
   double queue_us, host_us, device_us;
 } tm_serve_stats;
+
+/* Server flag: every request is planned with TM_FINE_PIECES (real signals
+ * folded on more CTAs when an iteration holds few requests). */
+#define TM_SERVE_FINE_PIECES 0x1u
 
 /* Signal registration flag: x is device memory to use in place (the caller
  * keeps it alive until tm_serve_destroy); otherwise x is host memory and

@@ -23,6 +23,8 @@ TM_I8_PM1, TM_BITS_PM1, TM_F16, TM_F32 = range(4)
 TM_MODE_AUTO, TM_MODE_PAPER, TM_MODE_EXPLICIT = range(3)
 TM_ALLOW_AMBIG = 0x1
 TM_THM2_SAMPLING = 0x2
+TM_FINE_PIECES = 0x8
+TM_SERVE_FINE_PIECES = 0x1
 TM_THREE_MODULI = 0x4
 TM_FOUND, TM_EMPTY, TM_RESOLVED = 0, 1, 2
 TM_RF_FULL_RESCORE = 0x100
@@ -226,15 +228,15 @@ def tm_plan_create(N, K, xdtype="i8", mode="paper", M1=0, M2=0, allow_ambig=Fals
     return Plan(N, K, xdtype, mode, M1, M2, allow_ambig)
 
 
-def _plan_flags(allow_ambig=False, thm2=False, three=False) -> int:
+def _plan_flags(allow_ambig=False, thm2=False, three=False, fine_pieces=False) -> int:
     return (TM_ALLOW_AMBIG if allow_ambig else 0) | (TM_THM2_SAMPLING if thm2 else 0) | \
-        (TM_THREE_MODULI if three else 0)
+        (TM_THREE_MODULI if three else 0) | (TM_FINE_PIECES if fine_pieces else 0)
 
 
 def _query_struct(x_ptr, t_ptr, N, K, xdtype, mode, M1=0, M2=0, allow_ambig=False, thm2=False, three=False,
-                  M3=0) -> tm_query:
+                  M3=0, fine_pieces=False) -> tm_query:
     return tm_query(x_ptr, t_ptr, int(N), int(K), DTYPE_CODES[xdtype], MODE_CODES[mode], int(M1), int(M2),
-                    _plan_flags(allow_ambig, thm2, three), int(M3), 0)
+                    _plan_flags(allow_ambig, thm2, three, fine_pieces), int(M3), 0)
 
 
 def _event_ptr(ev):
@@ -249,7 +251,7 @@ class Batch:
 
     `specs` is a list of dicts with keys x (CUDA tensor or None for host-input
     batches), t (CUDA tensor or None), N, K, xdtype, mode, and optionally M1,
-    M2, allow_ambig."""
+    M2, allow_ambig, thm2, three, M3, fine_pieces."""
 
     def __init__(self, specs: Sequence[dict], keep_corr: bool = False, host_inputs: bool = False,
                  pipelined: bool = False):
@@ -261,7 +263,7 @@ class Batch:
             tp = s["t"].data_ptr() if s.get("t") is not None else None
             arr[i] = _query_struct(xp, tp, s["N"], s["K"], s.get("xdtype", "i8"), s.get("mode", "paper"),
                                    s.get("M1", 0), s.get("M2", 0), s.get("allow_ambig", False), s.get("thm2", False),
-                                   s.get("three", False), s.get("M3", 0))
+                                   s.get("three", False), s.get("M3", 0), s.get("fine_pieces", False))
         self._arr = arr
         flags = (TM_BATCH_KEEP_CORR if keep_corr else 0) | (TM_BATCH_HOST_INPUTS if host_inputs else 0) | \
             (TM_BATCH_PIPELINED if pipelined else 0)
@@ -462,10 +464,10 @@ class Server:
 
     def __init__(self, n_streams: int = 2, max_batch: int = 512, queue_capacity: int = 65536,
                  arena_bytes: int = 0, hbm_reserve_bytes: int = 0, fold_cache_bytes: int = 0,
-                 idle_spin_us: int = 0):
+                 idle_spin_us: int = 0, fine_pieces: bool = False):
         L = lib()
-        cfg = tm_serve_cfg(n_streams, max_batch, queue_capacity, 0, arena_bytes, hbm_reserve_bytes, fold_cache_bytes,
-                           idle_spin_us)
+        cfg = tm_serve_cfg(n_streams, max_batch, queue_capacity, TM_SERVE_FINE_PIECES if fine_pieces else 0,
+                           arena_bytes, hbm_reserve_bytes, fold_cache_bytes, idle_spin_us)
         h = C.c_void_p()
         _check(L.tm_serve_create(C.byref(cfg), C.byref(h)), "tm_serve_create")
         self._h = h

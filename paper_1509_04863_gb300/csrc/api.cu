@@ -338,6 +338,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
   b->ssum.clear();
   b->ssum_of.assign(n, -1);
   b->ssum_cols = 0;
+  std::vector<uint8_t> fine_of(size_t(n), 0);   // fold descriptor -> TM_FINE_PIECES
   int64_t part = 0;
   for (int32_t dt = TM_I8_PM1; dt <= TM_F32; ++dt) {
     tm_batch_s::FoldGroup gr;
@@ -352,6 +353,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
       if (p.xdtype != dt) continue;
       const int32_t pos = gr.first + gr.count++;
       b->fold_of[i] = pos;
+      fine_of[pos] = (p.flags & TM_FINE_PIECES) ? 1 : 0;
       const int64_t nb = ((nofold && nofold[i]) || p.direct) ? 0 : fold_bytes(p.xdtype, p.N);
       FoldQ& f = b->fq[pos];
       f = FoldQ{};
@@ -397,7 +399,7 @@ tm_status batch_plan(tm_batch_s* b, const tm_query* q, int32_t n, uint32_t flags
       for (int32_t k = gr.first; k < gr.first + gr.count; ++k) {
         FoldQ& f = b->fq[k];
         if (f.nbytes == 0) continue;
-        f.piece = fold_piece_bytes(f.nbytes);
+        f.piece = fold_piece_bytes(f.nbytes, fine_of[k] != 0);
         for (int64_t o = 0; o < f.nbytes; o += f.piece) bounds.push_back(f.goff + o);
       }
       bounds.push_back(W);

@@ -498,6 +498,7 @@ tm_status tm_serve_create(const tm_serve_cfg* cfg_in, tm_server_t* out) {
   if (cfg.max_batch <= 0) cfg.max_batch = 512;
   if (cfg.queue_capacity <= 0) cfg.queue_capacity = 65536;
   if (cfg.idle_spin_us < 0) return fail(TM_EINVAL, "idle_spin_us must be >= 0");
+  if (cfg.flags & ~TM_SERVE_FINE_PIECES) return fail(TM_EINVAL, "unknown server flag");
   if (cfg.hbm_reserve_bytes <= 0) cfg.hbm_reserve_bytes = int64_t(4) << 30;
   tm_server_t sv = new (std::nothrow) tm_server_s();
   if (!sv) return fail(TM_ENOMEM, "host allocation");
@@ -576,6 +577,7 @@ tm_status build_request(tm_server_t sv, int32_t sig_id, const float* t_host, int
                         int32_t M2, uint32_t plan_flags, uint64_t tag, Req& r) {
   if (!t_host) return fail(TM_EINVAL, "null template");
   if (K < 1) return fail(TM_EINVAL, "empty template");
+  if (sv->cfg.flags & TM_SERVE_FINE_PIECES) plan_flags |= TM_FINE_PIECES;
   r.tag = tag;
   r.sig = sig_id;
   Signal sg;

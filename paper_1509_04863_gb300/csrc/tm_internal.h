@@ -138,10 +138,11 @@ inline void fold_args_first_queries(FoldArgs& a, const FoldQ* hq) {
 // Piece size of a real signal of `bytes` bytes: at least 2 MiB, at most 64
 // pieces, a multiple of 64 KiB (so that every stage of the fold's ring lies
 // inside one piece). Depends on the signal alone.
-inline int64_t fold_piece_bytes(int64_t bytes) {
+inline int64_t fold_piece_bytes(int64_t bytes, bool fine = false) {
   const int64_t unit = 65536;
-  const int64_t per = ((bytes + 63) / 64 + unit - 1) / unit * unit;
-  return per > (int64_t(2) << 20) ? per : (int64_t(2) << 20);
+  const int64_t most = fine ? 128 : 64, least = fine ? (int64_t(256) << 10) : (int64_t(2) << 20);
+  const int64_t per = ((bytes + most - 1) / most + unit - 1) / unit * unit;
+  return per > least ? per : least;
 }
 
 // ---------------------------------------------------------------- correlation kernel (steps 3-9)

@@ -54,9 +54,9 @@ def _standalone(tm, q, x_dev):
 SIGNALS = [((1 << 20) + 3, "i8"), (1 << 20, "bits"), ((1 << 19) + 1, "f32"), ((1 << 18) + 5, "f16")]
 
 
-@pytest.mark.parametrize("spin", [0, 200], ids=["sleep", "idle_spin"])
-def test_server_matches_standalone(tm, spin):
-    srv = tm.Server(n_streams=2, max_batch=32, arena_bytes=1 << 30, idle_spin_us=spin)
+@pytest.mark.parametrize("spin,fine", [(0, False), (200, False), (0, True)], ids=["sleep", "idle_spin", "fine_pieces"])
+def test_server_matches_standalone(tm, spin, fine):
+    srv = tm.Server(n_streams=2, max_batch=32, arena_bytes=1 << 30, idle_spin_us=spin, fine_pieces=fine)
     sigs, xs = [], []
     for k, (N, dt) in enumerate(SIGNALS):
         base = W.planted_query(9000 + k, N, 512, dt, mode="auto")

@@ -88,3 +88,28 @@ def test_correlate_twice_on_one_fold(tm):
     res = [tm.decode_results(o)[0] for o in outs]
     assert res[0] == res[1] == res[2]
     assert res[0]["shift"] == O.match_query(q)["shift"]
+
+
+def test_fine_pieces_real(tm):
+    """TM_FINE_PIECES: a 16 MiB fp32 signal in 64 pieces of 256 KiB (8 of
+    2 MiB without the flag): within the bars of the oracle, and the same
+    alone and among other signals with the flag, bit for bit."""
+    N, K = 1 << 22, 2048
+    mk = lambda s: W.planted_query(s, N, K, "f32", t_sigma=0.3, mode="paper")
+    q = mk(4400)
+    spec = dict(_spec(q), fine_pieces=True)
+    b1 = tm.Batch([spec], keep_corr=True)
+    out = tm.result_buffer(1)
+    b1.run(out)
+    torch.cuda.synchronize()
+    assert b1.device_error() == 0
+    r1 = tm.decode_results(out)[0]
+    check_real(b1, 0, q, r1, O.match_query(q))
+    others = [dict(_spec(mk(4500 + s)), fine_pieces=True) for s in range(6)]
+    bb = tm.Batch(others[:3] + [spec] + others[3:], keep_corr=True)
+    outb = tm.result_buffer(len(others) + 1)
+    bb.run(outb)
+    torch.cuda.synchronize()
+    assert bb.device_error() == 0
+    assert tm.decode_results(outb)[3] == r1
+    assert torch.equal(b1.folds(0).cpu(), bb.folds(3).cpu())
