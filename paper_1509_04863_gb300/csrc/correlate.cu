@@ -453,6 +453,57 @@ __device__ void collect_candidates(Cands& cs, int mj, int M, float delta, RFn rv
   __syncthreads();
 }
 
+// Step 7 for moduli 0 and 1 together (rv0, rv1 as above): one pass over
+// the columns for both maxima, one for both candidate lists, half the
+// barriers of two collect_candidates calls. The same lists in the same
+// order of discovery per modulus is not guaranteed (atomic slots), as
+// with collect_candidates; the rescoring takes the exact maximum with the
+// smallest index whatever the order.
+template <class RFn0, class RFn1>
+__device__ void collect_candidates2(Cands& cs, int M0, int M1, float delta, RFn0 rv0, RFn1 rv1) {
+  __shared__ float redv[2 * kWarps];
+  __shared__ int redi[2 * kWarps];
+  const int tid = threadIdx.x;
+  float bv0 = -INFINITY, bv1 = -INFINITY;
+  int bi0 = 0x7fffffff, bi1 = 0x7fffffff;
+  const int Mx = max(M0, M1);
+  for (int k = tid; k < Mx; k += kCorrThreads) {
+    if (k < M0) better(bv0, bi0, rv0(k), k);
+    if (k < M1) better(bv1, bi1, rv1(k), k);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    better(bv0, bi0, __shfl_xor_sync(0xffffffffu, bv0, o), __shfl_xor_sync(0xffffffffu, bi0, o));
+    better(bv1, bi1, __shfl_xor_sync(0xffffffffu, bv1, o), __shfl_xor_sync(0xffffffffu, bi1, o));
+  }
+  __syncthreads();
+  if ((tid & 31) == 0) {
+    redv[tid >> 5] = bv0; redi[tid >> 5] = bi0;
+    redv[kWarps + (tid >> 5)] = bv1; redi[kWarps + (tid >> 5)] = bi1;
+  }
+  if (tid == 0) { cs.ncand[0] = 0; cs.ncand[1] = 0; }
+  __syncthreads();
+  bv0 = redv[0]; bi0 = redi[0];
+  bv1 = redv[kWarps]; bi1 = redi[kWarps];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) {
+    better(bv0, bi0, redv[w], redi[w]);
+    better(bv1, bi1, redv[kWarps + w], redi[kWarps + w]);
+  }
+  const float thr0 = bv0 - 2.0f * delta, thr1 = bv1 - 2.0f * delta;
+  for (int k = tid; k < Mx; k += kCorrThreads) {
+    if (k < M0 && rv0(k) >= thr0) {
+      const int c = atomicAdd(&cs.ncand[0], 1);
+      if (c < kCandCap) cs.cand[0][c] = k;
+    }
+    if (k < M1 && rv1(k) >= thr1) {
+      const int c = atomicAdd(&cs.ncand[1], 1);
+      if (c < kCandCap) cs.cand[1][c] = k;
+    }
+  }
+  __syncthreads();
+}
+
 // Steps 7-9 after the candidates of every modulus are collected: exact
 // rescoring of each candidate from the exported folds (the chosen index is
 // the exact argmax), the closed-form intersection of the candidate sets
@@ -801,8 +852,24 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       ib[2 * pad_idx(k) + 1] = yin[P + k];
     }
   } else {
-    for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
-    __syncthreads();
+    // +-1 signals whose moduli in this pass all have R = 1: the slots are
+    // summed and turned into fold values in one pass over the columns,
+    // which writes every entry k < M_j (no zeroing of them first)
+    const int ma = pass == 0 ? 0 : 2, mb = pass == 0 ? 1 : -1;   // moduli in complex slots 0, 1
+    const bool fused = ints && Q.y_core == nullptr && Q.R[ma] == 1 && (mb < 0 || Q.R[mb] == 1);
+    if (fused) {
+      // zero what no fold value writes: k >= M_j (the extension then
+      // overwrites [M_j, M_j + K - 1) after a barrier), all of a slot
+      // without a modulus
+      const int Ma = Q.M[ma], Mb = mb >= 0 ? Q.M[mb] : 0;
+      for (int k = tid; k < P; k += kCorrThreads) {
+        if (k >= Ma) ib[2 * pad_idx(k)] = 0;
+        if (k >= Mb) ib[2 * pad_idx(k) + 1] = 0;
+      }
+    } else {
+      for (int k = tid; k < npad; k += kCorrThreads) sbuf[k] = make_float2(0.f, 0.f);
+      __syncthreads();
+    }
     if (Q.y_core != nullptr) {
       // the folds over k < M_j from a cache of this signal's folds (int32 or
       // float bits alike)
@@ -811,6 +878,63 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
         const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);
         if (mj < 0) continue;
         for (int k = tid; k < Q.M[mj]; k += kCorrThreads) ib[2 * pad_idx(k) + j] = yc[int64_t(mj) * Q.core_pitch + k];
+      }
+    } else if (fused) {
+      // column k of the M-fold: its slot counts c (of -1 entries for int8,
+      // +1 entries for bits) over the nk rows that reach it give the fold
+      // value nk - 2c (int8) or 2c - nk (bits); k >= Rw (the last row is
+      // short) also takes the wrap-around entry x_{k-Rw}. Slot rows are
+      // padded to 16 columns, so a quad read at k < M stays inside the row.
+      const bool ones = Q.xdtype == TM_BITS_PM1;
+      for (int j = 0; j < 2; ++j) {
+        const int mj = j == 0 ? ma : mb;
+        if (mj < 0) continue;
+        const int M = Q.M[mj];
+        const int L = int(Q.L[mj]);
+        const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
+        const int32_t* part = a.partial + Q.part + Q.moff[mj];
+        const int nq4 = (M + 3) >> 2;
+        with_sig(Q.xdtype, Q.x, [&](auto sx) {
+          for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
+            float xw[4][4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int k = 4 * (q0 + b * kCorrThreads) + i;
+                xw[b][i] = (k < M && k >= Rw && !Q.thm2) ? sx.val(k - Rw) : 0.f;
+              }
+            int4 c[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) c[b] = make_int4(0, 0, 0, 0);
+#pragma unroll 2
+            for (int sl = 0; sl < Q.nslots; ++sl) {
+              const int32_t* ps = part + int64_t(sl) * Q.stride;
+              int4 v[4];
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                const int q = q0 + b * kCorrThreads;
+                v[b] = q < nq4 ? __ldg(reinterpret_cast<const int4*>(ps) + q) : make_int4(0, 0, 0, 0);
+              }
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                c[b].x += v[b].x; c[b].y += v[b].y; c[b].z += v[b].z; c[b].w += v[b].w;
+              }
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const int cc[4] = {c[b].x, c[b].y, c[b].z, c[b].w};
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int k = 4 * (q0 + b * kCorrThreads) + i;
+                if (k < M) {
+                  const int nk = L - 1 + (k < Rw ? 1 : 0);
+                  ib[2 * pad_idx(k) + j] = (ones ? 2 * cc[i] - nk : nk - 2 * cc[i]) + int(xw[b][i]);
+                }
+              }
+            }
+          }
+        });
       }
     } else if (ints) {
       // Partial slots hold counts of -1 (int8) or +1 (bits) entries per column
@@ -1061,8 +1185,8 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   // Rounding bound on every r_j (fft_corr_error_bound, one product term).
   const float delta = fft_corr_error_bound(logP, t2, Tp, Zc, z2, 1);
   if (pass == 0) {
-    collect_candidates(cands, 0, Q.M[0], delta, [&](int k) { return sbuf[pad_idx(k)].x * invP; });
-    collect_candidates(cands, 1, Q.M[1], delta, [&](int k) { return -sbuf[pad_idx(k)].y * invP; });
+    collect_candidates2(cands, Q.M[0], Q.M[1], delta, [&](int k) { return sbuf[pad_idx(k)].x * invP; },
+                        [&](int k) { return -sbuf[pad_idx(k)].y * invP; });
   } else {
     collect_candidates(cands, 2, Q.M[2], delta, [&](int k) { return sbuf[pad_idx(k)].x * invP; });
   }
