@@ -776,9 +776,17 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   float2* stw = reinterpret_cast<float2*>(reinterpret_cast<char*>(sbuf) + a.smem_bytes) - kPassTw;
 
   // ------------------------------------------------ twiddles, a. template spectrum
-  // Twiddles, pass tables and the template are independent loads; each
-  // loop issues a batch of them before storing any.
+  // Twiddles, pass tables and the template are independent loads: the
+  // template's (this thread's entries k = tid + b 512, kept in registers)
+  // go out first, then the twiddles' in batches, before any is stored.
   constexpr int kTB = 8;
+  constexpr int kTper = (NBMAX == 1 ? kPMax / 2 : kPMax) / kCorrThreads;   // P / 512 at most
+  float tv[kTper];
+#pragma unroll
+  for (int b = 0; b < kTper; ++b) {
+    const int k = tid + b * kCorrThreads;
+    tv[b] = k < K ? __ldg(&t[k]) : 0.f;
+  }
   if (logP != loaded_logP) {
     loaded_logP = logP;
     const int stride = kPMax >> logP;
@@ -798,21 +806,13 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   float t1 = 0.f, t2 = 0.f;
   int tint = 1;
   // the padded template (the padding slots of sbuf are never read)
-  for (int k0 = tid; k0 < P; k0 += kTB * kCorrThreads) {
-    float v[kTB];
 #pragma unroll
-    for (int b = 0; b < kTB; ++b) {
-      const int k = k0 + b * kCorrThreads;
-      v[b] = k < K ? __ldg(&t[k]) : 0.f;
-    }
-#pragma unroll
-    for (int b = 0; b < kTB; ++b) {
-      const int k = k0 + b * kCorrThreads;
-      if (k < P) sbuf[pad_idx(k)] = make_float2(v[b], 0.f);
-      t1 += fabsf(v[b]);
-      t2 = fmaf(v[b], v[b], t2);
-      tint &= (v[b] == rintf(v[b]) && fabsf(v[b]) <= 1048576.f) ? 1 : 0;
-    }
+  for (int b = 0; b < kTper; ++b) {
+    const int k = tid + b * kCorrThreads;
+    if (k < P) sbuf[pad_idx(k)] = make_float2(tv[b], 0.f);
+    t1 += fabsf(tv[b]);
+    t2 = fmaf(tv[b], tv[b], t2);
+    tint &= (tv[b] == rintf(tv[b]) && fabsf(tv[b]) <= 1048576.f) ? 1 : 0;
   }
   block_sum2_and(t1, t2, tint, redf, redi);
   t2 = sqrtf(t2);

@@ -85,3 +85,42 @@ def test_noalloc_equals_tm_match_twice(tm, specs, xdtype, thm2):
             for key in ("r1", "r2", "score"):
                 assert _close(r_got[key], r_ref[key], tol), (key, r_got[key], r_ref[key])
         p.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_captured_in_a_graph(tm):
+    """A call captured into a CUDA graph (after a first call outside any
+    capture) replays correctly: its descriptors travel as kernel
+    parameters, so the graph holds no pointer to a host stack frame.
+    Replaying after the captured buffers are refilled with another query
+    of the same shape gives that query's result."""
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    N, K = (1 << 20) + 16, 2048   # a fold with 16 rows of shares: the slot sums are captured too
+    qa = W.planted_query(81, N, K, "i8", flip_p=0.05, mode="auto")
+    qb = W.planted_query(82, N, K, "i8", flip_p=0.05, mode="auto")
+    x = torch.from_numpy(qa.x).cuda()
+    t = torch.from_numpy(qa.t).cuda()
+    out = tm.result_buffer(1)
+    tm.tm_match_noalloc(x, t, out, N=N, K=K, xdtype="i8", mode="auto")   # first call: set-up outside capture
+    torch.cuda.synchronize()
+    want_a = tm.decode_results(out)[0]
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        tm.tm_match_noalloc(x, t, out, N=N, K=K, xdtype="i8", mode="auto", stream=s)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert tm.decode_results(out)[0] == want_a
+    # the same graph on another query's data in the captured buffers
+    ref_b = tm.result_buffer(1)
+    xb = torch.from_numpy(qb.x).cuda()
+    tb = torch.from_numpy(qb.t).cuda()
+    tm.tm_match_noalloc(xb, tb, ref_b, N=N, K=K, xdtype="i8", mode="auto")
+    torch.cuda.synchronize()
+    x.copy_(xb)
+    t.copy_(tb)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert tm.decode_results(out)[0] == tm.decode_results(ref_b)[0]
