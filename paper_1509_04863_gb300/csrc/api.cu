@@ -670,8 +670,20 @@ tm_status batch_correlate(tm_batch_t b, tm_result* out, cudaStream_t s, int pari
     TM_CUDA(launch_slot_sums(sa, s));
   }
   a.pdl = pdl ? 1 : 0;
+  if (after_fold && a.nq == 1 && a.ctas == 0) {
+    // one query on this launch: its descriptor goes as a kernel parameter,
+    // unless a graph is being captured (later tm_batch_set_inputs calls
+    // must reach the replays through the device copy)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    TM_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      a.lone = b->order[0];
+      a.q1 = b->cq[a.lone];
+    }
+  }
   if (a.nq > 0) TM_CUDA(launch_correlate(a, b->maxP, s));
   a.pdl = 0;
+  a.lone = -1;
   a.ctas = 0;
   a.first = 0;
   if (b->n_blocked > 0) {
@@ -1508,6 +1520,8 @@ extern "C" tm_status tm_match_noalloc(const tm_plan_desc* desc, const void* x, c
   ca.out = out;
   ca.err = err;
   ca.pdl = 1;   // after a kernel of this call (descriptors, fold or slot sums)
+  ca.lone = 0;  // the descriptor as a kernel parameter too
+  ca.q1 = c;
   TM_CUDA(launch_correlate(ca, p.P, s));
   return TM_OK;
 }

@@ -750,7 +750,9 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   // run time: a per-thread copy would sit in local memory)
   __shared__ CorrQ sQ;
   __syncthreads();   // the previous query's readers are done
-  if (tid < int(sizeof(CorrQ) / 4)) reinterpret_cast<int*>(&sQ)[tid] = reinterpret_cast<const int*>(a.q + qi)[tid];
+  if (tid < int(sizeof(CorrQ) / 4))
+    reinterpret_cast<int*>(&sQ)[tid] = a.lone >= 0 ? reinterpret_cast<const int*>(&a.q1)[tid]
+                                                    : reinterpret_cast<const int*>(a.q + qi)[tid];
   __syncthreads();
   const CorrQ& Q = sQ;
   const int P = Q.P, logP = Q.logP, K = Q.K;
@@ -1210,7 +1212,7 @@ template <int NBMAX>
 __global__ void __launch_bounds__(kCorrThreads, 1) corr_kernel(const CorrArgs a) {
   extern __shared__ __align__(16) float2 sbuf[];
   int loaded_logP = -1;
-  corr_query<NBMAX>(a, a.order[a.first + blockIdx.x], sbuf, loaded_logP);
+  corr_query<NBMAX>(a, a.lone >= 0 ? a.lone : a.order[a.first + blockIdx.x], sbuf, loaded_logP);
 }
 
 // ---------------------------------------------------------------- blocked correlation

@@ -270,9 +270,10 @@ tm_status launch_iteration(tm_server_t sv, Slot& sl) {
   TM_CUDA(cudaMemcpyAsync(sl.arena, h, up, cudaMemcpyHostToDevice, sl.s));
   st = batch_fold(sl.b, sl.s, 0, false);   // the copy cleared the error word
   if (st != TM_OK) return st;
-  st = batch_correlate(sl.b, sl.b->d_out, sl.s, 0, true);
+  // results straight into the pinned host array (mapped: the same address
+  // on the device), read once the iteration's event has completed
+  st = batch_correlate(sl.b, sl.h_out, sl.s, 0, true);
   if (st != TM_OK) return st;
-  TM_CUDA(cudaMemcpyAsync(sl.h_out, sl.b->d_out, size_t(n) * sizeof(tm_result), cudaMemcpyDeviceToHost, sl.s));
   TM_CUDA(cudaEventRecord(sl.ev, sl.s));
   if (cache_on) {
     sl.hits.clear();

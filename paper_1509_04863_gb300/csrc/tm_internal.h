@@ -202,6 +202,10 @@ struct CorrArgs {
   int32_t pdl = 0;        // programmatic dependent of the kernel before it in the stream
                           // (a fold or the slot sums): the template spectrum runs
                           // before that kernel has finished (one wave only)
+  int32_t lone = -1;      // >= 0: a launch of this one query, whose descriptor is q1
+                          // (no dependent global loads of order and descriptor ahead
+                          // of its work); launchers that a graph may capture leave it -1
+  CorrQ q1;
 };
 
 // Launch configuration with the programmatic stream-serialisation attribute
