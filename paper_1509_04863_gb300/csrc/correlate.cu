@@ -854,11 +854,11 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       ib[2 * pad_idx(k) + 1] = yin[P + k];
     }
   } else {
-    // +-1 signals whose moduli in this pass all have R = 1: the slots are
-    // summed and turned into fold values in one pass over the columns,
-    // which writes every entry k < M_j (no zeroing of them first)
+    // +-1 signals: the slots are summed and turned into fold values in one
+    // pass over the columns, which writes every entry k < M_j (no zeroing
+    // of them first)
     const int ma = pass == 0 ? 0 : 2, mb = pass == 0 ? 1 : -1;   // moduli in complex slots 0, 1
-    const bool fused = ints && Q.y_core == nullptr && Q.R[ma] == 1 && (mb < 0 || Q.R[mb] == 1);
+    const bool fused = ints && Q.y_core == nullptr;
     if (fused) {
       // zero what no fold value writes: k >= M_j (the extension then
       // overwrites [M_j, M_j + K - 1) after a barrier), all of a slot
@@ -891,128 +891,99 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       for (int j = 0; j < 2; ++j) {
         const int mj = j == 0 ? ma : mb;
         if (mj < 0) continue;
-        const int M = Q.M[mj];
+        const int M = Q.M[mj], Rr = Q.R[mj];
         const int L = int(Q.L[mj]);
         const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
         const int32_t* part = a.partial + Q.part + Q.moff[mj];
         const int nq4 = (M + 3) >> 2;
-        with_sig(Q.xdtype, Q.x, [&](auto sx) {
-          for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
-            float xw[4][4];
+        if (Rr == 1) {
+          with_sig(Q.xdtype, Q.x, [&](auto sx) {
+            for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
+              float xw[4][4];
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
+              for (int b = 0; b < 4; ++b)
 #pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const int k = 4 * (q0 + b * kCorrThreads) + i;
-                xw[b][i] = (k < M && k >= Rw && !Q.thm2) ? sx.val(k - Rw) : 0.f;
-              }
-            int4 c[4];
+                for (int i = 0; i < 4; ++i) {
+                  const int k = 4 * (q0 + b * kCorrThreads) + i;
+                  xw[b][i] = (k < M && k >= Rw && !Q.thm2) ? sx.val(k - Rw) : 0.f;
+                }
+              int4 c[4];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) c[b] = make_int4(0, 0, 0, 0);
+              for (int b = 0; b < 4; ++b) c[b] = make_int4(0, 0, 0, 0);
 #pragma unroll 2
-            for (int sl = 0; sl < Q.nslots; ++sl) {
-              const int32_t* ps = part + int64_t(sl) * Q.stride;
-              int4 v[4];
+              for (int sl = 0; sl < Q.nslots; ++sl) {
+                const int32_t* ps = part + int64_t(sl) * Q.stride;
+                int4 v[4];
 #pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                const int q = q0 + b * kCorrThreads;
-                v[b] = q < nq4 ? __ldg(reinterpret_cast<const int4*>(ps) + q) : make_int4(0, 0, 0, 0);
+                for (int b = 0; b < 4; ++b) {
+                  const int q = q0 + b * kCorrThreads;
+                  v[b] = q < nq4 ? __ldg(reinterpret_cast<const int4*>(ps) + q) : make_int4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                  c[b].x += v[b].x; c[b].y += v[b].y; c[b].z += v[b].z; c[b].w += v[b].w;
+                }
               }
 #pragma unroll
               for (int b = 0; b < 4; ++b) {
-                c[b].x += v[b].x; c[b].y += v[b].y; c[b].z += v[b].z; c[b].w += v[b].w;
-              }
-            }
+                const int cc[4] = {c[b].x, c[b].y, c[b].z, c[b].w};
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const int cc[4] = {c[b].x, c[b].y, c[b].z, c[b].w};
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const int k = 4 * (q0 + b * kCorrThreads) + i;
-                if (k < M) {
-                  const int nk = L - 1 + (k < Rw ? 1 : 0);
-                  ib[2 * pad_idx(k) + j] = (ones ? 2 * cc[i] - nk : nk - 2 * cc[i]) + int(xw[b][i]);
+                for (int i = 0; i < 4; ++i) {
+                  const int k = 4 * (q0 + b * kCorrThreads) + i;
+                  if (k < M) {
+                    const int nk = L - 1 + (k < Rw ? 1 : 0);
+                    ib[2 * pad_idx(k) + j] = (ones ? 2 * cc[i] - nk : nk - 2 * cc[i]) + int(xw[b][i]);
+                  }
                 }
               }
             }
-          }
-        });
-      }
-    } else if (ints) {
-      // Partial slots hold counts of -1 (int8) or +1 (bits) entries per column
-      // kp < Mp of the Mp-fold; column k of the M-fold gathers kp = k + r M,
-      // r < R. Slot rows are padded to 16 columns, so a quad read at kp < Mp
-      // stays inside the row; columns past Mp are dropped.
-      for (int j = 0; j < 2; ++j) {
-      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
-      if (mj < 0) continue;
-        const int M = Q.M[mj], Rr = Q.R[mj], Mp = Rr * M;
-        const int32_t* part = a.partial + Q.part + Q.moff[mj];
-        const int nq4 = (Mp + 3) >> 2;
-        for (int q0 = tid; q0 < nq4; q0 += 4 * kCorrThreads) {
-          int4 c[4];
+          });
+        } else {
+          // column k gathers the counts at k + r M, r < R, of every slot:
+          // kC columns per thread, their (slot, replica) terms eight at a
+          // time, all loads of a batch issued before any is added (no
+          // shared-memory atomics on the R replicas of a column)
+          constexpr int kC = 4, kT = 8;
+          const int nt = Q.nslots * Rr;
+          with_sig(Q.xdtype, Q.x, [&](auto sx) {
+            for (int k0 = tid; k0 < M; k0 += kC * kCorrThreads) {
+              float xw[kC];
+              int c[kC];
 #pragma unroll
-          for (int b = 0; b < 4; ++b) c[b] = make_int4(0, 0, 0, 0);
-#pragma unroll 2
-          for (int sl = 0; sl < Q.nslots; ++sl) {
-            const int32_t* ps = part + int64_t(sl) * Q.stride;
-            int4 v[4];
+              for (int b = 0; b < kC; ++b) {
+                const int k = k0 + b * kCorrThreads;
+                xw[b] = (k < M && k >= Rw && !Q.thm2) ? sx.val(k - Rw) : 0.f;
+                c[b] = 0;
+              }
+              int sl = 0, r = 0;
+              for (int t0 = 0; t0 < nt; t0 += kT) {
+                int v[kT][kC];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const int q = q0 + b * kCorrThreads;
-              v[b] = q < nq4 ? __ldg(reinterpret_cast<const int4*>(ps) + q) : make_int4(0, 0, 0, 0);
-            }
+                for (int u = 0; u < kT; ++u) {
+                  const int32_t* ps = part + int64_t(sl) * Q.stride + r * M;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              c[b].x += v[b].x; c[b].y += v[b].y; c[b].z += v[b].z; c[b].w += v[b].w;
-            }
-          }
+                  for (int b = 0; b < kC; ++b) {
+                    const int k = k0 + b * kCorrThreads;
+                    v[u][b] = (t0 + u < nt && k < M) ? __ldg(&ps[k]) : 0;
+                  }
+                  if (++r == Rr) { r = 0; ++sl; }
+                }
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int k0 = 4 * (q0 + b * kCorrThreads);
-            const int cc[4] = {c[b].x, c[b].y, c[b].z, c[b].w};
+                for (int u = 0; u < kT; ++u)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int kp = k0 + i;
-              if (kp < Mp && cc[i] != 0) {
-                const int e = 2 * pad_idx(Rr == 1 ? kp : kp % M) + j;
-                if (Rr == 1) ib[e] = cc[i];
-                else atomicAdd(&ib[e], cc[i]);
+                  for (int b = 0; b < kC; ++b) c[b] += v[u][b];
+              }
+#pragma unroll
+              for (int b = 0; b < kC; ++b) {
+                const int k = k0 + b * kCorrThreads;
+                if (k < M) {
+                  const int nk = L - 1 + (k < Rw ? 1 : 0);
+                  ib[2 * pad_idx(k) + j] = (ones ? 2 * c[b] - nk : nk - 2 * c[b]) + int(xw[b]);
+                }
               }
             }
-          }
+          });
         }
-      }
-      __syncthreads();
-      // counts -> fold values; column k >= Rw (the last row is short) also
-      // takes the wrap-around entry x_{k-Rw}
-      const bool ones = Q.xdtype == TM_BITS_PM1;   // bit-packed slots count +1 entries, int8 slots -1 entries
-      for (int j = 0; j < 2; ++j) {
-      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
-      if (mj < 0) continue;
-        const int M = Q.M[mj];
-        const int L = int(Q.L[mj]);
-        const int Rw = int(N - int64_t(L - 1) * M);   // length of the last (partial) row, 1..M
-        with_sig(Q.xdtype, Q.x, [&](auto sx) {
-          for (int k0 = tid; k0 < M; k0 += kB * kCorrThreads) {
-            float xv[kB];
-#pragma unroll
-            for (int b = 0; b < kB; ++b) {
-              const int k = k0 + b * kCorrThreads;
-              xv[b] = (k < M && k >= Rw && !Q.thm2) ? sx.val(k - Rw) : 0.f;
-            }
-#pragma unroll
-            for (int b = 0; b < kB; ++b) {
-              const int k = k0 + b * kCorrThreads;
-              if (k < M) {
-                // entries n < N with n = k (mod M): L of them for k < Rw, else L-1
-                const int e = 2 * pad_idx(k) + j;
-                const int nk = L - 1 + (k < Rw ? 1 : 0);
-                ib[e] = (ones ? 2 * ib[e] - nk : nk - 2 * ib[e]) + int(xv[b]);
-              }
-            }
-          }
-        });
       }
     } else {
       // partial slots hold fp32 column sums, added in a fixed order
