@@ -171,11 +171,14 @@ __device__ void build_pass_twiddles(float2* stw, int logP, const float2* __restr
 // natural order); tw holds W_P^m for m < P/2, stw the pass tables of
 // build_pass_twiddles. Each thread holds NBMAX x 16 points per pass.
 template <int NBMAX>
-__device__ __forceinline__ void fft(float2* buf, int logP, const float2* tw, const float2* stw) {
+__device__ __forceinline__ void fft(float2* buf, int logP, const float2* tw, const float2* stw,
+                                    bool skip_first = false) {
   const int P = 1 << logP;
   int logNs = 0;
   const int first = pass_first(logP);
-  if (first) {
+  if (first && skip_first) {
+    logNs = first;   // done by first_pass_regs
+  } else if (first) {
     const int twshift = logP - first;
     if (first == 1) fft_pass<2, NBMAX>(buf, P, 1, twshift, tw, nullptr);
     else if (first == 2) fft_pass<4, NBMAX>(buf, P, 1, twshift, tw, nullptr);
@@ -190,6 +193,36 @@ __device__ __forceinline__ void fft(float2* buf, int logP, const float2* tw, con
     if (!last && Ns > 1) off += 15 * Ns;
     logNs += 4;
   }
+}
+
+// The first pass of fft() for P = 8192 (radix 2) or 16384 (radix 4), whose
+// sub-transforms have length 1 (no twiddles), from registers: the thread
+// holds x[b] = the input at k = tid + 512 b, and since P / R0 = 8 x 512,
+// butterfly j = tid + 512 b takes the inputs j + r P / R0 = x[b + 8 r] of
+// the same thread. Writes buf (padded) exactly as fft_pass<R0> with Ns = 1;
+// the caller orders the writes (barrier) before fft(..., skip_first).
+__device__ __forceinline__ bool first_pass_in_regs(int logP) { return logP == 13 || logP == 14; }
+
+template <int R0, int NV>
+__device__ __forceinline__ void first_pass_regs_r(float2* buf, const float2 (&x)[NV]) {
+  constexpr int per = 8;   // butterflies per thread: P / R0 / 512
+  static_assert(R0 * per <= NV, "inputs of the thread's butterflies");
+#pragma unroll
+  for (int b = 0; b < per; ++b) {
+    float2 v[R0];
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[r] = x[b + r * per];
+    dft<R0>(v);
+    const int j = threadIdx.x + b * kCorrThreads;
+#pragma unroll
+    for (int r = 0; r < R0; ++r) buf[pad_idx(j * R0 + r)] = v[bitrev<R0>(r)];
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void first_pass_regs(float2* buf, int logP, const float2 (&x)[NV]) {
+  if (logP == 13) first_pass_regs_r<2>(buf, x);
+  else if constexpr (NV >= 32) first_pass_regs_r<4>(buf, x);
 }
 
 // ---------------------------------------------------------------- block reductions
@@ -807,19 +840,31 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   }
   float t1 = 0.f, t2 = 0.f;
   int tint = 1;
-  // the padded template (the padding slots of sbuf are never read)
+  // the padded template (the padding slots of sbuf are never read), or for
+  // P = 8192 and 16384 the FFT's first pass of it
 #pragma unroll
   for (int b = 0; b < kTper; ++b) {
-    const int k = tid + b * kCorrThreads;
-    if (k < P) sbuf[pad_idx(k)] = make_float2(tv[b], 0.f);
     t1 += fabsf(tv[b]);
     t2 = fmaf(tv[b], tv[b], t2);
     tint &= (tv[b] == rintf(tv[b]) && fabsf(tv[b]) <= 1048576.f) ? 1 : 0;
   }
-  block_sum2_and(t1, t2, tint, redf, redi);
+  const bool fuse_t = first_pass_in_regs(logP);
+  if (fuse_t) {
+    float2 x[kTper];
+#pragma unroll
+    for (int b = 0; b < kTper; ++b) x[b] = make_float2(tv[b], 0.f);
+    first_pass_regs(sbuf, logP, x);
+  } else {
+#pragma unroll
+    for (int b = 0; b < kTper; ++b) {
+      const int k = tid + b * kCorrThreads;
+      if (k < P) sbuf[pad_idx(k)] = make_float2(tv[b], 0.f);
+    }
+  }
+  block_sum2_and(t1, t2, tint, redf, redi);   // also orders the writes above
   t2 = sqrtf(t2);
   const bool t_integral = tint != 0;
-  fft<NBMAX>(sbuf, logP, tw, stw);
+  fft<NBMAX>(sbuf, logP, tw, stw, fuse_t);
   // the spectrum stays in shared memory when the launch left room for it
   float2* spec = (npad + halfP + P + kPassTw) * int(sizeof(float2)) <= a.smem_bytes ? tw + halfP
                                                                                    : a.spec + Q.spec_off;
@@ -1102,46 +1147,99 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
   // signals; fp32 sums for reals)
   float z2 = 0.f;
   int maxy = 0;
+  // P = 8192 (one radix-16 butterfly per thread and pass): z and, below,
+  // T conj(Z) are kept in registers and written as the FFT's first pass
+  constexpr int kZper = kPMax / 2 / kCorrThreads;   // 16
+  const bool fuse_z = NBMAX == 1 && logP == 13;
+  float2 zr[kZper];
   if (ints) {
     long long s2 = 0;
     int32_t* yi = static_cast<int32_t*>(a.y) + Q.y_off;
-    for (int k = tid; k < P; k += kCorrThreads) {
-      const int e = 2 * pad_idx(k);
-      const int v0 = ib[e], v1 = ib[e + 1];
-      if (Q.y_in == nullptr) {
-        yi[(pass == 0 ? 0 : 2) * P + k] = v0;
-        if (pass == 0) yi[P + k] = v1;
+    if (fuse_z) {
+#pragma unroll
+      for (int b = 0; b < kZper; ++b) {
+        const int k = tid + b * kCorrThreads;
+        const int e = 2 * pad_idx(k);
+        const int v0 = ib[e], v1 = ib[e + 1];
+        if (Q.y_in == nullptr) {
+          yi[(pass == 0 ? 0 : 2) * P + k] = v0;
+          if (pass == 0) yi[P + k] = v1;
+        }
+        zr[b] = make_float2(float(v0), float(v1));
+        s2 += (long long)v0 * v0 + (long long)v1 * v1;
+        maxy = max(maxy, max(abs(v0), abs(v1)));
       }
-      sbuf[pad_idx(k)] = make_float2(float(v0), float(v1));
-      s2 += (long long)v0 * v0 + (long long)v1 * v1;
-      maxy = max(maxy, max(abs(v0), abs(v1)));
+    } else {
+      for (int k = tid; k < P; k += kCorrThreads) {
+        const int e = 2 * pad_idx(k);
+        const int v0 = ib[e], v1 = ib[e + 1];
+        if (Q.y_in == nullptr) {
+          yi[(pass == 0 ? 0 : 2) * P + k] = v0;
+          if (pass == 0) yi[P + k] = v1;
+        }
+        sbuf[pad_idx(k)] = make_float2(float(v0), float(v1));
+        s2 += (long long)v0 * v0 + (long long)v1 * v1;
+        maxy = max(maxy, max(abs(v0), abs(v1)));
+      }
     }
     s2 = block_sum(s2, redl);
     z2 = sqrtf(float(s2));
     maxy = block_max(maxy, redi);
   } else {
     float* yf = static_cast<float*>(a.y) + Q.y_off;
-    for (int k = tid; k < P; k += kCorrThreads) {
-      const float2 v = sbuf[pad_idx(k)];
-      if (Q.y_in == nullptr) {
-        yf[(pass == 0 ? 0 : 2) * P + k] = v.x;
-        if (pass == 0) yf[P + k] = v.y;
+    if (fuse_z) {
+#pragma unroll
+      for (int b = 0; b < kZper; ++b) {
+        const int k = tid + b * kCorrThreads;
+        const float2 v = sbuf[pad_idx(k)];
+        if (Q.y_in == nullptr) {
+          yf[(pass == 0 ? 0 : 2) * P + k] = v.x;
+          if (pass == 0) yf[P + k] = v.y;
+        }
+        z2 = fmaf(v.x, v.x, fmaf(v.y, v.y, z2));
+        zr[b] = v;
       }
-      z2 = fmaf(v.x, v.x, fmaf(v.y, v.y, z2));
+    } else {
+      for (int k = tid; k < P; k += kCorrThreads) {
+        const float2 v = sbuf[pad_idx(k)];
+        if (Q.y_in == nullptr) {
+          yf[(pass == 0 ? 0 : 2) * P + k] = v.x;
+          if (pass == 0) yf[P + k] = v.y;
+        }
+        z2 = fmaf(v.x, v.x, fmaf(v.y, v.y, z2));
+      }
     }
     z2 = sqrtf(block_sum(z2, redf));
   }
 
   // ------------------------------------------------ c. correlation by FFT
-  fft<NBMAX>(sbuf, logP, tw, stw);
+  if (fuse_z) {
+    first_pass_regs(sbuf, logP, zr);   // every read of sbuf above precedes the block sums' barriers
+    __syncthreads();
+  }
+  fft<NBMAX>(sbuf, logP, tw, stw, fuse_z);
   float zc2 = 0.f;
-  for (int k = tid; k < P; k += kCorrThreads) {
-    const float2 z = sbuf[pad_idx(k)], T = spec[k];
-    zc2 = fmaxf(zc2, fmaf(z.x, z.x, z.y * z.y));
-    sbuf[pad_idx(k)] = make_float2(T.x * z.x + T.y * z.y, T.y * z.x - T.x * z.y);   // T conj(Z)
+  if (fuse_z) {
+#pragma unroll
+    for (int b = 0; b < kZper; ++b) {
+      const int k = tid + b * kCorrThreads;
+      const float2 z = sbuf[pad_idx(k)], T = spec[k];
+      zc2 = fmaxf(zc2, fmaf(z.x, z.x, z.y * z.y));
+      zr[b] = make_float2(T.x * z.x + T.y * z.y, T.y * z.x - T.x * z.y);   // T conj(Z)
+    }
+  } else {
+    for (int k = tid; k < P; k += kCorrThreads) {
+      const float2 z = sbuf[pad_idx(k)], T = spec[k];
+      zc2 = fmaxf(zc2, fmaf(z.x, z.x, z.y * z.y));
+      sbuf[pad_idx(k)] = make_float2(T.x * z.x + T.y * z.y, T.y * z.x - T.x * z.y);   // T conj(Z)
+    }
   }
   const float Zc = 1.0001f * sqrtf(block_maxf(zc2, redf));   // block_maxf also orders the writes above
-  fft<NBMAX>(sbuf, logP, tw, stw);
+  if (fuse_z) {
+    first_pass_regs(sbuf, logP, zr);   // the reads of sbuf above precede block_maxf's barriers
+    __syncthreads();
+  }
+  fft<NBMAX>(sbuf, logP, tw, stw, fuse_z);
   const float invP = 1.0f / float(P);   // exact: P is a power of two
 
   if (a.r != nullptr && Q.r_off >= 0) {
