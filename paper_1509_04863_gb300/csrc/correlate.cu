@@ -1,6 +1,7 @@
 // Steps 3 (completion) and 4-9 of Algorithm 1, one CTA per query.
 //
-//  a. Template spectrum T = FFT_P([t 0]) (steps 4-5), kept in global scratch.
+//  a. Template spectrum T = FFT_P([t 0]) (steps 4-5), kept in shared memory
+//     when the launch left room for it (P <= 8192), else in global scratch.
 //  b. Folds: y_j[k] (k < M_j) from the fold kernel's per-share counts, plus
 //     the wrap-around entry x_{k-R} for k >= R = N-(L-1)M (indexing mod N)
 //     and the (< 16) signal bytes the fold kernel did not cover; then the
@@ -15,11 +16,13 @@
 //  d. Step 7: argmax of r_j over j < M_j. The FFT values carry rounding
 //     error |dr| <= delta (a normwise bound, below); every j with
 //     r_j >= max - 2 delta is rescored exactly from the folds (integers in
-//     int32/int64, reals in fp64), which makes the chosen index exact.
+//     int32/int64, reals in double-float pairs on the FP32 pipes, reduced as
+//     pairs), which makes the chosen index exact.
 //  e. Steps 8-9: closed-form intersection (crt.h); several members are
 //     resolved by their exact (Tx)_m.
 //
-// FFT: Stockham autosort, radix 16 (plus one radix 2/4/8 pass), shared
+// FFT: Stockham autosort, radix 16 (plus one radix 2/4/8 pass, computed
+// from registers by the producing loop for P = 8192 and 16384), shared
 // memory resident (P <= 16384 complex entries, padded one entry per 16 to
 // avoid bank conflicts). Twiddles W_P^m, m < P/2, are copied once per CTA
 // into shared memory from a table computed on the host in double precision
