@@ -161,11 +161,14 @@ def test_submit_validation(tm):
     srv.close()
 
 
-def test_fold_cache(tm):
+@pytest.mark.parametrize("fine", [False, True], ids=["pieces", "fine_pieces"])
+def test_fold_cache(tm, fine):
     """Requests on resident signals whose moduli repeat are served from the
     fold cache (no O(N) fold): both servers meet the oracle bar and agree
     bit for bit (real folds follow fixed pieces), and the cache reports
-    hits after the first fold of each (signal, M1, M2)."""
+    hits after the first fold of each (signal, M1, M2). With fine pieces
+    the real signal's 4 MiB fold has 16 pieces, summed ahead by the slot-sum
+    kernel."""
     # N = 2^20 + 3: automatic moduli M1 = max(K, 1024), so every K <= 1024
     # shares one pair
     N = (1 << 20) + 3
@@ -180,7 +183,7 @@ def test_fold_cache(tm):
                 reqs.append((k, K, t))
     outs = []
     for cache in (0, 64 << 20):
-        srv = tm.Server(n_streams=2, max_batch=8, arena_bytes=1 << 28, fold_cache_bytes=cache)
+        srv = tm.Server(n_streams=2, max_batch=8, arena_bytes=1 << 28, fold_cache_bytes=cache, fine_pieces=fine)
         ids = [srv.register_signal(q.x, q.N, q.xdtype) for q in base]
         got = {}
         for i, (k, K, t) in enumerate(reqs):
