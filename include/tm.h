@@ -454,6 +454,12 @@ TM_API tm_status tm_serve_destroy(tm_server_t s);
 TM_API int32_t tm_crt_candidates(int64_t N, int32_t M1, int32_t M2, int32_t m1, int32_t m2,
                           int64_t* out, int32_t cap);
 
+/* sizeof of this header's public structs as compiled into the library, for
+ * bindings that lay them out themselves: which = 0 tm_plan_desc, 1
+ * tm_query, 2 tm_result, 3 tm_serve_cfg, 4 tm_result_tagged, 5
+ * tm_serve_stats; 0 for any other value. Host only, no device needed. */
+TM_API int64_t tm_struct_size(int32_t which);
+
 /* ------------------------------------------------- no-allocation variant */
 
 /* The paper has no counterpart to this entry point: it is a deployment

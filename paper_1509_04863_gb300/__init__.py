@@ -96,6 +96,7 @@ _SIGS = {
     "tm_match_batch": (C.c_int, [C.POINTER(tm_query), C.c_int32, C.c_void_p, C.c_void_p]),
     "tm_crt_candidates": (C.c_int32, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                       C.POINTER(C.c_int64), C.c_int32]),
+    "tm_struct_size": (C.c_int64, [C.c_int32]),
     "tm_match_noalloc": (C.c_int, [C.POINTER(tm_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tm_selftest_wait_timeout": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
     "tm_fold_slice": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),

@@ -1333,6 +1333,18 @@ int32_t tm_crt_candidates(int64_t N, int32_t M1, int32_t M2, int32_t m1, int32_t
   return int32_t(std::min<int64_t>(total, INT32_MAX));
 }
 
+int64_t tm_struct_size(int32_t which) {
+  switch (which) {
+    case 0: return int64_t(sizeof(tm_plan_desc));
+    case 1: return int64_t(sizeof(tm_query));
+    case 2: return int64_t(sizeof(tm_result));
+    case 3: return int64_t(sizeof(tm_serve_cfg));
+    case 4: return int64_t(sizeof(tm_result_tagged));
+    case 5: return int64_t(sizeof(tm_serve_stats));
+    default: return 0;
+  }
+}
+
 }  // extern "C"
 
 // ================================================================ no-allocation entry point

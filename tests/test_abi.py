@@ -48,6 +48,17 @@ def test_library_exports_every_declared_symbol(tm):
         assert getattr(tm.lib(), n) is not None
 
 
+def test_binding_struct_layouts_match_the_library(tm):
+    """The ctypes layouts of the binding have the sizes the compiled
+    library gives its public structs (a field added on one side only
+    would shift every later field)."""
+    import ctypes as C
+    structs = [tm.tm_plan_desc, tm.tm_query, tm.tm_result, tm.tm_serve_cfg, tm.tm_result_tagged, tm.tm_serve_stats]
+    for which, st in enumerate(structs):
+        assert tm.lib().tm_struct_size(which) == C.sizeof(st), (st.__name__, tm.lib().tm_struct_size(which))
+    assert tm.lib().tm_struct_size(99) == 0
+
+
 PLAN_CASES = [
     # N, K, mode, M1, M2, ambig
     (65536, 1024, "paper", 0, 0, False),
