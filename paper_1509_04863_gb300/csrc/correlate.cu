@@ -690,7 +690,7 @@ __device__ void resolve(const CorrArgs& a, const CorrQ& Q, int qi, bool t_integr
     const int64_t Ms[3] = {Q.M[0], Q.M[1], Q.M[2]}, ms[3] = {s_m[0], s_m[1], s_m[2]};
     crt = crt_intersect3(N, Ms, Q.inv, Q.inv3, ms);
   } else {
-    crt = crt_intersect(N, Q.M[0], Q.M[1], Q.inv, s_m[0], s_m[1]);
+    crt = crt_intersect_L(N, Q.M[0], Q.M[1], Q.L[0], Q.L[1], Q.inv, s_m[0], s_m[1]);
   }
   if (Q.thm2) crt.nw = 0;   // wrapped members fall in the zero padding
   const int64_t ncs = crt.nnat + crt.nw;

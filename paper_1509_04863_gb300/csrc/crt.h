@@ -40,21 +40,33 @@ TM_HD int64_t mod_inverse(int64_t a, int64_t m) {
   return ((s0 % m) + m) % m;
 }
 
-TM_HD CrtSet crt_intersect(int64_t N, int64_t M1, int64_t M2, int64_t inv, int64_t m1, int64_t m2) {
+// With L_i = ceil(N / M_i) given (the device has them in its descriptors).
+// 64-bit divisions are long instruction sequences on a GPU: the common cases
+// (residues already reduced, one natural solution, wrapped members below
+// the other modulus) skip them; the results are those of the plain
+// formulas in every case.
+TM_HD CrtSet crt_intersect_L(int64_t N, int64_t M1, int64_t M2, int64_t L1, int64_t L2, int64_t inv, int64_t m1,
+                             int64_t m2) {
   CrtSet c;
-  const int64_t L1 = (N + M1 - 1) / M1, L2 = (N + M2 - 1) / M2;
   // m0 = m1 + M1 * k with M1 * k = m2 - m1 (mod M2)
-  const int64_t d = ((m2 - m1) % M2 + M2) % M2;
-  const int64_t k = (d * inv) % M2;
+  int64_t d = m2 - m1;
+  if (d < 0) d += M2;
+  if (d < 0 || d >= M2) d = ((m2 - m1) % M2 + M2) % M2;
+  const int64_t k = int64_t(uint64_t(d) * uint64_t(inv) % uint64_t(M2));   // d, inv < M2 < 2^31
   c.m0 = m1 + M1 * k;
   c.step = M1 * M2;
-  c.nnat = c.m0 < N ? (N - 1 - c.m0) / c.step + 1 : 0;
+  const int64_t span = N - 1 - c.m0;
+  c.nnat = c.m0 < N ? (span < c.step ? 1 : span / c.step + 1) : 0;
   const int64_t w1 = m1 + (L1 - 1) * M1 - N;
   const int64_t w2 = m2 + (L2 - 1) * M2 - N;
   c.nw = 0;
-  if (w1 >= 0 && (w1 % M2 == m2 || w1 == w2)) c.w[c.nw++] = w1;
-  if (w2 >= 0 && w2 != w1 && w2 % M1 == m1) c.w[c.nw++] = w2;
+  if (w1 >= 0 && ((w1 < M2 ? w1 : w1 % M2) == m2 || w1 == w2)) c.w[c.nw++] = w1;
+  if (w2 >= 0 && w2 != w1 && (w2 < M1 ? w2 : w2 % M1) == m1) c.w[c.nw++] = w2;
   return c;
+}
+
+TM_HD CrtSet crt_intersect(int64_t N, int64_t M1, int64_t M2, int64_t inv, int64_t m1, int64_t m2) {
+  return crt_intersect_L(N, M1, M2, (N + M1 - 1) / M1, (N + M2 - 1) / M2, inv, m1, m2);
 }
 
 // Three moduli (Thm. 4): the naturals solve v = m_i (mod M_i), i = 1..3,

@@ -48,6 +48,42 @@ def test_library_exports_every_declared_symbol(tm):
         assert getattr(tm.lib(), n) is not None
 
 
+def test_crt_closed_form_large_values(tm):
+    """The closed form at the sizes the library runs (N up to 2^34, moduli
+    up to 2^25, residues anywhere), against the intersection counted from
+    its definition with Python integers: the naturals v < N with v = m1
+    (mod M1) and v = m2 (mod M2) from sympy's Chinese remainder solver, and
+    the two wrapped members w_i = m_i + (ceil(N/M_i) - 1) M_i - N tested for
+    membership in the other set."""
+    import math
+    import random
+    crt = pytest.importorskip("sympy.ntheory.modular").crt
+    rng = random.Random(12345)
+    for _ in range(300):
+        M1 = rng.randrange(2, 1 << 25)
+        M2 = rng.choice([M1 + 1, rng.randrange(2, 1 << 25)])
+        if math.gcd(M1, M2) != 1:
+            continue
+        N = rng.choice([rng.randrange(1, M1 * M2), rng.randrange(M1 * M2, 4 * M1 * M2), rng.randrange(1, 1 << 34)])
+        m1, m2 = rng.randrange(M1), rng.randrange(M2)
+        v = int(crt([M1, M2], [m1, m2])[0])   # the natural solution in [0, M1 M2)
+        nat = [] if v >= N else [v + j * M1 * M2 for j in range(min(3, (N - 1 - v) // (M1 * M2) + 1))]
+        n_nat = 0 if v >= N else (N - 1 - v) // (M1 * M2) + 1
+
+        def in_set(w, m, M):
+            return w % M == m or w == m + (-(-N // M) - 1) * M - N
+
+        wrapped = set()
+        for m, M, mo, Mo in ((m1, M1, m2, M2), (m2, M2, m1, M1)):
+            w = m + (-(-N // M) - 1) * M - N
+            if 0 <= w and in_set(w, mo, Mo):
+                wrapped.add(w)
+        want = sorted(set(nat) | wrapped)[:3]
+        got = tm.tm_crt_candidates(N, M1, M2, m1, m2, cap=3)
+        assert got == want, (N, M1, M2, m1, m2, got, want)
+        assert tm.lib().tm_crt_candidates(N, M1, M2, m1, m2, None, 0) == n_nat + len(wrapped), (N, M1, M2, m1, m2)
+
+
 def test_binding_struct_layouts_match_the_library(tm):
     """The ctypes layouts of the binding have the sizes the compiled
     library gives its public structs (a field added on one side only
