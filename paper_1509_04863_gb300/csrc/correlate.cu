@@ -1087,18 +1087,28 @@ __device__ __forceinline__ void corr_query(const CorrArgs& a, int qi, float2* sb
       }
     }
     __syncthreads();
-    if (tid == 0 && Q.y_core == nullptr) {
-      for (int64_t n = Q.nelem16; n < N; ++n) {
+    if (Q.y_core == nullptr) {
+      // the entries after the fold kernel's 16-byte blocks (fewer than 16
+      // bytes' worth); the count L or L-1 above includes each of them: as +1
+      // for int8 (counted -1 entries), as -1 for bits (counted +1 entries).
+      // Consecutive entries fall in distinct columns when there are no
+      // more of them than columns: one thread each, else thread 0 in order.
+      const int ntail = int(N - Q.nelem16);
+      const bool spread = ntail <= Q.M[ma] && (mb < 0 || ntail <= Q.M[mb]);
+      auto tail = [&](int64_t n) {
         for (int j = 0; j < 2; ++j) {
-      const int mj = pass == 0 ? j : (j == 0 ? 2 : -1);   // modulus in complex slot j
-      if (mj < 0) continue;
+          const int mj = j == 0 ? ma : mb;   // modulus in complex slot j
+          if (mj < 0) continue;
           const int e = 2 * pad_idx(int(n % Q.M[mj])) + j;
-          // the count L or L-1 above includes this entry: as +1 for int8
-          // (counted -1 entries), as -1 for bits (counted +1 entries)
           if (Q.xdtype == TM_I8_PM1) ib[e] -= sig.ival(n) < 0 ? 2 : 0;
           else if (Q.xdtype == TM_BITS_PM1) ib[e] += sig.ival(n) > 0 ? 2 : 0;
           else fb[e] += sig.val(n);
         }
+      };
+      if (spread) {
+        if (tid < ntail) tail(Q.nelem16 + tid);
+      } else if (tid == 0) {
+        for (int64_t n = Q.nelem16; n < N; ++n) tail(n);
       }
     }
     __syncthreads();
