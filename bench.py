@@ -907,13 +907,24 @@ def run_serve(args):
         srv = tm.Server(n_streams=args.streams, max_batch=args.max_batch, idle_spin_us=args.idle_spin_us,
                         fine_pieces=args.pieces == "fine")
         ids = [srv.register_signal(g["x"], g["N"], g["xdtype"]) for g in sigs]
-        got = {}
+        # the requests' fields as arrays (no per-request Python work while
+        # submitting or collecting, so the client keeps up with the server)
+        ids_a = np.array([ids[which[k % nreq]] for k in range(n_s)], dtype=np.int32)
+        tptr_a = np.array([temps[k % nreq].ctypes.data for k in range(n_s)], dtype=np.uint64)
+        ks_a = np.array([temps[k % nreq].shape[0] for k in range(n_s)], dtype=np.int32)
+        tags_a = np.arange(n_s, dtype=np.uint64)
+        lat_a = np.full(n_s, np.nan)
+        ndone = [0, 0]   # completed, failed
         done = threading.Event()
 
         def poller_s():
-            while len(got) < n_s:
-                for r in srv.poll(4096, timeout_us=2000):
-                    got[r["tag"]] = r
+            while ndone[0] + ndone[1] < n_s:
+                r = srv.poll_array(4096, timeout_us=2000)
+                if len(r):
+                    ok = r["status"] == tm.TM_OK
+                    lat_a[r["tag"][ok].astype(np.int64)] = r["latency_us"][ok]
+                    ndone[0] += int(ok.sum())
+                    ndone[1] += int((~ok).sum())
             done.set()
 
         th = threading.Thread(target=poller_s, daemon=True)
@@ -930,15 +941,15 @@ def run_serve(args):
                 continue
             j = min(j, i + 4096)
             late = max(late, now - arr_s[i])
-            ks = [k % nreq for k in range(i, j)]
-            i += srv.submit_many([ids[which[k]] for k in ks], [temps[k] for k in ks], list(range(i, j)), mode="auto")
+            i += srv.submit_many_arrays(ids_a[i:j], tptr_a[i:j], ks_a[i:j], tags_a[i:j], mode="auto")
         t_sub = time.perf_counter() - t_start
         done.wait(timeout=120)
         t_end = time.perf_counter()
-        lat = np.array([got[i]["latency_us"] for i in range(n_s) if i in got and i >= n_s // 10])
+        lat = lat_a[n_s // 10:]
+        lat = lat[~np.isnan(lat)]
         st = srv.stats()
         sweep.append({"offered_qps": rate_s, "requests": n_s, "submitted_qps": n_s / t_sub,
-                      "served_qps": len(got) / (t_end - t_start), "completed": len(got), "failed": st["failed"],
+                      "served_qps": ndone[0] / (t_end - t_start), "completed": ndone[0], "failed": st["failed"],
                       "p50_us": float(np.percentile(lat, 50)) if len(lat) else None,
                       "p99_us": float(np.percentile(lat, 99)) if len(lat) else None,
                       "mean_batch": st["mean_batch"], "iterations": st["iterations"],

@@ -516,6 +516,31 @@ class Server:
             raise TMError(-k, "tm_serve_submit_many")
         return k
 
+    def submit_many_arrays(self, sig_ids, t_ptrs, ks, tags, mode: str = "paper", allow_ambig: bool = False) -> int:
+        """tm_serve_submit_many with the request fields as contiguous numpy
+        arrays (int32 sig_ids, uint64 template addresses of float32 data,
+        int32 lengths, uint64 tags): no per-request Python work, for clients
+        that submit at high rates. Returns how many were queued."""
+        import numpy as np
+        n = int(sig_ids.shape[0])
+        for a, dt in ((sig_ids, np.int32), (t_ptrs, np.uint64), (ks, np.int32), (tags, np.uint64)):
+            assert a.dtype == dt and a.flags["C_CONTIGUOUS"] and a.shape[0] == n
+        k = lib().tm_serve_submit_many(self._h, n, sig_ids.ctypes.data, t_ptrs.ctypes.data, ks.ctypes.data,
+                                       MODE_CODES[mode], _plan_flags(allow_ambig), tags.ctypes.data)
+        if k < 0:
+            raise TMError(-k, "tm_serve_submit_many")
+        return k
+
+    def poll_array(self, max_results: int = 4096, timeout_us: int = 0):
+        """tm_serve_poll into a numpy structured array (fields tag, status,
+        latency_us and r, the tm_result fields): no per-result Python work."""
+        import numpy as np
+        buf = (tm_result_tagged * max_results)()
+        k = lib().tm_serve_poll(self._h, buf, max_results, timeout_us)
+        if k < 0:
+            raise TMError(-k, "tm_serve_poll")
+        return np.ctypeslib.as_array(buf)[:k].copy()
+
     def poll(self, max_results: int = 1024, timeout_us: int = 0):
         buf = (tm_result_tagged * max_results)()
         k = lib().tm_serve_poll(self._h, buf, max_results, timeout_us)

@@ -258,9 +258,23 @@ def test_submit_many(tm):
     for i, q in enumerate(qs):
         assert got[i]["req_status"] == tm.TM_OK
         check_result(q, got[i], O.match_query(q))
+    got_all = dict(got)
     assert srv.submit_many([ids[0], 99, ids[1]], ts[:3], [100, 101, 102], mode="auto") == 1
     got = _collect(srv, 1)
     assert got[100]["req_status"] == tm.TM_OK
     with pytest.raises(tm.TMError):
         srv.submit_many([99], ts[:1], [200], mode="auto")
+    # the array forms: the same 30 requests again, results as a structured array
+    n = len(ts)
+    assert srv.submit_many_arrays(np.array(sig, dtype=np.int32), np.array([t.ctypes.data for t in ts], dtype=np.uint64),
+                                  np.array([t.shape[0] for t in ts], dtype=np.int32),
+                                  np.arange(1000, 1000 + n, dtype=np.uint64), mode="auto") == n
+    rows, t0 = [], time.time()
+    while sum(len(r) for r in rows) < n and time.time() - t0 < 60:
+        rows.append(srv.poll_array(64, timeout_us=20000))
+    arr = np.concatenate(rows)
+    assert len(arr) == n and np.all(arr["status"] == tm.TM_OK)
+    for row in arr:
+        i = int(row["tag"]) - 1000
+        assert int(row["r"]["shift"]) == got_all[i]["shift"] and int(row["r"]["m1"]) == got_all[i]["m1"]
     srv.close()
