@@ -268,7 +268,8 @@ __device__ __forceinline__ void block_sum2_and(float& a, float& b, int& c, float
   }
 }
 
-// Four 64-bit sums over the block in one exchange (red: 4 kWarps entries).
+// Four 64-bit sums over the block in one exchange (red: 4 kWarps entries);
+// valid in thread 0.
 template <class T>
 __device__ __forceinline__ void block_sum4(T (&v)[4], T* red) {
 #pragma unroll
@@ -280,6 +281,7 @@ __device__ __forceinline__ void block_sum4(T (&v)[4], T* red) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) red[4 * (threadIdx.x >> 5) + i] = v[i];
   __syncthreads();
+  if (threadIdx.x != 0) return;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     T s = 0;

@@ -116,9 +116,10 @@ __device__ __forceinline__ DF warp_sum_df(DF a) {
 }
 
 // Pair sums over a block of NW warps, n at a time (red: n NW entries),
-// warps added in index order; the same in every thread. GB300's FP64 rate
-// is a small fraction of its FP32 rate: the reductions stay in fp32 pairs
-// and the caller converts the one result it needs to double.
+// warps added in index order; valid in thread 0 (the other threads keep
+// their warp's sums). GB300's FP64 rate is a small fraction of its FP32
+// rate: the reductions stay in fp32 pairs and thread 0 converts the one
+// result it needs to double.
 template <int NW, int n>
 __device__ __forceinline__ void block_sum_df(DF (&v)[n], float2* red) {
 #pragma unroll
@@ -128,6 +129,7 @@ __device__ __forceinline__ void block_sum_df(DF (&v)[n], float2* red) {
 #pragma unroll
     for (int i = 0; i < n; ++i) red[n * (threadIdx.x >> 5) + i] = make_float2(v[i].hi, v[i].lo);
   __syncthreads();
+  if (threadIdx.x != 0) return;
 #pragma unroll
   for (int i = 0; i < n; ++i) {
     DF s;
